@@ -1,0 +1,440 @@
+/*
+ * Plain CPU oracle for the divide-and-merge graph-index build of ScaleGANN
+ * (arxiv 2605.10135).  TEST INFRASTRUCTURE ONLY: the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark call it; the library never does.
+ *
+ * Everything here is a direct, slow restatement of the definitions: no
+ * blocking, no fusion, no reordering of sums beyond the plain loop order.  It
+ * shares no code, header or constant with the CUDA library.
+ *
+ * Precision.  Reported distances are FP64 sums of squared differences (the
+ * plain definition).  Where a floating-point value decides an integer (the
+ * nearest k-means centroid, the r nearest shards, the beam-search frontier)
+ * the decision is taken in FP32 with the sum evaluated term by term in index
+ * order, without fused multiply-add ("d32"), which is the precision the GPU
+ * kernels take the same decision in; FP64 sums of the k-means centroids follow
+ * the sample order.  Built with -ffp-contract=off so the compiler cannot fuse.
+ *
+ * Element types: 0 = float32, 1 = float16, 2 = bfloat16, 3 = uint8.
+ *
+ * Parity status: every function below is pinned by the CPU tests (brute force,
+ * hand-worked examples, library routines, invariants); none is unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PAD 0xFFFFFFFFu
+
+/* ---- element access: exact conversion of one stored element ---------- */
+
+static float half_to_float(uint16_t h) {
+    uint32_t sign = (uint32_t)(h >> 15) << 31;
+    uint32_t e = (h >> 10) & 0x1f, m = h & 0x3ff, bits;
+    if (e == 0) {
+        if (m == 0) {
+            bits = sign;
+        } else { /* subnormal: normalise */
+            int sh = 0;
+            while (!(m & 0x400)) { m <<= 1; sh++; }
+            m &= 0x3ff;
+            bits = sign | ((uint32_t)(127 - 15 - sh + 1) << 23) | (m << 13);
+        }
+    } else if (e == 31) {
+        bits = sign | 0x7f800000u | (m << 13);
+    } else {
+        bits = sign | ((e - 15 + 127) << 23) | (m << 13);
+    }
+    float f;
+    memcpy(&f, &bits, 4);
+    return f;
+}
+
+static float elem_f(const void* X, int dtype, int64_t i) {
+    switch (dtype) {
+    case 0: return ((const float*)X)[i];
+    case 1: return half_to_float(((const uint16_t*)X)[i]);
+    case 2: {
+        uint32_t b = (uint32_t)((const uint16_t*)X)[i] << 16;
+        float f;
+        memcpy(&f, &b, 4);
+        return f;
+    }
+    default: return (float)((const uint8_t*)X)[i];
+    }
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---- distances ------------------------------------------------------- */
+
+/* Squared Euclidean distance in FP64, the plain definition. */
+double or_d64(const void* X, int dtype, int64_t a, const void* Y, int ydtype, int64_t b, int d) {
+    double s = 0.0;
+    for (int t = 0; t < d; t++) {
+        double df = (double)elem_f(X, dtype, a * d + t) - (double)elem_f(Y, ydtype, b * d + t);
+        s += df * df;
+    }
+    return s;
+}
+
+/* Squared Euclidean distance in FP32, terms added in index order, unfused. */
+float or_d32(const void* X, int dtype, int64_t a, const void* Y, int ydtype, int64_t b, int d) {
+    float s = 0.0f;
+    for (int t = 0; t < d; t++) {
+        float df = elem_f(X, dtype, a * d + t) - elem_f(Y, ydtype, b * d + t);
+        float sq = df * df;
+        s = s + sq;
+    }
+    return s;
+}
+
+/* ---- k-means (Sec. IV Workflow step 1; Sec. II-B: shards by k-means) ----
+ * Lloyd iterations on a sample: assign every sample point to the nearest
+ * centroid by (d32, centroid id); each centroid becomes the FP64 mean of its
+ * points (sums taken in sample order), rounded to float; an empty cluster
+ * keeps its previous centroid. */
+void or_kmeans(const void* X, int64_t N, int d, int dtype, int C, const float* init,
+               const uint32_t* sample_idx, int64_t S, int iters, float* cent_out,
+               int32_t* labels_out) {
+    (void)N;
+    memcpy(cent_out, init, sizeof(float) * (size_t)C * d);
+    int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * (size_t)(S > 0 ? S : 1));
+    double* sums = (double*)malloc(sizeof(double) * (size_t)C * d);
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
+    for (int it = 0; it < iters; it++) {
+        #pragma omp parallel for schedule(static)
+        for (int64_t s = 0; s < S; s++) {
+            int best = 0;
+            float bd = or_d32(X, dtype, sample_idx[s], cent_out, 0, 0, d);
+            for (int c = 1; c < C; c++) {
+                float dc = or_d32(X, dtype, sample_idx[s], cent_out, 0, c, d);
+                if (dc < bd) { bd = dc; best = c; }
+            }
+            lab[s] = best;
+        }
+        memset(sums, 0, sizeof(double) * (size_t)C * d);
+        memset(cnt, 0, sizeof(int64_t) * (size_t)C);
+        for (int64_t s = 0; s < S; s++) {
+            int c = lab[s];
+            cnt[c] += 1;
+            for (int t = 0; t < d; t++)
+                sums[(size_t)c * d + t] += (double)elem_f(X, dtype, (int64_t)sample_idx[s] * d + t);
+        }
+        for (int c = 0; c < C; c++) {
+            if (cnt[c] == 0) continue;
+            for (int t = 0; t < d; t++)
+                cent_out[(size_t)c * d + t] = (float)(sums[(size_t)c * d + t] / (double)cnt[c]);
+        }
+    }
+    if (labels_out) memcpy(labels_out, lab, sizeof(int32_t) * (size_t)S);
+    free(lab); free(sums); free(cnt);
+}
+
+/* ---- replicated assignment (Sec. II-B: each vector in its r nearest
+ * shards, "typically two"; Sec. VI-B2: one replication) ----------------
+ * For every vector the r centroids that come first in the order
+ * (d32(x, c), c).  use_d64 != 0 takes the decision on FP64 distances
+ * instead (used only to pin the FP32 decision against the exact one). */
+void or_assign(const void* X, int64_t N, int d, int dtype, const float* cent, int C, int r,
+               int use_d64, uint32_t* assign_out) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+        double* dist = (double*)malloc(sizeof(double) * (size_t)C);
+        char* taken = (char*)calloc((size_t)C, 1);
+        for (int c = 0; c < C; c++)
+            dist[c] = use_d64 ? or_d64(X, dtype, i, cent, 0, c, d)
+                              : (double)or_d32(X, dtype, i, cent, 0, c, d);
+        for (int q = 0; q < r; q++) {
+            int best = -1;
+            for (int c = 0; c < C; c++) {
+                if (taken[c]) continue;
+                if (best < 0 || dist[c] < dist[best]) best = c;
+            }
+            taken[best] = 1;
+            assign_out[i * r + q] = (uint32_t)best;
+        }
+        free(dist); free(taken);
+    }
+}
+
+/* Shard member lists: shard c holds the ids of every vector assigned to it,
+ * in increasing id order (Sec. V-C: merging needs the original vector order). */
+void or_shards(const uint32_t* assign, int64_t N, int r, int C, uint32_t* members,
+               int64_t* offsets) {
+    int64_t* fill = (int64_t*)calloc((size_t)C + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < N * r; i++) fill[assign[i] + 1]++;
+    offsets[0] = 0;
+    for (int c = 0; c < C; c++) offsets[c + 1] = offsets[c] + fill[c + 1];
+    for (int c = 0; c < C; c++) fill[c] = offsets[c];
+    for (int64_t g = 0; g < N; g++)
+        for (int q = 0; q < r; q++) members[fill[assign[g * r + q]]++] = (uint32_t)g;
+    free(fill);
+}
+
+/* ---- exact per-shard kNN (Sec. IV Workflow step 2; the shard graph of
+ * intermediate degree L, Sec. III) ----------------------------------------
+ * For member p of its shard: the k other members with the smallest
+ * (d64, global id), self excluded by id, duplicates kept; missing slots are
+ * (OR_PAD, +inf).  rows[] lists the member positions to evaluate (all of
+ * them when rows == NULL); shard_of_row gives each listed row's shard. */
+static int64_t shard_of(const int64_t* offsets, int C, int64_t p) {
+    int lo = 0, hi = C - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (offsets[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+void or_shard_knn_rows(const void* X, int d, int dtype, const uint32_t* members,
+                       const int64_t* offsets, int C, int k, const int64_t* rows, int64_t nrows,
+                       uint32_t* id_out, double* d_out) {
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < nrows; q++) {
+        int64_t p = rows ? rows[q] : q;
+        int64_t s = shard_of(offsets, C, p);
+        uint32_t u = members[p];
+        uint32_t* ids = id_out + q * k;
+        double* ds = d_out + q * k;
+        for (int j = 0; j < k; j++) { ids[j] = OR_PAD; ds[j] = INFINITY; }
+        for (int64_t m = offsets[s]; m < offsets[s + 1]; m++) {
+            uint32_t v = members[m];
+            if (v == u) continue;
+            double dv = or_d64(X, dtype, u, X, dtype, v, d);
+            /* insert (dv, v) into the sorted list if it ranks within k */
+            int pos = k;
+            while (pos > 0 && (ds[pos - 1] > dv || (ds[pos - 1] == dv && ids[pos - 1] > v))) pos--;
+            if (pos >= k) continue;
+            for (int j = k - 1; j > pos; j--) { ids[j] = ids[j - 1]; ds[j] = ds[j - 1]; }
+            ids[pos] = v;
+            ds[pos] = dv;
+        }
+    }
+}
+
+/* ---- pruning L -> R (intermediate degree L to final degree R, Sec. III and
+ * Sec. VI-B2).  The paper does not print the rule; the reading used here is
+ * the rank-based detour count, defined on the lists alone:
+ *   L_u = [v_0 .. v_{m-1}] (valid entries), pos_w(v) = index of v in L_w;
+ *   c_j = #{ i < j : pos_{v_i}(v_j) < j };
+ *   keep the R entries with the smallest (c_j, j), emitted in increasing j.
+ * rule == 1 keeps the first R entries (plain truncation).  The list of a
+ * neighbour w is w's list in the same shard. */
+static int64_t row_in_shard(const uint32_t* members, int64_t lo, int64_t hi, uint32_t v) {
+    /* member lists are sorted by id: binary search */
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (members[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+void or_prune(const uint32_t* knn_id, const double* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int k, int R, int rule, uint32_t* pr_id,
+              double* pr_d) {
+    int64_t rows = offsets[C];
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < rows; p++) {
+        int64_t s = shard_of(offsets, C, p);
+        const uint32_t* L = knn_id + p * k;
+        int m = 0;
+        while (m < k && L[m] != OR_PAD) m++;
+        int* cnt = (int*)calloc((size_t)k, sizeof(int));
+        char* keep = (char*)calloc((size_t)k, 1);
+        if (rule == 0) {
+            for (int j = 0; j < m; j++) {
+                for (int i = 0; i < j; i++) {
+                    int64_t w = row_in_shard(members, offsets[s], offsets[s + 1], L[i]);
+                    const uint32_t* Lw = knn_id + w * k;
+                    int pos = -1;
+                    for (int t = 0; t < k; t++)
+                        if (Lw[t] == L[j]) { pos = t; break; }
+                    if (pos >= 0 && pos < j) cnt[j]++;
+                }
+            }
+            /* choose R entries by (c_j, j) */
+            int chosen = 0;
+            while (chosen < R && chosen < m) {
+                int best = -1;
+                for (int j = 0; j < m; j++) {
+                    if (keep[j]) continue;
+                    if (best < 0 || cnt[j] < cnt[best]) best = j;
+                }
+                keep[best] = 1;
+                chosen++;
+            }
+        } else {
+            for (int j = 0; j < m && j < R; j++) keep[j] = 1;
+        }
+        int o = 0;
+        for (int j = 0; j < m; j++) {
+            if (!keep[j]) continue;
+            pr_id[p * R + o] = L[j];
+            pr_d[p * R + o] = knn_d[p * k + j];
+            o++;
+        }
+        for (; o < R; o++) { pr_id[p * R + o] = OR_PAD; pr_d[p * R + o] = INFINITY; }
+        free(cnt); free(keep);
+    }
+}
+
+/* ---- merge by edge union (Sec. II-B; Sec. IV Workflow step 3) ----------
+ * For each global id g: the union of g's pruned lists over the shards that
+ * hold g, duplicates removed by id (the smaller distance kept), then the R
+ * smallest by (distance, id), sorted, padded with (OR_PAD, +inf).  gids[]
+ * lists the ids to evaluate (all when NULL). */
+void or_merge(const uint32_t* pr_id, const double* pr_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t N, int R, const int64_t* gids, int64_t ng,
+              uint32_t* graph, double* gdist, uint32_t* degree) {
+    int64_t rows = offsets[C];
+    /* rows of each g, by one counting pass over the member lists */
+    int64_t* start = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    for (int64_t p = 0; p < rows; p++) start[members[p] + 1]++;
+    for (int64_t g = 0; g < N; g++) start[g + 1] += start[g];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    memcpy(fill, start, sizeof(int64_t) * (size_t)N);
+    int64_t* rowlist = (int64_t*)malloc(sizeof(int64_t) * (size_t)(rows > 0 ? rows : 1));
+    for (int64_t p = 0; p < rows; p++) rowlist[fill[members[p]]++] = p;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < ng; q++) {
+        int64_t g = gids ? gids[q] : q;
+        int64_t cap = (start[g + 1] - start[g]) * R;
+        uint32_t* cid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
+        double* cd = (double*)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+        int64_t n = 0;
+        for (int64_t a = start[g]; a < start[g + 1]; a++) {
+            int64_t p = rowlist[a];
+            for (int j = 0; j < R; j++) {
+                uint32_t v = pr_id[p * R + j];
+                if (v == OR_PAD) continue;
+                double dv = pr_d[p * R + j];
+                int64_t e = 0;
+                while (e < n && cid[e] != v) e++;
+                if (e < n) {
+                    if (dv < cd[e]) cd[e] = dv;
+                } else {
+                    cid[n] = v; cd[n] = dv; n++;
+                }
+            }
+        }
+        /* R smallest by (distance, id) by repeated selection */
+        uint32_t* go = graph + q * R;
+        double* gd = gdist + q * R;
+        char* used = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+        int o = 0;
+        for (; o < R && o < n; o++) {
+            int64_t best = -1;
+            for (int64_t e = 0; e < n; e++) {
+                if (used[e]) continue;
+                if (best < 0 || cd[e] < cd[best] || (cd[e] == cd[best] && cid[e] < cid[best])) best = e;
+            }
+            used[best] = 1;
+            go[o] = cid[best];
+            gd[o] = cd[best];
+        }
+        degree[q] = (uint32_t)o;
+        for (; o < R; o++) { go[o] = OR_PAD; gd[o] = INFINITY; }
+        free(cid); free(cd); free(used);
+    }
+    free(start); free(fill); free(rowlist);
+}
+
+/* ---- query evaluation (Sec. VI-B2: a CPU query following DiskANN's search
+ * strategy; top-10 recall) ---------------------------------------------
+ * Medoid: the vector nearest (d32) to the FP64 mean rounded to float, ties to
+ * the smaller id. */
+int64_t or_medoid(const void* X, int64_t N, int d, int dtype) {
+    double* mean = (double*)calloc((size_t)d, sizeof(double));
+    float* mf = (float*)malloc(sizeof(float) * (size_t)d);
+    for (int64_t i = 0; i < N; i++)
+        for (int t = 0; t < d; t++) mean[t] += (double)elem_f(X, dtype, i * d + t);
+    for (int t = 0; t < d; t++) mf[t] = (float)(mean[t] / (double)N);
+    int64_t best = 0;
+    float bd = or_d32(X, dtype, 0, mf, 0, 0, d);
+    for (int64_t i = 1; i < N; i++) {
+        float di = or_d32(X, dtype, i, mf, 0, 0, d);
+        if (di < bd) { bd = di; best = i; }
+    }
+    free(mean); free(mf);
+    return best;
+}
+
+/* Best-first beam search with list size Ls: start at the entry vertex; take
+ * the closest unexpanded entry of the list, expand it (each out-neighbour not
+ * yet seen is marked seen, its d32 distance computed and inserted if it ranks
+ * within Ls by (distance, id)); stop when every listed entry is expanded.
+ * Returns the first topk ids and, per query, the number of distances computed. */
+void or_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
+               int d, int dtype, const void* Q, int qdtype, int64_t nq, int64_t entry, int Ls,
+               int topk, uint32_t* out_ids, int64_t* out_count) {
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < nq; q++) {
+        char* seen = (char*)calloc((size_t)N, 1);
+        uint32_t* lid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)Ls);
+        float* ld = (float*)malloc(sizeof(float) * (size_t)Ls);
+        char* lexp = (char*)malloc((size_t)Ls);
+        int n = 1;
+        int64_t count = 1;
+        lid[0] = (uint32_t)entry;
+        ld[0] = or_d32(Q, qdtype, q, X, dtype, entry, d);
+        lexp[0] = 0;
+        seen[entry] = 1;
+        for (;;) {
+            int cur = -1;
+            for (int e = 0; e < n; e++)
+                if (!lexp[e]) { cur = e; break; }
+            if (cur < 0) break;
+            lexp[cur] = 1;
+            uint32_t u = lid[cur];
+            for (uint32_t j = 0; j < degree[u]; j++) {
+                uint32_t v = graph[(int64_t)u * R + j];
+                if (v == OR_PAD || seen[v]) continue;
+                seen[v] = 1;
+                float dv = or_d32(Q, qdtype, q, X, dtype, v, d);
+                count++;
+                int pos = n;
+                while (pos > 0 && (ld[pos - 1] > dv || (ld[pos - 1] == dv && lid[pos - 1] > v))) pos--;
+                if (pos >= Ls) continue;
+                int last = n < Ls ? n : Ls - 1;
+                for (int e = last; e > pos; e--) { lid[e] = lid[e - 1]; ld[e] = ld[e - 1]; lexp[e] = lexp[e - 1]; }
+                lid[pos] = v; ld[pos] = dv; lexp[pos] = 0;
+                if (n < Ls) n++;
+            }
+        }
+        for (int e = 0; e < topk; e++) out_ids[q * topk + e] = e < n ? lid[e] : OR_PAD;
+        out_count[q] = count;
+        free(seen); free(lid); free(ld); free(lexp);
+    }
+}
+
+/* Exact top-k of every query over all N vectors by (d64, id): the ground
+ * truth of the recall measurement. */
+void or_bruteforce(const void* X, int64_t N, int d, int dtype, const void* Q, int qdtype,
+                   int64_t nq, int k, uint32_t* id_out, double* d_out) {
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nq; q++) {
+        uint32_t* ids = id_out + q * k;
+        double* ds = d_out + q * k;
+        for (int j = 0; j < k; j++) { ids[j] = OR_PAD; ds[j] = INFINITY; }
+        for (int64_t v = 0; v < N; v++) {
+            double dv = or_d64(Q, qdtype, q, X, dtype, v, d);
+            int pos = k;
+            while (pos > 0 && (ds[pos - 1] > dv || (ds[pos - 1] == dv && ids[pos - 1] > v))) pos--;
+            if (pos >= k) continue;
+            for (int j = k - 1; j > pos; j--) { ids[j] = ids[j - 1]; ds[j] = ds[j - 1]; }
+            ids[pos] = (uint32_t)v;
+            ds[pos] = dv;
+        }
+    }
+}

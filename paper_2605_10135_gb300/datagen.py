@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Table 3 datasets).
+
+This module holds no arithmetic of the indexing method itself: it only draws
+vectors, query sets, the k-means sample and the k-means initial centroids.
+Both the CPU oracle tests and the CUDA path take their inputs from here, so the
+two sides always see bit-identical arrays.
+
+The paper's datasets (Sift100M u8 d=128, Deep100M f32 d=96, Laion100M f32
+d=768; Table 3) are not available; every generator below is a stand-in with the
+same dimension, element type and clustered structure:
+
+* ``gaussian_mixture_f32`` - isotropic mixture, centres ~ N(0, centre_std^2 I),
+  points = centre + N(0, I) (small float workload).
+* ``clustered_u8`` - Sift-like: centres ~ U[lo, hi]^d, points
+  round(clip(centre + N(0, sigma^2 I), 0, 255)); duplicates occur.
+* ``anisotropic_mixture`` - Deep/Laion-like: per component a random rotation Q
+  and eigenvalues lambda_i ~ i^-1 scaled to a fixed trace; optionally
+  L2-normalised; returned as f32 or f16.
+* ``powerlaw_gaussian`` - embedding-like: one zero-mean Gaussian whose
+  eigenvalues decay as i^-alpha, under a random rotation.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "gaussian_mixture_f32",
+    "clustered_u8",
+    "anisotropic_mixture",
+    "powerlaw_gaussian",
+    "kmeans_sample",
+    "uneven_shards",
+]
+
+
+def gaussian_mixture_f32(n: int, d: int, n_centres: int = 16, centre_std: float = 2.0,
+                         seed: int = 1001) -> np.ndarray:
+    """Isotropic Gaussian mixture, equal weights, float32 [n, d]."""
+    rng = np.random.default_rng(seed)
+    centres = rng.normal(0.0, centre_std, size=(n_centres, d))
+    lab = rng.integers(0, n_centres, size=n)
+    x = centres[lab] + rng.normal(0.0, 1.0, size=(n, d))
+    return np.ascontiguousarray(x.astype(np.float32))
+
+
+def clustered_u8(n: int, d: int, n_centres: int = 256, lo: float = 32.0, hi: float = 224.0,
+                 sigma: float = 20.0, seed: int = 1002) -> np.ndarray:
+    """Sift-like clustered uint8 vectors [n, d] (rounded and clipped to 0..255)."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(lo, hi, size=(n_centres, d)).astype(np.float32)
+    lab = rng.integers(0, n_centres, size=n)
+    out = np.empty((n, d), dtype=np.uint8)
+    step = 1 << 18
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        z = rng.standard_normal(size=(e - s, d), dtype=np.float32) * np.float32(sigma)
+        v = np.rint(centres[lab[s:e]] + z)
+        out[s:e] = np.clip(v, 0, 255).astype(np.uint8)
+    return out
+
+
+def _random_orthogonal(rng: np.random.Generator, d: int) -> np.ndarray:
+    q, r = np.linalg.qr(rng.normal(size=(d, d)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def anisotropic_mixture(n: int, d: int, n_comp: int, trace: float = 0.25, normalise: bool = True,
+                        out_dtype=np.float32, seed: int = 1003, rotations: int = 16) -> np.ndarray:
+    """Anisotropic Gaussian mixture [n, d].
+
+    Component c has centre ~ N(0, I) and covariance Q_c diag(lambda) Q_c^T with
+    lambda_i proportional to i^-1, scaled so that sum(lambda) = trace.  To keep
+    generation cheap at 10^7 points, components share ``rotations`` random
+    orthogonal matrices (component c uses rotation c % rotations).
+    """
+    rng = np.random.default_rng(seed)
+    lam = 1.0 / np.arange(1, d + 1, dtype=np.float64)
+    lam *= trace / lam.sum()
+    sd = np.sqrt(lam).astype(np.float32)
+    centres = rng.normal(size=(n_comp, d)).astype(np.float32)
+    rots = [(_random_orthogonal(rng, d).astype(np.float32)) for _ in range(rotations)]
+    lab = rng.integers(0, n_comp, size=n)
+    out = np.empty((n, d), dtype=out_dtype)
+    step = 1 << 17
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        z = rng.standard_normal(size=(e - s, d), dtype=np.float32) * sd[None, :]
+        lb = lab[s:e]
+        v = centres[lb].copy()
+        rid = lb % rotations
+        for q in range(rotations):
+            m = rid == q
+            if m.any():
+                v[m] += z[m] @ rots[q].T
+        if normalise:
+            v /= np.linalg.norm(v, axis=1, keepdims=True).astype(np.float32)
+        out[s:e] = v.astype(out_dtype)
+    return out
+
+
+def powerlaw_gaussian(n: int, d: int, alpha: float = 0.8, seed: int = 1004) -> np.ndarray:
+    """Zero-mean Gaussian with eigenvalues i^-alpha under a random rotation, f32 [n, d]."""
+    rng = np.random.default_rng(seed)
+    sd = np.power(np.arange(1, d + 1, dtype=np.float64), -alpha / 2.0).astype(np.float32)
+    q = _random_orthogonal(rng, d).astype(np.float32)
+    out = np.empty((n, d), dtype=np.float32)
+    step = 1 << 16
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        z = rng.standard_normal(size=(e - s, d), dtype=np.float32) * sd[None, :]
+        out[s:e] = z @ q.T
+    return out
+
+
+def kmeans_sample(n: int, n_centroids: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """The k-means training sample and the initial centroid rows.
+
+    Sample size S = min(n, max(256 * C, n // 100)), drawn without replacement
+    and sorted; the initial centroids are the rows of the first C entries of a
+    seeded permutation of the sample.  Returns (sample_idx [S] uint32,
+    init_rows [C] uint32), both global row indices.
+    """
+    rng = np.random.default_rng(seed)
+    s = min(n, max(256 * n_centroids, n // 100))
+    sample = np.sort(rng.choice(n, size=s, replace=False)).astype(np.uint32)
+    perm = rng.permutation(s)[:n_centroids]
+    return sample, sample[perm].astype(np.uint32)
+
+
+def uneven_shards(n: int, n_shards: int, r: int, lo: int, hi: int, seed: int
+                  ) -> tuple[np.ndarray, np.ndarray]:
+    """Synthetic uneven shards for the grouped form.
+
+    Shard sizes are drawn log-uniform on [lo, hi] and rescaled so that they sum
+    to r * n; every vector is then placed in r distinct shards by size-weighted
+    sampling without replacement.  Returns (members [r*n] uint32 sorted by id
+    within each shard, offsets [n_shards + 1] int64).
+    """
+    rng = np.random.default_rng(seed)
+    raw = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_shards))
+    size = np.floor(raw / raw.sum() * r * n).astype(np.int64)
+    size[np.argsort(-raw)[: r * n - size.sum()]] += 1
+    cap = size.copy()
+    owner = np.empty((n, r), dtype=np.int64)
+    order = rng.permutation(n)
+    for g in order:
+        w = cap.astype(np.float64)
+        pick = []
+        for _ in range(r):
+            p = w / w.sum()
+            c = int(rng.choice(n_shards, p=p))
+            pick.append(c)
+            w[c] = 0.0
+        for c in pick:
+            cap[c] -= 1
+        owner[g] = pick
+    offsets = np.zeros(n_shards + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(size)
+    members = np.empty(r * n, dtype=np.uint32)
+    fill = offsets[:-1].copy()
+    for g in range(n):
+        for c in owner[g]:
+            members[fill[c]] = g
+            fill[c] += 1
+    return members, offsets
