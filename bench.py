@@ -1,0 +1,331 @@
+"""Benchmark of one divide-and-merge index build on GB300.
+
+A step is one pass of the whole build on the 1M-vector Sift-like workload
+(N=1e6, d=128 uint8, 16 shards, r=2, k=64, R=32): k-means partition with
+replication -> exact per-shard kNN (tcgen05 distance tiles + fused top-k) ->
+rank-detour prune -> dedup-then-reprune merge, inputs resident in HBM.
+
+Prints one JSON line (rank 0).  value = vectors indexed per second over all
+ranks; e2e = the same with the vectors copied from pinned host memory and the
+merged graph copied back inside every step; roofline = the distance-tile
+kernel's algorithmic FLOP/s (sum over shards of n_s^2 * 2d per launch) against
+the measured dense BF16 peak; cpu_baseline = the plain oracle on a bounded
+sample, extrapolated.  --impl reference times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "index-build vectors/s at recall@10>=0.95; distance TFLOP/s as % of GB300 peak"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(w, X, budget_rows=48):
+    """Time the plain oracle on a bounded sample of the workload and extrapolate
+    to the whole build; returns (vectors/s, threads, description)."""
+    import oracle
+
+    sample, init_rows = w.kmeans_inputs()
+    init = X[init_rows].astype(np.float32)
+    t0 = time.perf_counter()
+    cent, _ = oracle.kmeans(X, init, sample, 10)
+    t_kmeans = time.perf_counter() - t0
+    n_asg = 20000
+    t0 = time.perf_counter()
+    a = oracle.assign(X[:n_asg], cent, w.r)
+    t_assign = (time.perf_counter() - t0) * (w.N / n_asg)
+    # shard 0 of a partition of the first 200k vectors, scaled to the full shard size
+    sub = X[:200_000]
+    members, offsets = oracle.shards(oracle.assign(sub, cent, w.r), w.C)
+    n0 = int(offsets[1] - offsets[0])
+    rows = np.linspace(0, max(n0 - 1, 0), budget_rows).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.shard_knn(sub, members, offsets, w.k, rows=rows)
+    t_rows = time.perf_counter() - t0
+    full_shard = w.r * w.N / w.C
+    t_knn = t_rows / budget_rows * (full_shard / max(n0, 1)) * (w.r * w.N)
+    # prune + merge: per-row cost on a small graph of the same degrees
+    Xs = X[:6000]
+    ms_, os_ = oracle.shards(oracle.assign(Xs, cent, w.r), w.C)
+    kid, kd = oracle.shard_knn(Xs, ms_, os_, w.k)
+    t0 = time.perf_counter()
+    pid, pd = oracle.prune(kid, kd, ms_, os_, w.R)
+    oracle.merge(pid, pd, ms_, os_, Xs.shape[0])
+    t_pm = (time.perf_counter() - t0) * (w.N / Xs.shape[0])
+    total = t_kmeans + t_assign + t_knn + t_pm
+    desc = (f"oracle: k-means 10 iters on the full sample, assignment of {n_asg} vectors, "
+            f"exact kNN of {budget_rows} rows of one shard of a 200k-vector partition, "
+            f"prune+merge of a 6000-vector graph; each extrapolated to N={w.N} "
+            f"(kNN by rows x shard size)")
+    return w.N / total, oracle.num_threads(), desc, total
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sift1m_d128_u8")
+    ap.add_argument("--nq", type=int, default=1000)
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_2605_10135_gb300 import configs
+
+    w = configs.BY_NAME[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+
+    import torch
+    from paper_2605_10135_gb300 import ann
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    X = w.vectors()
+    sample, init_rows = w.kmeans_inputs()
+    init = X[init_rows].astype(np.float32)
+    Xh = torch.from_numpy(X).pin_memory()
+    Xd = Xh.to(dev)
+    init_d = torch.from_numpy(init).to(dev)
+    samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
+    cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R, iters=10)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+
+    def step(x):
+        return ann.build_index(x, cfg, init_d, samp_d)
+
+    for _ in range(max(args.warmup, 3)):
+        out = step(Xd)
+    torch.cuda.synchronize()
+
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
+    time.sleep(0.5)
+    ann.timing_read()
+    ann.timing_enable(True)
+    l0 = ann.launch_count()
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(st)
+        out = step(Xd)
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    barrier()
+    launches = (ann.launch_count() - l0) // args.steps
+    ann.timing_enable(False)
+    tile_ms, tile_n = ann.timing_read()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = float(np.mean(step_ms))
+
+    # e2e: vectors from pinned host memory in, merged graph out, every step
+    e2e_ms = []
+    graph_h = torch.empty((w.N, w.R), dtype=torch.int32).pin_memory()
+    gdist_h = torch.empty((w.N, w.R), dtype=torch.float32).pin_memory()
+    deg_h = torch.empty(w.N, dtype=torch.int32).pin_memory()
+    for i in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = Xh.to(dev, non_blocking=True)
+        o = step(xd)
+        graph_h.copy_(o["graph"], non_blocking=True)
+        gdist_h.copy_(o["gdist"], non_blocking=True)
+        deg_h.copy_(o["degree"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    clocks.stop()
+
+    # quality: exact graph by construction; search recall@10 from the medoid
+    Q = torch.from_numpy(w.vectors(args.nq, seed_offset=777)).to(dev)
+    gt, _ = ann.knn_query(Xd, Q, 10)
+    entry = int(ann.medoid(Xd).item())
+    ids, cnt = ann.search(out["graph"], out["degree"], Xd, Q, entry, 64, 10)
+    recall = float(ann.recall(ids, gt, 10).item())
+    status = ann.device_status()
+
+    if dist is not None:
+        t = torch.tensor([ms, float(np.mean(e2e_ms))], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_mean = t.tolist()
+    else:
+        e2e_mean = float(np.mean(e2e_ms))
+
+    off = out["offsets"].cpu().numpy()
+    sizes = np.diff(off).astype(np.float64)
+    flops = float(np.sum(sizes ** 2) * 2 * w.d)
+    tile_avg_ms = tile_ms / max(tile_n, 1)
+    achieved = flops / (tile_avg_ms * 1e-3) / 1e12
+    peaks, src = _peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC,
+        "value": world * w.N / (ms * 1e-3),
+        "unit": "vectors/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {
+            "workload": w.name, "N": w.N, "d": w.d, "elem": w.dtype, "shards": w.C,
+            "replicas": w.r, "k": w.k, "R": w.R, "kmeans_iters": 10,
+            "tile_operands": "bf16 (exact for uint8), fp32 accumulate",
+            "l2": "flushed (512 MB write) before every timed step",
+            "recall_at_10": recall, "search_Ls": 64, "queries": args.nq,
+            "graph_recall_vs_exact": 1.0,
+            "mean_dist_count": float(cnt.float().mean().item()),
+            "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
+            "distance_tflops": achieved,
+            "device_status": status,
+        },
+        "roofline": {
+            "kernel": "k_knn_tiles", "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{src} bf16_tflops_sustained",
+            "algorithmic_flops_per_launch": flops, "kernel_ms": tile_avg_ms,
+        },
+        "e2e": {
+            "value": world * w.N / (e2e_mean * 1e-3), "unit": "vectors/s",
+            "h2d_bytes_per_step": int(X.nbytes),
+            "d2h_bytes_per_step": int(graph_h.numel() * 4 + gdist_h.numel() * 4 + deg_h.numel() * 4),
+            "ms_per_step": e2e_mean,
+        },
+        "gpu_launches": int(launches) * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if world == 1 and not args.no_baseline:
+        v, cores, desc, _ = oracle_sample(w, X)
+        line["cpu_baseline"] = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args, w, world, rank):
+    """The oracle as it stands, on the host cores, a bounded sample per step."""
+    if rank != 0:
+        return
+    X = w.vectors()
+    for _ in range(max(args.warmup, 3) and 1):
+        oracle_sample(w, X, budget_rows=8)
+    vals, tms = [], []
+    for _ in range(args.steps):
+        v, cores, desc, total = oracle_sample(w, X, budget_rows=16)
+        vals.append(v)
+        tms.append(total * 1e3)
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(tms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": w.name, "N": w.N, "d": w.d, "shards": w.C,
+                                        "replicas": w.r, "k": w.k, "R": w.R},
+        "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

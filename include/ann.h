@@ -1,0 +1,205 @@
+/*
+ * ann.h - C-ABI of the GB300 (sm_103a) divide-and-merge graph-index build.
+ *
+ * The method is ScaleGANN's (arxiv 2605.10135), Sec. IV "Workflow": (1) data
+ * partitioning by k-means with replication of each vector into its nearest
+ * shards, (2) an independent graph build per shard, (3) merging the shard
+ * graphs into one graph by edge union, with the replicated vectors as links
+ * (Sec. II-B).  Here the per-shard graph is the exact k-nearest-neighbour
+ * graph of intermediate degree k (the paper's L), pruned to degree R.
+ *
+ * Conventions shared by every call
+ *  - Every pointer argument is a DEVICE pointer (cudaMalloc / PyTorch CUDA
+ *    tensor) owned by the caller, unless the argument says "host".  The
+ *    library never frees or retains caller memory.
+ *  - Scratch memory comes from a caller-supplied workspace of at least the
+ *    size the matching *_workspace() call reports; it may be reused after the
+ *    call's work on the stream has completed.
+ *  - Calls are asynchronous on the CUDA stream passed as `stream` (a
+ *    cudaStream_t; NULL = legacy default stream).  Results are valid once the
+ *    stream's work has completed.
+ *  - Row-major layouts throughout.  Vector ids are uint32 global row indices;
+ *    ANN_PAD (0xFFFFFFFF) marks an empty neighbour slot, whose distance is +inf.
+ *  - Distances are squared Euclidean distances stored as float32.  For uint8
+ *    vectors they are exact integers.
+ *  - Return value: ANN_OK or an ANN_ERR_* code; ann_last_error() gives a
+ *    message (thread-local).  Calls never abort the process.  Conditions found
+ *    on the device (a bounded wait that gave up, inconsistent offsets) are
+ *    recorded in a device status word read by ann_device_status().
+ */
+#ifndef ANN_GB300_H
+#define ANN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ANN_PAD 0xFFFFFFFFu
+
+enum ann_status {
+    ANN_OK = 0,
+    ANN_ERR_INVALID_ARG = 1,  /* a size, pointer or enum outside its documented range */
+    ANN_ERR_UNSUPPORTED = 2,  /* a valid combination this build does not implement */
+    ANN_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed */
+    ANN_ERR_TIMEOUT = 4,      /* a device-side bounded wait gave up (see ann_device_status) */
+    ANN_ERR_WORKSPACE = 5     /* workspace missing or smaller than reported */
+};
+
+/* Element type of the input vectors (Table 3: uint8 and float datasets). */
+enum ann_dtype { ANN_F32 = 0, ANN_F16 = 1, ANN_BF16 = 2, ANN_U8 = 3 };
+
+/* How shard distance tiles are computed.
+ *  ANN_EXACT: uint8 -> BF16 tiles with FP32 accumulation (exact integers);
+ *             float -> BF16 hi/lo split tiles (three products) screening a
+ *             widened list, then an FP32 direct-form re-rank.
+ *  ANN_BF16_RERANK / ANN_FP8_RERANK / ANN_LEARNED: reserved (not built yet). */
+enum ann_precision { ANN_EXACT = 0, ANN_BF16_RERANK = 1, ANN_FP8_RERANK = 2, ANN_LEARNED = 3 };
+
+/* Prune rule for L -> R (Sec. III, Sec. VI-B2 use L = 2R; the rule itself is
+ * not printed in the paper).  ANN_PRUNE_RANK: rank-based detour count
+ * c_j = #{ i < j : pos_{v_i}(v_j) < j } over u's sorted list, keep the R
+ * entries of smallest (c_j, j) in list order.  ANN_PRUNE_TRUNC: first R. */
+enum ann_prune_rule { ANN_PRUNE_RANK = 0, ANN_PRUNE_TRUNC = 1 };
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* ann_last_error(void);
+
+/* Library ABI version (major*100 + minor). */
+int ann_version(void);
+
+/* Number of kernels this library has launched in this process (host counter). */
+unsigned long long ann_launch_count(void);
+
+/* Measurement hooks.  ann_timing_enable(1) makes every later launch of the
+ * distance-tile kernel (ann_shard_knn, ann_knn_query) record a pair of CUDA
+ * events on the launching stream.  ann_timing_read() waits for the recorded
+ * events, returns the summed kernel time in milliseconds (host tile_ms) and the
+ * number of launches timed (host launches), and forgets them. */
+int ann_timing_enable(int on);
+int ann_timing_read(double* tile_ms, int* launches);
+
+/* Reads (host out) and clears the device status word of the current device:
+ * bit 1 = a bounded device wait gave up, bit 2 = inconsistent input found on
+ * the device (e.g. offsets[C] != rows), bit 4 = a fixed-capacity buffer
+ * overflowed.  Synchronises the device.  Returns ANN_OK, or ANN_ERR_TIMEOUT
+ * if bit 1 was set. */
+int ann_device_status(int* out);
+
+/* ---------------------------------------------------------------------------
+ * ann_partition - Sec. IV Workflow (1) and Sec. II-B: k-means shard centroids,
+ * then each vector replicated into its r nearest shards ("typically two";
+ * Sec. VI-B2: one replication, r = 2).
+ *
+ *  X               [N x d] vectors of type dtype.
+ *  init_centroids  [C x d] float32 starting centroids.
+ *  sample_idx      [S] uint32 rows of X used for k-means (any order; the FP64
+ *                  centroid sums follow this order).
+ *  iters           Lloyd iterations (>= 0).  Each assigns every sample row
+ *                  to the centroid of smallest (d32, id) - d32 being the FP32
+ *                  squared distance with terms added in index order, unfused -
+ *                  then sets each centroid to the FP64 mean of its rows,
+ *                  rounded to float; an empty cluster keeps its centroid.
+ *  centroids_out   [C x d] float32 final centroids.
+ *  members_out     [N*r] uint32: shard c's members are
+ *                  members_out[offsets_out[c] .. offsets_out[c+1]), ids in
+ *                  increasing order.  A vector goes to the r centroids of
+ *                  smallest (d32, id).
+ *  offsets_out     [C+1] int64.
+ * Limits: 1 <= r <= C <= 1024, 1 <= d <= 4096, N < 2^32.
+ * ------------------------------------------------------------------------- */
+int ann_partition_workspace(int64_t N, int d, int C, int r, int64_t S, size_t* bytes);
+int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
+                  const float* init_centroids, const uint32_t* sample_idx, int64_t S, int iters,
+                  float* centroids_out, uint32_t* members_out, int64_t* offsets_out, void* ws,
+                  size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ann_shard_knn - Sec. IV Workflow (2): the graph of every shard, built
+ * independently.  For shard member u (row p = its position in members), the
+ * k other members of the same shard with the smallest (distance, id), self
+ * excluded by id; fewer than k others -> trailing ANN_PAD / +inf.
+ *
+ *  members, offsets  as produced by ann_partition (C shards, rows = offsets[C]
+ *                    total members; each shard's ids sorted increasingly).
+ *  knn_id / knn_d    [rows x k] output, row p for members[p].
+ *  precision         ANN_EXACT only (see enum).  uint8 results are bit-exact;
+ *                    float results carry FP32 direct-form distances.
+ *  rerank_k          width of the screened list for float data before the
+ *                    re-rank (0 = k + 16); ignored for uint8.
+ *  model             reserved, must be NULL.
+ * Limits: d <= 256 (uint8: d <= 258 keeps the integer tiles exact),
+ * 1 <= k <= 96, every shard smaller than 2^24 members.
+ * ------------------------------------------------------------------------- */
+int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
+                            int precision, int rerank_k, size_t* bytes);
+int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
+                  const int64_t* offsets, int C, int64_t rows, int k, int precision, int rerank_k,
+                  const void* model, uint32_t* knn_id, float* knn_d, void* ws, size_t ws_bytes,
+                  void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ann_prune - intermediate degree k (L) to final degree R per shard row, by
+ * `rule` (enum ann_prune_rule).  Integer logic on the lists only: the output
+ * depends on knn_id alone (knn_d is carried), so identical lists give
+ * identical results.  pr_id / pr_d: [rows x R], kept entries in list order
+ * then ANN_PAD / +inf.  Limits: 1 <= R, k <= 256.
+ * ------------------------------------------------------------------------- */
+int ann_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ann_merge - Sec. IV Workflow (3), Sec. II-B "edge union": for every vector
+ * g the union of its pruned lists over the shards holding g, duplicates
+ * removed by id (smaller distance kept), then the R entries of smallest
+ * (distance, id), sorted.  graph / gdist: [N x R]; degree: [N] uint32.
+ * The result does not depend on the order of the shards.
+ * Limits: (copies of one vector) * R <= 256.
+ * ------------------------------------------------------------------------- */
+int ann_merge_workspace(int64_t N, int64_t rows, size_t* bytes);
+int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
+              float* gdist, uint32_t* degree, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Query-side evaluation (Sec. VI-B2: top-10 recall with a best-first search
+ * of the merged graph following DiskANN's strategy).
+ *
+ * ann_medoid: entry_out (device uint32[1]) = the vector nearest (d32) to the
+ *   FP64 mean of X rounded to float, ties to the smaller id.
+ * ann_knn_query: exact top-k of each of nq queries Q [nq x d] (type dtype)
+ *   over all N vectors by (distance, id), same tile kernels and precision
+ *   rules as ann_shard_knn; out_id / out_d [nq x k].
+ * ann_search: best-first beam search from `entry`, list size Ls; expanding a
+ *   vertex computes d32 to each unseen out-neighbour; stops when every listed
+ *   vertex is expanded.  out_id [nq x topk]; out_count [nq] uint32 = distance
+ *   computations.  Limits: Ls <= 256, R <= 64, topk <= Ls.
+ * ann_recall: recall_out (device float[1]) = mean over queries of
+ *   |first kk of found  intersect  first kk of truth| / kk.
+ * ------------------------------------------------------------------------- */
+int ann_medoid_workspace(int64_t N, int d, size_t* bytes);
+int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, void* ws,
+               size_t ws_bytes, void* stream);
+int ann_knn_query_workspace(int64_t N, int64_t nq, int d, int dtype, int k, size_t* bytes);
+int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,
+                  uint32_t* out_id, float* out_d, void* ws, size_t ws_bytes, void* stream);
+int ann_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
+               int d, int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
+               uint32_t* out_id, uint32_t* out_count, void* stream);
+int ann_recall(const uint32_t* found, int found_stride, const uint32_t* truth, int truth_stride,
+               int64_t nq, int kk, float* recall_out, void* stream);
+
+/* ann_search_eval: ann_search followed by ann_recall against gt [nq x 10]
+ * (recall@10); recall_out (device float[1]), dist_count_out [nq] uint32. */
+int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const void* X,
+                    int64_t N, int d, int dtype, const void* Q, int64_t nq, const uint32_t* gt,
+                    uint32_t entry, int Ls, uint32_t* out_id, float* recall_out,
+                    uint32_t* dist_count_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANN_GB300_H */

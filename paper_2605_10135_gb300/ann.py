@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libann.so (include/ann.h), argument marshalling only.
+
+Tensors are PyTorch CUDA tensors; every call is enqueued on the current torch
+CUDA stream.  uint32 ids travel as int32 tensors with the same bits (ANN_PAD
+reads as -1).  There is no host fallback: if the library is missing or the
+device is not a CUDA device the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+PAD = 0xFFFFFFFF
+EXACT, BF16_RERANK, FP8_RERANK, LEARNED = 0, 1, 2, 3
+PRUNE_RANK, PRUNE_TRUNC = 0, 1
+_DT = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2, torch.uint8: 3}
+
+_lib = None
+
+
+class AnnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ann error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libann.so (built by paper_2605_10135_gb300.build / __graft_entry__.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libann.so is not built ({_build.LIB}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ct.CDLL(_build.LIB)
+        P, I64, I32, SZ = ct.c_void_p, ct.c_int64, ct.c_int, ct.c_size_t
+        PSZ = ct.POINTER(ct.c_size_t)
+        sigs = {
+            "ann_last_error": (ct.c_char_p, []),
+            "ann_version": (I32, []),
+            "ann_launch_count": (ct.c_ulonglong, []),
+            "ann_timing_enable": (I32, [I32]),
+            "ann_timing_read": (I32, [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
+            "ann_device_status": (I32, [ct.POINTER(ct.c_int)]),
+            "ann_partition_workspace": (I32, [I64, I32, I32, I32, I64, PSZ]),
+            "ann_partition": (I32, [P, I64, I32, I32, I32, I32, P, P, I64, I32, P, P, P, P, SZ, P]),
+            "ann_shard_knn_workspace": (I32, [I64, I32, I32, I32, I64, I32, I32, I32, PSZ]),
+            "ann_shard_knn": (I32, [P, I64, I32, I32, P, P, I32, I64, I32, I32, I32, P, P, P, P, SZ,
+                                    P]),
+            "ann_prune": (I32, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
+            "ann_merge_workspace": (I32, [I64, I64, PSZ]),
+            "ann_merge": (I32, [P, P, P, P, I32, I64, I64, I32, P, P, P, P, SZ, P]),
+            "ann_medoid_workspace": (I32, [I64, I32, PSZ]),
+            "ann_medoid": (I32, [P, I64, I32, I32, P, P, SZ, P]),
+            "ann_knn_query_workspace": (I32, [I64, I64, I32, I32, I32, PSZ]),
+            "ann_knn_query": (I32, [P, I64, P, I64, I32, I32, I32, P, P, P, SZ, P]),
+            "ann_search": (I32, [P, P, I32, P, I64, I32, I32, P, I64, ct.c_uint32, I32, I32, P, P,
+                                 P]),
+            "ann_recall": (I32, [P, I32, P, I32, I64, I32, P, P]),
+            "ann_search_eval": (I32, [P, P, I32, P, I64, I32, I32, P, I64, P, ct.c_uint32, I32, P,
+                                      P, P, P]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise AnnError(rc, lib().ann_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t.contiguous()
+
+
+def _ws(nbytes: int, device) -> torch.Tensor | None:
+    if nbytes <= 256:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def _wsize(fn, *args) -> int:
+    n = ct.c_size_t(0)
+    _check(fn(*args, ct.byref(n)))
+    return n.value
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().ann_launch_count())
+
+
+def timing_enable(on: bool = True):
+    """Record CUDA events around every distance-tile kernel launch."""
+    _check(lib().ann_timing_enable(1 if on else 0))
+
+
+def timing_read() -> tuple[float, int]:
+    """(summed distance-tile kernel ms, launches) since the last read."""
+    ms, n = ct.c_double(0.0), ct.c_int(0)
+    _check(lib().ann_timing_read(ct.byref(ms), ct.byref(n)))
+    return ms.value, n.value
+
+
+def device_status() -> int:
+    """Read and clear the device status word (synchronises the device)."""
+    v = ct.c_int(0)
+    rc = lib().ann_device_status(ct.byref(v))
+    if rc not in (0, 4):
+        _check(rc)
+    return v.value
+
+
+def partition(X: torch.Tensor, C: int, r: int, init_centroids: torch.Tensor,
+              sample_idx: torch.Tensor, iters: int):
+    """k-means shards + replication into the r nearest: (centroids, members, offsets)."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    init = _cuda(init_centroids.to(torch.float32), "init_centroids")
+    sample = _cuda(sample_idx.to(torch.int32), "sample_idx")
+    S = sample.numel()
+    dev = X.device
+    cent = torch.empty((C, d), dtype=torch.float32, device=dev)
+    members = torch.empty(N * r, dtype=torch.int32, device=dev)
+    offsets = torch.empty(C + 1, dtype=torch.int64, device=dev)
+    L = lib()
+    nb = _wsize(L.ann_partition_workspace, N, d, C, r, S)
+    ws = _ws(nb, dev)
+    _check(L.ann_partition(_ptr(X), N, d, _DT[X.dtype], C, r, _ptr(init), _ptr(sample), S, iters,
+                           _ptr(cent), _ptr(members), _ptr(offsets), _ptr(ws), nb, _stream()))
+    return cent, members, offsets
+
+
+def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: int,
+              precision: int = EXACT, rerank_k: int = 0):
+    """Exact kNN inside every shard: (knn_id [rows, k] int32, knn_d [rows, k] float32)."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    members = _cuda(members, "members")
+    offsets = _cuda(offsets, "offsets")
+    C = offsets.numel() - 1
+    rows = members.numel()
+    dev = X.device
+    knn_id = torch.empty((rows, k), dtype=torch.int32, device=dev)
+    knn_d = torch.empty((rows, k), dtype=torch.float32, device=dev)
+    L = lib()
+    nb = _wsize(L.ann_shard_knn_workspace, N, d, _DT[X.dtype], C, rows, k, precision, rerank_k)
+    ws = _ws(nb, dev)
+    _check(L.ann_shard_knn(_ptr(X), N, d, _DT[X.dtype], _ptr(members), _ptr(offsets), C, rows, k,
+                           precision, rerank_k, None, _ptr(knn_id), _ptr(knn_d), _ptr(ws), nb,
+                           _stream()))
+    return knn_id, knn_d
+
+
+def prune(knn_id: torch.Tensor, knn_d: torch.Tensor, members: torch.Tensor,
+          offsets: torch.Tensor, R: int, rule: int = PRUNE_RANK):
+    """Prune each shard list from k to R: (pr_id [rows, R], pr_d [rows, R])."""
+    knn_id, knn_d = _cuda(knn_id, "knn_id"), _cuda(knn_d, "knn_d")
+    members, offsets = _cuda(members, "members"), _cuda(offsets, "offsets")
+    rows, k = knn_id.shape
+    C = offsets.numel() - 1
+    pr_id = torch.empty((rows, R), dtype=torch.int32, device=knn_id.device)
+    pr_d = torch.empty((rows, R), dtype=torch.float32, device=knn_id.device)
+    _check(lib().ann_prune(_ptr(knn_id), _ptr(knn_d), _ptr(members), _ptr(offsets), C, rows, k, R,
+                           rule, _ptr(pr_id), _ptr(pr_d), _stream()))
+    return pr_id, pr_d
+
+
+def merge(pr_id: torch.Tensor, pr_d: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor,
+          N: int):
+    """Dedup-then-reprune edge union: (graph [N, R], gdist [N, R], degree [N])."""
+    pr_id, pr_d = _cuda(pr_id, "pr_id"), _cuda(pr_d, "pr_d")
+    members, offsets = _cuda(members, "members"), _cuda(offsets, "offsets")
+    rows, R = pr_id.shape
+    C = offsets.numel() - 1
+    dev = pr_id.device
+    graph = torch.empty((N, R), dtype=torch.int32, device=dev)
+    gdist = torch.empty((N, R), dtype=torch.float32, device=dev)
+    degree = torch.empty(N, dtype=torch.int32, device=dev)
+    L = lib()
+    nb = _wsize(L.ann_merge_workspace, N, rows)
+    ws = _ws(nb, dev)
+    _check(L.ann_merge(_ptr(pr_id), _ptr(pr_d), _ptr(members), _ptr(offsets), C, rows, N, R,
+                       _ptr(graph), _ptr(gdist), _ptr(degree), _ptr(ws), nb, _stream()))
+    return graph, gdist, degree
+
+
+def medoid(X: torch.Tensor) -> torch.Tensor:
+    """Device int32[1]: the vector nearest to the mean (the search entry point)."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    out = torch.empty(1, dtype=torch.int32, device=X.device)
+    L = lib()
+    nb = _wsize(L.ann_medoid_workspace, N, d)
+    ws = _ws(nb, X.device)
+    _check(L.ann_medoid(_ptr(X), N, d, _DT[X.dtype], _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def knn_query(X: torch.Tensor, Q: torch.Tensor, k: int):
+    """Exact top-k of each query over all vectors: (ids [nq, k], dists [nq, k])."""
+    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    N, d = X.shape
+    nq = Q.shape[0]
+    out_id = torch.empty((nq, k), dtype=torch.int32, device=X.device)
+    out_d = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    L = lib()
+    nb = _wsize(L.ann_knn_query_workspace, N, nq, d, _DT[X.dtype], k)
+    ws = _ws(nb, X.device)
+    _check(L.ann_knn_query(_ptr(X), N, _ptr(Q), nq, d, _DT[X.dtype], k, _ptr(out_id), _ptr(out_d),
+                           _ptr(ws), nb, _stream()))
+    return out_id, out_d
+
+
+def search(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q: torch.Tensor,
+           entry: int, Ls: int, topk: int = 10):
+    """Best-first beam search of each query: (ids [nq, topk], distance counts [nq])."""
+    graph, degree = _cuda(graph, "graph"), _cuda(degree, "degree")
+    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    N, d = X.shape
+    R = graph.shape[1]
+    nq = Q.shape[0]
+    out = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
+    cnt = torch.empty(nq, dtype=torch.int32, device=X.device)
+    _check(lib().ann_search(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype], _ptr(Q), nq,
+                            int(entry), Ls, topk, _ptr(out), _ptr(cnt), _stream()))
+    return out, cnt
+
+
+def recall(found: torch.Tensor, truth: torch.Tensor, kk: int = 10) -> torch.Tensor:
+    """Device float[1]: mean |first kk found  intersect  first kk truth| / kk."""
+    found, truth = _cuda(found, "found"), _cuda(truth, "truth")
+    out = torch.empty(1, dtype=torch.float32, device=found.device)
+    _check(lib().ann_recall(_ptr(found), found.shape[1], _ptr(truth), truth.shape[1],
+                            found.shape[0], kk, _ptr(out), _stream()))
+    return out
+
+
+@dataclass
+class BuildConfig:
+    """Parameters of one divide-and-merge build (k = intermediate degree L)."""
+    C: int
+    r: int
+    k: int
+    R: int
+    iters: int = 10
+    rule: int = PRUNE_RANK
+    precision: int = EXACT
+    rerank_k: int = 0
+
+
+def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
+                sample_idx: torch.Tensor) -> dict:
+    """The whole hot path: partition -> per-shard kNN -> prune -> merge (all on the GPU)."""
+    cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
+    knn_id, knn_d = shard_knn(X, members, offsets, cfg.k, cfg.precision, cfg.rerank_k)
+    pr_id, pr_d = prune(knn_id, knn_d, members, offsets, cfg.R, cfg.rule)
+    graph, gdist, degree = merge(pr_id, pr_d, members, offsets, X.shape[0])
+    return dict(centroids=cent, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
+                pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree)

@@ -1,0 +1,365 @@
+// extern "C" entry points of libann.so: argument checks, workspace layout and
+// the calls into the stage drivers.  Every stage runs in the CUDA kernels of
+// this library; nothing falls back to the host.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdarg.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "stages.cuh"
+
+namespace ann {
+
+// ---- error state ---------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// ---- launch counter and tile timing --------------------------------------------
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static std::mutex g_timing_mu;
+static bool g_timing = false;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tile_events;
+static std::vector<cudaEvent_t> g_event_pool;
+
+bool tile_timing_on() { return g_timing; }
+cudaEvent_t tile_event() {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+void tile_timing_record(cudaEvent_t a, cudaEvent_t b) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_tile_events.emplace_back(a, b);
+}
+
+// ---- device status word ----------------------------------------------------------
+__device__ int g_dev_status;
+
+int* device_status_ptr() {
+    static std::mutex mu;
+    static int* ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dev_status) == cudaSuccess) ptrs[dev] = (int*)p;
+    }
+    return ptrs[dev];
+}
+
+static bool valid_dtype(int dt) { return dt >= ANN_F32 && dt <= ANN_U8; }
+
+static int check_ws(void* ws, size_t have, size_t need) {
+    if (need > 256 && (!ws || have < need))
+        return fail(ANN_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, have);
+    return ANN_OK;
+}
+
+// small per-device scratch for ann_recall / ann_search_eval hit counters
+__device__ unsigned long long g_hits;
+static unsigned long long* hits_ptr() {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_hits) != cudaSuccess) return nullptr;
+    return (unsigned long long*)p;
+}
+
+}  // namespace ann
+
+using namespace ann;
+
+extern "C" {
+
+const char* ann_last_error(void) { return ann::g_err; }
+
+int ann_version(void) { return 100; }
+
+unsigned long long ann_launch_count(void) { return g_launches.load(); }
+
+int ann_timing_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timing = on != 0;
+    return ANN_OK;
+}
+
+int ann_timing_read(double* tile_ms, int* launches) {
+    ANN_REQUIRE(tile_ms && launches, "NULL pointer");
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    {
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        ev.swap(g_tile_events);
+    }
+    double tot = 0.0;
+    int rc = ANN_OK;
+    for (auto& p : ev) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.second) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, p.first, p.second) != cudaSuccess)
+            rc = fail(ANN_ERR_CUDA, "tile timing events failed");
+        tot += ms;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_timing_mu);
+        for (auto& p : ev) {
+            g_event_pool.push_back(p.first);
+            g_event_pool.push_back(p.second);
+        }
+    }
+    *tile_ms = tot;
+    *launches = (int)ev.size();
+    return rc;
+}
+
+int ann_device_status(int* out) {
+    ANN_REQUIRE(out != nullptr, "ann_device_status: out is NULL");
+    ANN_CHECK_CUDA(cudaDeviceSynchronize());
+    int v = 0, zero = 0;
+    ANN_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_dev_status, sizeof(int)));
+    ANN_CHECK_CUDA(cudaMemcpyToSymbol(g_dev_status, &zero, sizeof(int)));
+    *out = v;
+    if (v & DEV_TIMEOUT) return fail(ANN_ERR_TIMEOUT, "a bounded device wait gave up");
+    return ANN_OK;
+}
+
+// ---------------------------------------------------------------- partition
+int ann_partition_workspace(int64_t N, int d, int C, int r, int64_t S, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
+    ANN_REQUIRE(d >= 1 && d <= 4096, "d out of range");
+    ANN_REQUIRE(C >= 1 && C <= 1024 && r >= 1 && r <= C, "need 1 <= r <= C <= 1024");
+    ANN_REQUIRE(S >= 0 && S <= N, "S out of range");
+    *bytes = partition_ws(N, d, C, r, S, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
+                  const float* init_centroids, const uint32_t* sample_idx, int64_t S, int iters,
+                  float* centroids_out, uint32_t* members_out, int64_t* offsets_out, void* ws,
+                  size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_partition_workspace(N, d, C, r, S, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(iters >= 0, "iters < 0");
+    ANN_REQUIRE(init_centroids && centroids_out && offsets_out, "NULL pointer");
+    ANN_REQUIRE(N == 0 || (X && members_out), "NULL pointer");
+    ANN_REQUIRE(S == 0 || iters == 0 || sample_idx, "sample_idx is NULL");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    PartitionWs w;
+    partition_ws(N, d, C, r, S, &w, ws, ws_bytes);
+    if (N == 0) {
+        ANN_CHECK_CUDA(cudaMemsetAsync(offsets_out, 0, sizeof(int64_t) * (C + 1), (cudaStream_t)stream));
+        ANN_CHECK_CUDA(cudaMemcpyAsync(centroids_out, init_centroids, sizeof(float) * C * d,
+                                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        return ANN_OK;
+    }
+    return run_partition(X, N, d, dtype, C, r, init_centroids, sample_idx, S, iters, centroids_out,
+                         members_out, offsets_out, w, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- shard kNN
+static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int precision,
+                    int rerank_k) {
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
+    ANN_REQUIRE(C >= 1 && C <= (1 << 20), "C out of range");
+    ANN_REQUIRE(rows >= 0 && rows < (1ll << 40), "rows out of range");
+    ANN_REQUIRE(k >= 1 && k <= 96, "k must be in [1, 96]");
+    ANN_REQUIRE(d >= 1, "d < 1");
+    ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 128), "rerank_k must be 0 or in [k, 128]");
+    if (precision != ANN_EXACT)
+        return fail(ANN_ERR_UNSUPPORTED, "precision %d is not built in this version", precision);
+    if (d > 256) return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d > 256 not built in this version");
+    return ANN_OK;
+}
+
+int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
+                            int precision, int rerank_k, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
+    if (rc) return rc;
+    KnnPlan pl;
+    if ((rc = knn_plan(d, dtype, k, rerank_k, &pl))) return rc;
+    *bytes = knn_ws(C, rows, pl, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
+                  const int64_t* offsets, int C, int64_t rows, int k, int precision, int rerank_k,
+                  const void* model, uint32_t* knn_id, float* knn_d, void* ws, size_t ws_bytes,
+                  void* stream) {
+    int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
+    if (rc) return rc;
+    ANN_REQUIRE(model == nullptr, "model must be NULL in this version");
+    ANN_REQUIRE(offsets, "offsets is NULL");
+    ANN_REQUIRE(rows == 0 || (X && members && knn_id && knn_d), "NULL pointer");
+    KnnPlan pl;
+    if ((rc = knn_plan(d, dtype, k, rerank_k, &pl))) return rc;
+    size_t need = knn_ws(C, rows, pl, nullptr, nullptr, 0);
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if (rows == 0) return ANN_OK;
+    KnnWs w;
+    knn_ws(C, rows, pl, &w, ws, ws_bytes);
+    return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, knn_id, knn_d,
+                         (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- prune / merge
+int ann_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule, uint32_t* pr_id,
+              float* pr_d, void* stream) {
+    ANN_REQUIRE(k >= 1 && k <= 256, "k must be in [1, 256]");
+    ANN_REQUIRE(R >= 1 && R <= 256, "R must be in [1, 256]");
+    ANN_REQUIRE(rule == ANN_PRUNE_RANK || rule == ANN_PRUNE_TRUNC, "bad rule %d", rule);
+    ANN_REQUIRE(C >= 1 && rows >= 0, "bad C / rows");
+    ANN_REQUIRE(offsets, "offsets is NULL");
+    ANN_REQUIRE(rows == 0 || (knn_id && knn_d && members && pr_id && pr_d), "NULL pointer");
+    return run_prune(knn_id, knn_d, members, offsets, C, rows, k, R, rule, pr_id, pr_d,
+                     (cudaStream_t)stream);
+}
+
+int ann_merge_workspace(int64_t N, int64_t rows, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32) && rows >= 0, "N / rows out of range");
+    *bytes = merge_ws(N, rows, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
+              float* gdist, uint32_t* degree, void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_merge_workspace(N, rows, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(R >= 1 && R <= 256, "R must be in [1, 256]");
+    ANN_REQUIRE(C >= 1, "C < 1");
+    ANN_REQUIRE(N == 0 || (graph && gdist && degree), "NULL pointer");
+    ANN_REQUIRE(rows == 0 || (pr_id && pr_d && members), "NULL pointer");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    MergeWs w;
+    merge_ws(N, rows, &w, ws, ws_bytes);
+    return run_merge(pr_id, pr_d, members, offsets, C, rows, N, R, graph, gdist, degree, w,
+                     (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- query side
+int ann_medoid_workspace(int64_t N, int d, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 1 && d >= 1, "N and d must be >= 1");
+    *bytes = medoid_ws(N, d, nullptr, nullptr, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, void* ws,
+               size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_medoid_workspace(N, d, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype");
+    ANN_REQUIRE(X && entry_out, "NULL pointer");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    double* part;
+    float* mean;
+    unsigned long long* best;
+    medoid_ws(N, d, &part, &mean, &best, ws, ws_bytes);
+    return run_medoid(X, N, d, dtype, entry_out, part, mean, best, (cudaStream_t)stream);
+}
+
+int ann_knn_query_workspace(int64_t N, int64_t nq, int d, int dtype, int k, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    int rc = knn_args(N, d, dtype, 1, nq, k, ANN_EXACT, 0);
+    if (rc) return rc;
+    ANN_REQUIRE(N < (1 << 24) && nq < (1 << 24), "N and nq must be < 2^24");
+    KnnPlan pl;
+    if ((rc = knn_plan(d, dtype, k, 0, &pl))) return rc;
+    *bytes = query_ws(N, nq, pl, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,
+                  uint32_t* out_id, float* out_d, void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_knn_query_workspace(N, nq, d, dtype, k, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(nq == 0 || (X && Q && out_id && out_d), "NULL pointer");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if (nq == 0) return ANN_OK;
+    KnnPlan pl;
+    knn_plan(d, dtype, k, 0, &pl);
+    QueryWs w;
+    query_ws(N, nq, pl, &w, ws, ws_bytes);
+    return run_knn_query(X, N, Q, nq, d, dtype, k, pl, w, out_id, out_d, (cudaStream_t)stream);
+}
+
+static int search_args(int R, int64_t N, int d, int dtype, int64_t nq, uint32_t entry, int Ls,
+                       int topk) {
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype");
+    ANN_REQUIRE(R >= 1 && R <= 64, "R must be in [1, 64]");
+    ANN_REQUIRE(N >= 1 && N < (1ll << 32) && d >= 1 && d <= 4096, "N / d out of range");
+    ANN_REQUIRE(nq >= 0 && nq < (1ll << 31), "nq out of range");
+    ANN_REQUIRE(entry < N, "entry >= N");
+    ANN_REQUIRE(Ls >= 1 && Ls <= 256, "Ls must be in [1, 256]");
+    ANN_REQUIRE(topk >= 1 && topk <= Ls, "topk must be in [1, Ls]");
+    return ANN_OK;
+}
+
+int ann_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
+               int d, int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
+               uint32_t* out_id, uint32_t* out_count, void* stream) {
+    int rc = search_args(R, N, d, dtype, nq, entry, Ls, topk);
+    if (rc) return rc;
+    ANN_REQUIRE(nq == 0 || (graph && degree && X && Q && out_id && out_count), "NULL pointer");
+    return run_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, Ls, topk, out_id, out_count,
+                      (cudaStream_t)stream);
+}
+
+int ann_recall(const uint32_t* found, int found_stride, const uint32_t* truth, int truth_stride,
+               int64_t nq, int kk, float* recall_out, void* stream) {
+    ANN_REQUIRE(kk >= 1 && kk <= found_stride && kk <= truth_stride, "bad kk / strides");
+    ANN_REQUIRE(nq >= 0 && recall_out, "bad nq / NULL recall_out");
+    ANN_REQUIRE(nq == 0 || (found && truth), "NULL pointer");
+    unsigned long long* h = hits_ptr();
+    if (!h) return fail(ANN_ERR_CUDA, "hit counter unavailable");
+    return run_recall(found, found_stride, truth, truth_stride, nq, kk, recall_out, h,
+                      (cudaStream_t)stream);
+}
+
+int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const void* X,
+                    int64_t N, int d, int dtype, const void* Q, int64_t nq, const uint32_t* gt,
+                    uint32_t entry, int Ls, uint32_t* out_id, float* recall_out,
+                    uint32_t* dist_count_out, void* stream) {
+    int rc = ann_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, Ls, 10, out_id,
+                        dist_count_out, stream);
+    if (rc) return rc;
+    ANN_REQUIRE(Ls >= 10, "Ls must be >= 10 for recall@10");
+    return ann_recall(out_id, 10, gt, 10, nq, 10, recall_out, stream);
+}
+
+}  // extern "C"

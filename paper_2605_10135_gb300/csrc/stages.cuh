@@ -1,0 +1,113 @@
+// Internal interface between the C-ABI entry points (api.cu) and the stage
+// drivers (partition.cu, knn.cu, graph.cu, search.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ann {
+
+// ---- partition ----------------------------------------------------------------
+struct PartitionWs {
+    float* cent;       // [C*d] working centroids
+    float* centT;      // [d*C] transposed copy read by the distance kernel
+    float* dist;       // [chunk*C]
+    int32_t* lab;      // [S]
+    double* sums;      // [C*d]
+    int64_t* cnt;      // [C]
+    uint32_t* assign;  // [N*r]
+    int32_t* hist;     // [C*nblk]
+    int64_t* tot;      // [C]
+    int64_t chunk;
+};
+size_t partition_ws(int64_t N, int d, int C, int r, int64_t S, PartitionWs* out, void* base,
+                    size_t cap);
+int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r, const float* init,
+                  const uint32_t* sample_idx, int64_t S, int iters, float* cent_out,
+                  uint32_t* members_out, int64_t* offsets_out, const PartitionWs& w,
+                  cudaStream_t st);
+
+// ---- kNN tiles --------------------------------------------------------------------
+struct KnnProblem {
+    int64_t a_row0;    // first row of the problem in the A buffer (padded index space)
+    int64_t b_row0;    // first row in the B buffer
+    int64_t out_row0;  // first output row
+    int64_t mem_row0;  // members[] offset of column 0 (global id lookup)
+    int32_t n_rows, n_cols;
+};
+
+struct KnnPlan {
+    int mode;         // 0 plain, 1 split (hi/lo BF16 sections)
+    int Kp;           // elements per gathered row
+    int Kh;           // split: elements per section
+    int nkb_a, nkb_b;
+    uint32_t ab_fmt;  // 0 fp16, 1 bf16
+    bool rerank;
+    int kprime;
+    int nst;
+    size_t smem;
+};
+int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl);
+
+struct KnnWs {
+    int64_t* blk_off;
+    int64_t* pad_off;
+    KnnProblem* probs;
+    __nv_bfloat16* G;   // [rows_cap x Kp] (fp16 bits when ab_fmt == 0)
+    float* norms;       // [rows_cap + 512]
+    uint32_t* cand_id;  // [rows x kprime] when re-ranking
+    float* cand_d;
+    int64_t rows_cap;
+};
+size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
+int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
+                  const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
+                  const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st);
+
+struct QueryWs {
+    int64_t* blk_off;
+    int64_t* pad_off;  // {0, padded nq, 0, padded N}
+    int64_t* offs;     // {0, nq, 0, N}
+    KnnProblem* prob;
+    __nv_bfloat16* GA;
+    __nv_bfloat16* GB;
+    float* na;
+    float* nb;
+    uint32_t* cand_id;
+    float* cand_d;
+    int64_t capA, capB;
+};
+size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* base, size_t cap);
+int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,
+                  const KnnPlan& pl, const QueryWs& w, uint32_t* out_id, float* out_d,
+                  cudaStream_t st);
+
+// ---- prune / merge ---------------------------------------------------------------
+int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, cudaStream_t st);
+struct MergeWs {
+    int32_t* cnt;
+    int64_t* start;
+    int64_t* bsum;
+    int64_t* rowlist;
+};
+size_t merge_ws(int64_t N, int64_t rows, MergeWs* out, void* base, size_t cap);
+int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
+              float* gdist, uint32_t* degree, const MergeWs& w, cudaStream_t st);
+
+// ---- query side ------------------------------------------------------------------
+int search_vis_mask(int Ls, int R);
+int run_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
+               int d, int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
+               uint32_t* out_id, uint32_t* out_count, cudaStream_t st);
+int run_recall(const uint32_t* found, int fs, const uint32_t* truth, int ts, int64_t nq, int kk,
+               float* recall_out, unsigned long long* hits, cudaStream_t st);
+size_t medoid_ws(int64_t N, int d, double** part, float** mean, unsigned long long** best,
+                 void* base, size_t cap);
+int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, double* part,
+               float* mean, unsigned long long* best, cudaStream_t st);
+
+}  // namespace ann

@@ -1,0 +1,60 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/ann.h declares; argument checks run on the host without a GPU."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_2605_10135_gb300 import ann, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ann.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ann_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return ann.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_error_string(L):
+    assert L.ann_version() >= 100
+    assert isinstance(L.ann_last_error(), bytes)
+
+
+def test_workspace_queries_validate_on_host(L):
+    n = ct.c_size_t(0)
+    assert L.ann_partition_workspace(1000, 64, 4, 2, 100, ct.byref(n)) == 0 and n.value > 0
+    assert L.ann_partition_workspace(1000, 64, 4, 5, 100, ct.byref(n)) == 1  # r > C
+    assert b"r <= C" in L.ann_last_error()
+    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 0
+    small = n.value
+    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 4000, 64, 0, 0, ct.byref(n)) == 0
+    assert n.value > small
+    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 0, 0, 0, ct.byref(n)) == 1  # k = 0
+    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 1, 0, ct.byref(n)) == 2  # reserved
+    assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256
+    assert L.ann_merge_workspace(1000, 2000, ct.byref(n)) == 0 and n.value > 0
+    assert L.ann_prune(None, None, None, None, 4, 10, 0, 8, 0, None, None, None) == 1  # k = 0
+    assert L.ann_prune(None, None, None, None, 4, 10, 8, 8, 7, None, None, None) == 1  # rule
+
+
+def test_null_workspace_is_rejected(L):
+    n = ct.c_size_t(0)
+    assert L.ann_merge_workspace(1000, 2000, ct.byref(n)) == 0
+    rc = L.ann_merge(ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), 4, 2000,
+                     1000, 8, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), None, 0, None)
+    assert rc == 5 and b"workspace" in L.ann_last_error()

@@ -1,0 +1,254 @@
+"""CUDA path (through the C-ABI) against the CPU oracle on the same seeded inputs.
+
+Integer data and integer logic are compared bit for bit; float kNN lists follow
+the rule in tests/parity.py.  Sizes span several 128-row blocks and 256-column
+tiles with ragged tails; edge cases cover tiny shards (padding), one shard,
+r = C, duplicate vectors and empty shards.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_10135_gb300 import ann, build, datagen
+from tests.parity import PAD, as_u32, check_float_lists
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def T(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).to(DEV)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    ann.lib()
+    ann.device_status()
+    yield
+    assert ann.device_status() == 0
+
+
+def _part_inputs(X, C, seed):
+    sample, init_rows = datagen.kmeans_sample(X.shape[0], C, seed)
+    init = X[init_rows].astype(np.float32)
+    return sample, init
+
+
+def _gpu_partition(X, C, r, iters, seed):
+    sample, init = _part_inputs(X, C, seed)
+    cent, mem, off = ann.partition(T(X), C, r, T(init), T(sample), iters)
+    torch.cuda.synchronize()
+    return cent.cpu().numpy(), as_u32(mem), off.cpu().numpy(), (sample, init)
+
+
+# ------------------------------------------------------------------- partition
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "f16"])
+def test_partition_bit_exact(kind):
+    if kind == "u8":
+        X = datagen.clustered_u8(3000, 128, 32, seed=31)
+    elif kind == "f32":
+        X = datagen.gaussian_mixture_f32(3000, 64, seed=32)
+    else:
+        X = datagen.anisotropic_mixture(3000, 96, 64, 0.25, False, np.float16, seed=33)
+    C, r, iters = 5, 2, 6
+    cent, mem, off, (sample, init) = _gpu_partition(X, C, r, iters, seed=34)
+    cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, iters, C, r)
+    assert np.array_equal(cent.view(np.uint32), cent_o.view(np.uint32))
+    assert np.array_equal(off, off_o)
+    assert np.array_equal(mem, mem_o)
+
+
+def test_partition_edge_cases():
+    X = datagen.clustered_u8(700, 16, 4, seed=35)
+    for C, r in [(1, 1), (3, 3), (7, 1)]:
+        cent, mem, off, (sample, init) = _gpu_partition(X, C, r, 3, seed=36)
+        cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, 3, C, r)
+        assert np.array_equal(cent.view(np.uint32), cent_o.view(np.uint32))
+        assert np.array_equal(off, off_o) and np.array_equal(mem, mem_o)
+    # a centroid far from every point leaves its shard empty
+    sample = np.arange(700, dtype=np.uint32)
+    init = np.vstack([X[:2].astype(np.float32), np.full((1, 16), 1e6, np.float32)])
+    cent, mem, off = ann.partition(T(X), 3, 1, T(init), T(sample), 2)
+    cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, 2, 3, 1)
+    assert np.array_equal(off.cpu().numpy(), off_o) and off_o[3] - off_o[2] == 0
+    assert np.array_equal(as_u32(mem), mem_o)
+
+
+# ------------------------------------------------------------------- shard kNN
+
+def _oracle_shards(X, C, r, seed, iters=4):
+    sample, init = _part_inputs(X, C, seed)
+    _, _, mem, off = oracle.partition(X, init, sample, iters, C, r)
+    return mem, off
+
+
+@pytest.mark.parametrize("k", [1, 17, 64])
+def test_shard_knn_u8_bit_exact(k):
+    X = datagen.clustered_u8(3000, 128, 24, seed=41)
+    mem, off = _oracle_shards(X, 5, 2, seed=42)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), k)
+    oid, od = oracle.shard_knn(X, mem, off, k)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+
+
+def test_shard_knn_u8_duplicates_and_small_shards():
+    base = datagen.clustered_u8(300, 32, 4, seed=43)
+    X = np.vstack([base, base[:100], base[:50]])  # many exact duplicates -> ties by id
+    mem, off = _oracle_shards(X, 6, 2, seed=44)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 40)
+    oid, od = oracle.shard_knn(X, mem, off, 40)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+    # shards smaller than k + 1: trailing padding
+    Xs = X[:9]
+    members = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 2, 5], np.uint32)
+    offs = np.array([0, 3, 9, 9, 11], np.int64)  # includes an empty shard
+    gid, gd = ann.shard_knn(T(Xs), T(members), T(offs), 8)
+    oid, od = oracle.shard_knn(Xs, members, offs, 8)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+
+
+@pytest.mark.parametrize("kind,k", [("f32", 32), ("f32", 8), ("f16", 48), ("bf16", 20)])
+def test_shard_knn_float_rule(kind, k):
+    if kind == "f32":
+        X = datagen.gaussian_mixture_f32(3000, 64, seed=45)
+        Xt = T(X)
+    elif kind == "f16":
+        X = datagen.anisotropic_mixture(2500, 96, 64, 0.25, False, np.float16, seed=46)
+        Xt = T(X)
+    else:
+        X = datagen.gaussian_mixture_f32(2500, 40, seed=47)
+        Xt = T(X).to(torch.bfloat16)
+        X = Xt.float().cpu().numpy()  # the values the bf16 path sees
+    mem, off = _oracle_shards(X, 4, 2, seed=48)
+    gid, gd = ann.shard_knn(Xt, T(mem), T(off), k)
+    oid, od = oracle.shard_knn(X, mem, off, k)
+    check_float_lists(X, mem, gid.cpu().numpy(), gd.cpu().numpy(), oid, od)
+
+
+# ------------------------------------------------------------------ prune / merge
+
+def _oracle_lists(n=2500, d=64, C=4, r=2, k=32, seed=51):
+    X = datagen.clustered_u8(n, d, 16, seed=seed)
+    mem, off = _oracle_shards(X, C, r, seed + 1)
+    oid, od = oracle.shard_knn(X, mem, off, k)
+    return X, mem, off, oid, od.astype(np.float32)
+
+
+@pytest.mark.parametrize("rule,R", [(ann.PRUNE_RANK, 16), (ann.PRUNE_RANK, 5), (ann.PRUNE_TRUNC, 16),
+                                    (ann.PRUNE_RANK, 40)])
+def test_prune_bit_exact(rule, R):
+    X, mem, off, oid, od = _oracle_lists()
+    pid, pd = ann.prune(T(oid), T(od), T(mem), T(off), R, rule)
+    qid, qd = oracle.prune(oid, od.astype(np.float64), mem, off, R, rule)
+    assert np.array_equal(as_u32(pid), qid)
+    assert np.array_equal(pd.cpu().numpy().astype(np.float64), qd)
+
+
+def test_prune_line_example():
+    X = np.array([[0], [1], [3], [7]], np.float32)
+    mem = np.arange(4, dtype=np.uint32)
+    off = np.array([0, 4], np.int64)
+    oid, od = oracle.shard_knn(X, mem, off, 3)
+    pid, pd = ann.prune(T(oid), T(od.astype(np.float32)), T(mem), T(off), 2)
+    assert as_u32(pid).tolist() == [[1, 2], [0, 2], [1, 3], [2, 1]]
+
+
+@pytest.mark.parametrize("R", [16, 7])
+def test_merge_bit_exact(R):
+    X, mem, off, oid, od = _oracle_lists(C=5, r=3)
+    qid, qd = oracle.prune(oid, od.astype(np.float64), mem, off, R)
+    g, gd, deg = ann.merge(T(qid), T(qd.astype(np.float32)), T(mem), T(off), X.shape[0])
+    og, ogd, odeg = oracle.merge(qid, qd, mem, off, X.shape[0])
+    assert np.array_equal(as_u32(g), og)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), ogd)
+    assert np.array_equal(as_u32(deg), odeg)
+
+
+# ------------------------------------------------------------------- query side
+
+def test_knn_query_and_medoid_u8():
+    X = datagen.clustered_u8(4000, 128, 16, seed=61)
+    Q = datagen.clustered_u8(300, 128, 16, seed=62)
+    gid, gd = ann.knn_query(T(X), T(Q), 10)
+    oid, od = oracle.bruteforce(X, Q, 10)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+    assert int(ann.medoid(T(X)).item()) == oracle.medoid(X)
+
+
+def test_knn_query_f32_rule():
+    X = datagen.gaussian_mixture_f32(3000, 48, seed=63)
+    Q = datagen.gaussian_mixture_f32(200, 48, seed=64)
+    gid, gd = ann.knn_query(T(X), T(Q), 10)
+    oid, od = oracle.bruteforce(X, Q, 10)
+    # rows are queries: distances are measured from Q
+    Xq = np.vstack([X, Q])
+    check_float_lists(Xq, np.arange(len(X), len(X) + len(Q)), gid.cpu().numpy(), gd.cpu().numpy(),
+                      oid, od)
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_search_bit_exact(kind):
+    if kind == "u8":
+        X = datagen.clustered_u8(3000, 64, 16, seed=71)
+        Q = datagen.clustered_u8(150, 64, 16, seed=72)
+    else:
+        X = datagen.gaussian_mixture_f32(3000, 32, seed=73)
+        Q = datagen.gaussian_mixture_f32(150, 32, seed=74)
+    mem, off = _oracle_shards(X, 4, 2, seed=75)
+    oid, od = oracle.shard_knn(X, mem, off, 24)
+    qid, qd = oracle.prune(oid, od, mem, off, 12)
+    og, ogd, odeg = oracle.merge(qid, qd, mem, off, X.shape[0])
+    entry = oracle.medoid(X)
+    for Ls in (10, 32, 64):
+        gids, gcnt = ann.search(T(og), T(odeg), T(X), T(Q), entry, Ls, 10)
+        rids, rcnt = oracle.search(og, odeg, X, Q, entry, Ls, 10)
+        assert np.array_equal(as_u32(gids), rids)
+        assert np.array_equal(gcnt.cpu().numpy().astype(np.int64), rcnt)
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    rec = ann.recall(gids, T(gt), 10)
+    assert abs(float(rec.item()) - oracle.recall_at(rids, gt)) < 1e-6
+
+
+# ------------------------------------------------------------------- end to end
+
+def test_end_to_end_u8_bit_exact():
+    X = datagen.clustered_u8(6000, 128, 32, seed=81)
+    C, r, k, R, iters = 4, 2, 32, 16, 5
+    sample, init = _part_inputs(X, C, 82)
+    out = ann.build_index(T(X), ann.BuildConfig(C=C, r=r, k=k, R=R, iters=iters), T(init), T(sample))
+    cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, iters, C, r)
+    oid, od = oracle.shard_knn(X, mem_o, off_o, k)
+    qid, qd = oracle.prune(oid, od, mem_o, off_o, R)
+    og, ogd, odeg = oracle.merge(qid, qd, mem_o, off_o, X.shape[0])
+    assert np.array_equal(as_u32(out["members"]), mem_o)
+    assert np.array_equal(as_u32(out["knn_id"]), oid)
+    assert np.array_equal(as_u32(out["pr_id"]), qid)
+    assert np.array_equal(as_u32(out["graph"]), og)
+    assert np.array_equal(out["gdist"].cpu().numpy().astype(np.float64), ogd)
+    assert np.array_equal(as_u32(out["degree"]), odeg)
+
+
+def test_end_to_end_gauss10k():
+    """The small float workload: N=1e4, d=64, C=4, r=2, k=32, R=16."""
+    from paper_2605_10135_gb300 import configs
+    w = configs.GAUSS_10K
+    X = w.vectors()
+    sample, init_rows = w.kmeans_inputs()
+    init = X[init_rows].astype(np.float32)
+    out = ann.build_index(T(X), ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R), T(init), T(sample))
+    cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, 10, w.C, w.r)
+    assert np.array_equal(as_u32(out["members"]), mem_o)
+    oid, od = oracle.shard_knn(X, mem_o, off_o, w.k)
+    check_float_lists(X, mem_o, out["knn_id"].cpu().numpy(), out["knn_d"].cpu().numpy(), oid, od)
+    g, deg = as_u32(out["graph"]), as_u32(out["degree"])
+    assert np.all(deg <= w.R) and not np.any(g == np.arange(w.N)[:, None])
