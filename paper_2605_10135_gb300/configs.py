@@ -28,17 +28,28 @@ class Workload:
     def vectors(self, n: int | None = None, seed_offset: int = 0) -> np.ndarray:
         n = self.N if n is None else n
         s = self.seed + seed_offset
-        if self.name.startswith("gauss"):
+        base = self.name.split("@")[0]
+        if base.startswith("gauss"):
             return datagen.gaussian_mixture_f32(n, self.d, 16, 2.0, seed=s)
-        if self.name.startswith("sift"):
+        if base.startswith("sift"):
             return datagen.clustered_u8(n, self.d, 256, seed=s)
-        if self.name.startswith("deep"):
+        if base.startswith("deep"):
             return datagen.anisotropic_mixture(n, self.d, 1024, 0.25, True, np.float32, seed=s)
-        if self.name.startswith("laion"):
+        if base.startswith("laion"):
             return datagen.powerlaw_gaussian(n, self.d, 0.8, seed=s)
-        if self.name.startswith("embed"):
+        if base.startswith("embed"):
             return datagen.anisotropic_mixture(n, self.d, 4096, 0.25, False, np.float16, seed=s)
         raise KeyError(self.name)
+
+    def vectors_and_queries(self, nq: int):
+        """The vectors plus nq held-out queries from the same distribution."""
+        base = self.name.split("@")[0]
+        if base.startswith("gauss"):
+            return datagen.gaussian_mixture_f32(self.N, self.d, 16, 2.0, seed=self.seed, queries=nq)
+        if base.startswith("sift"):
+            return datagen.clustered_u8(self.N, self.d, 256, seed=self.seed, queries=nq)
+        X = self.vectors()
+        return X, self.vectors(nq, seed_offset=777)
 
     def kmeans_inputs(self, n: int | None = None):
         return datagen.kmeans_sample(self.N if n is None else n, self.C, seed=self.seed + 7)

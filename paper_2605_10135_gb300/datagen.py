@@ -34,20 +34,42 @@ __all__ = [
 
 
 def gaussian_mixture_f32(n: int, d: int, n_centres: int = 16, centre_std: float = 2.0,
-                         seed: int = 1001) -> np.ndarray:
-    """Isotropic Gaussian mixture, equal weights, float32 [n, d]."""
+                         seed: int = 1001, queries: int = 0):
+    """Isotropic Gaussian mixture, equal weights, float32 [n, d] (plus a held-out
+    query set from the same centres when queries > 0)."""
     rng = np.random.default_rng(seed)
     centres = rng.normal(0.0, centre_std, size=(n_centres, d))
     lab = rng.integers(0, n_centres, size=n)
     x = centres[lab] + rng.normal(0.0, 1.0, size=(n, d))
-    return np.ascontiguousarray(x.astype(np.float32))
+    x = np.ascontiguousarray(x.astype(np.float32))
+    if queries:
+        lq = rng.integers(0, n_centres, size=queries)
+        q = centres[lq] + rng.normal(0.0, 1.0, size=(queries, d))
+        return x, np.ascontiguousarray(q.astype(np.float32))
+    return x
 
 
 def clustered_u8(n: int, d: int, n_centres: int = 256, lo: float = 32.0, hi: float = 224.0,
-                 sigma: float = 20.0, seed: int = 1002) -> np.ndarray:
-    """Sift-like clustered uint8 vectors [n, d] (rounded and clipped to 0..255)."""
+                 sigma: float = 20.0, seed: int = 1002, queries: int = 0):
+    """Sift-like clustered uint8 vectors [n, d] (rounded and clipped to 0..255).
+
+    With queries > 0 also returns a held-out query set [queries, d] drawn from
+    the same centres after the data (the data itself does not change)."""
     rng = np.random.default_rng(seed)
     centres = rng.uniform(lo, hi, size=(n_centres, d)).astype(np.float32)
+
+    def draw(m):
+        lab = rng.integers(0, n_centres, size=m)
+        out = np.empty((m, d), dtype=np.uint8)
+        step = 1 << 18
+        for s in range(0, m, step):
+            e = min(m, s + step)
+            z = rng.standard_normal(size=(e - s, d), dtype=np.float32) * np.float32(sigma)
+            v = np.rint(centres[lab[s:e]] + z)
+            out[s:e] = np.clip(v, 0, 255).astype(np.uint8)
+        return out
+
+    # labels of the data are drawn before its noise, as a single block
     lab = rng.integers(0, n_centres, size=n)
     out = np.empty((n, d), dtype=np.uint8)
     step = 1 << 18
@@ -56,6 +78,8 @@ def clustered_u8(n: int, d: int, n_centres: int = 256, lo: float = 32.0, hi: flo
         z = rng.standard_normal(size=(e - s, d), dtype=np.float32) * np.float32(sigma)
         v = np.rint(centres[lab[s:e]] + z)
         out[s:e] = np.clip(v, 0, 255).astype(np.uint8)
+    if queries:
+        return out, draw(queries)
     return out
 
 
