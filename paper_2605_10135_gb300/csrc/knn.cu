@@ -2,30 +2,36 @@
 // independently, with no exchange between shards).
 //
 // Distance tiles are dense contractions on the 5th-generation tensor cores:
-//   dist(i, j) = |x_i|^2 + |y_j|^2 - 2 x_i . y_j
-// The row term |x_i|^2 is constant along a row, so rows are ranked by
-// key(i, j) = |y_j|^2 - 2 x_i . y_j and |x_i|^2 is added back at the end.
+//   dist(i, j) = |x_i|^2 + |y_j|^2 - 2 x_i . y_j = |x_i|^2 + 2 key(i, j),
+//   key(i, j)  = |y_j|^2 / 2 - x_i . y_j.
+// |x_i|^2 is constant along a row, so rows are ranked by key.  The key comes out
+// of the tensor cores whole: the main MMAs run with A negated (-x . y) and one
+// extra K=16 step adds [1, 1, 1, 0, ...] . [h, m, l, 0, ...], where h + m + l
+// is |y_j|^2 / 2 split exactly into three BF16 values.
 //
 // Kernel k_knn_tiles: one CTA per 128-row block of one problem (a shard, or a
 // query batch against all vectors).  Warp roles:
-//   warp 0   : TMA producer.  The CTA's A rows (all K) are loaded once and stay
-//              in shared memory; B tiles of 256 rows x 64 K-elements stream
-//              through an NST-stage ring (128-byte swizzle).
-//   warp 1   : allocates 512 TMEM columns (two 128x256 FP32 accumulators) and
-//              issues tcgen05.mma (M=128, N=256, K=16) from one thread.
-//   warps 2-5: epilogue, one thread per row (TMEM lane).  Each 32-column chunk
-//              is read with tcgen05.ld, turned into keys, reduced to a chunk
-//              minimum and skipped unless it beats the row's current k-th key;
-//              survivors replace the root of a per-row max-heap in shared
-//              memory (composite (key, column) order, so ties go to the
-//              smaller column = smaller global id).
+//   warp 0   : TMA producer.  The CTA's A rows (all K) stay resident in shared
+//              memory; B tiles of 128 rows stream through an NST-stage ring of
+//              16 KB stages, one 64-element K block (128-byte swizzle) per stage
+//              plus the 16-element norm block (32-byte swizzle).
+//   warp 1   : allocates 512 TMEM columns (four 128x128 FP32 accumulators) and
+//              issues tcgen05.mma (M=128, N=128, K=16) from one thread.
+//   warps 2-5: epilogue, one thread per row (TMEM lane).  16-column chunks are
+//              read with tcgen05.ld (the next chunk's load overlaps the current
+//              chunk's work), reduced with 3-input minima and skipped unless
+//              they beat the row's current k-th key.  Survivors are appended to
+//              a per-row buffer in shared memory; when any row's buffer is near
+//              full, all 32 rows of the warp insert their buffers into per-row
+//              max-heaps in lockstep (composite (key, column) order, so ties go
+//              to the smaller column = smaller global id).
 // Every wait is bounded; on a timeout the CTA records DEV_TIMEOUT, drains its
 // copies, frees TMEM and returns.
 //
 // Operand modes:
-//   plain : A = B = one BF16/FP16 copy of the vectors.  uint8 values and their
-//           products/sums up to 2^24 are exact in BF16 x BF16 -> FP32, so the
-//           integer keys are exact (d <= 258).
+//   plain : A = B = one BF16/FP16 copy of the vectors.  uint8 values, their
+//           products and all partial sums (integers or half-integers below
+//           2^23 for d <= 128) are exact in BF16 x BF16 -> FP32.
 //   split : float vectors stored as hi = bf16(x), lo = bf16(x - hi) in two
 //           K sections; x.y ~ hi.hi + hi.lo + lo.hi (three products), used to
 //           screen a widened list that k_rerank re-scores in FP32.
@@ -38,21 +44,24 @@ namespace ann {
 
 namespace kt {
 constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int KB = 64;                      // K elements per 128-byte block
-constexpr int A_BLK_BYTES = BM * 128;       // 16 KB
-constexpr int B_BLK_BYTES = BN * 128;       // 32 KB
+constexpr int BN = 128;
+constexpr int KB = 64;                  // K elements per 128-byte block
+constexpr int KAUG = 16;                // norm block: 16 elements (32 bytes)
+constexpr int BLK_BYTES = 128 * 128;    // one K block of 128 rows (A or B)
+constexpr int AUG_BYTES = 128 * 32;     // one norm block of 128 rows
+constexpr int NACC = 4;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr int MAX_NST = 6;
+constexpr uint32_t TMEM_COLS = NACC * BN;
+constexpr int MAX_NST = 8;
+constexpr int CAP = 32;                 // survivor buffer entries per row
+constexpr int CHUNK = 16;
 }  // namespace kt
 
 struct KnnParams {
     const int64_t* blk_off;  // [nprob+1] prefix sums of row blocks
     const KnnProblem* probs;
     int nprob;
-    const float* nb;  // key bias per B row: |y|^2
-    const float* na;  // |x|^2 per A row
+    const float* na;          // |x|^2 per A row
     const uint32_t* members;  // column -> global id (NULL: identity)
     int self_exclude;
     int mode;      // 0 plain, 1 split
@@ -61,29 +70,31 @@ struct KnnParams {
     int kprime;    // heap entries per row
     int k_out;     // entries written per row
     int nst;       // pipeline stages
-    uint32_t idesc;
+    uint32_t idesc_neg, idesc_aug;
     uint32_t* out_id;
     float* out_d;
     int* status;
 };
 
 struct KnnSmemLayout {
-    uint32_t a, b, heap, scratch, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, heap, buf, bars, tmem_slot, abort_flag, total;
 };
 
 __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int kprime) {
     KnnSmemLayout L;
     uint32_t o = 0;
     L.a = o;
-    o += nkb_a * kt::A_BLK_BYTES;
+    o += nkb_a * kt::BLK_BYTES;
+    L.aaug = o;
+    o += 1024 * ((kt::AUG_BYTES + 1023) / 1024);
     L.b = o;
-    o += nst * kt::B_BLK_BYTES;
+    o += nst * kt::BLK_BYTES;
     L.heap = o;
     o += kprime * kt::BM * 8;
-    L.scratch = o;
-    o += kt::BM * 128;
+    L.buf = o;
+    o += kt::CAP * kt::BM * 8;
     L.bars = o;
-    o += (2 * kt::MAX_NST + 6) * 8;
+    o += (2 * kt::MAX_NST + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
     o += 4;
     L.abort_flag = o;
@@ -100,14 +111,13 @@ __device__ __forceinline__ uint64_t heap_init_val() {
 __device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, uint64_t x) {
     int e = 0;
     for (;;) {
-        int l = 2 * e + 1;
+        const int l = 2 * e + 1;
         if (l >= n) break;
-        uint64_t hl = H[l * kt::BM + row];
+        uint64_t hc = H[l * kt::BM + row];
         int c = l;
-        uint64_t hc = hl;
         if (l + 1 < n) {
-            uint64_t hr = H[(l + 1) * kt::BM + row];
-            if (hr > hl) { c = l + 1; hc = hr; }
+            const uint64_t hr = H[(l + 1) * kt::BM + row];
+            if (hr > hc) { c = l + 1; hc = hr; }
         }
         if (hc <= x) break;
         H[e * kt::BM + row] = hc;
@@ -117,16 +127,15 @@ __device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, u
 }
 
 __device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
-    uint64_t x = H[e * kt::BM + row];
+    const uint64_t x = H[e * kt::BM + row];
     for (;;) {
-        int l = 2 * e + 1;
+        const int l = 2 * e + 1;
         if (l >= n) break;
-        uint64_t hl = H[l * kt::BM + row];
+        uint64_t hc = H[l * kt::BM + row];
         int c = l;
-        uint64_t hc = hl;
         if (l + 1 < n) {
-            uint64_t hr = H[(l + 1) * kt::BM + row];
-            if (hr > hl) { c = l + 1; hc = hr; }
+            const uint64_t hr = H[(l + 1) * kt::BM + row];
+            if (hr > hc) { c = l + 1; hc = hr; }
         }
         if (hc <= x) break;
         H[e * kt::BM + row] = hc;
@@ -135,16 +144,103 @@ __device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
     H[e * kt::BM + row] = x;
 }
 
+// 32 lanes x 16 consecutive columns: thread t gets lane (taddr.lane + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// Wait for outstanding tcgen05.ld; the registers are tied to the wait so that no
+// use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset: 8 rows x 32 B
+    d |= (uint64_t)1 << 46;                 // descriptor version (sm_100 family)
+    d |= (uint64_t)6 << 61;                 // layout: SWIZZLE_32B
+    return d;
+}
+
+struct EpiState {
+    uint64_t* H;
+    uint64_t* B;
+    int row, kp, cnt;
+    float tau;
+};
+
+// Insert every buffered survivor of every row of the warp into its heap.
+__device__ __forceinline__ void epi_flush(EpiState& s) {
+    const int mx = __reduce_max_sync(0xffffffffu, s.cnt);
+    for (int q = 0; q < mx; ++q) {
+        if (q < s.cnt) {
+            const uint64_t x = s.B[q * kt::BM + s.row];
+            if (x < s.H[s.row]) heap_replace_root(s.H, s.row, s.kp, x);
+        }
+    }
+    s.cnt = 0;
+    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
+}
+
+__device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], int j0, int i,
+                                          int n_cols, int self_exclude) {
+    float key[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) key[u] = __uint_as_float(v[u]);
+    if ((j0 + 16 > n_cols) || (self_exclude && (unsigned)(i - j0) < 16u)) {  // warp-uniform
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int j = j0 + u;
+            if (j >= n_cols || (self_exclude && j == i)) key[u] = INFINITY;
+        }
+    }
+    const float m0 = min3f(key[0], key[1], key[2]);
+    const float m1 = min3f(key[3], key[4], key[5]);
+    const float m2 = min3f(key[6], key[7], key[8]);
+    const float m3 = min3f(key[9], key[10], key[11]);
+    const float m4 = min3f(key[12], key[13], key[14]);
+    const float m = min3f(min3f(m0, m1, m2), min3f(m3, m4, key[15]), INFINITY);
+    if (!__any_sync(0xffffffffu, m < s.tau)) return;
+    if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush(s);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        if (key[u] < s.tau) {
+            s.B[s.cnt * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | (uint32_t)(j0 + u);
+            ++s.cnt;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kt::THREADS, 1)
     k_knn_tiles(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const KnnParams P) {
+                const __grid_constant__ CUtensorMap tmAaug,
+                const __grid_constant__ CUtensorMap tmBaug, const KnnParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // Find this CTA's problem and row block.
     const int64_t bid = blockIdx.x;
     if (bid >= P.blk_off[P.nprob]) return;
     int lo = 0, hi = P.nprob - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (P.blk_off[mid] <= bid) lo = mid; else hi = mid - 1;
     }
     const KnnProblem pr = P.probs[lo];
@@ -154,13 +250,13 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const KnnSmemLayout L = knn_smem_layout(P.nkb_a, P.nst, P.kprime);
     const uint32_t sA = smem_u32(base + L.a);
+    const uint32_t sAaug = smem_u32(base + L.aaug);
     const uint32_t sB = smem_u32(base + L.b);
-    uint64_t* H = (uint64_t*)(base + L.heap);
-    float* scratch = (float*)(base + L.scratch);
     const uint32_t bars = smem_u32(base + L.bars);
     const uint32_t full_bar = bars, empty_bar = bars + kt::MAX_NST * 8;
-    const uint32_t accf_bar = bars + 2 * kt::MAX_NST * 8, acce_bar = accf_bar + 16;
-    const uint32_t a_bar = acce_bar + 16, done_bar = a_bar + 8;
+    const uint32_t accf_bar = bars + 2 * kt::MAX_NST * 8;
+    const uint32_t acce_bar = accf_bar + kt::NACC * 8;
+    const uint32_t a_bar = acce_bar + kt::NACC * 8, done_bar = a_bar + 8;
     volatile uint32_t* tmem_slot = (volatile uint32_t*)(base + L.tmem_slot);
     volatile int* abort_flag = (volatile int*)(base + L.abort_flag);
 
@@ -170,7 +266,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             mbar_init(full_bar + 8 * s, 1);
             mbar_init(empty_bar + 8 * s, 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < kt::NACC; ++a) {
             mbar_init(accf_bar + 8 * a, 1);
             mbar_init(acce_bar + 8 * a, 4);
         }
@@ -187,27 +283,36 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int loads_per_tile = P.nkb_b + 1;
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             tma_prefetch_desc(&tmA);
             tma_prefetch_desc(&tmB);
+            tma_prefetch_desc(&tmAaug);
+            tma_prefetch_desc(&tmBaug);
             const int a_y = (int)(pr.a_row0 + (int64_t)rb * kt::BM);
-            mbar_expect_tx(a_bar, P.nkb_a * kt::A_BLK_BYTES);
+            mbar_expect_tx(a_bar, P.nkb_a * kt::BLK_BYTES + kt::AUG_BYTES);
             for (int b = 0; b < P.nkb_a; ++b)
-                tma_load_2d(sA + b * kt::A_BLK_BYTES, &tmA, a_bar, b * kt::KB, a_y);
-            uint32_t last_par = 0;   // parity of the last load per stage (bit s)
-            uint32_t used = 0;       // stages ever loaded (bit s)
+                tma_load_2d(sA + b * kt::BLK_BYTES, &tmA, a_bar, b * kt::KB, a_y);
+            tma_load_2d(sAaug, &tmAaug, a_bar, 0, 0);
+            uint32_t last_par = 0, used = 0;
             int st = 0;
             uint32_t ph = 0;
             bool ok = true;
             for (int t = 0; t < ntiles && ok; ++t) {
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
-                for (int j = 0; j < P.nkb_b; ++j) {
+                for (int j = 0; j < loads_per_tile; ++j) {
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
-                    mbar_expect_tx(full_bar + 8 * st, kt::B_BLK_BYTES);
-                    tma_load_2d(sB + st * kt::B_BLK_BYTES, &tmB, full_bar + 8 * st, j * kt::KB, b_y);
+                    const uint32_t dst = sB + st * kt::BLK_BYTES;
+                    if (j < P.nkb_b) {
+                        mbar_expect_tx(full_bar + 8 * st, kt::BLK_BYTES);
+                        tma_load_2d(dst, &tmB, full_bar + 8 * st, j * kt::KB, b_y);
+                    } else {
+                        mbar_expect_tx(full_bar + 8 * st, kt::AUG_BYTES);
+                        tma_load_2d(dst, &tmBaug, full_bar + 8 * st, 0, b_y);
+                    }
                     used |= 1u << st;
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
@@ -216,7 +321,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             // Drain: every issued copy must land before the CTA may exit.
             int dummy = 0;
             for (int s = 0; s < P.nst; ++s)
-                if (used >> s & 1) mbar_wait(full_bar + 8 * s, (last_par >> s) & 1, &dummy, 200000000ull);
+                if (used >> s & 1)
+                    mbar_wait(full_bar + 8 * s, (last_par >> s) & 1, &dummy, 200000000ull);
             mbar_wait(a_bar, 0, &dummy, 200000000ull);
             if (!ok) atomicOr(P.status, DEV_TIMEOUT);
         }
@@ -229,35 +335,42 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             uint32_t ph = 0;
             const int H2 = P.nkb_b >> 1;
             for (int t = 0; t < ntiles && ok; ++t) {
-                const int a = t & 1;
-                if (!mbar_wait(acce_bar + 8 * a, ((t >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                const int a = t % kt::NACC;
+                if (!mbar_wait(acce_bar + 8 * a, ((t / kt::NACC) & 1) ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + a * kt::BN;
                 uint32_t accum = 0;
-                for (int j = 0; j < P.nkb_b; ++j) {
+                for (int j = 0; j < loads_per_tile; ++j) {
                     if (!mbar_wait(full_bar + 8 * st, ph, abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t bsm = sB + st * kt::B_BLK_BYTES;
-                    // A blocks paired with this B block.
-                    int ablk[2];
-                    int na = 1;
-                    if (P.mode == 0) {
-                        ablk[0] = j;
-                    } else if (j < H2) {
-                        ablk[0] = j;        // hi.hi
-                        ablk[1] = H2 + j;   // lo.hi
-                        na = 2;
-                    } else {
-                        ablk[0] = j - H2;   // hi.lo
-                    }
-                    for (int q = 0; q < na; ++q) {
-                        const uint32_t asm_ = sA + ablk[q] * kt::A_BLK_BYTES;
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) {
-                            umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
-                                     P.idesc, accum);
-                            accum = 1;
+                    const uint32_t bsm = sB + st * kt::BLK_BYTES;
+                    if (j < P.nkb_b) {
+                        int ablk[2];
+                        int na = 1;
+                        if (P.mode == 0) {
+                            ablk[0] = j;
+                        } else if (j < H2) {
+                            ablk[0] = j;       // hi . hi
+                            ablk[1] = H2 + j;  // lo . hi
+                            na = 2;
+                        } else {
+                            ablk[0] = j - H2;  // hi . lo
                         }
+                        for (int q = 0; q < na; ++q) {
+                            const uint32_t asm_ = sA + ablk[q] * kt::BLK_BYTES;
+#pragma unroll
+                            for (int s = 0; s < kt::KB / 16; ++s) {
+                                umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                         sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                accum = 1;
+                            }
+                        }
+                    } else {
+                        umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(bsm), P.idesc_aug, accum);
+                        accum = 1;
                     }
                     umma_commit(empty_bar + 8 * st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
@@ -265,8 +378,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 if (!ok) break;
                 umma_commit(accf_bar + 8 * a);
             }
-            // Wait for every issued MMA before TMEM is released.
-            umma_commit(done_bar);
+            umma_commit(done_bar);  // every issued MMA completes before TMEM is released
             int dummy = 0;
             mbar_wait(done_bar, 0, &dummy, 200000000ull);
             if (!ok) atomicOr(P.status, DEV_TIMEOUT);
@@ -274,68 +386,39 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     } else {
         // -------------------------------------------------------- epilogue
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        const int row = q * 32 + lane;
-        const int i = rb * kt::BM + row;  // row index inside the problem
-        const int kp = P.kprime;
+        EpiState s;
+        s.row = q * 32 + lane;
+        s.H = (uint64_t*)(base + L.heap);
+        s.B = (uint64_t*)(base + L.buf);
+        s.kp = P.kprime;
+        s.cnt = 0;
+        s.tau = INFINITY;
+        const int i = rb * kt::BM + s.row;  // row index inside the problem
         const uint64_t init = heap_init_val();
-        for (int e = 0; e < kp; ++e) H[e * kt::BM + row] = init;
-        float tau = INFINITY;
-        const float* nbp = P.nb + pr.b_row0;
+        for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        float* scr = scratch + row;  // element u at scr[u * BM]: conflict-free
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
-            const int a = t & 1;
-            if (!mbar_wait(accf_bar + 8 * a, (t >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int a = t % kt::NACC;
+            if (!mbar_wait(accf_bar + 8 * a, (t / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            for (int c = 0; c < kt::BN / 32; ++c) {
-                const int j0 = t * kt::BN + c * 32;
-                uint32_t v[32];
+            const uint32_t tb = tmem + lane_addr + a * kt::BN;
+            const int jt = t * kt::BN;
+            uint32_t va[16], vb[16];
+            __syncwarp();
+            tmem_ld16(tb, va);
+#pragma unroll
+            for (int c = 0; c < kt::BN / kt::CHUNK; c += 2) {
+                tmem_wait_ld16(va);
+                tmem_ld16(tb + (c + 1) * kt::CHUNK, vb);
+                if (jt + c * kt::CHUNK < pr.n_cols)
+                    epi_chunk(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude);
                 __syncwarp();
-                tmem_ld32(tmem + lane_addr + a * kt::BN + c * 32, v);
-                tmem_wait_ld();
-                if (j0 >= pr.n_cols) continue;  // uniform over the warp
-                float key[32];
-                const float4* nb4 = (const float4*)(nbp + j0);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    float4 nn = __ldg(nb4 + u);
-                    key[4 * u + 0] = fmaf(-2.0f, __uint_as_float(v[4 * u + 0]), nn.x);
-                    key[4 * u + 1] = fmaf(-2.0f, __uint_as_float(v[4 * u + 1]), nn.y);
-                    key[4 * u + 2] = fmaf(-2.0f, __uint_as_float(v[4 * u + 2]), nn.z);
-                    key[4 * u + 3] = fmaf(-2.0f, __uint_as_float(v[4 * u + 3]), nn.w);
-                }
-                const bool edge = (j0 + 32 > pr.n_cols) ||
-                                  (P.self_exclude && (unsigned)(i - j0) < 32u);
-                if (edge) {
-#pragma unroll
-                    for (int u = 0; u < 32; ++u) {
-                        const int j = j0 + u;
-                        if (j >= pr.n_cols || (P.self_exclude && j == i)) key[u] = INFINITY;
-                    }
-                }
-                float m = key[0];
-#pragma unroll
-                for (int u = 1; u < 32; ++u) m = fminf(m, key[u]);
-                if (!__any_sync(0xffffffffu, m < tau)) continue;
-                uint32_t bits = 0;
-#pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    bits |= (key[u] < tau ? 1u : 0u) << u;
-                    scr[u * kt::BM] = key[u];
-                }
-                while (__any_sync(0xffffffffu, bits != 0)) {
-                    if (bits) {
-                        const int u = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const float kv = scr[u * kt::BM];
-                        if (kv < tau) {
-                            const uint64_t x = ((uint64_t)f2ord(kv) << 32) | (uint32_t)(j0 + u);
-                            heap_replace_root(H, row, kp, x);
-                            tau = ord2f((uint32_t)(H[row] >> 32));
-                        }
-                    }
-                }
+                tmem_wait_ld16(vb);
+                if (c + 2 < kt::BN / kt::CHUNK) tmem_ld16(tb + (c + 2) * kt::CHUNK, va);
+                if (jt + (c + 1) * kt::CHUNK < pr.n_cols)
+                    epi_chunk(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols, P.self_exclude);
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -343,27 +426,32 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         }
         if (!ok) {
             atomicOr(P.status, DEV_TIMEOUT);
-        } else if (i < pr.n_rows) {
-            // Heap sort ascending, then write (global id, |x|^2 + key).
-            for (int end = kp - 1; end > 0; --end) {
-                uint64_t top = H[row];
-                H[row] = H[end * kt::BM + row];
-                H[end * kt::BM + row] = top;
-                heap_sift(H, row, 0, end);
-            }
-            const float nx = P.na[pr.a_row0 + i];
-            const int64_t orow = pr.out_row0 + i;
-            for (int e = 0; e < P.k_out; ++e) {
-                const uint64_t x = H[e * kt::BM + row];
-                const uint32_t j = (uint32_t)x;
-                uint32_t id = ANN_PAD;
-                float dd = INFINITY;
-                if (j != 0xFFFFFFFFu) {
-                    id = P.members ? __ldg(P.members + pr.mem_row0 + j) : j;
-                    dd = nx + ord2f((uint32_t)(x >> 32));
+        } else {
+            epi_flush(s);
+            if (i < pr.n_rows) {
+                // Heap sort ascending, then write (global id, |x|^2 + 2 key).
+                uint64_t* H = s.H;
+                const int row = s.row, kp = s.kp;
+                for (int end = kp - 1; end > 0; --end) {
+                    const uint64_t top = H[row];
+                    H[row] = H[end * kt::BM + row];
+                    H[end * kt::BM + row] = top;
+                    heap_sift(H, row, 0, end);
                 }
-                P.out_id[orow * P.k_out + e] = id;
-                P.out_d[orow * P.k_out + e] = dd;
+                const float nx = P.na[pr.a_row0 + i];
+                const int64_t orow = pr.out_row0 + i;
+                for (int e = 0; e < P.k_out; ++e) {
+                    const uint64_t x = H[e * kt::BM + row];
+                    const uint32_t j = (uint32_t)x;
+                    uint32_t id = ANN_PAD;
+                    float dd = INFINITY;
+                    if (j != 0xFFFFFFFFu) {
+                        id = P.members ? __ldg(P.members + pr.mem_row0 + j) : j;
+                        dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
+                    }
+                    P.out_id[orow * P.k_out + e] = id;
+                    P.out_d[orow * P.k_out + e] = dd;
+                }
             }
         }
     }
@@ -397,7 +485,7 @@ __global__ void k_shard_tables(const int64_t* __restrict__ offsets, int C, int64
         pr.n_rows = (int32_t)n;
         pr.n_cols = (int32_t)n;
         probs[s] = pr;
-        int64_t nbk = (n + kt::BM - 1) / kt::BM;
+        const int64_t nbk = (n + kt::BM - 1) / kt::BM;
         b += nbk;
         p += nbk * kt::BM;
     }
@@ -406,9 +494,12 @@ __global__ void k_shard_tables(const int64_t* __restrict__ offsets, int C, int64
     if (bad) atomicOr(status, DEV_BAD_INPUT);
 }
 
-// Gather rows into the tile layout: row p' of G (pitch Kp elements) holds the
-// operand copy of member (pad_off -> shard, local index) or zeros.
-// mode 0: Kp >= d, element t = cvt(x_t).  mode 1: [hi | lo] sections of Kh each.
+// [1, 1, 1, 0 x 13] in every one of 128 rows: the A side of the norm K step.
+__global__ void k_ones_tile(__nv_bfloat16* __restrict__ t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 128 * kt::KAUG) t[i] = __float2bfloat16_rn((i % kt::KAUG) < 3 ? 1.0f : 0.0f);
+}
+
 template <typename T>
 __device__ __forceinline__ T cvt_from_float(float v);
 template <>
@@ -416,11 +507,16 @@ __device__ __forceinline__ __nv_bfloat16 cvt_from_float(float v) { return __floa
 template <>
 __device__ __forceinline__ __half cvt_from_float(float v) { return __float2half_rn(v); }
 
+// Gather rows into the tile layout: row p' of G (pitch Kp elements) holds the
+// operand copy of member (pad_off -> shard, local index) or zeros; norms[p'] =
+// |x|^2 and aug[p'] = |x|^2 / 2 split exactly into three BF16 values (hi, mid,
+// lo) followed by zeros.
+// mode 0: element t = cvt(x_t).  mode 1: [hi | lo] sections of Kh elements.
 template <typename T>
 __global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __restrict__ members,
                          const int64_t* __restrict__ offsets, const int64_t* __restrict__ pad_off,
                          int C, int64_t rows_cap, int mode, int Kp, int Kh, T* __restrict__ G,
-                         float* __restrict__ norms) {
+                         float* __restrict__ norms, __nv_bfloat16* __restrict__ aug) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -429,12 +525,12 @@ __global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __rest
         if (pr < pad_off[C]) {
             int lo = 0, hi = C - 1;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
+                const int mid = (lo + hi + 1) >> 1;
                 if (pad_off[mid] <= pr) lo = mid; else hi = mid - 1;
             }
-            int64_t li = pr - pad_off[lo];
+            const int64_t li = pr - pad_off[lo];
             if (li < offsets[lo + 1] - offsets[lo]) {
-                int64_t p = offsets[lo] + li;
+                const int64_t p = offsets[lo] + li;
                 src = members ? (int64_t)members[p] : p;
             }
         }
@@ -449,11 +545,11 @@ __global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __rest
                 }
                 g[t] = cvt_from_float<T>(v);
             } else {
-                int tt = t < Kh ? t : t - Kh;
+                const int tt = t < Kh ? t : t - Kh;
                 T out = cvt_from_float<T>(0.0f);
                 if (src >= 0 && tt < d) {
                     v = load_elem(X, dtype, src * d + tt);
-                    T h = cvt_from_float<T>(v);
+                    const T h = cvt_from_float<T>(v);
                     if (t < Kh) {
                         out = h;
                         nrm = fmaf(v, v, nrm);
@@ -466,6 +562,18 @@ __global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __rest
         }
         for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
         if (lane == 0) norms[pr] = nrm;
+        if (lane < kt::KAUG) {
+            const float half = 0.5f * nrm;
+            const __nv_bfloat16 h = __float2bfloat16_rn(half);
+            const float r1 = half - __bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            __nv_bfloat16 o = __float2bfloat16_rn(0.0f);
+            if (lane == 0) o = h;
+            if (lane == 1) o = m;
+            if (lane == 2) o = l;
+            aug[pr * kt::KAUG + lane] = o;
+        }
     }
 }
 
@@ -485,9 +593,9 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int i = lane * E + e;
-                    uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v[e], lp);
-                    uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v[e] >> 32), lp);
-                    uint64_t o = ((uint64_t)hi << 32) | lo;
+                    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v[e], lp);
+                    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v[e] >> 32), lp);
+                    const uint64_t o = ((uint64_t)hi << 32) | lo;
                     const bool up = (i & k) == 0, lower = (i & j) == 0;
                     const uint64_t mn = v[e] < o ? v[e] : o, mx = v[e] < o ? o : v[e];
                     v[e] = (lower == up) ? mn : mx;
@@ -525,7 +633,8 @@ __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
         if (v == ANN_PAD) continue;  // uniform
         float s = 0.0f;
         for (int t = lane; t < d; t += 32) {
-            float df = __fsub_rn(load_elem(Xrow, dtype, u * d + t), load_elem(X, dtype, (int64_t)v * d + t));
+            const float df = __fsub_rn(load_elem(Xrow, dtype, u * d + t),
+                                       load_elem(X, dtype, (int64_t)v * d + t));
             s = __fadd_rn(s, __fmul_rn(df, df));
         }
         for (int o = 16; o > 0; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
@@ -568,16 +677,18 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-static int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int Kp, int box_rows) {
+// 2-D tensor map over a [rows x inner] 16-bit matrix with box {box_inner, box_rows}.
+static int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int box_inner,
+                     int box_rows, CUtensorMapSwizzle swz) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return fail(ANN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)G, dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ANN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return ANN_OK;
 }
@@ -602,10 +713,9 @@ int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl) {
     p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : k + 16) : k;
     if (p.kprime < k) p.kprime = k;
     if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
-    // Stages: as many as fit (2 .. MAX_NST).
     const size_t cap = 227 * 1024;
     p.nst = 0;
-    for (int nst = kt::MAX_NST; nst >= 2; --nst) {
+    for (int nst = kt::MAX_NST; nst >= 3; --nst) {
         if (knn_smem_layout(p.nkb_a, nst, p.kprime).total <= cap) { p.nst = nst; break; }
     }
     if (!p.nst)
@@ -624,6 +734,8 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.pad_off = cv.take<int64_t>(C + 1);
     w.probs = cv.take<KnnProblem>(C);
     w.G = cv.take<__nv_bfloat16>((size_t)w.rows_cap * pl.Kp);
+    w.aug = cv.take<__nv_bfloat16>((size_t)w.rows_cap * kt::KAUG);
+    w.ones = cv.take<__nv_bfloat16>((size_t)128 * kt::KAUG);
     w.norms = cv.take<float>((size_t)w.rows_cap + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)rows * pl.kprime) : nullptr;
     w.cand_d = pl.rerank ? cv.take<float>((size_t)rows * pl.kprime) : nullptr;
@@ -631,12 +743,14 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     return cv.used + 256;
 }
 
-static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const void* GB,
-                        int64_t rowsB, const KnnParams& P, int64_t grid, cudaStream_t st) {
-    CUtensorMap ta, tb;
-    int rc = make_tmap(&ta, GA, rowsA, pl.Kp, kt::BM);
-    if (rc) return rc;
-    rc = make_tmap(&tb, GB, rowsB, pl.Kp, kt::BN);
+static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const void* ones,
+                        const void* GB, const void* augB, int64_t rowsB, const KnnParams& P,
+                        int64_t grid, cudaStream_t st) {
+    CUtensorMap ta, tb, taa, tba;
+    int rc = make_tmap(&ta, GA, rowsA, pl.Kp, kt::KB, kt::BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (!rc) rc = make_tmap(&tb, GB, rowsB, pl.Kp, kt::KB, kt::BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (!rc) rc = make_tmap(&taa, ones, 128, kt::KAUG, kt::KAUG, kt::BM, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!rc) rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
     ANN_CHECK_CUDA(cudaFuncSetAttribute(k_knn_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
@@ -647,7 +761,7 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         e1 = tile_event();
         ANN_CHECK_CUDA(cudaEventRecord(e0, st));
     }
-    k_knn_tiles<<<(unsigned)grid, kt::THREADS, pl.smem, st>>>(ta, tb, P);
+    k_knn_tiles<<<(unsigned)grid, kt::THREADS, pl.smem, st>>>(ta, tb, taa, tba, P);
     ANN_CHECK_LAUNCH();
     if (e0) {
         ANN_CHECK_CUDA(cudaEventRecord(e1, st));
@@ -663,11 +777,50 @@ static int launch_rerank(const void* X, const void* Xrow, int dtype, int d, cons
     const unsigned grid = (unsigned)((nrows * 32 + threads - 1) / threads);
     if (nrows == 0) return ANN_OK;
     if (kc <= 64)
-        k_rerank<2><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k, out_id, out_d);
+        k_rerank<2><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
+                                              out_id, out_d);
     else
-        k_rerank<4><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k, out_id, out_d);
+        k_rerank<4><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
+                                              out_id, out_d);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
+}
+
+static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
+                             const KnnProblem* probs, int nprob, const float* na,
+                             const uint32_t* members, int self_exclude, uint32_t* out_id,
+                             float* out_d) {
+    KnnParams P;
+    P.blk_off = blk_off;
+    P.probs = probs;
+    P.nprob = nprob;
+    P.na = na;
+    P.members = members;
+    P.self_exclude = self_exclude;
+    P.mode = pl.mode;
+    P.nkb_a = pl.nkb_a;
+    P.nkb_b = pl.nkb_b;
+    P.kprime = pl.kprime;
+    P.k_out = pl.rerank ? pl.kprime : k;
+    P.nst = pl.nst;
+    P.idesc_neg = idesc_f16(kt::BM, kt::BN, pl.ab_fmt) | (1u << 13);  // negate A
+    P.idesc_aug = idesc_f16(kt::BM, kt::BN, 1);                       // BF16 norm step
+    P.out_id = out_id;
+    P.out_d = out_d;
+    P.status = device_status_ptr();
+    return P;
+}
+
+template <typename T>
+static void launch_gather(const void* X, int dtype, int d, const uint32_t* members,
+                          const int64_t* offsets, const int64_t* pad_off, int C, int64_t rows_cap,
+                          const KnnPlan& pl, void* G, float* norms, __nv_bfloat16* aug,
+                          cudaStream_t st) {
+    const int threads = 256;
+    const int64_t want = (rows_cap * 32 + threads - 1) / threads;
+    const unsigned grid = (unsigned)(want < 152 * 64 ? want : 152 * 64);
+    k_gather<T><<<grid, threads, 0, st>>>(X, dtype, d, members, offsets, pad_off, C, rows_cap,
+                                          pl.mode, pl.Kp, pl.Kh, (T*)G, norms, aug);
 }
 
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
@@ -677,40 +830,19 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     k_shard_tables<<<1, 32, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs,
                                      device_status_ptr());
     ANN_CHECK_LAUNCH();
-    {
-        const int threads = 256;
-        int64_t want = (w.rows_cap * 32 + threads - 1) / threads;
-        unsigned grid = (unsigned)(want < 152 * 64 ? want : 152 * 64);
-        if (pl.ab_fmt == 1)
-            k_gather<__nv_bfloat16><<<grid, threads, 0, st>>>(X, dtype, d, members, offsets, w.pad_off,
-                                                              C, w.rows_cap, pl.mode, pl.Kp, pl.Kh,
-                                                              w.G, w.norms);
-        else
-            k_gather<__half><<<grid, threads, 0, st>>>(X, dtype, d, members, offsets, w.pad_off, C,
-                                                      w.rows_cap, pl.mode, pl.Kp, pl.Kh,
-                                                      (__half*)w.G, w.norms);
-        ANN_CHECK_LAUNCH();
-    }
-    KnnParams P;
-    P.blk_off = w.blk_off;
-    P.probs = w.probs;
-    P.nprob = C;
-    P.nb = w.norms;
-    P.na = w.norms;
-    P.members = members;
-    P.self_exclude = 1;
-    P.mode = pl.mode;
-    P.nkb_a = pl.nkb_a;
-    P.nkb_b = pl.nkb_b;
-    P.kprime = pl.kprime;
-    P.k_out = pl.rerank ? pl.kprime : k;
-    P.nst = pl.nst;
-    P.idesc = idesc_f16(kt::BM, kt::BN, pl.ab_fmt);
-    P.out_id = pl.rerank ? w.cand_id : knn_id;
-    P.out_d = pl.rerank ? w.cand_d : knn_d;
-    P.status = device_status_ptr();
+    k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
+    ANN_CHECK_LAUNCH();
+    if (pl.ab_fmt == 1)
+        launch_gather<__nv_bfloat16>(X, dtype, d, members, offsets, w.pad_off, C, w.rows_cap, pl,
+                                     w.G, w.norms, w.aug, st);
+    else
+        launch_gather<__half>(X, dtype, d, members, offsets, w.pad_off, C, w.rows_cap, pl, w.G,
+                              w.norms, w.aug, st);
+    ANN_CHECK_LAUNCH();
+    KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, members, 1,
+                              pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
     const int64_t grid = rows / kt::BM + C + 1;  // upper bound on row blocks
-    int rc = launch_tiles(pl, w.G, w.rows_cap, w.G, w.rows_cap, P, grid, st);
+    int rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st);
     if (rc) return rc;
     if (pl.rerank)
         return launch_rerank(X, X, dtype, d, members, rows, w.cand_id, pl.kprime, k, knn_id,
@@ -730,6 +862,9 @@ size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* ba
     w.prob = cv.take<KnnProblem>(1);
     w.GA = cv.take<__nv_bfloat16>((size_t)w.capA * pl.Kp);
     w.GB = cv.take<__nv_bfloat16>((size_t)w.capB * pl.Kp);
+    w.augA = cv.take<__nv_bfloat16>((size_t)w.capA * kt::KAUG);
+    w.augB = cv.take<__nv_bfloat16>((size_t)w.capB * kt::KAUG);
+    w.ones = cv.take<__nv_bfloat16>((size_t)128 * kt::KAUG);
     w.na = cv.take<float>((size_t)w.capA + 512);
     w.nb = cv.take<float>((size_t)w.capB + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)nq * pl.kprime) : nullptr;
@@ -743,9 +878,9 @@ __global__ void k_query_tables(int64_t N, int64_t nq, int64_t* blk_off, int64_t*
     if (threadIdx.x || blockIdx.x) return;
     blk_off[0] = 0;
     blk_off[1] = (nq + kt::BM - 1) / kt::BM;
-    offs4[0] = 0;   // A side (queries): offsets {0, nq}, padded {0, nq rounded up}
+    offs4[0] = 0;  // A side (queries): offsets {0, nq}, padded {0, nq rounded up}
     offs4[1] = nq;
-    offs4[2] = 0;   // B side (all vectors): offsets {0, N}
+    offs4[2] = 0;  // B side (all vectors): offsets {0, N}
     offs4[3] = N;
     pad4[0] = 0;
     pad4[1] = blk_off[1] * kt::BM;
@@ -766,49 +901,28 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
                   cudaStream_t st) {
     k_query_tables<<<1, 32, 0, st>>>(N, nq, w.blk_off, w.pad_off, w.offs, w.prob);
     ANN_CHECK_LAUNCH();
-    const int threads = 256;
-    auto grid_for = [&](int64_t rows_cap) {
-        int64_t want = (rows_cap * 32 + threads - 1) / threads;
-        return (unsigned)(want < 152 * 64 ? want : 152 * 64);
-    };
+    k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
+    ANN_CHECK_LAUNCH();
     if (pl.ab_fmt == 1) {
-        k_gather<__nv_bfloat16><<<grid_for(w.capA), threads, 0, st>>>(
-            Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl.mode, pl.Kp, pl.Kh, w.GA, w.na);
-        k_gather<__nv_bfloat16><<<grid_for(w.capB), threads, 0, st>>>(
-            X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB, pl.mode, pl.Kp, pl.Kh, w.GB,
-            w.nb);
+        launch_gather<__nv_bfloat16>(Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl, w.GA,
+                                     w.na, w.augA, st);
+        launch_gather<__nv_bfloat16>(X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB,
+                                     pl, w.GB, w.nb, w.augB, st);
     } else {
-        k_gather<__half><<<grid_for(w.capA), threads, 0, st>>>(
-            Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl.mode, pl.Kp, pl.Kh,
-            (__half*)w.GA, w.na);
-        k_gather<__half><<<grid_for(w.capB), threads, 0, st>>>(
-            X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB, pl.mode, pl.Kp, pl.Kh,
-            (__half*)w.GB, w.nb);
+        launch_gather<__half>(Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl, w.GA, w.na,
+                              w.augA, st);
+        launch_gather<__half>(X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB, pl,
+                              w.GB, w.nb, w.augB, st);
     }
     ANN_CHECK_LAUNCH();
-    KnnParams P;
-    P.blk_off = w.blk_off;
-    P.probs = w.prob;
-    P.nprob = 1;
-    P.nb = w.nb;
-    P.na = w.na;
-    P.members = nullptr;
-    P.self_exclude = 0;
-    P.mode = pl.mode;
-    P.nkb_a = pl.nkb_a;
-    P.nkb_b = pl.nkb_b;
-    P.kprime = pl.kprime;
-    P.k_out = pl.rerank ? pl.kprime : k;
-    P.nst = pl.nst;
-    P.idesc = idesc_f16(kt::BM, kt::BN, pl.ab_fmt);
-    P.out_id = pl.rerank ? w.cand_id : out_id;
-    P.out_d = pl.rerank ? w.cand_d : out_d;
-    P.status = device_status_ptr();
+    KnnParams P = base_params(pl, k, w.blk_off, w.prob, 1, w.na, nullptr, 0,
+                              pl.rerank ? w.cand_id : out_id, pl.rerank ? w.cand_d : out_d);
     const int64_t grid = (nq + kt::BM - 1) / kt::BM;
-    int rc = launch_tiles(pl, w.GA, w.capA, w.GB, w.capB, P, grid, st);
+    int rc = launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st);
     if (rc) return rc;
     if (pl.rerank)
-        return launch_rerank(X, Q, dtype, d, nullptr, nq, w.cand_id, pl.kprime, k, out_id, out_d, st);
+        return launch_rerank(X, Q, dtype, d, nullptr, nq, w.cand_id, pl.kprime, k, out_id, out_d,
+                             st);
     return ANN_OK;
 }
 

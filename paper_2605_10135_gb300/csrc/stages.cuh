@@ -54,8 +54,10 @@ struct KnnWs {
     int64_t* blk_off;
     int64_t* pad_off;
     KnnProblem* probs;
-    __nv_bfloat16* G;   // [rows_cap x Kp] (fp16 bits when ab_fmt == 0)
-    float* norms;       // [rows_cap + 512]
+    __nv_bfloat16* G;     // [rows_cap x Kp] (fp16 bits when ab_fmt == 0)
+    __nv_bfloat16* aug;   // [rows_cap x 16]: |y|^2 / 2 as three BF16 values, then zeros
+    __nv_bfloat16* ones;  // [128 x 16]: 1, 1, 1, then zeros
+    float* norms;         // [rows_cap + 512]
     uint32_t* cand_id;  // [rows x kprime] when re-ranking
     float* cand_d;
     int64_t rows_cap;
@@ -72,6 +74,9 @@ struct QueryWs {
     KnnProblem* prob;
     __nv_bfloat16* GA;
     __nv_bfloat16* GB;
+    __nv_bfloat16* augA;
+    __nv_bfloat16* augB;
+    __nv_bfloat16* ones;
     float* na;
     float* nb;
     uint32_t* cand_id;
