@@ -142,6 +142,9 @@ def main():
     ap.add_argument("--nq", type=int, default=1000)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
+    ap.add_argument("--tile-counters", action="store_true",
+                    help="after timing, run one step with the counting kernel variant and "
+                         "report its per-role cycle counters")
     args = ap.parse_args()
 
     from paper_2605_10135_gb300 import configs
@@ -238,6 +241,14 @@ def main():
     recall = float(ann.recall(ids, gt, 10).item())
     status = ann.device_status()
 
+    counters = None
+    if args.tile_counters:
+        ann.tile_counters_read()
+        ann.tile_counters_enable(True)
+        step(Xd)
+        counters = ann.tile_counters_read()
+        ann.tile_counters_enable(False)
+
     if dist is not None:
         t = torch.tensor([ms, float(np.mean(e2e_ms))], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -298,6 +309,8 @@ def main():
         "gpu_launches": int(launches) * args.steps,
         "clocks": clocks.summary(),
     }
+    if counters is not None:
+        line["tile_counters"] = counters
     if world == 1 and not args.no_baseline:
         v, cores, desc, _ = oracle_sample(w, X)
         line["cpu_baseline"] = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",

@@ -81,6 +81,17 @@ unsigned long long ann_launch_count(void);
 int ann_timing_enable(int on);
 int ann_timing_read(double* tile_ms, int* launches);
 
+/* Profiling hook.  ann_tile_counters_enable(1) switches later distance-tile
+ * launches to a variant that accumulates per-role clock64() cycle counts and
+ * event counts into a device array; ann_tile_counters_read() synchronises the
+ * device, copies up to n counters to host out[] and clears them.  Order:
+ * epilogue cycles, epilogue wait cycles, epilogue flush cycles, chunks, slow
+ * chunks, flushes, flush iterations, heap inserts, appended survivors, MMA
+ * wait-for-data cycles, MMA wait-for-accumulator cycles, producer wait cycles,
+ * CTA cycles, CTAs. */
+int ann_tile_counters_enable(int on);
+int ann_tile_counters_read(unsigned long long* out, int n);
+
 /* Reads (host out) and clears the device status word of the current device:
  * bit 1 = a bounded device wait gave up, bit 2 = inconsistent input found on
  * the device (e.g. offsets[C] != rows), bit 4 = a fixed-capacity buffer

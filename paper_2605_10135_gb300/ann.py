@@ -49,6 +49,8 @@ def lib():
             "ann_launch_count": (ct.c_ulonglong, []),
             "ann_timing_enable": (I32, [I32]),
             "ann_timing_read": (I32, [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int)]),
+            "ann_tile_counters_enable": (I32, [I32]),
+            "ann_tile_counters_read": (I32, [ct.POINTER(ct.c_ulonglong), I32]),
             "ann_device_status": (I32, [ct.POINTER(ct.c_int)]),
             "ann_partition_workspace": (I32, [I64, I32, I32, I32, I64, PSZ]),
             "ann_partition": (I32, [P, I64, I32, I32, I32, I32, P, P, I64, I32, P, P, P, P, SZ, P]),
@@ -122,6 +124,23 @@ def timing_read() -> tuple[float, int]:
     ms, n = ct.c_double(0.0), ct.c_int(0)
     _check(lib().ann_timing_read(ct.byref(ms), ct.byref(n)))
     return ms.value, n.value
+
+
+TILE_COUNTERS = ("epi_cycles", "epi_wait", "epi_flush", "chunks", "slow_chunks", "flushes",
+                 "flush_iters", "inserts", "appends", "mma_wait_full", "mma_wait_acc",
+                 "prod_wait", "cta_cycles", "ctas")
+
+
+def tile_counters_enable(on: bool = True):
+    """Switch the distance-tile kernel to its counting variant (profiling only)."""
+    _check(lib().ann_tile_counters_enable(1 if on else 0))
+
+
+def tile_counters_read() -> dict:
+    """Counters accumulated since the last read (synchronises the device)."""
+    arr = (ct.c_ulonglong * len(TILE_COUNTERS))()
+    _check(lib().ann_tile_counters_read(arr, len(TILE_COUNTERS)))
+    return dict(zip(TILE_COUNTERS, [int(v) for v in arr]))
 
 
 def device_status() -> int:

@@ -43,6 +43,8 @@ static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_tile_events;
 static std::vector<cudaEvent_t> g_event_pool;
 
 bool tile_timing_on() { return g_timing; }
+static bool g_counters = false;
+bool tile_counters_on() { return g_counters; }
 cudaEvent_t tile_event() {
     std::lock_guard<std::mutex> lk(g_timing_mu);
     if (!g_event_pool.empty()) {
@@ -107,6 +109,16 @@ int ann_timing_enable(int on) {
     std::lock_guard<std::mutex> lk(g_timing_mu);
     g_timing = on != 0;
     return ANN_OK;
+}
+
+int ann_tile_counters_enable(int on) {
+    g_counters = on != 0;
+    return ANN_OK;
+}
+
+int ann_tile_counters_read(unsigned long long* out, int n) {
+    ANN_REQUIRE(out && n >= 0, "bad arguments");
+    return tile_counters_read(out, n, true);
 }
 
 int ann_timing_read(double* tile_ms, int* launches) {

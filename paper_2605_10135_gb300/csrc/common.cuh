@@ -41,6 +41,9 @@ struct TileTimer {
 bool tile_timing_on();
 void tile_timing_record(cudaEvent_t a, cudaEvent_t b);
 cudaEvent_t tile_event();
+// Optional cycle/event counters inside the distance-tile kernel (ann_tile_counters_*).
+bool tile_counters_on();
+int tile_counters_read(unsigned long long* out, int n, bool reset);
 
 #define ANN_REQUIRE(cond, ...)                                                     \
     do {                                                                           \

@@ -57,6 +57,26 @@ constexpr int CAP = 32;                 // survivor buffer entries per row
 constexpr int CHUNK = 16;
 }  // namespace kt
 
+// Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
+enum TileCounter {
+    TC_EPI_CYCLES = 0,   // epilogue threads: cycles from first wait to the end of the sweep
+    TC_EPI_WAIT,         // epilogue threads: cycles waiting for a finished accumulator
+    TC_EPI_FLUSH,        // epilogue threads: cycles inside heap flushes
+    TC_CHUNKS,           // warp-level: 16-column chunks examined
+    TC_SLOW_CHUNKS,      // warp-level: chunks where some row had a survivor
+    TC_FLUSHES,          // warp-level: flush calls
+    TC_FLUSH_ITERS,      // warp-level: lockstep insert iterations
+    TC_INSERTS,          // thread-level: heap insertions
+    TC_APPENDS,          // thread-level: buffered survivors
+    TC_MMA_WAIT_FULL,    // MMA thread: cycles waiting for B stages
+    TC_MMA_WAIT_ACC,     // MMA thread: cycles waiting for a free accumulator
+    TC_PROD_WAIT,        // producer: cycles waiting for a free stage
+    TC_CTA_CYCLES,       // thread 0: cycles from start to teardown
+    TC_CTAS,             // CTAs that ran
+    TC_N
+};
+__device__ unsigned long long g_tile_counters[TC_N];
+
 struct KnnParams {
     const int64_t* blk_off;  // [nprob+1] prefix sums of row blocks
     const KnnProblem* probs;
@@ -186,23 +206,38 @@ struct EpiState {
     uint64_t* B;
     int row, kp, cnt;
     float tau;
+    // counters (used only by the profiling instantiation)
+    unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
 };
 
 // Insert every buffered survivor of every row of the warp into its heap.
+template <bool PROF>
 __device__ __forceinline__ void epi_flush(EpiState& s) {
+    long long t0 = 0;
+    if (PROF) t0 = clock64();
     const int mx = __reduce_max_sync(0xffffffffu, s.cnt);
     for (int q = 0; q < mx; ++q) {
         if (q < s.cnt) {
             const uint64_t x = s.B[q * kt::BM + s.row];
-            if (x < s.H[s.row]) heap_replace_root(s.H, s.row, s.kp, x);
+            if (x < s.H[s.row]) {
+                heap_replace_root(s.H, s.row, s.kp, x);
+                if (PROF) ++s.c_ins;
+            }
         }
     }
     s.cnt = 0;
     s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
+    if (PROF) {
+        s.c_flush_cyc += clock64() - t0;
+        ++s.c_flushes;
+        s.c_iters += mx;
+    }
 }
 
+template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], int j0, int i,
                                           int n_cols, int self_exclude) {
+    if (PROF) ++s.c_chunks;
     float key[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) key[u] = __uint_as_float(v[u]);
@@ -220,16 +255,27 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
     const float m4 = min3f(key[12], key[13], key[14]);
     const float m = min3f(min3f(m0, m1, m2), min3f(m3, m4, key[15]), INFINITY);
     if (!__any_sync(0xffffffffu, m < s.tau)) return;
-    if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush(s);
+    if (PROF) ++s.c_slow;
+    if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush<PROF>(s);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         if (key[u] < s.tau) {
             s.B[s.cnt * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | (uint32_t)(j0 + u);
             ++s.cnt;
+            if (PROF) ++s.c_app;
         }
     }
 }
 
+__device__ __forceinline__ void prof_add(int which, unsigned long long v) {
+    if (v) atomicAdd(&g_tile_counters[which], v);
+}
+__device__ __forceinline__ void prof_add_warp(int which, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) prof_add(which, v);
+}
+
+template <bool PROF>
 __global__ void __launch_bounds__(kt::THREADS, 1)
     k_knn_tiles(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmAaug,
@@ -261,6 +307,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     volatile int* abort_flag = (volatile int*)(base + L.abort_flag);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long cta_t0 = 0;
+    if (PROF) cta_t0 = clock64();
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.nst; ++s) {
             mbar_init(full_bar + 8 * s, 1);
@@ -301,10 +349,14 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             int st = 0;
             uint32_t ph = 0;
             bool ok = true;
+            unsigned long long prod_wait = 0;
             for (int t = 0; t < ntiles && ok; ++t) {
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
                 for (int j = 0; j < loads_per_tile; ++j) {
+                    long long w0 = 0;
+                    if (PROF) w0 = clock64();
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
+                    if (PROF) prod_wait += clock64() - w0;
                     const uint32_t dst = sB + st * kt::BLK_BYTES;
                     if (j < P.nkb_b) {
                         mbar_expect_tx(full_bar + 8 * st, kt::BLK_BYTES);
@@ -325,6 +377,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     mbar_wait(full_bar + 8 * s, (last_par >> s) & 1, &dummy, 200000000ull);
             mbar_wait(a_bar, 0, &dummy, 200000000ull);
             if (!ok) atomicOr(P.status, DEV_TIMEOUT);
+            if (PROF) prof_add(TC_PROD_WAIT, prod_wait);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA
@@ -334,17 +387,23 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             int st = 0;
             uint32_t ph = 0;
             const int H2 = P.nkb_b >> 1;
+            unsigned long long w_full = 0, w_acc = 0;
             for (int t = 0; t < ntiles && ok; ++t) {
                 const int a = t % kt::NACC;
+                long long w0 = 0;
+                if (PROF) w0 = clock64();
                 if (!mbar_wait(acce_bar + 8 * a, ((t / kt::NACC) & 1) ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
+                if (PROF) w_acc += clock64() - w0;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + a * kt::BN;
                 uint32_t accum = 0;
                 for (int j = 0; j < loads_per_tile; ++j) {
+                    if (PROF) w0 = clock64();
                     if (!mbar_wait(full_bar + 8 * st, ph, abort_flag)) { ok = false; break; }
+                    if (PROF) w_full += clock64() - w0;
                     tc_fence_after();
                     const uint32_t bsm = sB + st * kt::BLK_BYTES;
                     if (j < P.nkb_b) {
@@ -382,6 +441,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             int dummy = 0;
             mbar_wait(done_bar, 0, &dummy, 200000000ull);
             if (!ok) atomicOr(P.status, DEV_TIMEOUT);
+            if (PROF) {
+                prof_add(TC_MMA_WAIT_FULL, w_full);
+                prof_add(TC_MMA_WAIT_ACC, w_acc);
+            }
         }
     } else {
         // -------------------------------------------------------- epilogue
@@ -393,6 +456,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.kp = P.kprime;
         s.cnt = 0;
         s.tau = INFINITY;
+        s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
+        unsigned long long e_wait = 0;
+        long long e_t0 = 0;
+        if (PROF) e_t0 = clock64();
         const int i = rb * kt::BM + s.row;  // row index inside the problem
         const uint64_t init = heap_init_val();
         for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
@@ -400,7 +467,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
             const int a = t % kt::NACC;
+            long long w0 = 0;
+            if (PROF) w0 = clock64();
             if (!mbar_wait(accf_bar + 8 * a, (t / kt::NACC) & 1, abort_flag)) { ok = false; break; }
+            if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
             const uint32_t tb = tmem + lane_addr + a * kt::BN;
             const int jt = t * kt::BN;
@@ -412,22 +482,35 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 tmem_wait_ld16(va);
                 tmem_ld16(tb + (c + 1) * kt::CHUNK, vb);
                 if (jt + c * kt::CHUNK < pr.n_cols)
-                    epi_chunk(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude);
+                    epi_chunk<PROF>(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude);
                 __syncwarp();
                 tmem_wait_ld16(vb);
                 if (c + 2 < kt::BN / kt::CHUNK) tmem_ld16(tb + (c + 2) * kt::CHUNK, va);
                 if (jt + (c + 1) * kt::CHUNK < pr.n_cols)
-                    epi_chunk(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols, P.self_exclude);
+                    epi_chunk<PROF>(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols, P.self_exclude);
                 __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar + 8 * a);
         }
+        if (PROF) {
+            prof_add_warp(TC_EPI_CYCLES, (unsigned long long)(clock64() - e_t0));
+            prof_add_warp(TC_EPI_WAIT, e_wait);
+            prof_add_warp(TC_EPI_FLUSH, s.c_flush_cyc);
+            prof_add_warp(TC_INSERTS, s.c_ins);
+            prof_add_warp(TC_APPENDS, s.c_app);
+            if (lane == 0) {
+                prof_add(TC_CHUNKS, s.c_chunks);
+                prof_add(TC_SLOW_CHUNKS, s.c_slow);
+                prof_add(TC_FLUSHES, s.c_flushes);
+                prof_add(TC_FLUSH_ITERS, s.c_iters);
+            }
+        }
         if (!ok) {
             atomicOr(P.status, DEV_TIMEOUT);
         } else {
-            epi_flush(s);
+            epi_flush<false>(s);
             if (i < pr.n_rows) {
                 // Heap sort ascending, then write (global id, |x|^2 + 2 key).
                 uint64_t* H = s.H;
@@ -457,6 +540,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PROF && threadIdx.x == 0) {
+        prof_add(TC_CTA_CYCLES, (unsigned long long)(clock64() - cta_t0));
+        prof_add(TC_CTAS, 1);
+    }
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -752,7 +839,9 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
     if (!rc) rc = make_tmap(&taa, ones, 128, kt::KAUG, kt::KAUG, kt::BM, CU_TENSOR_MAP_SWIZZLE_32B);
     if (!rc) rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
-    ANN_CHECK_CUDA(cudaFuncSetAttribute(k_knn_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const bool prof = tile_counters_on();
+    auto kern = prof ? k_knn_tiles<true> : k_knn_tiles<false>;
+    ANN_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
     if (grid <= 0) return ANN_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -761,7 +850,7 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         e1 = tile_event();
         ANN_CHECK_CUDA(cudaEventRecord(e0, st));
     }
-    k_knn_tiles<<<(unsigned)grid, kt::THREADS, pl.smem, st>>>(ta, tb, taa, tba, P);
+    kern<<<(unsigned)grid, kt::THREADS, pl.smem, st>>>(ta, tb, taa, tba, P);
     ANN_CHECK_LAUNCH();
     if (e0) {
         ANN_CHECK_CUDA(cudaEventRecord(e1, st));
@@ -923,6 +1012,18 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     if (pl.rerank)
         return launch_rerank(X, Q, dtype, d, nullptr, nq, w.cand_id, pl.kprime, k, out_id, out_d,
                              st);
+    return ANN_OK;
+}
+
+int tile_counters_read(unsigned long long* out, int n, bool reset) {
+    unsigned long long tmp[TC_N];
+    ANN_CHECK_CUDA(cudaDeviceSynchronize());
+    ANN_CHECK_CUDA(cudaMemcpyFromSymbol(tmp, g_tile_counters, sizeof(tmp)));
+    for (int i = 0; i < n && i < TC_N; ++i) out[i] = tmp[i];
+    if (reset) {
+        unsigned long long z[TC_N] = {0};
+        ANN_CHECK_CUDA(cudaMemcpyToSymbol(g_tile_counters, z, sizeof(z)));
+    }
     return ANN_OK;
 }
 
