@@ -128,7 +128,7 @@ def timing_read() -> tuple[float, int]:
 
 TILE_COUNTERS = ("epi_cycles", "epi_wait", "epi_flush", "chunks", "slow_chunks", "flushes",
                  "flush_iters", "inserts", "appends", "mma_wait_full", "mma_wait_acc",
-                 "prod_wait", "cta_cycles", "ctas")
+                 "prod_wait", "cta_cycles", "ctas", "ld_wait", "filter", "append")
 
 
 def tile_counters_enable(on: bool = True):

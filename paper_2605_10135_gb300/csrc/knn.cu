@@ -73,6 +73,9 @@ enum TileCounter {
     TC_PROD_WAIT,        // producer: cycles waiting for a free stage
     TC_CTA_CYCLES,       // thread 0: cycles from start to teardown
     TC_CTAS,             // CTAs that ran
+    TC_LD_WAIT,          // epilogue threads: cycles blocked in tcgen05.wait::ld
+    TC_FILTER,           // epilogue threads: cycles in the chunk filter (min + vote)
+    TC_APPEND,           // epilogue threads: cycles appending survivors (incl. flush)
     TC_N
 };
 __device__ unsigned long long g_tile_counters[TC_N];
@@ -208,6 +211,7 @@ struct EpiState {
     float tau;
     // counters (used only by the profiling instantiation)
     unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
+    unsigned long long c_ldw, c_filter, c_append;
 };
 
 // Insert every buffered survivor of every row of the warp into its heap.
@@ -237,7 +241,11 @@ __device__ __forceinline__ void epi_flush(EpiState& s) {
 template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], int j0, int i,
                                           int n_cols, int self_exclude) {
-    if (PROF) ++s.c_chunks;
+    long long f0 = 0;
+    if (PROF) {
+        ++s.c_chunks;
+        f0 = clock64();
+    }
     float key[16];
 #pragma unroll
     for (int u = 0; u < 16; ++u) key[u] = __uint_as_float(v[u]);
@@ -254,7 +262,13 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
     const float m3 = min3f(key[9], key[10], key[11]);
     const float m4 = min3f(key[12], key[13], key[14]);
     const float m = min3f(min3f(m0, m1, m2), min3f(m3, m4, key[15]), INFINITY);
-    if (!__any_sync(0xffffffffu, m < s.tau)) return;
+    const bool any = __any_sync(0xffffffffu, m < s.tau);
+    if (PROF) {
+        const long long f1 = clock64();
+        s.c_filter += f1 - f0;
+        f0 = f1;
+    }
+    if (!any) return;
     if (PROF) ++s.c_slow;
     if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush<PROF>(s);
 #pragma unroll
@@ -265,6 +279,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
             if (PROF) ++s.c_app;
         }
     }
+    if (PROF) s.c_append += clock64() - f0;
 }
 
 __device__ __forceinline__ void prof_add(int which, unsigned long long v) {
@@ -457,6 +472,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.cnt = 0;
         s.tau = INFINITY;
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
+        s.c_ldw = s.c_filter = s.c_append = 0;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
@@ -479,12 +495,17 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             tmem_ld16(tb, va);
 #pragma unroll
             for (int c = 0; c < kt::BN / kt::CHUNK; c += 2) {
+                long long l0 = 0;
+                if (PROF) l0 = clock64();
                 tmem_wait_ld16(va);
+                if (PROF) s.c_ldw += clock64() - l0;
                 tmem_ld16(tb + (c + 1) * kt::CHUNK, vb);
                 if (jt + c * kt::CHUNK < pr.n_cols)
                     epi_chunk<PROF>(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude);
                 __syncwarp();
+                if (PROF) l0 = clock64();
                 tmem_wait_ld16(vb);
+                if (PROF) s.c_ldw += clock64() - l0;
                 if (c + 2 < kt::BN / kt::CHUNK) tmem_ld16(tb + (c + 2) * kt::CHUNK, va);
                 if (jt + (c + 1) * kt::CHUNK < pr.n_cols)
                     epi_chunk<PROF>(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols, P.self_exclude);
@@ -500,6 +521,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             prof_add_warp(TC_EPI_FLUSH, s.c_flush_cyc);
             prof_add_warp(TC_INSERTS, s.c_ins);
             prof_add_warp(TC_APPENDS, s.c_app);
+            prof_add_warp(TC_LD_WAIT, s.c_ldw);
+            prof_add_warp(TC_FILTER, s.c_filter);
+            prof_add_warp(TC_APPEND, s.c_append);
             if (lane == 0) {
                 prof_add(TC_CHUNKS, s.c_chunks);
                 prof_add(TC_SLOW_CHUNKS, s.c_slow);
