@@ -55,6 +55,7 @@ constexpr uint32_t TMEM_COLS = NACC * BN;
 constexpr int MAX_NST = 8;
 constexpr int CAP = 32;                 // survivor buffer entries per row
 constexpr int CHUNK = 16;
+constexpr int CELL = 1024;              // rows per pivot cell
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -85,8 +86,10 @@ struct KnnParams {
     const KnnProblem* probs;
     int nprob;
     const float* na;          // |x|^2 per A row
-    const uint32_t* members;  // column -> global id (NULL: identity)
+    const uint32_t* gid;      // global id per B row (NULL: the column index itself)
+    const int64_t* outrow;    // output row per A row (NULL: out_row0 + row index)
     int self_exclude;
+    int local_first;          // sweep the columns near the row block first
     int mode;      // 0 plain, 1 split
     int nkb_a;     // resident A k-blocks
     int nkb_b;     // B k-blocks per tile
@@ -238,9 +241,12 @@ __device__ __forceinline__ void epi_flush(EpiState& s) {
     }
 }
 
+// One 16-column chunk: keys come straight from TMEM; masked columns become NaN
+// (every comparison with NaN is false, and the 3-input minimum skips NaN).
 template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], int j0, int i,
-                                          int n_cols, int self_exclude) {
+                                          int n_cols, int self_exclude,
+                                          const uint32_t* __restrict__ gidrow) {
     long long f0 = 0;
     if (PROF) {
         ++s.c_chunks;
@@ -253,7 +259,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int j = j0 + u;
-            if (j >= n_cols || (self_exclude && j == i)) key[u] = INFINITY;
+            if (j >= n_cols || (self_exclude && j == i)) key[u] = __uint_as_float(0x7fc00000u);
         }
     }
     const float m0 = min3f(key[0], key[1], key[2]);
@@ -262,7 +268,8 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
     const float m3 = min3f(key[9], key[10], key[11]);
     const float m4 = min3f(key[12], key[13], key[14]);
     const float m = min3f(min3f(m0, m1, m2), min3f(m3, m4, key[15]), INFINITY);
-    const bool any = __any_sync(0xffffffffu, m < s.tau);
+    // "<=": a key equal to the current k-th may still win on the global id
+    const bool any = __any_sync(0xffffffffu, m <= s.tau);
     if (PROF) {
         const long long f1 = clock64();
         s.c_filter += f1 - f0;
@@ -271,10 +278,15 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
     if (!any) return;
     if (PROF) ++s.c_slow;
     if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush<PROF>(s);
+    // global ids of the chunk's 16 columns: one coalesced load, then broadcasts
+    const int lane = threadIdx.x & 31;
+    uint32_t g_l = (uint32_t)(j0 + lane);
+    if (gidrow && lane < 16 && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
-        if (key[u] < s.tau) {
-            s.B[s.cnt * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | (uint32_t)(j0 + u);
+        const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
+        if (key[u] <= s.tau) {
+            s.B[s.cnt * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
             ++s.cnt;
             if (PROF) ++s.c_app;
         }
@@ -307,6 +319,15 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     const KnnProblem pr = P.probs[lo];
     const int rb = (int)(bid - P.blk_off[lo]);
     const int ntiles = (pr.n_cols + kt::BN - 1) / kt::BN;
+    // Sweep order: tile t0, t0+1, ... wrapping around.  With local_first the sweep
+    // starts a few tiles before the block's own rows (rows are ordered by cell),
+    // so each row's k-th key tightens early.
+    int t0 = 0;
+    if (P.local_first) {
+        t0 = (rb * kt::BM) / kt::BN - 4;
+        if (t0 < 0) t0 = 0;
+        if (t0 >= ntiles) t0 = 0;
+    }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const KnnSmemLayout L = knn_smem_layout(P.nkb_a, P.nst, P.kprime);
@@ -365,7 +386,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             unsigned long long prod_wait = 0;
-            for (int t = 0; t < ntiles && ok; ++t) {
+            for (int tt = 0; tt < ntiles && ok; ++tt) {
+                const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
                 for (int j = 0; j < loads_per_tile; ++j) {
                     long long w0 = 0;
@@ -481,11 +503,13 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
-        for (int t = 0; t < ntiles; ++t) {
-            const int a = t % kt::NACC;
+        const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
+        for (int tt = 0; tt < ntiles; ++tt) {
+            const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
+            const int a = tt % kt::NACC;
             long long w0 = 0;
             if (PROF) w0 = clock64();
-            if (!mbar_wait(accf_bar + 8 * a, (t / kt::NACC) & 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
             const uint32_t tb = tmem + lane_addr + a * kt::BN;
@@ -501,14 +525,16 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 if (PROF) s.c_ldw += clock64() - l0;
                 tmem_ld16(tb + (c + 1) * kt::CHUNK, vb);
                 if (jt + c * kt::CHUNK < pr.n_cols)
-                    epi_chunk<PROF>(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude);
+                    epi_chunk<PROF>(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude,
+                                    gidrow);
                 __syncwarp();
                 if (PROF) l0 = clock64();
                 tmem_wait_ld16(vb);
                 if (PROF) s.c_ldw += clock64() - l0;
                 if (c + 2 < kt::BN / kt::CHUNK) tmem_ld16(tb + (c + 2) * kt::CHUNK, va);
                 if (jt + (c + 1) * kt::CHUNK < pr.n_cols)
-                    epi_chunk<PROF>(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols, P.self_exclude);
+                    epi_chunk<PROF>(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols,
+                                    P.self_exclude, gidrow);
                 __syncwarp();
             }
             tc_fence_before();
@@ -546,14 +572,14 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     heap_sift(H, row, 0, end);
                 }
                 const float nx = P.na[pr.a_row0 + i];
-                const int64_t orow = pr.out_row0 + i;
+                const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
                 for (int e = 0; e < P.k_out; ++e) {
                     const uint64_t x = H[e * kt::BM + row];
-                    const uint32_t j = (uint32_t)x;
+                    const uint32_t g = (uint32_t)x;  // global id (or column index)
                     uint32_t id = ANN_PAD;
                     float dd = INFINITY;
-                    if (j != 0xFFFFFFFFu) {
-                        id = P.members ? __ldg(P.members + pr.mem_row0 + j) : j;
+                    if (g != 0xFFFFFFFFu) {
+                        id = g;
                         dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
                     }
                     P.out_id[orow * P.k_out + e] = id;
@@ -619,32 +645,19 @@ template <>
 __device__ __forceinline__ __half cvt_from_float(float v) { return __float2half_rn(v); }
 
 // Gather rows into the tile layout: row p' of G (pitch Kp elements) holds the
-// operand copy of member (pad_off -> shard, local index) or zeros; norms[p'] =
-// |x|^2 and aug[p'] = |x|^2 / 2 split exactly into three BF16 values (hi, mid,
-// lo) followed by zeros.
+// operand copy of vector src[p'] (zeros when src[p'] < 0); norms[p'] = |x|^2
+// and aug[p'] = |x|^2 / 2 split exactly into three BF16 values (hi, mid, lo)
+// followed by zeros.
 // mode 0: element t = cvt(x_t).  mode 1: [hi | lo] sections of Kh elements.
 template <typename T>
-__global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __restrict__ members,
-                         const int64_t* __restrict__ offsets, const int64_t* __restrict__ pad_off,
-                         int C, int64_t rows_cap, int mode, int Kp, int Kh, T* __restrict__ G,
+__global__ void k_gather(const void* X, int dtype, int d, const int64_t* __restrict__ srcrow,
+                         int64_t rows_cap, int mode, int Kp, int Kh, T* __restrict__ G,
                          float* __restrict__ norms, __nv_bfloat16* __restrict__ aug) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t pr = warp_g; pr < rows_cap; pr += nwarps) {
-        int64_t src = -1;
-        if (pr < pad_off[C]) {
-            int lo = 0, hi = C - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (pad_off[mid] <= pr) lo = mid; else hi = mid - 1;
-            }
-            const int64_t li = pr - pad_off[lo];
-            if (li < offsets[lo + 1] - offsets[lo]) {
-                const int64_t p = offsets[lo] + li;
-                src = members ? (int64_t)members[p] : p;
-            }
-        }
+        const int64_t src = srcrow[pr];
         T* g = G + pr * Kp;
         float nrm = 0.0f;
         for (int t = lane; t < Kp; t += 32) {
@@ -685,6 +698,143 @@ __global__ void k_gather(const void* X, int dtype, int d, const uint32_t* __rest
             if (lane == 2) o = l;
             aug[pr * kt::KAUG + lane] = o;
         }
+    }
+}
+
+// ---- row maps: which vector each gathered row holds ----------------------------
+__device__ __forceinline__ int shard_of_padded(const int64_t* __restrict__ pad_off, int C,
+                                               int64_t pr) {
+    int lo = 0, hi = C - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pad_off[mid] <= pr) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Shard order as given: row pad_off[s] + li holds member offsets[s] + li.
+__global__ void k_rowmap_plain(const uint32_t* __restrict__ members,
+                               const int64_t* __restrict__ offsets,
+                               const int64_t* __restrict__ pad_off, int C, int64_t rows_cap,
+                               int64_t* __restrict__ src) {
+    for (int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pr < rows_cap;
+         pr += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = -1;
+        if (pr < pad_off[C]) {
+            const int s = shard_of_padded(pad_off, C, pr);
+            const int64_t li = pr - pad_off[s];
+            if (li < offsets[s + 1] - offsets[s]) {
+                const int64_t p = offsets[s] + li;
+                v = members ? (int64_t)members[p] : p;
+            }
+        }
+        src[pr] = v;
+    }
+}
+
+// Pivots of every shard: P_s = ceil(n_s / cell) evenly spaced members (cells of
+// about `cell` rows).  Tables for the pivot-assignment launch: A = the shard's
+// rows, B = its pivots.
+__global__ void k_pivot_tables(const int64_t* __restrict__ offsets, int C, int cell,
+                               const int64_t* __restrict__ pad_off, int64_t* __restrict__ ppad_off,
+                               int32_t* __restrict__ npiv, KnnProblem* __restrict__ pprobs) {
+    if (threadIdx.x || blockIdx.x) return;
+    int64_t p = 0;
+    for (int s = 0; s < C; ++s) {
+        int64_t n = offsets[s + 1] - offsets[s];
+        if (n < 0) n = 0;
+        int64_t P = (n + cell - 1) / cell;
+        if (P < 1) P = 1;
+        if (P > 1024) P = 1024;
+        npiv[s] = (int32_t)P;
+        ppad_off[s] = p;
+        KnnProblem pr;
+        pr.a_row0 = pad_off[s];
+        pr.b_row0 = p;
+        pr.out_row0 = offsets[s];
+        pr.mem_row0 = 0;
+        pr.n_rows = (int32_t)n;
+        pr.n_cols = n > 0 ? (int32_t)P : 0;
+        pprobs[s] = pr;
+        p += (P + kt::BM - 1) / kt::BM * kt::BM;
+    }
+    ppad_off[C] = p;
+}
+
+__global__ void k_rowmap_pivots(const uint32_t* __restrict__ members,
+                                const int64_t* __restrict__ offsets,
+                                const int64_t* __restrict__ ppad_off,
+                                const int32_t* __restrict__ npiv, int C, int64_t rows_cap,
+                                int64_t* __restrict__ src) {
+    for (int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pr < rows_cap;
+         pr += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = -1;
+        if (pr < ppad_off[C]) {
+            const int s = shard_of_padded(ppad_off, C, pr);
+            const int64_t q = pr - ppad_off[s];
+            const int64_t n = offsets[s + 1] - offsets[s];
+            if (q < npiv[s] && n > 0) v = (int64_t)members[offsets[s] + q * n / npiv[s]];
+        }
+        src[pr] = v;
+    }
+}
+
+// Counting sort of each shard's rows by cell (the nearest pivot): perm[off_s + pos]
+// = local index.  The order inside a cell does not affect any result.
+__global__ void k_cell_sort(const uint32_t* __restrict__ cellid,
+                            const int64_t* __restrict__ offsets, const int32_t* __restrict__ npiv,
+                            uint32_t* __restrict__ perm) {
+    __shared__ int32_t cnt[1024];
+    __shared__ int32_t base[1024];
+    const int s = blockIdx.x;
+    const int64_t o = offsets[s], n = offsets[s + 1] - o;
+    const int P = npiv[s];
+    for (int c = threadIdx.x; c < P; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        uint32_t c = cellid[o + i];
+        if (c >= (uint32_t)P) c = 0;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int c = 0; c < P; ++c) {
+            base[c] = acc;
+            acc += cnt[c];
+        }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        uint32_t c = cellid[o + i];
+        if (c >= (uint32_t)P) c = 0;
+        const int32_t pos = atomicAdd(&base[c], 1);
+        perm[o + pos] = (uint32_t)i;
+    }
+}
+
+// Cell order: row pad_off[s] + pos holds member offsets[s] + perm[...]; also the
+// global id of each row and the output row it belongs to.
+__global__ void k_rowmap_cells(const uint32_t* __restrict__ members,
+                               const int64_t* __restrict__ offsets,
+                               const int64_t* __restrict__ pad_off,
+                               const uint32_t* __restrict__ perm, int C, int64_t rows_cap,
+                               int64_t* __restrict__ src, uint32_t* __restrict__ gid,
+                               int64_t* __restrict__ outrow) {
+    for (int64_t pr = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pr < rows_cap;
+         pr += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = -1, orow = -1;
+        if (pr < pad_off[C]) {
+            const int s = shard_of_padded(pad_off, C, pr);
+            const int64_t pos = pr - pad_off[s];
+            if (pos < offsets[s + 1] - offsets[s]) {
+                orow = offsets[s] + perm[offsets[s] + pos];
+                v = (int64_t)members[orow];
+            }
+        }
+        src[pr] = v;
+        gid[pr] = v >= 0 ? (uint32_t)v : ANN_PAD;
+        outrow[pr] = orow;
     }
 }
 
@@ -850,26 +1000,40 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.norms = cv.take<float>((size_t)w.rows_cap + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)rows * pl.kprime) : nullptr;
     w.cand_d = pl.rerank ? cv.take<float>((size_t)rows * pl.kprime) : nullptr;
+    w.src = cv.take<int64_t>((size_t)w.rows_cap);
+    w.gid = cv.take<uint32_t>((size_t)w.rows_cap);
+    w.outrow = cv.take<int64_t>((size_t)w.rows_cap);
+    w.prows_cap = rows / kt::CELL + (int64_t)(kt::BM + 1) * C + kt::BN;
+    w.ppad_off = cv.take<int64_t>(C + 1);
+    w.npiv = cv.take<int32_t>(C);
+    w.pprobs = cv.take<KnnProblem>(C);
+    w.psrc = cv.take<int64_t>((size_t)w.prows_cap);
+    w.GP = cv.take<__nv_bfloat16>((size_t)w.prows_cap * pl.Kp);
+    w.paug = cv.take<__nv_bfloat16>((size_t)w.prows_cap * kt::KAUG);
+    w.pnorms = cv.take<float>((size_t)w.prows_cap + 512);
+    w.cell = cv.take<uint32_t>((size_t)rows);
+    w.cell_d = cv.take<float>((size_t)rows);
+    w.perm = cv.take<uint32_t>((size_t)rows);
     if (out) *out = w;
     return cv.used + 256;
 }
 
 static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const void* ones,
                         const void* GB, const void* augB, int64_t rowsB, const KnnParams& P,
-                        int64_t grid, cudaStream_t st) {
+                        int64_t grid, cudaStream_t st, bool timed) {
     CUtensorMap ta, tb, taa, tba;
     int rc = make_tmap(&ta, GA, rowsA, pl.Kp, kt::KB, kt::BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = make_tmap(&tb, GB, rowsB, pl.Kp, kt::KB, kt::BN, CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = make_tmap(&taa, ones, 128, kt::KAUG, kt::KAUG, kt::BM, CU_TENSOR_MAP_SWIZZLE_32B);
     if (!rc) rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
-    const bool prof = tile_counters_on();
+    const bool prof = timed && tile_counters_on();
     auto kern = prof ? k_knn_tiles<true> : k_knn_tiles<false>;
     ANN_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
     if (grid <= 0) return ANN_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (tile_timing_on()) {
+    if (timed && tile_timing_on()) {
         e0 = tile_event();
         e1 = tile_event();
         ANN_CHECK_CUDA(cudaEventRecord(e0, st));
@@ -901,15 +1065,17 @@ static int launch_rerank(const void* X, const void* Xrow, int dtype, int d, cons
 
 static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
                              const KnnProblem* probs, int nprob, const float* na,
-                             const uint32_t* members, int self_exclude, uint32_t* out_id,
-                             float* out_d) {
+                             const uint32_t* gid, const int64_t* outrow, int self_exclude,
+                             int local_first, uint32_t* out_id, float* out_d) {
     KnnParams P;
     P.blk_off = blk_off;
     P.probs = probs;
     P.nprob = nprob;
     P.na = na;
-    P.members = members;
+    P.gid = gid;
+    P.outrow = outrow;
     P.self_exclude = self_exclude;
+    P.local_first = local_first;
     P.mode = pl.mode;
     P.nkb_a = pl.nkb_a;
     P.nkb_b = pl.nkb_b;
@@ -924,38 +1090,77 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     return P;
 }
 
-template <typename T>
-static void launch_gather(const void* X, int dtype, int d, const uint32_t* members,
-                          const int64_t* offsets, const int64_t* pad_off, int C, int64_t rows_cap,
-                          const KnnPlan& pl, void* G, float* norms, __nv_bfloat16* aug,
-                          cudaStream_t st) {
+static int launch_gather(const void* X, int dtype, int d, const int64_t* src, int64_t rows_cap,
+                         const KnnPlan& pl, void* G, float* norms, __nv_bfloat16* aug,
+                         cudaStream_t st) {
     const int threads = 256;
     const int64_t want = (rows_cap * 32 + threads - 1) / threads;
     const unsigned grid = (unsigned)(want < 152 * 64 ? want : 152 * 64);
-    k_gather<T><<<grid, threads, 0, st>>>(X, dtype, d, members, offsets, pad_off, C, rows_cap,
-                                          pl.mode, pl.Kp, pl.Kh, (T*)G, norms, aug);
+    if (pl.ab_fmt == 1)
+        k_gather<__nv_bfloat16><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode,
+                                                          pl.Kp, pl.Kh, (__nv_bfloat16*)G, norms,
+                                                          aug);
+    else
+        k_gather<__half><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode, pl.Kp,
+                                                  pl.Kh, (__half*)G, norms, aug);
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
 }
 
+static unsigned grid_rows(int64_t rows, int threads) {
+    const int64_t want = (rows + threads - 1) / threads;
+    return (unsigned)(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
+}
+
+// Rows of a shard are first grouped into cells around evenly spaced pivot
+// members (the pivot assignment is itself a k = 1 launch of the tile kernel), so
+// that each row block sweeps its own cell first; results do not depend on the
+// order (ties are broken by global id), only the amount of top-k work does.
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
                   const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st) {
     (void)N;
-    k_shard_tables<<<1, 32, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs,
-                                     device_status_ptr());
+    int* status = device_status_ptr();
+    k_shard_tables<<<1, 32, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs, status);
     ANN_CHECK_LAUNCH();
     k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
     ANN_CHECK_LAUNCH();
-    if (pl.ab_fmt == 1)
-        launch_gather<__nv_bfloat16>(X, dtype, d, members, offsets, w.pad_off, C, w.rows_cap, pl,
-                                     w.G, w.norms, w.aug, st);
-    else
-        launch_gather<__half>(X, dtype, d, members, offsets, w.pad_off, C, w.rows_cap, pl, w.G,
-                              w.norms, w.aug, st);
+    int rc;
+    // 1. pivots and the cell of every row
+    KnnPlan pp = pl;
+    pp.kprime = 1;
+    pp.rerank = false;
+    pp.smem = knn_smem_layout(pp.nkb_a, pp.nst, 1).total;
+    k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, kt::CELL, w.pad_off, w.ppad_off, w.npiv, w.pprobs);
     ANN_CHECK_LAUNCH();
-    KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, members, 1,
+    k_rowmap_plain<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, C,
+                                                               w.rows_cap, w.src);
+    ANN_CHECK_LAUNCH();
+    k_rowmap_pivots<<<grid_rows(w.prows_cap, 256), 256, 0, st>>>(members, offsets, w.ppad_off,
+                                                                 w.npiv, C, w.prows_cap, w.psrc);
+    ANN_CHECK_LAUNCH();
+    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, st))) return rc;
+    if ((rc = launch_gather(X, dtype, d, w.psrc, w.prows_cap, pl, w.GP, w.pnorms, w.paug, st)))
+        return rc;
+    KnnParams PP = base_params(pp, 1, w.blk_off, w.pprobs, C, w.norms, nullptr, nullptr, 0, 0,
+                               w.cell, w.cell_d);
+    PP.k_out = 1;
+    rc = launch_tiles(pp, w.G, w.rows_cap, w.ones, w.GP, w.paug, w.prows_cap, PP,
+                      rows / kt::BM + C + 1, st, false);
+    if (rc) return rc;
+    // 2. cell order
+    k_cell_sort<<<C, 512, 0, st>>>(w.cell, offsets, w.npiv, w.perm);
+    ANN_CHECK_LAUNCH();
+    k_rowmap_cells<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, w.perm,
+                                                               C, w.rows_cap, w.src, w.gid,
+                                                               w.outrow);
+    ANN_CHECK_LAUNCH();
+    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, st))) return rc;
+    // 3. the kNN sweep
+    KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
-    const int64_t grid = rows / kt::BM + C + 1;  // upper bound on row blocks
-    int rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st);
+    rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P,
+                      rows / kt::BM + C + 1, st, true);
     if (rc) return rc;
     if (pl.rerank)
         return launch_rerank(X, X, dtype, d, members, rows, w.cand_id, pl.kprime, k, knn_id,
@@ -982,6 +1187,8 @@ size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* ba
     w.nb = cv.take<float>((size_t)w.capB + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)nq * pl.kprime) : nullptr;
     w.cand_d = pl.rerank ? cv.take<float>((size_t)nq * pl.kprime) : nullptr;
+    w.srcA = cv.take<int64_t>((size_t)w.capA);
+    w.srcB = cv.take<int64_t>((size_t)w.capB);
     if (out) *out = w;
     return cv.used + 256;
 }
@@ -1016,22 +1223,19 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     ANN_CHECK_LAUNCH();
     k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
     ANN_CHECK_LAUNCH();
-    if (pl.ab_fmt == 1) {
-        launch_gather<__nv_bfloat16>(Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl, w.GA,
-                                     w.na, w.augA, st);
-        launch_gather<__nv_bfloat16>(X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB,
-                                     pl, w.GB, w.nb, w.augB, st);
-    } else {
-        launch_gather<__half>(Q, dtype, d, nullptr, w.offs, w.pad_off, 1, w.capA, pl, w.GA, w.na,
-                              w.augA, st);
-        launch_gather<__half>(X, dtype, d, nullptr, w.offs + 2, w.pad_off + 2, 1, w.capB, pl,
-                              w.GB, w.nb, w.augB, st);
-    }
+    k_rowmap_plain<<<grid_rows(w.capA, 256), 256, 0, st>>>(nullptr, w.offs, w.pad_off, 1, w.capA,
+                                                           w.srcA);
     ANN_CHECK_LAUNCH();
-    KnnParams P = base_params(pl, k, w.blk_off, w.prob, 1, w.na, nullptr, 0,
+    k_rowmap_plain<<<grid_rows(w.capB, 256), 256, 0, st>>>(nullptr, w.offs + 2, w.pad_off + 2, 1,
+                                                           w.capB, w.srcB);
+    ANN_CHECK_LAUNCH();
+    int rc = launch_gather(Q, dtype, d, w.srcA, w.capA, pl, w.GA, w.na, w.augA, st);
+    if (!rc) rc = launch_gather(X, dtype, d, w.srcB, w.capB, pl, w.GB, w.nb, w.augB, st);
+    if (rc) return rc;
+    KnnParams P = base_params(pl, k, w.blk_off, w.prob, 1, w.na, nullptr, nullptr, 0, 0,
                               pl.rerank ? w.cand_id : out_id, pl.rerank ? w.cand_d : out_d);
     const int64_t grid = (nq + kt::BM - 1) / kt::BM;
-    int rc = launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st);
+    rc = launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st, true);
     if (rc) return rc;
     if (pl.rerank)
         return launch_rerank(X, Q, dtype, d, nullptr, nq, w.cand_id, pl.kprime, k, out_id, out_d,

@@ -61,6 +61,21 @@ struct KnnWs {
     uint32_t* cand_id;  // [rows x kprime] when re-ranking
     float* cand_d;
     int64_t rows_cap;
+    // cell ordering
+    int64_t* src;       // [rows_cap] vector held by each gathered row (-1: padding)
+    uint32_t* gid;      // [rows_cap] its global id
+    int64_t* outrow;    // [rows_cap] the output row it belongs to
+    int64_t prows_cap;  // pivot rows (padded per shard)
+    int64_t* ppad_off;  // [C+1]
+    int32_t* npiv;      // [C]
+    KnnProblem* pprobs; // [C]
+    int64_t* psrc;      // [prows_cap]
+    __nv_bfloat16* GP;  // [prows_cap x Kp]
+    __nv_bfloat16* paug;
+    float* pnorms;
+    uint32_t* cell;     // [rows] nearest pivot of each member row
+    float* cell_d;
+    uint32_t* perm;     // [rows] local index of the row at each cell-ordered position
 };
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
@@ -82,6 +97,8 @@ struct QueryWs {
     uint32_t* cand_id;
     float* cand_d;
     int64_t capA, capB;
+    int64_t* srcA;
+    int64_t* srcB;
 };
 size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* base, size_t cap);
 int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,
