@@ -50,11 +50,11 @@ constexpr int KAUG = 16;                // norm block: 16 elements (32 bytes)
 constexpr int BLK_BYTES = 128 * 128;    // one K block of 128 rows (A or B)
 constexpr int AUG_BYTES = 128 * 32;     // one norm block of 128 rows
 constexpr int NACC = 4;
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;             // two warps per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BN;
 constexpr int MAX_NST = 8;
 constexpr int CAP = 32;                 // survivor buffer entries per row
-constexpr int CHUNK = 16;
 constexpr int CELL = 1024;              // rows per pivot cell
 }  // namespace kt
 
@@ -103,7 +103,7 @@ struct KnnParams {
 };
 
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, heap, buf, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, heap, buf, cnt, locks, bars, tmem_slot, abort_flag, total;
 };
 
 __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int kprime) {
@@ -119,6 +119,10 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     o += kprime * kt::BM * 8;
     L.buf = o;
     o += kt::CAP * kt::BM * 8;
+    L.cnt = o;
+    o += kt::BM * 4;
+    L.locks = o;
+    o += 4 * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -191,6 +195,18 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -207,24 +223,55 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     return d;
 }
 
+// Per-row top-k state shared by the two epilogue warps of a TMEM lane quarter:
+// max-heap H (kp entries), survivor buffer B (CAP entries) and its fill count,
+// guarded by one lock per quarter.  Each thread keeps a private copy of the
+// row's k-th key (tau), refreshed whenever it holds the lock; a stale copy only
+// lets more columns through to the exact check.
 struct EpiState {
     uint64_t* H;
     uint64_t* B;
-    int row, kp, cnt;
+    int* cnt;
+    int* lock;
+    volatile int* abort;
+    int row, kp;
     float tau;
     // counters (used only by the profiling instantiation)
     unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
     unsigned long long c_ldw, c_filter, c_append;
 };
 
-// Insert every buffered survivor of every row of the warp into its heap.
+__device__ __forceinline__ void quarter_lock(EpiState& s) {
+    if ((threadIdx.x & 31) == 0) {
+        const uint64_t t0 = globaltimer();
+        for (uint32_t it = 0;; ++it) {
+            if (atomicCAS(s.lock, 0, 1) == 0) break;
+            if ((it & 255u) == 255u && globaltimer() - t0 > 1000000000ull) {
+                *s.abort = 1;  // cannot happen unless a holder died; give up the lock
+                break;
+            }
+        }
+        __threadfence_block();
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void quarter_unlock(EpiState& s) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        atomicExch(s.lock, 0);
+    }
+}
+
+// Insert every buffered survivor of the warp's 32 rows into their heaps (lock held).
 template <bool PROF>
-__device__ __forceinline__ void epi_flush(EpiState& s) {
+__device__ __forceinline__ int epi_flush(EpiState& s, int c) {
     long long t0 = 0;
     if (PROF) t0 = clock64();
-    const int mx = __reduce_max_sync(0xffffffffu, s.cnt);
+    const int mx = __reduce_max_sync(0xffffffffu, c);
     for (int q = 0; q < mx; ++q) {
-        if (q < s.cnt) {
+        if (q < c) {
             const uint64_t x = s.B[q * kt::BM + s.row];
             if (x < s.H[s.row]) {
                 heap_replace_root(s.H, s.row, s.kp, x);
@@ -232,42 +279,47 @@ __device__ __forceinline__ void epi_flush(EpiState& s) {
             }
         }
     }
-    s.cnt = 0;
     s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
     if (PROF) {
         s.c_flush_cyc += clock64() - t0;
         ++s.c_flushes;
         s.c_iters += mx;
     }
+    return 0;
 }
 
-// One 16-column chunk: keys come straight from TMEM; masked columns become NaN
-// (every comparison with NaN is false, and the 3-input minimum skips NaN).
+__device__ __forceinline__ float min32(const float (&k)[32]) {
+    float a[11];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) a[q] = min3f(k[3 * q], k[3 * q + 1], k[3 * q + 2]);
+    a[10] = fminf(k[30], k[31]);
+    const float b0 = min3f(a[0], a[1], a[2]), b1 = min3f(a[3], a[4], a[5]);
+    const float b2 = min3f(a[6], a[7], a[8]), b3 = fminf(a[9], a[10]);
+    return fminf(min3f(b0, b1, b2), b3);
+}
+
+// One 32-column chunk: keys come straight from TMEM; masked columns become NaN
+// (every comparison with NaN is false, and the minimum skips NaN).
 template <bool PROF>
-__device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], int j0, int i,
-                                          int n_cols, int self_exclude,
+__device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], int j0, int i,
+                                          int n_cols, int self_exclude, bool edge,
                                           const uint32_t* __restrict__ gidrow) {
     long long f0 = 0;
     if (PROF) {
         ++s.c_chunks;
         f0 = clock64();
     }
-    float key[16];
+    float key[32];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) key[u] = __uint_as_float(v[u]);
-    if ((j0 + 16 > n_cols) || (self_exclude && (unsigned)(i - j0) < 16u)) {  // warp-uniform
+    for (int u = 0; u < 32; ++u) key[u] = __uint_as_float(v[u]);
+    if (edge) {  // warp-uniform
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < 32; ++u) {
             const int j = j0 + u;
             if (j >= n_cols || (self_exclude && j == i)) key[u] = __uint_as_float(0x7fc00000u);
         }
     }
-    const float m0 = min3f(key[0], key[1], key[2]);
-    const float m1 = min3f(key[3], key[4], key[5]);
-    const float m2 = min3f(key[6], key[7], key[8]);
-    const float m3 = min3f(key[9], key[10], key[11]);
-    const float m4 = min3f(key[12], key[13], key[14]);
-    const float m = min3f(min3f(m0, m1, m2), min3f(m3, m4, key[15]), INFINITY);
+    const float m = min32(key);
     // "<=": a key equal to the current k-th may still win on the global id
     const bool any = __any_sync(0xffffffffu, m <= s.tau);
     if (PROF) {
@@ -277,20 +329,28 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[16], 
     }
     if (!any) return;
     if (PROF) ++s.c_slow;
-    if (__any_sync(0xffffffffu, s.cnt > kt::CAP - 16)) epi_flush<PROF>(s);
-    // global ids of the chunk's 16 columns: one coalesced load, then broadcasts
     const int lane = threadIdx.x & 31;
-    uint32_t g_l = (uint32_t)(j0 + lane);
-    if (gidrow && lane < 16 && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
+    uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
+    if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
+    quarter_lock(s);
+    int c = s.cnt[s.row];
+    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
-        if (key[u] <= s.tau) {
-            s.B[s.cnt * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
-            ++s.cnt;
-            if (PROF) ++s.c_app;
+    for (int half = 0; half < 2; ++half) {
+        if (__any_sync(0xffffffffu, c > kt::CAP - 16)) c = epi_flush<PROF>(s, c);
+#pragma unroll
+        for (int uu = 0; uu < 16; ++uu) {
+            const int u = half * 16 + uu;
+            const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
+            if (key[u] <= s.tau) {
+                s.B[c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
+                ++c;
+                if (PROF) ++s.c_app;
+            }
         }
     }
+    s.cnt[s.row] = c;
+    quarter_unlock(s);
     if (PROF) s.c_append += clock64() - f0;
 }
 
@@ -352,7 +412,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         }
         for (int a = 0; a < kt::NACC; ++a) {
             mbar_init(accf_bar + 8 * a, 1);
-            mbar_init(acce_bar + 8 * a, 4);
+            mbar_init(acce_bar + 8 * a, kt::EPI_WARPS);
         }
         mbar_init(a_bar, 1);
         mbar_init(done_bar, 1);
@@ -362,6 +422,14 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     if (warp == 1) {
         tmem_alloc(smem_u32((const void*)tmem_slot), kt::TMEM_COLS);
         tmem_relinquish();
+    }
+    if (warp >= 2 && warp < 6) {  // heaps, survivor counts and quarter locks
+        uint64_t* H = (uint64_t*)(base + L.heap);
+        const int row = (warp & 3) * 32 + lane;
+        const uint64_t init = heap_init_val();
+        for (int e = 0; e < P.kprime; ++e) H[e * kt::BM + row] = init;
+        ((int*)(base + L.cnt))[row] = 0;
+        if (lane == 0) ((int*)(base + L.locks))[warp & 3] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -485,22 +553,26 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        // Warp (q, h): TMEM lane quarter q (rows 32q..32q+31), columns
+        // [64h, 64h + 64) of every tile.
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         EpiState s;
         s.row = q * 32 + lane;
         s.H = (uint64_t*)(base + L.heap);
         s.B = (uint64_t*)(base + L.buf);
+        s.cnt = (int*)(base + L.cnt);
+        s.lock = (int*)(base + L.locks) + q;
+        s.abort = abort_flag;
         s.kp = P.kprime;
-        s.cnt = 0;
         s.tau = INFINITY;
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
         s.c_ldw = s.c_filter = s.c_append = 0;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
-        const int i = rb * kt::BM + s.row;  // row index inside the problem
-        const uint64_t init = heap_init_val();
-        for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
+        const int i = rb * kt::BM + s.row;     // row index inside the problem
+        const int i0 = rb * kt::BM + q * 32;   // first row of this warp
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
@@ -512,31 +584,25 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
-            const uint32_t tb = tmem + lane_addr + a * kt::BN;
-            const int jt = t * kt::BN;
-            uint32_t va[16], vb[16];
+            const uint32_t tb = tmem + lane_addr + a * kt::BN + h * 64;
+            const int jt = t * kt::BN + h * 64;
+            const bool edge = (jt + 64 > pr.n_cols) ||
+                              (P.self_exclude && i0 + 32 > jt && i0 < jt + 64);
+            uint32_t va[32], vb[32];
             __syncwarp();
-            tmem_ld16(tb, va);
-#pragma unroll
-            for (int c = 0; c < kt::BN / kt::CHUNK; c += 2) {
-                long long l0 = 0;
-                if (PROF) l0 = clock64();
-                tmem_wait_ld16(va);
-                if (PROF) s.c_ldw += clock64() - l0;
-                tmem_ld16(tb + (c + 1) * kt::CHUNK, vb);
-                if (jt + c * kt::CHUNK < pr.n_cols)
-                    epi_chunk<PROF>(s, va, jt + c * kt::CHUNK, i, pr.n_cols, P.self_exclude,
-                                    gidrow);
-                __syncwarp();
-                if (PROF) l0 = clock64();
-                tmem_wait_ld16(vb);
-                if (PROF) s.c_ldw += clock64() - l0;
-                if (c + 2 < kt::BN / kt::CHUNK) tmem_ld16(tb + (c + 2) * kt::CHUNK, va);
-                if (jt + (c + 1) * kt::CHUNK < pr.n_cols)
-                    epi_chunk<PROF>(s, vb, jt + (c + 1) * kt::CHUNK, i, pr.n_cols,
-                                    P.self_exclude, gidrow);
-                __syncwarp();
-            }
+            tmem_ld32(tb, va);
+            long long l0 = 0;
+            if (PROF) l0 = clock64();
+            tmem_wait_ld32(va);
+            if (PROF) s.c_ldw += clock64() - l0;
+            tmem_ld32(tb + 32, vb);
+            if (jt < pr.n_cols)
+                epi_chunk<PROF>(s, va, jt, i, pr.n_cols, P.self_exclude, edge, gidrow);
+            if (PROF) l0 = clock64();
+            tmem_wait_ld32(vb);
+            if (PROF) s.c_ldw += clock64() - l0;
+            if (jt + 32 < pr.n_cols)
+                epi_chunk<PROF>(s, vb, jt + 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar + 8 * a);
@@ -557,10 +623,12 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 prof_add(TC_FLUSH_ITERS, s.c_iters);
             }
         }
-        if (!ok) {
-            atomicOr(P.status, DEV_TIMEOUT);
-        } else {
-            epi_flush<false>(s);
+        // both warps of the quarter are done with the rows: h = 0 finishes them
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(64) : "memory");
+        if (!ok || *abort_flag) {
+            if (h == 0 && lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+        } else if (h == 0) {
+            epi_flush<false>(s, s.cnt[s.row]);
             if (i < pr.n_rows) {
                 // Heap sort ascending, then write (global id, |x|^2 + 2 key).
                 uint64_t* H = s.H;
