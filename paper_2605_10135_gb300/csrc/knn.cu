@@ -56,6 +56,7 @@ constexpr uint32_t TMEM_COLS = NACC * BN;
 constexpr int MAX_NST = 8;
 constexpr int CAP = 32;                 // survivor buffer entries per row
 constexpr int CELL = 1024;              // rows per pivot cell
+constexpr int WARM = 12;                // leading tiles handled by one warp per quarter
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -121,8 +122,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     o += kt::CAP * kt::BM * 8;
     L.cnt = o;
     o += kt::BM * 4;
-    L.locks = o;
-    o += 4 * 4;
+    L.locks = o;  // 4 quarter locks, then 4 "warm-up done" flags
+    o += 8 * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -235,6 +236,7 @@ struct EpiState {
     int* lock;
     volatile int* abort;
     int row, kp;
+    bool shared;  // false while the partner warp is idle: no lock needed
     float tau;
     // counters (used only by the profiling instantiation)
     unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
@@ -242,11 +244,13 @@ struct EpiState {
 };
 
 __device__ __forceinline__ void quarter_lock(EpiState& s) {
+    if (!s.shared) return;
     if ((threadIdx.x & 31) == 0) {
         const uint64_t t0 = globaltimer();
         for (uint32_t it = 0;; ++it) {
             if (atomicCAS(s.lock, 0, 1) == 0) break;
-            if ((it & 255u) == 255u && globaltimer() - t0 > 1000000000ull) {
+            __nanosleep(64);
+            if ((it & 63u) == 63u && globaltimer() - t0 > 1000000000ull) {
                 *s.abort = 1;  // cannot happen unless a holder died; give up the lock
                 break;
             }
@@ -257,6 +261,7 @@ __device__ __forceinline__ void quarter_lock(EpiState& s) {
 }
 
 __device__ __forceinline__ void quarter_unlock(EpiState& s) {
+    if (!s.shared) return;
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         __threadfence_block();
@@ -429,7 +434,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const uint64_t init = heap_init_val();
         for (int e = 0; e < P.kprime; ++e) H[e * kt::BM + row] = init;
         ((int*)(base + L.cnt))[row] = 0;
-        if (lane == 0) ((int*)(base + L.locks))[warp & 3] = 0;
+        if (lane == 0) {
+            ((int*)(base + L.locks))[warp & 3] = 0;
+            ((int*)(base + L.locks))[4 + (warp & 3)] = 0;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -565,6 +573,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.lock = (int*)(base + L.locks) + q;
         s.abort = abort_flag;
         s.kp = P.kprime;
+        s.shared = false;
         s.tau = INFINITY;
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
         s.c_ldw = s.c_filter = s.c_append = 0;
@@ -584,25 +593,60 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
-            const uint32_t tb = tmem + lane_addr + a * kt::BN + h * 64;
-            const int jt = t * kt::BN + h * 64;
-            const bool edge = (jt + 64 > pr.n_cols) ||
-                              (P.self_exclude && i0 + 32 > jt && i0 < jt + 64);
-            uint32_t va[32], vb[32];
-            __syncwarp();
-            tmem_ld32(tb, va);
-            long long l0 = 0;
-            if (PROF) l0 = clock64();
-            tmem_wait_ld32(va);
-            if (PROF) s.c_ldw += clock64() - l0;
-            tmem_ld32(tb + 32, vb);
-            if (jt < pr.n_cols)
-                epi_chunk<PROF>(s, va, jt, i, pr.n_cols, P.self_exclude, edge, gidrow);
-            if (PROF) l0 = clock64();
-            tmem_wait_ld32(vb);
-            if (PROF) s.c_ldw += clock64() - l0;
-            if (jt + 32 < pr.n_cols)
-                epi_chunk<PROF>(s, vb, jt + 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
+            // The first WARM tiles (the row block's own cell, where most chunks hold
+            // survivors) are handled by warp h = 0 alone and without locking; after
+            // that the two warps take one column half each.
+            const bool warm = tt < kt::WARM;
+            if (tt == kt::WARM) {
+                // hand-over: warp h = 1 starts only after h = 0 has finished the
+                // lock-free warm-up tiles (bounded wait on a shared-memory flag)
+                volatile int* done = (volatile int*)(base + L.locks) + 4 + q;
+                if (h == 0) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        *done = 1;
+                    }
+                } else {
+                    if (lane == 0) {
+                        const uint64_t w0 = globaltimer();
+                        while (*done == 0) {
+                            if (*abort_flag) { ok = false; break; }
+                            if (globaltimer() - w0 > 2000000000ull) {
+                                *abort_flag = 1;
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(128);
+                        }
+                        __threadfence_block();
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
+                }
+                s.shared = true;
+            }
+            for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
+                const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * 64;
+                const int jt = t * kt::BN + hh * 64;
+                const bool edge = (jt + 64 > pr.n_cols) ||
+                                  (P.self_exclude && i0 + 32 > jt && i0 < jt + 64);
+                uint32_t va[32], vb[32];
+                __syncwarp();
+                tmem_ld32(tb, va);
+                long long l0 = 0;
+                if (PROF) l0 = clock64();
+                tmem_wait_ld32(va);
+                if (PROF) s.c_ldw += clock64() - l0;
+                tmem_ld32(tb + 32, vb);
+                if (jt < pr.n_cols)
+                    epi_chunk<PROF>(s, va, jt, i, pr.n_cols, P.self_exclude, edge, gidrow);
+                if (PROF) l0 = clock64();
+                tmem_wait_ld32(vb);
+                if (PROF) s.c_ldw += clock64() - l0;
+                if (jt + 32 < pr.n_cols)
+                    epi_chunk<PROF>(s, vb, jt + 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acce_bar + 8 * a);
