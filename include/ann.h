@@ -88,7 +88,8 @@ int ann_timing_read(double* tile_ms, int* launches);
  * epilogue cycles, epilogue wait cycles, epilogue flush cycles, chunks, slow
  * chunks, flushes, flush iterations, heap inserts, appended survivors, MMA
  * wait-for-data cycles, MMA wait-for-accumulator cycles, producer wait cycles,
- * CTA cycles, CTAs, TMEM-load wait cycles, filter cycles, append cycles. */
+ * CTA cycles, CTAs, TMEM-load wait cycles, filter cycles, append cycles, MMA
+ * issue cycles, MMA commit cycles, MMA loop cycles. */
 int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 

@@ -78,6 +78,9 @@ enum TileCounter {
     TC_LD_WAIT,          // epilogue threads: cycles blocked in tcgen05.wait::ld
     TC_FILTER,           // epilogue threads: cycles in the chunk filter (min + vote)
     TC_APPEND,           // epilogue threads: cycles appending survivors (incl. flush)
+    TC_MMA_ISSUE,        // MMA thread: cycles issuing tcgen05.mma
+    TC_MMA_COMMIT,       // MMA thread: cycles in tcgen05.commit
+    TC_MMA_LOOP,         // MMA thread: cycles from the A wait to the end of the tile loop
     TC_N
 };
 __device__ unsigned long long g_tile_counters[TC_N];
@@ -500,7 +503,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             int st = 0;
             uint32_t ph = 0;
             const int H2 = P.nkb_b >> 1;
-            unsigned long long w_full = 0, w_acc = 0;
+            unsigned long long w_full = 0, w_acc = 0, c_iss = 0, c_com = 0;
+            long long loop0 = 0;
+            if (PROF) loop0 = clock64();
             for (int t = 0; t < ntiles && ok; ++t) {
                 const int a = t % kt::NACC;
                 long long w0 = 0;
@@ -518,6 +523,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (!mbar_wait(full_bar + 8 * st, ph, abort_flag)) { ok = false; break; }
                     if (PROF) w_full += clock64() - w0;
                     tc_fence_after();
+                    if (PROF) w0 = clock64();
                     const uint32_t bsm = sB + st * kt::BLK_BYTES;
                     if (j < P.nkb_b) {
                         int ablk[2];
@@ -544,11 +550,22 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                         umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(bsm), P.idesc_aug, accum);
                         accum = 1;
                     }
+                    long long w1 = 0;
+                    if (PROF) {
+                        w1 = clock64();
+                        c_iss += w1 - w0;
+                    }
                     umma_commit(empty_bar + 8 * st);
+                    if (PROF) c_com += clock64() - w1;
                     if (++st == P.nst) { st = 0; ph ^= 1; }
                 }
                 if (!ok) break;
                 umma_commit(accf_bar + 8 * a);
+            }
+            if (PROF) {
+                prof_add(TC_MMA_LOOP, (unsigned long long)(clock64() - loop0));
+                prof_add(TC_MMA_ISSUE, c_iss);
+                prof_add(TC_MMA_COMMIT, c_com);
             }
             umma_commit(done_bar);  // every issued MMA completes before TMEM is released
             int dummy = 0;
