@@ -157,11 +157,14 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
  * `rule` (enum ann_prune_rule).  Integer logic on the lists only: the output
  * depends on knn_id alone (knn_d is carried), so identical lists give
  * identical results.  pr_id / pr_d: [rows x R], kept entries in list order
- * then ANN_PAD / +inf.  Limits: 1 <= R, k <= 256.
+ * then ANN_PAD / +inf.  N = number of vectors (ids < N).  The workspace holds
+ * the inverse of the member lists (the rows of every id).
+ * Limits: 1 <= R, k <= 256.
  * ------------------------------------------------------------------------- */
+int ann_prune_workspace(int64_t N, int64_t rows, size_t* bytes);
 int ann_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
-              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule,
-              uint32_t* pr_id, float* pr_d, void* stream);
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ann_merge - Sec. IV Workflow (3), Sec. II-B "edge union": for every vector

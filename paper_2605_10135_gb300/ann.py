@@ -57,7 +57,8 @@ def lib():
             "ann_shard_knn_workspace": (I32, [I64, I32, I32, I32, I64, I32, I32, I32, PSZ]),
             "ann_shard_knn": (I32, [P, I64, I32, I32, P, P, I32, I64, I32, I32, I32, P, P, P, P, SZ,
                                     P]),
-            "ann_prune": (I32, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
+            "ann_prune_workspace": (I32, [I64, I64, PSZ]),
+            "ann_prune": (I32, [P, P, P, P, I32, I64, I64, I32, I32, I32, P, P, P, SZ, P]),
             "ann_merge_workspace": (I32, [I64, I64, PSZ]),
             "ann_merge": (I32, [P, P, P, P, I32, I64, I64, I32, P, P, P, P, SZ, P]),
             "ann_medoid_workspace": (I32, [I64, I32, PSZ]),
@@ -195,16 +196,23 @@ def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: 
 
 
 def prune(knn_id: torch.Tensor, knn_d: torch.Tensor, members: torch.Tensor,
-          offsets: torch.Tensor, R: int, rule: int = PRUNE_RANK):
-    """Prune each shard list from k to R: (pr_id [rows, R], pr_d [rows, R])."""
+          offsets: torch.Tensor, R: int, rule: int = PRUNE_RANK, N: int | None = None):
+    """Prune each shard list from k to R: (pr_id [rows, R], pr_d [rows, R]).
+
+    N is the number of vectors (ids < N); by default one more than the largest member id."""
     knn_id, knn_d = _cuda(knn_id, "knn_id"), _cuda(knn_d, "knn_d")
     members, offsets = _cuda(members, "members"), _cuda(offsets, "offsets")
     rows, k = knn_id.shape
     C = offsets.numel() - 1
+    if N is None:
+        N = int(members.max().item()) + 1 if rows else 0
     pr_id = torch.empty((rows, R), dtype=torch.int32, device=knn_id.device)
     pr_d = torch.empty((rows, R), dtype=torch.float32, device=knn_id.device)
-    _check(lib().ann_prune(_ptr(knn_id), _ptr(knn_d), _ptr(members), _ptr(offsets), C, rows, k, R,
-                           rule, _ptr(pr_id), _ptr(pr_d), _stream()))
+    L = lib()
+    nb = _wsize(L.ann_prune_workspace, N, rows)
+    ws = _ws(nb, knn_id.device)
+    _check(L.ann_prune(_ptr(knn_id), _ptr(knn_d), _ptr(members), _ptr(offsets), C, rows, N, k, R,
+                       rule, _ptr(pr_id), _ptr(pr_d), _ptr(ws), nb, _stream()))
     return pr_id, pr_d
 
 
@@ -296,7 +304,7 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
     """The whole hot path: partition -> per-shard kNN -> prune -> merge (all on the GPU)."""
     cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
     knn_id, knn_d = shard_knn(X, members, offsets, cfg.k, cfg.precision, cfg.rerank_k)
-    pr_id, pr_d = prune(knn_id, knn_d, members, offsets, cfg.R, cfg.rule)
+    pr_id, pr_d = prune(knn_id, knn_d, members, offsets, cfg.R, cfg.rule, N=X.shape[0])
     graph, gdist, degree = merge(pr_id, pr_d, members, offsets, X.shape[0])
     return dict(centroids=cent, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
                 pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree)

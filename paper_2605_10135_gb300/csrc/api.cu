@@ -244,23 +244,36 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
 }
 
 // ---------------------------------------------------------------- prune / merge
+int ann_prune_workspace(int64_t N, int64_t rows, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32) && rows >= 0, "N / rows out of range");
+    *bytes = rowlist_ws(N, rows, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
 int ann_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
-              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule, uint32_t* pr_id,
-              float* pr_d, void* stream) {
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, void* ws, size_t ws_bytes, void* stream) {
     ANN_REQUIRE(k >= 1 && k <= 256, "k must be in [1, 256]");
     ANN_REQUIRE(R >= 1 && R <= 256, "R must be in [1, 256]");
     ANN_REQUIRE(rule == ANN_PRUNE_RANK || rule == ANN_PRUNE_TRUNC, "bad rule %d", rule);
     ANN_REQUIRE(C >= 1 && rows >= 0, "bad C / rows");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
     ANN_REQUIRE(offsets, "offsets is NULL");
     ANN_REQUIRE(rows == 0 || (knn_id && knn_d && members && pr_id && pr_d), "NULL pointer");
-    return run_prune(knn_id, knn_d, members, offsets, C, rows, k, R, rule, pr_id, pr_d,
+    size_t need = rowlist_ws(N, rows, nullptr, nullptr, 0);
+    int rc = check_ws(ws, ws_bytes, need);
+    if (rc) return rc;
+    RowlistWs w;
+    rowlist_ws(N, rows, &w, ws, ws_bytes);
+    return run_prune(knn_id, knn_d, members, offsets, C, rows, N, k, R, rule, pr_id, pr_d, w,
                      (cudaStream_t)stream);
 }
 
 int ann_merge_workspace(int64_t N, int64_t rows, size_t* bytes) {
     ANN_REQUIRE(bytes, "bytes is NULL");
     ANN_REQUIRE(N >= 0 && N < (1ll << 32) && rows >= 0, "N / rows out of range");
-    *bytes = merge_ws(N, rows, nullptr, nullptr, 0);
+    *bytes = rowlist_ws(N, rows, nullptr, nullptr, 0);
     return ANN_OK;
 }
 
@@ -275,8 +288,8 @@ int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
     ANN_REQUIRE(N == 0 || (graph && gdist && degree), "NULL pointer");
     ANN_REQUIRE(rows == 0 || (pr_id && pr_d && members), "NULL pointer");
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
-    MergeWs w;
-    merge_ws(N, rows, &w, ws, ws_bytes);
+    RowlistWs w;
+    rowlist_ws(N, rows, &w, ws, ws_bytes);
     return run_merge(pr_id, pr_d, members, offsets, C, rows, N, R, graph, gdist, degree, w,
                      (cudaStream_t)stream);
 }

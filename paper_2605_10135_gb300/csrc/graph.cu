@@ -77,11 +77,34 @@ __device__ __forceinline__ uint32_t hash_slot(uint32_t id, int hs_mask) {
 }
 
 // ---- prune ------------------------------------------------------------------------
+// start[g] .. start[g+1] index rowlist[], the rows p (all shards) with members[p] == g.
+__device__ __forceinline__ int64_t row_in_range(const int64_t* __restrict__ start,
+                                                const int64_t* __restrict__ rowlist, uint32_t v,
+                                                int64_t m0, int64_t m1) {
+    const int64_t a1 = start[v + 1];
+    for (int64_t a = start[v]; a < a1; ++a) {
+        const int64_t p = rowlist[a];
+        if (p >= m0 && p < m1) return p;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int hash_find(const uint32_t* hkey, const int32_t* hval, int hs_mask,
+                                         uint32_t x) {
+    uint32_t h = hash_slot(x, hs_mask);
+    for (;;) {
+        const uint32_t key = hkey[h];
+        if (key == x) return hval[h];
+        if (key == ANN_PAD) return -1;
+        h = (h + 1) & (uint32_t)hs_mask;
+    }
+}
+
 template <int E>  // 32*E >= k
 __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __restrict__ knn_d,
-                        const uint32_t* __restrict__ members, const int64_t* __restrict__ offsets,
-                        int C, int64_t rows, int k, int R, int rule, uint32_t* __restrict__ pr_id,
-                        float* __restrict__ pr_d) {
+                        const int64_t* __restrict__ offsets, const int64_t* __restrict__ start,
+                        const int64_t* __restrict__ rowlist, int C, int64_t rows, int k, int R,
+                        int rule, uint32_t* __restrict__ pr_id, float* __restrict__ pr_d) {
     constexpr int KM = 32 * E, HS = 2 * KM;
     extern __shared__ __align__(16) uint8_t sm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -93,6 +116,7 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
     int64_t* nrow = (int64_t*)(hval + HS);
     int32_t* cnt = (int32_t*)(nrow + KM);
     const uint32_t lt = (1u << lane) - 1;
+    const bool vec = (k & 3) == 0;
 
     for (int64_t p = blockIdx.x * (int64_t)nwb + wib; p < rows; p += (int64_t)gridDim.x * nwb) {
         const int s = shard_of(offsets, C, p);
@@ -123,30 +147,40 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                     if (prev == ANN_PAD || prev == id) { hval[h] = j; break; }
                     h = (h + 1) & (HS - 1);
                 }
-                // row of neighbour id inside this shard (ids sorted): lower bound
-                int64_t lo = m0, hi = m1;
-                while (lo < hi) {
-                    const int64_t mid = lo + ((hi - lo) >> 1);
-                    if (__ldg(members + mid) < id) lo = mid + 1; else hi = mid;
-                }
-                nrow[j] = (lo < m1 && __ldg(members + lo) == id) ? lo : -1;
             }
             __syncwarp();
-            for (int i = 0; i < m; ++i) {
-                const int64_t w = nrow[i];
+            // Lane-parallel over the neighbours v_i: each lane reads whole lists
+            // (16-byte loads), so all of a row's list reads are in flight at once.
+            for (int i = lane; i < m; i += 32) {
+                const int64_t w = row_in_range(start, rowlist, list[i], m0, m1);
                 if (w < 0) continue;
-                for (int t = lane; t < k; t += 32) {
-                    const uint32_t x = __ldg(knn_id + w * k + t);
-                    if (x == ANN_PAD) continue;
-                    uint32_t h = hash_slot(x, HS - 1);
-                    int j = -1;
-                    for (;;) {
-                        const uint32_t key = hkey[h];
-                        if (key == x) { j = hval[h]; break; }
-                        if (key == ANN_PAD) break;
-                        h = (h + 1) & (HS - 1);
+                const uint32_t* Lw = knn_id + w * k;
+                if (vec) {
+                    for (int t0 = 0; t0 < k; t0 += 16) {
+                        uint4 q4[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            q4[r] = t0 + 4 * r < k ? __ldg((const uint4*)(Lw + t0) + r)
+                                                   : make_uint4(ANN_PAD, ANN_PAD, ANN_PAD, ANN_PAD);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const uint32_t xs[4] = {q4[r].x, q4[r].y, q4[r].z, q4[r].w};
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int t = t0 + 4 * r + c;
+                                if (xs[c] == ANN_PAD || t >= k) continue;
+                                const int j = hash_find(hkey, hval, HS - 1, xs[c]);
+                                if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                            }
+                        }
                     }
-                    if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                } else {
+                    for (int t = 0; t < k; ++t) {
+                        const uint32_t x = __ldg(Lw + t);
+                        if (x == ANN_PAD) continue;
+                        const int j = hash_find(hkey, hval, HS - 1, x);
+                        if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                    }
                 }
             }
             __syncwarp();
@@ -364,36 +398,9 @@ __global__ void k_merge(const uint32_t* __restrict__ pr_id, const float* __restr
 }
 
 // ---- host drivers ----------------------------------------------------------------
-int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
-              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule, uint32_t* pr_id,
-              float* pr_d, cudaStream_t st) {
-    if (rows == 0) return ANN_OK;
-    const int warps = 4;
-    const int64_t want = (rows + warps - 1) / warps;
-    const unsigned grid = (unsigned)(want < 152 * 32 ? want : 152 * 32);
-#define ANN_PRUNE_CASE(EE)                                                                   \
-    {                                                                                        \
-        constexpr int KM = 32 * EE;                                                          \
-        const size_t smem = (size_t)warps * (KM * 4 + 2 * KM * 8 + KM * 8 + KM * 4);         \
-        if (smem > 48 * 1024)                                                                \
-            ANN_CHECK_CUDA(cudaFuncSetAttribute(k_prune<EE>,                                 \
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                (int)smem));                                 \
-        k_prune<EE><<<grid, warps * 32, smem, st>>>(knn_id, knn_d, members, offsets, C, rows, \
-                                                    k, R, rule, pr_id, pr_d);                \
-    }
-    if (k <= 32) ANN_PRUNE_CASE(1)
-    else if (k <= 64) ANN_PRUNE_CASE(2)
-    else if (k <= 128) ANN_PRUNE_CASE(4)
-    else ANN_PRUNE_CASE(8)
-#undef ANN_PRUNE_CASE
-    ANN_CHECK_LAUNCH();
-    return ANN_OK;
-}
-
-size_t merge_ws(int64_t N, int64_t rows, MergeWs* out, void* base, size_t cap) {
+size_t rowlist_ws(int64_t N, int64_t rows, RowlistWs* out, void* base, size_t cap) {
     Carver cv(base, cap);
-    MergeWs w;
+    RowlistWs w;
     w.cnt = cv.take<int32_t>((size_t)N + 1);
     w.start = cv.take<int64_t>((size_t)N + 1);
     w.bsum = cv.take<int64_t>((size_t)(N / SCAN_CHUNK + 2));
@@ -402,17 +409,15 @@ size_t merge_ws(int64_t N, int64_t rows, MergeWs* out, void* base, size_t cap) {
     return cv.used + 256;
 }
 
-int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
-              const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
-              float* gdist, uint32_t* degree, const MergeWs& w, cudaStream_t st) {
-    (void)offsets;
-    (void)C;
-    if (N == 0) return ANN_OK;
+static unsigned grid_of(int64_t n, int t) {
+    const int64_t g = (n + t - 1) / t;
+    return (unsigned)(g < 152 * 64 ? (g > 0 ? g : 1) : 152 * 64);
+}
+
+// Inverse of members[]: for every id g the rows holding it (any order).
+int build_rowlist(const uint32_t* members, int64_t rows, int64_t N, const RowlistWs& w,
+                  cudaStream_t st) {
     const int tpb = 256;
-    auto grid_of = [](int64_t n, int t) {
-        int64_t g = (n + t - 1) / t;
-        return (unsigned)(g < 152 * 64 ? (g > 0 ? g : 1) : 152 * 64);
-    };
     ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (N + 1), st));
     k_count_ids<<<grid_of(rows, tpb), tpb, 0, st>>>(members, rows, N, w.cnt, device_status_ptr());
     ANN_CHECK_LAUNCH();
@@ -426,9 +431,53 @@ int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
     ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (N + 1), st));
     k_fill_rowlist<<<grid_of(rows, tpb), tpb, 0, st>>>(members, rows, N, w.start, w.cnt, w.rowlist);
     ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, const RowlistWs& w, cudaStream_t st) {
+    if (rows == 0) return ANN_OK;
+    if (rule == ANN_PRUNE_RANK) {
+        int rc = build_rowlist(members, rows, N, w, st);
+        if (rc) return rc;
+    }
+    const int warps = 4;
+    const int64_t want = (rows + warps - 1) / warps;
+    const unsigned grid = (unsigned)(want < 152 * 32 ? want : 152 * 32);
+#define ANN_PRUNE_CASE(EE)                                                                   \
+    {                                                                                        \
+        constexpr int KM = 32 * EE;                                                          \
+        const size_t smem = (size_t)warps * (KM * 4 + 2 * KM * 8 + KM * 8 + KM * 4);         \
+        if (smem > 48 * 1024)                                                                \
+            ANN_CHECK_CUDA(cudaFuncSetAttribute(k_prune<EE>,                                 \
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                (int)smem));                                 \
+        k_prune<EE><<<grid, warps * 32, smem, st>>>(knn_id, knn_d, offsets, w.start,          \
+                                                    w.rowlist, C, rows, k, R, rule, pr_id,   \
+                                                    pr_d);                                   \
+    }
+    if (k <= 32) ANN_PRUNE_CASE(1)
+    else if (k <= 64) ANN_PRUNE_CASE(2)
+    else if (k <= 128) ANN_PRUNE_CASE(4)
+    else ANN_PRUNE_CASE(8)
+#undef ANN_PRUNE_CASE
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
+              float* gdist, uint32_t* degree, const RowlistWs& w, cudaStream_t st) {
+    (void)offsets;
+    (void)C;
+    if (N == 0) return ANN_OK;
+    int rc = build_rowlist(members, rows, N, w, st);
+    if (rc) return rc;
+    const int tpb = 256;
     const unsigned mg = (unsigned)((N * 32 + tpb - 1) / tpb);
     k_merge<<<mg, tpb, 0, st>>>(pr_id, pr_d, w.start, w.rowlist, N, R, graph, gdist, degree,
-                                   device_status_ptr());
+                                device_status_ptr());
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }

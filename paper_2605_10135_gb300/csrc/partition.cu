@@ -69,7 +69,10 @@ __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
     }
 }
 
-// FP64 sums in sample order: thread = one dimension, block = DB dimensions.
+// FP64 sums in sample order: thread = one dimension, block = DB (<= 32) dimensions.
+// Labels and row indices of 32 consecutive samples are fetched with one
+// coalesced load and broadcast; the 32 element loads of a batch are issued
+// before any of them is added, then added strictly in sample order.
 __global__ void k_kmeans_sums(const void* X, int dtype, int d, const uint32_t* __restrict__ sample,
                               int64_t S, const int32_t* __restrict__ lab, int C, int DB,
                               double* __restrict__ sums) {
@@ -78,12 +81,24 @@ __global__ void k_kmeans_sums(const void* X, int dtype, int d, const uint32_t* _
     const int t = blockIdx.x * DB + tl;
     for (int i = threadIdx.x; i < C * DB; i += blockDim.x) acc[i] = 0.0;
     __syncthreads();
-    if (tl < DB && t < d) {
-#pragma unroll 4
-        for (int64_t s = 0; s < S; ++s) {
-            int c = __ldg(lab + s);
-            float v = load_elem(X, dtype, (int64_t)__ldg(sample + s) * d + t);
-            acc[c * DB + tl] = __dadd_rn(acc[c * DB + tl], (double)v);
+    if (threadIdx.x < 32) {
+        const bool active = tl < DB && t < d;
+        for (int64_t s0 = 0; s0 < S; s0 += 32) {
+            const int64_t sl = s0 + tl;
+            const int myc = sl < S ? __ldg(lab + sl) : 0;
+            const uint32_t myr = sl < S ? __ldg(sample + sl) : 0u;
+            const int nb = S - s0 < 32 ? (int)(S - s0) : 32;
+            float v[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const uint32_t r = __shfl_sync(0xffffffffu, myr, u);
+                v[u] = (active && u < nb) ? load_elem(X, dtype, (int64_t)r * d + t) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                const int c = __shfl_sync(0xffffffffu, myc, u);
+                if (active && u < nb) acc[c * DB + tl] = __dadd_rn(acc[c * DB + tl], (double)v[u]);
+            }
         }
     }
     __syncthreads();
@@ -264,7 +279,7 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
             ANN_CHECK_LAUNCH();
         }
         ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * C, st));
-        k_kmeans_sums<<<(unsigned)((d + DB - 1) / DB), 32 * ((DB + 31) / 32), sum_smem, st>>>(
+        k_kmeans_sums<<<(unsigned)((d + DB - 1) / DB), 32, sum_smem, st>>>(
             X, dtype, d, sample_idx, S, w.lab, C, DB, w.sums);
         ANN_CHECK_LAUNCH();
         k_count_labels<<<nb(S, tpb) < 4096u ? nb(S, tpb) : 4096u, tpb, 0, st>>>(w.lab, S, w.cnt);

@@ -106,19 +106,22 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
                   cudaStream_t st);
 
 // ---- prune / merge ---------------------------------------------------------------
-int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
-              const int64_t* offsets, int C, int64_t rows, int k, int R, int rule,
-              uint32_t* pr_id, float* pr_d, cudaStream_t st);
-struct MergeWs {
+// Inverse of the member lists: start[g] .. start[g+1] index rowlist[], the rows
+// holding vector g.  Shared by prune (to find a neighbour's row in the same shard)
+// and merge (to gather a vector's lists from all its shards).
+struct RowlistWs {
     int32_t* cnt;
     int64_t* start;
     int64_t* bsum;
     int64_t* rowlist;
 };
-size_t merge_ws(int64_t N, int64_t rows, MergeWs* out, void* base, size_t cap);
+size_t rowlist_ws(int64_t N, int64_t rows, RowlistWs* out, void* base, size_t cap);
+int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* members,
+              const int64_t* offsets, int C, int64_t rows, int64_t N, int k, int R, int rule,
+              uint32_t* pr_id, float* pr_d, const RowlistWs& w, cudaStream_t st);
 int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
               const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
-              float* gdist, uint32_t* degree, const MergeWs& w, cudaStream_t st);
+              float* gdist, uint32_t* degree, const RowlistWs& w, cudaStream_t st);
 
 // ---- query side ------------------------------------------------------------------
 int search_vis_mask(int Ls, int R);

@@ -48,8 +48,10 @@ def test_workspace_queries_validate_on_host(L):
     assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 1, 0, ct.byref(n)) == 2  # reserved
     assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256
     assert L.ann_merge_workspace(1000, 2000, ct.byref(n)) == 0 and n.value > 0
-    assert L.ann_prune(None, None, None, None, 4, 10, 0, 8, 0, None, None, None) == 1  # k = 0
-    assert L.ann_prune(None, None, None, None, 4, 10, 8, 8, 7, None, None, None) == 1  # rule
+    assert L.ann_prune(None, None, None, None, 4, 10, 100, 0, 8, 0, None, None, None, 0,
+                       None) == 1  # k = 0
+    assert L.ann_prune(None, None, None, None, 4, 10, 100, 8, 8, 7, None, None, None, 0,
+                       None) == 1  # rule
 
 
 def test_null_workspace_is_rejected(L):
