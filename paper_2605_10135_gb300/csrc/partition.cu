@@ -69,41 +69,36 @@ __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
     }
 }
 
-// FP64 sums in sample order: thread = one dimension, block = DB (<= 32) dimensions.
-// Labels and row indices of 32 consecutive samples are fetched with one
-// coalesced load and broadcast; the 32 element loads of a batch are issued
-// before any of them is added, then added strictly in sample order.
+// FP64 sums in sample order.  One warp per (centroid c, 32 consecutive
+// dimensions): every lane keeps its own register accumulator and adds the
+// samples labelled c in sample order, so each (c, t) sum is the plain sequential
+// one; the C x d/32 warps are independent, which hides the FP64 add latency.
+// Labels and rows of 32 consecutive samples come in one coalesced load each; a
+// ballot picks the samples of label c.
 __global__ void k_kmeans_sums(const void* X, int dtype, int d, const uint32_t* __restrict__ sample,
-                              int64_t S, const int32_t* __restrict__ lab, int C, int DB,
+                              int64_t S, const int32_t* __restrict__ lab, int C,
                               double* __restrict__ sums) {
-    extern __shared__ double acc[];  // [C][DB]
-    const int tl = threadIdx.x;
-    const int t = blockIdx.x * DB + tl;
-    for (int i = threadIdx.x; i < C * DB; i += blockDim.x) acc[i] = 0.0;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const bool active = tl < DB && t < d;
-        for (int64_t s0 = 0; s0 < S; s0 += 32) {
-            const int64_t sl = s0 + tl;
-            const int myc = sl < S ? __ldg(lab + sl) : 0;
-            const uint32_t myr = sl < S ? __ldg(sample + sl) : 0u;
-            const int nb = S - s0 < 32 ? (int)(S - s0) : 32;
-            float v[32];
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                const uint32_t r = __shfl_sync(0xffffffffu, myr, u);
-                v[u] = (active && u < nb) ? load_elem(X, dtype, (int64_t)r * d + t) : 0.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                const int c = __shfl_sync(0xffffffffu, myc, u);
-                if (active && u < nb) acc[c * DB + tl] = __dadd_rn(acc[c * DB + tl], (double)v[u]);
-            }
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int nt = (d + 31) / 32;
+    if (w >= (int64_t)C * nt) return;
+    const int c = (int)(w / nt);
+    const int t = (int)(w % nt) * 32 + lane;
+    const bool active = t < d;
+    double acc = 0.0;
+    for (int64_t s0 = 0; s0 < S; s0 += 32) {
+        const int64_t sl = s0 + lane;
+        const int myc = sl < S ? __ldg(lab + sl) : -1;
+        const uint32_t myr = sl < S ? __ldg(sample + sl) : 0u;
+        uint32_t m = __ballot_sync(0xffffffffu, myc == c);
+        while (m) {
+            const int u = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t r = __shfl_sync(0xffffffffu, myr, u);
+            if (active) acc = __dadd_rn(acc, (double)load_elem(X, dtype, (int64_t)r * d + t));
         }
     }
-    __syncthreads();
-    if (tl < DB && t < d)
-        for (int c = 0; c < C; ++c) sums[(int64_t)c * d + t] = acc[c * DB + tl];
+    if (active) sums[(int64_t)c * d + t] = acc;
 }
 
 __global__ void k_count_labels(const int32_t* __restrict__ lab, int64_t S, int64_t* cnt) {
@@ -262,13 +257,6 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
     auto nb = [](int64_t n, int t) { return (unsigned)((n + t - 1) / t); };
     k_transpose_cent<<<nb(cd, tpb), tpb, 0, st>>>(init_centroids, C, d, w.cent, w.centT);
     ANN_CHECK_LAUNCH();
-    int DB = 32;
-    while (DB > 1 && (size_t)C * DB * sizeof(double) > 96 * 1024) DB >>= 1;
-    size_t sum_smem = (size_t)C * DB * sizeof(double);
-    if (sum_smem > 48 * 1024)
-        ANN_CHECK_CUDA(cudaFuncSetAttribute(k_kmeans_sums,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)sum_smem));
     for (int it = 0; it < iters && S > 0; ++it) {
         for (int64_t p0 = 0; p0 < S; p0 += w.chunk) {
             int64_t np = S - p0 < w.chunk ? S - p0 : w.chunk;
@@ -279,8 +267,11 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
             ANN_CHECK_LAUNCH();
         }
         ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * C, st));
-        k_kmeans_sums<<<(unsigned)((d + DB - 1) / DB), 32, sum_smem, st>>>(
-            X, dtype, d, sample_idx, S, w.lab, C, DB, w.sums);
+        {
+            const int64_t warps = (int64_t)C * ((d + 31) / 32);
+            k_kmeans_sums<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, dtype, d, sample_idx, S,
+                                                                     w.lab, C, w.sums);
+        }
         ANN_CHECK_LAUNCH();
         k_count_labels<<<nb(S, tpb) < 4096u ? nb(S, tpb) : 4096u, tpb, 0, st>>>(w.lab, S, w.cnt);
         ANN_CHECK_LAUNCH();
