@@ -72,8 +72,10 @@ __device__ __forceinline__ int shard_of(const int64_t* __restrict__ offsets, int
     return lo;
 }
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t id, int hs_mask) {
-    return (id * 2654435761u) & (uint32_t)hs_mask;
+// Shared memory of one prune warp: table keys, list, overflow list, counts,
+// overflow count, table positions, overflow positions.
+__host__ __device__ constexpr size_t prune_warp_smem(int KM) {
+    return (size_t)1024 * 4 + (size_t)KM * 12 + 16 + 1024 + (size_t)KM;
 }
 
 // ---- prune ------------------------------------------------------------------------
@@ -89,15 +91,24 @@ __device__ __forceinline__ int64_t row_in_range(const int64_t* __restrict__ star
     return -1;
 }
 
-__device__ __forceinline__ int hash_find(const uint32_t* hkey, const int32_t* hval, int hs_mask,
-                                         uint32_t x) {
-    uint32_t h = hash_slot(x, hs_mask);
-    for (;;) {
-        const uint32_t key = hkey[h];
-        if (key == x) return hval[h];
-        if (key == ANN_PAD) return -1;
-        h = (h + 1) & (uint32_t)hs_mask;
-    }
+// Position of id x in the row's list: a direct-mapped table of TS slots keyed by
+// the top bits of a multiplicative hash (one probe); ids that collide with an
+// occupied slot go to a short overflow list, scanned only when the slot holds a
+// different id and the overflow list is not empty.
+constexpr int TS = 1024, TSHIFT = 22;  // 2^(32 - TSHIFT) = TS slots
+
+__device__ __forceinline__ uint32_t tslot(uint32_t x) { return (x * 2654435761u) >> TSHIFT; }
+
+__device__ __forceinline__ int table_find(const uint32_t* tkey, const uint8_t* tpos,
+                                          const uint32_t* ovf, const uint8_t* ovf_pos, int novf,
+                                          uint32_t x) {
+    const uint32_t h = tslot(x);
+    const uint32_t key = tkey[h];
+    if (key == x) return tpos[h];
+    if (key == ANN_PAD || novf == 0) return -1;
+    for (int o = 0; o < novf; ++o)
+        if (ovf[o] == x) return ovf_pos[o];
+    return -1;
 }
 
 template <int E>  // 32*E >= k
@@ -105,16 +116,18 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                         const int64_t* __restrict__ offsets, const int64_t* __restrict__ start,
                         const int64_t* __restrict__ rowlist, int C, int64_t rows, int k, int R,
                         int rule, uint32_t* __restrict__ pr_id, float* __restrict__ pr_d) {
-    constexpr int KM = 32 * E, HS = 2 * KM;
+    constexpr int KM = 32 * E;
     extern __shared__ __align__(16) uint8_t sm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
-    uint8_t* my = sm + (size_t)wib * (KM * 4 + HS * 8 + KM * 8 + KM * 4);
-    uint32_t* list = (uint32_t*)my;
-    uint32_t* hkey = list + KM;
-    int32_t* hval = (int32_t*)(hkey + HS);
-    int64_t* nrow = (int64_t*)(hval + HS);
-    int32_t* cnt = (int32_t*)(nrow + KM);
+    uint8_t* my = sm + (size_t)wib * prune_warp_smem(KM);
+    uint32_t* tkey = (uint32_t*)my;              // [TS]
+    uint32_t* list = tkey + TS;                  // [KM]
+    uint32_t* ovf = list + KM;                   // [KM]
+    int32_t* cnt = (int32_t*)(ovf + KM);         // [KM]
+    int* novf_p = cnt + KM;                      // [1] (+pad)
+    uint8_t* tpos = (uint8_t*)(novf_p + 4);      // [TS]
+    uint8_t* ovf_pos = tpos + TS;                // [KM]
     const uint32_t lt = (1u << lane) - 1;
     const bool vec = (k & 3) == 0;
 
@@ -136,19 +149,23 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 sel[e] = j < m ? (uint32_t)j : 0xFFFFFFFFu;
             }
         } else {
-            for (int h = lane; h < HS; h += 32) hkey[h] = ANN_PAD;
+            for (int h = lane; h < TS; h += 32) tkey[h] = ANN_PAD;
             for (int j = lane; j < KM; j += 32) cnt[j] = 0;
+            if (lane == 0) *novf_p = 0;
             __syncwarp();
             for (int j = lane; j < m; j += 32) {
                 const uint32_t id = list[j];
-                uint32_t h = hash_slot(id, HS - 1);
-                for (;;) {
-                    const uint32_t prev = atomicCAS(&hkey[h], ANN_PAD, id);
-                    if (prev == ANN_PAD || prev == id) { hval[h] = j; break; }
-                    h = (h + 1) & (HS - 1);
+                const uint32_t h = tslot(id);
+                if (atomicCAS(&tkey[h], ANN_PAD, id) == ANN_PAD) {
+                    tpos[h] = (uint8_t)j;
+                } else {
+                    const int o = atomicAdd(novf_p, 1);
+                    ovf[o] = id;
+                    ovf_pos[o] = (uint8_t)j;
                 }
             }
             __syncwarp();
+            const int novf = *novf_p;
             // Lane-parallel over the neighbours v_i: each lane reads whole lists
             // (16-byte loads), so all of a row's list reads are in flight at once.
             for (int i = lane; i < m; i += 32) {
@@ -168,17 +185,14 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const int t = t0 + 4 * r + c;
-                                if (xs[c] == ANN_PAD || t >= k) continue;
-                                const int j = hash_find(hkey, hval, HS - 1, xs[c]);
+                                const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, xs[c]);
                                 if (j > i && t < j) atomicAdd(&cnt[j], 1);
                             }
                         }
                     }
                 } else {
                     for (int t = 0; t < k; ++t) {
-                        const uint32_t x = __ldg(Lw + t);
-                        if (x == ANN_PAD) continue;
-                        const int j = hash_find(hkey, hval, HS - 1, x);
+                        const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, __ldg(Lw + t));
                         if (j > i && t < j) atomicAdd(&cnt[j], 1);
                     }
                 }
@@ -448,7 +462,7 @@ int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* member
 #define ANN_PRUNE_CASE(EE)                                                                   \
     {                                                                                        \
         constexpr int KM = 32 * EE;                                                          \
-        const size_t smem = (size_t)warps * (KM * 4 + 2 * KM * 8 + KM * 8 + KM * 4);         \
+        const size_t smem = (size_t)warps * prune_warp_smem(KM);                             \
         if (smem > 48 * 1024)                                                                \
             ANN_CHECK_CUDA(cudaFuncSetAttribute(k_prune<EE>,                                 \
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
