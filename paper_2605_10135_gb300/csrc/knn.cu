@@ -12,19 +12,23 @@
 // Kernel k_knn_tiles: one CTA per 128-row block of one problem (a shard, or a
 // query batch against all vectors).  Warp roles:
 //   warp 0   : TMA producer.  The CTA's A rows (all K) stay resident in shared
-//              memory; B tiles of 128 rows stream through an NST-stage ring of
-//              16 KB stages, one 64-element K block (128-byte swizzle) per stage
-//              plus the 16-element norm block (32-byte swizzle).
-//   warp 1   : allocates 512 TMEM columns (four 128x128 FP32 accumulators) and
-//              issues tcgen05.mma (M=128, N=128, K=16) from one thread.
-//   warps 2-5: epilogue, one thread per row (TMEM lane).  16-column chunks are
+//              memory; B tiles of 256 rows stream through a ring of 32 KB stages
+//              (one 64-element K block, 128-byte swizzle) and their 16-element
+//              norm blocks through a second, small ring (32-byte swizzle).
+//   warp 1   : allocates 512 TMEM columns (two 128x256 FP32 accumulators) and
+//              issues tcgen05.mma (M=128, N=256, K=16) from one thread.  The issue
+//              of an MMA waits for room in the tensor pipe, so the thread does
+//              little else: one commit per stage and one per tile.
+//   warps 2-5: epilogue, one thread per row (TMEM lane).  32-column chunks are
 //              read with tcgen05.ld (the next chunk's load overlaps the current
-//              chunk's work), reduced with 3-input minima and skipped unless
-//              they beat the row's current k-th key.  Survivors are appended to
-//              a per-row buffer in shared memory; when any row's buffer is near
-//              full, all 32 rows of the warp insert their buffers into per-row
-//              max-heaps in lockstep (composite (key, column) order, so ties go
-//              to the smaller column = smaller global id).
+//              chunk's work) and reduced with 3-input minima; a chunk is skipped
+//              unless some row of the warp has a key at or below its current
+//              k-th key.  Surviving keys replace the root of the row's max-heap in
+//              shared memory, all 32 rows of the warp in lockstep (composite
+//              (key, global id) order, so ties go to the smaller id).
+// Rows are ordered by cell (see run_shard_knn) and each sweep starts near the
+// block's own rows, so the k-th key is tight after the first few tiles and
+// later chunks are almost always skipped.
 // Every wait is bounded; on a timeout the CTA records DEV_TIMEOUT, drains its
 // copies, frees TMEM and returns.
 //
@@ -44,32 +48,33 @@ namespace ann {
 
 namespace kt {
 constexpr int BM = 128;
-constexpr int BN = 128;
+constexpr int BN = 256;
 constexpr int KB = 64;                  // K elements per 128-byte block
 constexpr int KAUG = 16;                // norm block: 16 elements (32 bytes)
-constexpr int BLK_BYTES = 128 * 128;    // one K block of 128 rows (A or B)
-constexpr int AUG_BYTES = 128 * 32;     // one norm block of 128 rows
-constexpr int NACC = 4;
-constexpr int EPI_WARPS = 8;             // two warps per TMEM lane quarter
+constexpr int A_BLK_BYTES = BM * 128;   // one K block of the 128 A rows
+constexpr int B_BLK_BYTES = BN * 128;   // one K block of the 256 B rows
+constexpr int A_AUG_BYTES = BM * 32;
+constexpr int B_AUG_BYTES = BN * 32;
+constexpr int NAUG = 2;                 // norm-block ring depth
+constexpr int NACC = 2;
+constexpr int EPI_WARPS = 4;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BN;
-constexpr int MAX_NST = 8;
-constexpr int CAP = 32;                 // survivor buffer entries per row
+constexpr int MAX_NST = 6;
 constexpr int CELL = 1024;              // rows per pivot cell
-constexpr int WARM = 12;                // leading tiles handled by one warp per quarter
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
 enum TileCounter {
     TC_EPI_CYCLES = 0,   // epilogue threads: cycles from first wait to the end of the sweep
     TC_EPI_WAIT,         // epilogue threads: cycles waiting for a finished accumulator
-    TC_EPI_FLUSH,        // epilogue threads: cycles inside heap flushes
-    TC_CHUNKS,           // warp-level: 16-column chunks examined
-    TC_SLOW_CHUNKS,      // warp-level: chunks where some row had a survivor
-    TC_FLUSHES,          // warp-level: flush calls
+    TC_EPI_FLUSH,        // epilogue threads: cycles inserting into heaps
+    TC_CHUNKS,           // warp-level: 32-column chunks examined
+    TC_SLOW_CHUNKS,      // warp-level: chunks where some row had a candidate
+    TC_FLUSHES,          // warp-level: unused (kept for the counter layout)
     TC_FLUSH_ITERS,      // warp-level: lockstep insert iterations
     TC_INSERTS,          // thread-level: heap insertions
-    TC_APPENDS,          // thread-level: buffered survivors
+    TC_APPENDS,          // thread-level: candidates at or below the k-th key
     TC_MMA_WAIT_FULL,    // MMA thread: cycles waiting for B stages
     TC_MMA_WAIT_ACC,     // MMA thread: cycles waiting for a free accumulator
     TC_PROD_WAIT,        // producer: cycles waiting for a free stage
@@ -77,7 +82,7 @@ enum TileCounter {
     TC_CTAS,             // CTAs that ran
     TC_LD_WAIT,          // epilogue threads: cycles blocked in tcgen05.wait::ld
     TC_FILTER,           // epilogue threads: cycles in the chunk filter (min + vote)
-    TC_APPEND,           // epilogue threads: cycles appending survivors (incl. flush)
+    TC_APPEND,           // epilogue threads: cycles in the slow path
     TC_MMA_ISSUE,        // MMA thread: cycles issuing tcgen05.mma
     TC_MMA_COMMIT,       // MMA thread: cycles in tcgen05.commit
     TC_MMA_LOOP,         // MMA thread: cycles from the A wait to the end of the tile loop
@@ -99,7 +104,7 @@ struct KnnParams {
     int nkb_b;     // B k-blocks per tile
     int kprime;    // heap entries per row
     int k_out;     // entries written per row
-    int nst;       // pipeline stages
+    int nst;       // main pipeline stages
     uint32_t idesc_neg, idesc_aug;
     uint32_t* out_id;
     float* out_d;
@@ -107,28 +112,24 @@ struct KnnParams {
 };
 
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, heap, buf, cnt, locks, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, baug, heap, bars, tmem_slot, abort_flag, total;
 };
 
 __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int kprime) {
     KnnSmemLayout L;
     uint32_t o = 0;
     L.a = o;
-    o += nkb_a * kt::BLK_BYTES;
+    o += nkb_a * kt::A_BLK_BYTES;
     L.aaug = o;
-    o += 1024 * ((kt::AUG_BYTES + 1023) / 1024);
+    o += 1024 * ((kt::A_AUG_BYTES + 1023) / 1024);
     L.b = o;
-    o += nst * kt::BLK_BYTES;
+    o += nst * kt::B_BLK_BYTES;
+    L.baug = o;
+    o += kt::NAUG * kt::B_AUG_BYTES;
     L.heap = o;
     o += kprime * kt::BM * 8;
-    L.buf = o;
-    o += kt::CAP * kt::BM * 8;
-    L.cnt = o;
-    o += kt::BM * 4;
-    L.locks = o;  // 4 quarter locks, then 4 "warm-up done" flags
-    o += 8 * 4;
     L.bars = o;
-    o += (2 * kt::MAX_NST + 2 * kt::NACC + 2) * 8;
+    o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
     o += 4;
     L.abort_flag = o;
@@ -178,27 +179,8 @@ __device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
     H[e * kt::BM + row] = x;
 }
 
-// 32 lanes x 16 consecutive columns: thread t gets lane (taddr.lane + t).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
 // Wait for outstanding tcgen05.ld; the registers are tied to the wait so that no
 // use of them can be scheduled before it.
-__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-                 :
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
@@ -227,75 +209,6 @@ __device__ __forceinline__ uint64_t sdesc_sw32(uint32_t saddr) {
     return d;
 }
 
-// Per-row top-k state shared by the two epilogue warps of a TMEM lane quarter:
-// max-heap H (kp entries), survivor buffer B (CAP entries) and its fill count,
-// guarded by one lock per quarter.  Each thread keeps a private copy of the
-// row's k-th key (tau), refreshed whenever it holds the lock; a stale copy only
-// lets more columns through to the exact check.
-struct EpiState {
-    uint64_t* H;
-    uint64_t* B;
-    int* cnt;
-    int* lock;
-    volatile int* abort;
-    int row, kp;
-    bool shared;  // false while the partner warp is idle: no lock needed
-    float tau;
-    // counters (used only by the profiling instantiation)
-    unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
-    unsigned long long c_ldw, c_filter, c_append;
-};
-
-__device__ __forceinline__ void quarter_lock(EpiState& s) {
-    if (!s.shared) return;
-    if ((threadIdx.x & 31) == 0) {
-        const uint64_t t0 = globaltimer();
-        for (uint32_t it = 0;; ++it) {
-            if (atomicCAS(s.lock, 0, 1) == 0) break;
-            __nanosleep(64);
-            if ((it & 63u) == 63u && globaltimer() - t0 > 1000000000ull) {
-                *s.abort = 1;  // cannot happen unless a holder died; give up the lock
-                break;
-            }
-        }
-        __threadfence_block();
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ void quarter_unlock(EpiState& s) {
-    if (!s.shared) return;
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        __threadfence_block();
-        atomicExch(s.lock, 0);
-    }
-}
-
-// Insert every buffered survivor of the warp's 32 rows into their heaps (lock held).
-template <bool PROF>
-__device__ __forceinline__ int epi_flush(EpiState& s, int c) {
-    long long t0 = 0;
-    if (PROF) t0 = clock64();
-    const int mx = __reduce_max_sync(0xffffffffu, c);
-    for (int q = 0; q < mx; ++q) {
-        if (q < c) {
-            const uint64_t x = s.B[q * kt::BM + s.row];
-            if (x < s.H[s.row]) {
-                heap_replace_root(s.H, s.row, s.kp, x);
-                if (PROF) ++s.c_ins;
-            }
-        }
-    }
-    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
-    if (PROF) {
-        s.c_flush_cyc += clock64() - t0;
-        ++s.c_flushes;
-        s.c_iters += mx;
-    }
-    return 0;
-}
-
 __device__ __forceinline__ float min32(const float (&k)[32]) {
     float a[11];
 #pragma unroll
@@ -305,6 +218,16 @@ __device__ __forceinline__ float min32(const float (&k)[32]) {
     const float b2 = min3f(a[6], a[7], a[8]), b3 = fminf(a[9], a[10]);
     return fminf(min3f(b0, b1, b2), b3);
 }
+
+// Per-row state of one epilogue thread.
+struct EpiState {
+    uint64_t* H;  // max-heap of kp entries, strided by BM
+    int row, kp;
+    float tau;    // key of the heap root (the row's current k-th)
+    // counters (used only by the profiling instantiation)
+    unsigned long long c_ins_cyc, c_chunks, c_slow, c_iters, c_ins, c_cand;
+    unsigned long long c_ldw, c_filter, c_slowcyc;
+};
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
 // (every comparison with NaN is false, and the minimum skips NaN).
@@ -340,26 +263,26 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     const int lane = threadIdx.x & 31;
     uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
     if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
-    quarter_lock(s);
-    int c = s.cnt[s.row];
-    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
+    // Lockstep over the chunk's columns: each column some row may take is
+    // inserted by every row that takes it (one heap replacement each).
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        if (__any_sync(0xffffffffu, c > kt::CAP - 16)) c = epi_flush<PROF>(s, c);
-#pragma unroll
-        for (int uu = 0; uu < 16; ++uu) {
-            const int u = half * 16 + uu;
-            const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
-            if (key[u] <= s.tau) {
-                s.B[c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
-                ++c;
-                if (PROF) ++s.c_app;
+    for (int u = 0; u < 32; ++u) {
+        const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
+        const bool cand = key[u] <= s.tau;
+        if (__any_sync(0xffffffffu, cand)) {
+            if (PROF) ++s.c_iters;
+            if (cand) {
+                if (PROF) ++s.c_cand;
+                const uint64_t x = ((uint64_t)f2ord(key[u]) << 32) | g;
+                if (x < s.H[s.row]) {
+                    heap_replace_root(s.H, s.row, s.kp, x);
+                    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
+                    if (PROF) ++s.c_ins;
+                }
             }
         }
     }
-    s.cnt[s.row] = c;
-    quarter_unlock(s);
-    if (PROF) s.c_append += clock64() - f0;
+    if (PROF) s.c_slowcyc += clock64() - f0;
 }
 
 __device__ __forceinline__ void prof_add(int which, unsigned long long v) {
@@ -388,13 +311,12 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     const int rb = (int)(bid - P.blk_off[lo]);
     const int ntiles = (pr.n_cols + kt::BN - 1) / kt::BN;
     // Sweep order: tile t0, t0+1, ... wrapping around.  With local_first the sweep
-    // starts a few tiles before the block's own rows (rows are ordered by cell),
-    // so each row's k-th key tightens early.
+    // starts near the block's own rows (rows are ordered by cell), so each row's
+    // k-th key tightens early.
     int t0 = 0;
     if (P.local_first) {
-        t0 = (rb * kt::BM) / kt::BN - 4;
-        if (t0 < 0) t0 = 0;
-        if (t0 >= ntiles) t0 = 0;
+        t0 = (rb * kt::BM - 512) / kt::BN;
+        if (t0 < 0 || t0 >= ntiles) t0 = 0;
     }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -402,9 +324,11 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     const uint32_t sA = smem_u32(base + L.a);
     const uint32_t sAaug = smem_u32(base + L.aaug);
     const uint32_t sB = smem_u32(base + L.b);
+    const uint32_t sBaug = smem_u32(base + L.baug);
     const uint32_t bars = smem_u32(base + L.bars);
     const uint32_t full_bar = bars, empty_bar = bars + kt::MAX_NST * 8;
-    const uint32_t accf_bar = bars + 2 * kt::MAX_NST * 8;
+    const uint32_t afull_bar = bars + 2 * kt::MAX_NST * 8, aempty_bar = afull_bar + kt::NAUG * 8;
+    const uint32_t accf_bar = aempty_bar + kt::NAUG * 8;
     const uint32_t acce_bar = accf_bar + kt::NACC * 8;
     const uint32_t a_bar = acce_bar + kt::NACC * 8, done_bar = a_bar + 8;
     volatile uint32_t* tmem_slot = (volatile uint32_t*)(base + L.tmem_slot);
@@ -417,6 +341,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         for (int s = 0; s < P.nst; ++s) {
             mbar_init(full_bar + 8 * s, 1);
             mbar_init(empty_bar + 8 * s, 1);
+        }
+        for (int s = 0; s < kt::NAUG; ++s) {
+            mbar_init(afull_bar + 8 * s, 1);
+            mbar_init(aempty_bar + 8 * s, 1);
         }
         for (int a = 0; a < kt::NACC; ++a) {
             mbar_init(accf_bar + 8 * a, 1);
@@ -431,22 +359,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         tmem_alloc(smem_u32((const void*)tmem_slot), kt::TMEM_COLS);
         tmem_relinquish();
     }
-    if (warp >= 2 && warp < 6) {  // heaps, survivor counts and quarter locks
-        uint64_t* H = (uint64_t*)(base + L.heap);
-        const int row = (warp & 3) * 32 + lane;
-        const uint64_t init = heap_init_val();
-        for (int e = 0; e < P.kprime; ++e) H[e * kt::BM + row] = init;
-        ((int*)(base + L.cnt))[row] = 0;
-        if (lane == 0) {
-            ((int*)(base + L.locks))[warp & 3] = 0;
-            ((int*)(base + L.locks))[4 + (warp & 3)] = 0;
-        }
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int loads_per_tile = P.nkb_b + 1;
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
@@ -456,41 +372,45 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             tma_prefetch_desc(&tmAaug);
             tma_prefetch_desc(&tmBaug);
             const int a_y = (int)(pr.a_row0 + (int64_t)rb * kt::BM);
-            mbar_expect_tx(a_bar, P.nkb_a * kt::BLK_BYTES + kt::AUG_BYTES);
+            mbar_expect_tx(a_bar, P.nkb_a * kt::A_BLK_BYTES + kt::A_AUG_BYTES);
             for (int b = 0; b < P.nkb_a; ++b)
-                tma_load_2d(sA + b * kt::BLK_BYTES, &tmA, a_bar, b * kt::KB, a_y);
+                tma_load_2d(sA + b * kt::A_BLK_BYTES, &tmA, a_bar, b * kt::KB, a_y);
             tma_load_2d(sAaug, &tmAaug, a_bar, 0, 0);
-            uint32_t last_par = 0, used = 0;
-            int st = 0;
-            uint32_t ph = 0;
+            uint32_t last_par = 0, used = 0, alast_par = 0, aused = 0;
+            int st = 0, sa = 0;
+            uint32_t ph = 0, aph = 0;
             bool ok = true;
             unsigned long long prod_wait = 0;
             for (int tt = 0; tt < ntiles && ok; ++tt) {
                 const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
-                for (int j = 0; j < loads_per_tile; ++j) {
+                for (int j = 0; j < P.nkb_b; ++j) {
                     long long w0 = 0;
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
                     if (PROF) prod_wait += clock64() - w0;
-                    const uint32_t dst = sB + st * kt::BLK_BYTES;
-                    if (j < P.nkb_b) {
-                        mbar_expect_tx(full_bar + 8 * st, kt::BLK_BYTES);
-                        tma_load_2d(dst, &tmB, full_bar + 8 * st, j * kt::KB, b_y);
-                    } else {
-                        mbar_expect_tx(full_bar + 8 * st, kt::AUG_BYTES);
-                        tma_load_2d(dst, &tmBaug, full_bar + 8 * st, 0, b_y);
-                    }
+                    mbar_expect_tx(full_bar + 8 * st, kt::B_BLK_BYTES);
+                    tma_load_2d(sB + st * kt::B_BLK_BYTES, &tmB, full_bar + 8 * st, j * kt::KB, b_y);
                     used |= 1u << st;
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
                 }
+                if (!ok) break;
+                if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(afull_bar + 8 * sa, kt::B_AUG_BYTES);
+                tma_load_2d(sBaug + sa * kt::B_AUG_BYTES, &tmBaug, afull_bar + 8 * sa, 0, b_y);
+                aused |= 1u << sa;
+                alast_par = (alast_par & ~(1u << sa)) | (aph << sa);
+                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
             }
             // Drain: every issued copy must land before the CTA may exit.
             int dummy = 0;
             for (int s = 0; s < P.nst; ++s)
                 if (used >> s & 1)
                     mbar_wait(full_bar + 8 * s, (last_par >> s) & 1, &dummy, 200000000ull);
+            for (int s = 0; s < kt::NAUG; ++s)
+                if (aused >> s & 1)
+                    mbar_wait(afull_bar + 8 * s, (alast_par >> s) & 1, &dummy, 200000000ull);
             mbar_wait(a_bar, 0, &dummy, 200000000ull);
             if (!ok) atomicOr(P.status, DEV_TIMEOUT);
             if (PROF) prof_add(TC_PROD_WAIT, prod_wait);
@@ -500,8 +420,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (lane == 0) {
             bool ok = mbar_wait(a_bar, 0, abort_flag);
             tc_fence_after();
-            int st = 0;
-            uint32_t ph = 0;
+            int st = 0, sa = 0;
+            uint32_t ph = 0, aph = 0;
             const int H2 = P.nkb_b >> 1;
             unsigned long long w_full = 0, w_acc = 0, c_iss = 0, c_com = 0;
             long long loop0 = 0;
@@ -518,37 +438,32 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + a * kt::BN;
                 uint32_t accum = 0;
-                for (int j = 0; j < loads_per_tile; ++j) {
+                for (int j = 0; j < P.nkb_b; ++j) {
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(full_bar + 8 * st, ph, abort_flag)) { ok = false; break; }
                     if (PROF) w_full += clock64() - w0;
                     tc_fence_after();
                     if (PROF) w0 = clock64();
-                    const uint32_t bsm = sB + st * kt::BLK_BYTES;
-                    if (j < P.nkb_b) {
-                        int ablk[2];
-                        int na = 1;
-                        if (P.mode == 0) {
-                            ablk[0] = j;
-                        } else if (j < H2) {
-                            ablk[0] = j;       // hi . hi
-                            ablk[1] = H2 + j;  // lo . hi
-                            na = 2;
-                        } else {
-                            ablk[0] = j - H2;  // hi . lo
-                        }
-                        for (int q = 0; q < na; ++q) {
-                            const uint32_t asm_ = sA + ablk[q] * kt::BLK_BYTES;
-#pragma unroll
-                            for (int s = 0; s < kt::KB / 16; ++s) {
-                                umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
-                                         sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
-                                accum = 1;
-                            }
-                        }
+                    const uint32_t bsm = sB + st * kt::B_BLK_BYTES;
+                    int ablk[2];
+                    int na = 1;
+                    if (P.mode == 0) {
+                        ablk[0] = j;
+                    } else if (j < H2) {
+                        ablk[0] = j;       // hi . hi
+                        ablk[1] = H2 + j;  // lo . hi
+                        na = 2;
                     } else {
-                        umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(bsm), P.idesc_aug, accum);
-                        accum = 1;
+                        ablk[0] = j - H2;  // hi . lo
+                    }
+                    for (int q = 0; q < na; ++q) {
+                        const uint32_t asm_ = sA + ablk[q] * kt::A_BLK_BYTES;
+#pragma unroll
+                        for (int s = 0; s < kt::KB / 16; ++s) {
+                            umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
+                                     P.idesc_neg, accum);
+                            accum = 1;
+                        }
                     }
                     long long w1 = 0;
                     if (PROF) {
@@ -560,6 +475,14 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (++st == P.nst) { st = 0; ph ^= 1; }
                 }
                 if (!ok) break;
+                if (PROF) w0 = clock64();
+                if (!mbar_wait(afull_bar + 8 * sa, aph, abort_flag)) { ok = false; break; }
+                if (PROF) w_full += clock64() - w0;
+                tc_fence_after();
+                umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(sBaug + sa * kt::B_AUG_BYTES),
+                         P.idesc_aug, accum);
+                umma_commit(aempty_bar + 8 * sa);
+                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
                 umma_commit(accf_bar + 8 * a);
             }
             if (PROF) {
@@ -578,22 +501,16 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
-        // Warp (q, h): TMEM lane quarter q (rows 32q..32q+31), columns
-        // [64h, 64h + 64) of every tile.
-        const int q = warp & 3;
-        const int h = (warp - 2) >> 2;
+        const int q = warp & 3;  // TMEM lane quarter this warp may access
         EpiState s;
         s.row = q * 32 + lane;
         s.H = (uint64_t*)(base + L.heap);
-        s.B = (uint64_t*)(base + L.buf);
-        s.cnt = (int*)(base + L.cnt);
-        s.lock = (int*)(base + L.locks) + q;
-        s.abort = abort_flag;
         s.kp = P.kprime;
-        s.shared = false;
         s.tau = INFINITY;
-        s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
-        s.c_ldw = s.c_filter = s.c_append = 0;
+        s.c_ins_cyc = s.c_chunks = s.c_slow = s.c_iters = s.c_ins = s.c_cand = 0;
+        s.c_ldw = s.c_filter = s.c_slowcyc = 0;
+        const uint64_t init = heap_init_val();
+        for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
@@ -610,59 +527,31 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
-            // The first WARM tiles (the row block's own cell, where most chunks hold
-            // survivors) are handled by warp h = 0 alone and without locking; after
-            // that the two warps take one column half each.
-            const bool warm = tt < kt::WARM;
-            if (tt == kt::WARM) {
-                // hand-over: warp h = 1 starts only after h = 0 has finished the
-                // lock-free warm-up tiles (bounded wait on a shared-memory flag)
-                volatile int* done = (volatile int*)(base + L.locks) + 4 + q;
-                if (h == 0) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        __threadfence_block();
-                        *done = 1;
-                    }
-                } else {
-                    if (lane == 0) {
-                        const uint64_t w0 = globaltimer();
-                        while (*done == 0) {
-                            if (*abort_flag) { ok = false; break; }
-                            if (globaltimer() - w0 > 2000000000ull) {
-                                *abort_flag = 1;
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(128);
-                        }
-                        __threadfence_block();
-                    }
-                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                    if (!ok) break;
-                }
-                s.shared = true;
-            }
-            for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
-                const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * 64;
-                const int jt = t * kt::BN + hh * 64;
-                const bool edge = (jt + 64 > pr.n_cols) ||
-                                  (P.self_exclude && i0 + 32 > jt && i0 < jt + 64);
-                uint32_t va[32], vb[32];
-                __syncwarp();
-                tmem_ld32(tb, va);
+            const uint32_t tb = tmem + lane_addr + a * kt::BN;
+            const int jt = t * kt::BN;
+            const bool edge = (jt + kt::BN > pr.n_cols) ||
+                              (P.self_exclude && i0 + 32 > jt && i0 < jt + kt::BN);
+            uint32_t va[32], vb[32];
+            __syncwarp();
+            tmem_ld32(tb, va);
+#pragma unroll
+            for (int c = 0; c < kt::BN / 32; c += 2) {
                 long long l0 = 0;
                 if (PROF) l0 = clock64();
                 tmem_wait_ld32(va);
                 if (PROF) s.c_ldw += clock64() - l0;
-                tmem_ld32(tb + 32, vb);
-                if (jt < pr.n_cols)
-                    epi_chunk<PROF>(s, va, jt, i, pr.n_cols, P.self_exclude, edge, gidrow);
+                tmem_ld32(tb + (c + 1) * 32, vb);
+                if (jt + c * 32 < pr.n_cols)
+                    epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
+                __syncwarp();
                 if (PROF) l0 = clock64();
                 tmem_wait_ld32(vb);
                 if (PROF) s.c_ldw += clock64() - l0;
-                if (jt + 32 < pr.n_cols)
-                    epi_chunk<PROF>(s, vb, jt + 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
+                if (c + 2 < kt::BN / 32) tmem_ld32(tb + (c + 2) * 32, va);
+                if (jt + (c + 1) * 32 < pr.n_cols)
+                    epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude, edge,
+                                    gidrow);
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -671,49 +560,42 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (PROF) {
             prof_add_warp(TC_EPI_CYCLES, (unsigned long long)(clock64() - e_t0));
             prof_add_warp(TC_EPI_WAIT, e_wait);
-            prof_add_warp(TC_EPI_FLUSH, s.c_flush_cyc);
             prof_add_warp(TC_INSERTS, s.c_ins);
-            prof_add_warp(TC_APPENDS, s.c_app);
+            prof_add_warp(TC_APPENDS, s.c_cand);
             prof_add_warp(TC_LD_WAIT, s.c_ldw);
             prof_add_warp(TC_FILTER, s.c_filter);
-            prof_add_warp(TC_APPEND, s.c_append);
+            prof_add_warp(TC_APPEND, s.c_slowcyc);
             if (lane == 0) {
                 prof_add(TC_CHUNKS, s.c_chunks);
                 prof_add(TC_SLOW_CHUNKS, s.c_slow);
-                prof_add(TC_FLUSHES, s.c_flushes);
                 prof_add(TC_FLUSH_ITERS, s.c_iters);
             }
         }
-        // both warps of the quarter are done with the rows: h = 0 finishes them
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(64) : "memory");
-        if (!ok || *abort_flag) {
-            if (h == 0 && lane == 0) atomicOr(P.status, DEV_TIMEOUT);
-        } else if (h == 0) {
-            epi_flush<false>(s, s.cnt[s.row]);
-            if (i < pr.n_rows) {
-                // Heap sort ascending, then write (global id, |x|^2 + 2 key).
-                uint64_t* H = s.H;
-                const int row = s.row, kp = s.kp;
-                for (int end = kp - 1; end > 0; --end) {
-                    const uint64_t top = H[row];
-                    H[row] = H[end * kt::BM + row];
-                    H[end * kt::BM + row] = top;
-                    heap_sift(H, row, 0, end);
+        if (!ok) {
+            atomicOr(P.status, DEV_TIMEOUT);
+        } else if (i < pr.n_rows) {
+            // Heap sort ascending, then write (global id, |x|^2 + 2 key).
+            uint64_t* H = s.H;
+            const int row = s.row, kp = s.kp;
+            for (int end = kp - 1; end > 0; --end) {
+                const uint64_t top = H[row];
+                H[row] = H[end * kt::BM + row];
+                H[end * kt::BM + row] = top;
+                heap_sift(H, row, 0, end);
+            }
+            const float nx = P.na[pr.a_row0 + i];
+            const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
+            for (int e = 0; e < P.k_out; ++e) {
+                const uint64_t x = H[e * kt::BM + row];
+                const uint32_t g = (uint32_t)x;  // global id (or column index)
+                uint32_t id = ANN_PAD;
+                float dd = INFINITY;
+                if (g != 0xFFFFFFFFu) {
+                    id = g;
+                    dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
                 }
-                const float nx = P.na[pr.a_row0 + i];
-                const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
-                for (int e = 0; e < P.k_out; ++e) {
-                    const uint64_t x = H[e * kt::BM + row];
-                    const uint32_t g = (uint32_t)x;  // global id (or column index)
-                    uint32_t id = ANN_PAD;
-                    float dd = INFINITY;
-                    if (g != 0xFFFFFFFFu) {
-                        id = g;
-                        dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
-                    }
-                    P.out_id[orow * P.k_out + e] = id;
-                    P.out_d[orow * P.k_out + e] = dd;
-                }
+                P.out_id[orow * P.k_out + e] = id;
+                P.out_d[orow * P.k_out + e] = dd;
             }
         }
     }
@@ -1105,7 +987,7 @@ int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl) {
     if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
     const size_t cap = 227 * 1024;
     p.nst = 0;
-    for (int nst = kt::MAX_NST; nst >= 3; --nst) {
+    for (int nst = kt::MAX_NST; nst >= 2; --nst) {
         if (knn_smem_layout(p.nkb_a, nst, p.kprime).total <= cap) { p.nst = nst; break; }
     }
     if (!p.nst)
@@ -1154,7 +1036,8 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
     int rc = make_tmap(&ta, GA, rowsA, pl.Kp, kt::KB, kt::BM, CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = make_tmap(&tb, GB, rowsB, pl.Kp, kt::KB, kt::BN, CU_TENSOR_MAP_SWIZZLE_128B);
     if (!rc) rc = make_tmap(&taa, ones, 128, kt::KAUG, kt::KAUG, kt::BM, CU_TENSOR_MAP_SWIZZLE_32B);
-    if (!rc) rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!rc)
+        rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
     const bool prof = timed && tile_counters_on();
     auto kern = prof ? k_knn_tiles<true> : k_knn_tiles<false>;
