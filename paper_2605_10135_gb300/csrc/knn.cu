@@ -55,9 +55,11 @@ constexpr int A_BLK_BYTES = BM * 128;   // one K block of the 128 A rows
 constexpr int B_BLK_BYTES = BN * 128;   // one K block of the 256 B rows
 constexpr int A_AUG_BYTES = BM * 32;
 constexpr int B_AUG_BYTES = BN * 32;
-constexpr int NAUG = 2;                 // norm-block ring depth
+constexpr int NAUG = 1;                 // norm-block slots (loaded first in each tile)
 constexpr int NACC = 2;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
+constexpr int CAP = 16;                 // survivor buffer entries per row
+constexpr int WARM = 6;                 // leading tiles handled by one warp per quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BN;
 constexpr int MAX_NST = 6;
@@ -68,13 +70,13 @@ constexpr int CELL = 1024;              // rows per pivot cell
 enum TileCounter {
     TC_EPI_CYCLES = 0,   // epilogue threads: cycles from first wait to the end of the sweep
     TC_EPI_WAIT,         // epilogue threads: cycles waiting for a finished accumulator
-    TC_EPI_FLUSH,        // epilogue threads: cycles inserting into heaps
+    TC_EPI_FLUSH,        // epilogue threads: cycles inside heap flushes
     TC_CHUNKS,           // warp-level: 32-column chunks examined
     TC_SLOW_CHUNKS,      // warp-level: chunks where some row had a candidate
-    TC_FLUSHES,          // warp-level: unused (kept for the counter layout)
+    TC_FLUSHES,          // warp-level: flush calls
     TC_FLUSH_ITERS,      // warp-level: lockstep insert iterations
     TC_INSERTS,          // thread-level: heap insertions
-    TC_APPENDS,          // thread-level: candidates at or below the k-th key
+    TC_APPENDS,          // thread-level: buffered survivors
     TC_MMA_WAIT_FULL,    // MMA thread: cycles waiting for B stages
     TC_MMA_WAIT_ACC,     // MMA thread: cycles waiting for a free accumulator
     TC_PROD_WAIT,        // producer: cycles waiting for a free stage
@@ -82,7 +84,7 @@ enum TileCounter {
     TC_CTAS,             // CTAs that ran
     TC_LD_WAIT,          // epilogue threads: cycles blocked in tcgen05.wait::ld
     TC_FILTER,           // epilogue threads: cycles in the chunk filter (min + vote)
-    TC_APPEND,           // epilogue threads: cycles in the slow path
+    TC_APPEND,           // epilogue threads: cycles appending survivors (incl. flush)
     TC_MMA_ISSUE,        // MMA thread: cycles issuing tcgen05.mma
     TC_MMA_COMMIT,       // MMA thread: cycles in tcgen05.commit
     TC_MMA_LOOP,         // MMA thread: cycles from the A wait to the end of the tile loop
@@ -112,7 +114,7 @@ struct KnnParams {
 };
 
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, baug, heap, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, baug, heap, buf, cnt, locks, bars, tmem_slot, abort_flag, total;
 };
 
 __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int kprime) {
@@ -128,6 +130,12 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     o += kt::NAUG * kt::B_AUG_BYTES;
     L.heap = o;
     o += kprime * kt::BM * 8;
+    L.buf = o;
+    o += kt::CAP * kt::BM * 8;
+    L.cnt = o;
+    o += kt::BM * 4;
+    L.locks = o;  // 4 quarter locks, then 4 "warm-up done" flags
+    o += 8 * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -219,15 +227,74 @@ __device__ __forceinline__ float min32(const float (&k)[32]) {
     return fminf(min3f(b0, b1, b2), b3);
 }
 
-// Per-row state of one epilogue thread.
+// Per-row top-k state shared by the two epilogue warps of a TMEM lane quarter:
+// max-heap H (kp entries), survivor buffer B (CAP entries) and its fill count,
+// guarded by one lock per quarter.  Each thread keeps a private copy of the
+// row's k-th key (tau), refreshed whenever it holds the lock; a stale copy only
+// lets more columns through to the exact check.
 struct EpiState {
-    uint64_t* H;  // max-heap of kp entries, strided by BM
+    uint64_t* H;
+    uint64_t* B;
+    int* cnt;
+    int* lock;
+    volatile int* abort;
     int row, kp;
-    float tau;    // key of the heap root (the row's current k-th)
+    bool shared;  // false while the partner warp is idle: no lock needed
+    float tau;
     // counters (used only by the profiling instantiation)
-    unsigned long long c_ins_cyc, c_chunks, c_slow, c_iters, c_ins, c_cand;
-    unsigned long long c_ldw, c_filter, c_slowcyc;
+    unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
+    unsigned long long c_ldw, c_filter, c_append;
 };
+
+__device__ __forceinline__ void quarter_lock(EpiState& s) {
+    if (!s.shared) return;
+    if ((threadIdx.x & 31) == 0) {
+        const uint64_t t0 = globaltimer();
+        for (uint32_t it = 0;; ++it) {
+            if (atomicCAS(s.lock, 0, 1) == 0) break;
+            __nanosleep(64);
+            if ((it & 63u) == 63u && globaltimer() - t0 > 1000000000ull) {
+                *s.abort = 1;  // cannot happen unless a holder died; give up the lock
+                break;
+            }
+        }
+        __threadfence_block();
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void quarter_unlock(EpiState& s) {
+    if (!s.shared) return;
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        atomicExch(s.lock, 0);
+    }
+}
+
+// Insert every buffered survivor of the warp's 32 rows into their heaps.
+template <bool PROF>
+__device__ __forceinline__ int epi_flush(EpiState& s, int c) {
+    long long t0 = 0;
+    if (PROF) t0 = clock64();
+    const int mx = __reduce_max_sync(0xffffffffu, c);
+    for (int q = 0; q < mx; ++q) {
+        if (q < c) {
+            const uint64_t x = s.B[q * kt::BM + s.row];
+            if (x < s.H[s.row]) {
+                heap_replace_root(s.H, s.row, s.kp, x);
+                if (PROF) ++s.c_ins;
+            }
+        }
+    }
+    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
+    if (PROF) {
+        s.c_flush_cyc += clock64() - t0;
+        ++s.c_flushes;
+        s.c_iters += mx;
+    }
+    return 0;
+}
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
 // (every comparison with NaN is false, and the minimum skips NaN).
@@ -263,26 +330,26 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     const int lane = threadIdx.x & 31;
     uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
     if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
-    // Lockstep over the chunk's columns: each column some row may take is
-    // inserted by every row that takes it (one heap replacement each).
+    quarter_lock(s);
+    int c = s.cnt[s.row];
+    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
-        const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
-        const bool cand = key[u] <= s.tau;
-        if (__any_sync(0xffffffffu, cand)) {
-            if (PROF) ++s.c_iters;
-            if (cand) {
-                if (PROF) ++s.c_cand;
-                const uint64_t x = ((uint64_t)f2ord(key[u]) << 32) | g;
-                if (x < s.H[s.row]) {
-                    heap_replace_root(s.H, s.row, s.kp, x);
-                    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
-                    if (PROF) ++s.c_ins;
-                }
+    for (int half = 0; half < 2; ++half) {
+        if (__any_sync(0xffffffffu, c > kt::CAP - 16)) c = epi_flush<PROF>(s, c);
+#pragma unroll
+        for (int uu = 0; uu < 16; ++uu) {
+            const int u = half * 16 + uu;
+            const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
+            if (key[u] <= s.tau) {
+                s.B[c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
+                ++c;
+                if (PROF) ++s.c_app;
             }
         }
     }
-    if (PROF) s.c_slowcyc += clock64() - f0;
+    s.cnt[s.row] = c;
+    quarter_unlock(s);
+    if (PROF) s.c_append += clock64() - f0;
 }
 
 __device__ __forceinline__ void prof_add(int which, unsigned long long v) {
@@ -359,6 +426,17 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         tmem_alloc(smem_u32((const void*)tmem_slot), kt::TMEM_COLS);
         tmem_relinquish();
     }
+    if (warp >= 2 && warp < 6) {  // heaps, survivor counts, quarter locks and flags
+        uint64_t* H = (uint64_t*)(base + L.heap);
+        const int row = (warp & 3) * 32 + lane;
+        const uint64_t init = heap_init_val();
+        for (int e = 0; e < P.kprime; ++e) H[e * kt::BM + row] = init;
+        ((int*)(base + L.cnt))[row] = 0;
+        if (lane == 0) {
+            ((int*)(base + L.locks))[warp & 3] = 0;
+            ((int*)(base + L.locks))[4 + (warp & 3)] = 0;
+        }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -384,6 +462,13 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             for (int tt = 0; tt < ntiles && ok; ++tt) {
                 const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
+                // the norm block first: its MMA opens the tile, so the slot frees early
+                if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(afull_bar + 8 * sa, kt::B_AUG_BYTES);
+                tma_load_2d(sBaug + sa * kt::B_AUG_BYTES, &tmBaug, afull_bar + 8 * sa, 0, b_y);
+                aused |= 1u << sa;
+                alast_par = (alast_par & ~(1u << sa)) | (aph << sa);
+                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
                 for (int j = 0; j < P.nkb_b; ++j) {
                     long long w0 = 0;
                     if (PROF) w0 = clock64();
@@ -395,13 +480,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
                 }
-                if (!ok) break;
-                if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
-                mbar_expect_tx(afull_bar + 8 * sa, kt::B_AUG_BYTES);
-                tma_load_2d(sBaug + sa * kt::B_AUG_BYTES, &tmBaug, afull_bar + 8 * sa, 0, b_y);
-                aused |= 1u << sa;
-                alast_par = (alast_par & ~(1u << sa)) | (aph << sa);
-                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
             }
             // Drain: every issued copy must land before the CTA may exit.
             int dummy = 0;
@@ -437,7 +515,16 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 if (PROF) w_acc += clock64() - w0;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + a * kt::BN;
-                uint32_t accum = 0;
+                // D = [1,1,1,0..] . [h,m,l,0..] (= |y|^2 / 2), then D -= x . y
+                if (PROF) w0 = clock64();
+                if (!mbar_wait(afull_bar + 8 * sa, aph, abort_flag)) { ok = false; break; }
+                if (PROF) w_full += clock64() - w0;
+                tc_fence_after();
+                umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(sBaug + sa * kt::B_AUG_BYTES),
+                         P.idesc_aug, 0);
+                umma_commit(aempty_bar + 8 * sa);
+                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
+                const uint32_t accum = 1;
                 for (int j = 0; j < P.nkb_b; ++j) {
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(full_bar + 8 * st, ph, abort_flag)) { ok = false; break; }
@@ -462,7 +549,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                         for (int s = 0; s < kt::KB / 16; ++s) {
                             umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
                                      P.idesc_neg, accum);
-                            accum = 1;
                         }
                     }
                     long long w1 = 0;
@@ -475,14 +561,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (++st == P.nst) { st = 0; ph ^= 1; }
                 }
                 if (!ok) break;
-                if (PROF) w0 = clock64();
-                if (!mbar_wait(afull_bar + 8 * sa, aph, abort_flag)) { ok = false; break; }
-                if (PROF) w_full += clock64() - w0;
-                tc_fence_after();
-                umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(sBaug + sa * kt::B_AUG_BYTES),
-                         P.idesc_aug, accum);
-                umma_commit(aempty_bar + 8 * sa);
-                if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
                 umma_commit(accf_bar + 8 * a);
             }
             if (PROF) {
@@ -501,16 +579,22 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         }
     } else {
         // -------------------------------------------------------- epilogue
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        // Warp (q, h): TMEM lane quarter q (rows 32q..32q+31), columns
+        // [128h, 128h + 128) of every tile.
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         EpiState s;
         s.row = q * 32 + lane;
         s.H = (uint64_t*)(base + L.heap);
+        s.B = (uint64_t*)(base + L.buf);
+        s.cnt = (int*)(base + L.cnt);
+        s.lock = (int*)(base + L.locks) + q;
+        s.abort = abort_flag;
         s.kp = P.kprime;
+        s.shared = false;
         s.tau = INFINITY;
-        s.c_ins_cyc = s.c_chunks = s.c_slow = s.c_iters = s.c_ins = s.c_cand = 0;
-        s.c_ldw = s.c_filter = s.c_slowcyc = 0;
-        const uint64_t init = heap_init_val();
-        for (int e = 0; e < s.kp; ++e) s.H[e * kt::BM + s.row] = init;
+        s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
+        s.c_ldw = s.c_filter = s.c_append = 0;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
@@ -519,6 +603,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
+        constexpr int HALF = kt::BN / 2;
         for (int tt = 0; tt < ntiles; ++tt) {
             const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
             const int a = tt % kt::NACC;
@@ -527,31 +612,67 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
-            const uint32_t tb = tmem + lane_addr + a * kt::BN;
-            const int jt = t * kt::BN;
-            const bool edge = (jt + kt::BN > pr.n_cols) ||
-                              (P.self_exclude && i0 + 32 > jt && i0 < jt + kt::BN);
-            uint32_t va[32], vb[32];
-            __syncwarp();
-            tmem_ld32(tb, va);
+            // The first WARM tiles (the row block's own cell, where most chunks hold
+            // survivors) are handled by warp h = 0 alone and without locking; after
+            // that the two warps take one column half each.
+            const bool warm = tt < kt::WARM;
+            if (tt == kt::WARM) {
+                // hand-over: warp h = 1 starts only after h = 0 has finished the
+                // lock-free warm-up tiles (bounded wait on a shared-memory flag)
+                volatile int* done = (volatile int*)(base + L.locks) + 4 + q;
+                if (h == 0) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        *done = 1;
+                    }
+                } else {
+                    if (lane == 0) {
+                        const uint64_t wt = globaltimer();
+                        while (*done == 0) {
+                            if (*abort_flag) { ok = false; break; }
+                            if (globaltimer() - wt > 2000000000ull) {
+                                *abort_flag = 1;
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(128);
+                        }
+                        __threadfence_block();
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
+                }
+                s.shared = true;
+            }
+            for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
+                const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * HALF;
+                const int jt = t * kt::BN + hh * HALF;
+                const bool edge = (jt + HALF > pr.n_cols) ||
+                                  (P.self_exclude && i0 + 32 > jt && i0 < jt + HALF);
+                uint32_t va[32], vb[32];
+                __syncwarp();
+                tmem_ld32(tb, va);
 #pragma unroll
-            for (int c = 0; c < kt::BN / 32; c += 2) {
-                long long l0 = 0;
-                if (PROF) l0 = clock64();
-                tmem_wait_ld32(va);
-                if (PROF) s.c_ldw += clock64() - l0;
-                tmem_ld32(tb + (c + 1) * 32, vb);
-                if (jt + c * 32 < pr.n_cols)
-                    epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge, gidrow);
-                __syncwarp();
-                if (PROF) l0 = clock64();
-                tmem_wait_ld32(vb);
-                if (PROF) s.c_ldw += clock64() - l0;
-                if (c + 2 < kt::BN / 32) tmem_ld32(tb + (c + 2) * 32, va);
-                if (jt + (c + 1) * 32 < pr.n_cols)
-                    epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude, edge,
-                                    gidrow);
-                __syncwarp();
+                for (int c = 0; c < HALF / 32; c += 2) {
+                    long long l0 = 0;
+                    if (PROF) l0 = clock64();
+                    tmem_wait_ld32(va);
+                    if (PROF) s.c_ldw += clock64() - l0;
+                    tmem_ld32(tb + (c + 1) * 32, vb);
+                    if (jt + c * 32 < pr.n_cols)
+                        epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge,
+                                        gidrow);
+                    __syncwarp();
+                    if (PROF) l0 = clock64();
+                    tmem_wait_ld32(vb);
+                    if (PROF) s.c_ldw += clock64() - l0;
+                    if (c + 2 < HALF / 32) tmem_ld32(tb + (c + 2) * 32, va);
+                    if (jt + (c + 1) * 32 < pr.n_cols)
+                        epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
+                                        edge, gidrow);
+                    __syncwarp();
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -560,42 +681,49 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (PROF) {
             prof_add_warp(TC_EPI_CYCLES, (unsigned long long)(clock64() - e_t0));
             prof_add_warp(TC_EPI_WAIT, e_wait);
+            prof_add_warp(TC_EPI_FLUSH, s.c_flush_cyc);
             prof_add_warp(TC_INSERTS, s.c_ins);
-            prof_add_warp(TC_APPENDS, s.c_cand);
+            prof_add_warp(TC_APPENDS, s.c_app);
             prof_add_warp(TC_LD_WAIT, s.c_ldw);
             prof_add_warp(TC_FILTER, s.c_filter);
-            prof_add_warp(TC_APPEND, s.c_slowcyc);
+            prof_add_warp(TC_APPEND, s.c_append);
             if (lane == 0) {
                 prof_add(TC_CHUNKS, s.c_chunks);
                 prof_add(TC_SLOW_CHUNKS, s.c_slow);
+                prof_add(TC_FLUSHES, s.c_flushes);
                 prof_add(TC_FLUSH_ITERS, s.c_iters);
             }
         }
-        if (!ok) {
-            atomicOr(P.status, DEV_TIMEOUT);
-        } else if (i < pr.n_rows) {
-            // Heap sort ascending, then write (global id, |x|^2 + 2 key).
-            uint64_t* H = s.H;
-            const int row = s.row, kp = s.kp;
-            for (int end = kp - 1; end > 0; --end) {
-                const uint64_t top = H[row];
-                H[row] = H[end * kt::BM + row];
-                H[end * kt::BM + row] = top;
-                heap_sift(H, row, 0, end);
-            }
-            const float nx = P.na[pr.a_row0 + i];
-            const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
-            for (int e = 0; e < P.k_out; ++e) {
-                const uint64_t x = H[e * kt::BM + row];
-                const uint32_t g = (uint32_t)x;  // global id (or column index)
-                uint32_t id = ANN_PAD;
-                float dd = INFINITY;
-                if (g != 0xFFFFFFFFu) {
-                    id = g;
-                    dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
+        // both warps of the quarter are done with the rows: h = 0 finishes them
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(64) : "memory");
+        if (!ok || *abort_flag) {
+            if (h == 0 && lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+        } else if (h == 0) {
+            epi_flush<false>(s, s.cnt[s.row]);
+            if (i < pr.n_rows) {
+                // Heap sort ascending, then write (global id, |x|^2 + 2 key).
+                uint64_t* H = s.H;
+                const int row = s.row, kp = s.kp;
+                for (int end = kp - 1; end > 0; --end) {
+                    const uint64_t top = H[row];
+                    H[row] = H[end * kt::BM + row];
+                    H[end * kt::BM + row] = top;
+                    heap_sift(H, row, 0, end);
                 }
-                P.out_id[orow * P.k_out + e] = id;
-                P.out_d[orow * P.k_out + e] = dd;
+                const float nx = P.na[pr.a_row0 + i];
+                const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
+                for (int e = 0; e < P.k_out; ++e) {
+                    const uint64_t x = H[e * kt::BM + row];
+                    const uint32_t g = (uint32_t)x;  // global id (or column index)
+                    uint32_t id = ANN_PAD;
+                    float dd = INFINITY;
+                    if (g != 0xFFFFFFFFu) {
+                        id = g;
+                        dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
+                    }
+                    P.out_id[orow * P.k_out + e] = id;
+                    P.out_d[orow * P.k_out + e] = dd;
+                }
             }
         }
     }
