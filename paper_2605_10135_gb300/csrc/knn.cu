@@ -134,8 +134,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     o += kt::CAP * kt::BM * 8;
     L.cnt = o;
     o += kt::BM * 4;
-    L.locks = o;  // 4 quarter locks, then 4 "warm-up done" flags
-    o += 8 * 4;
+    L.locks = o;  // 4 quarter locks, then 8 "warm-up done" flags (one per warp)
+    o += 12 * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -298,9 +298,11 @@ __device__ __forceinline__ int epi_flush(EpiState& s, int c) {
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
 // (every comparison with NaN is false, and the minimum skips NaN).
+// own == false: the row belongs to the partner warp in this phase; the lane only
+// takes part in the warp-wide steps.
 template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], int j0, int i,
-                                          int n_cols, int self_exclude, bool edge,
+                                          int n_cols, int self_exclude, bool edge, bool own,
                                           const uint32_t* __restrict__ gidrow) {
     long long f0 = 0;
     if (PROF) {
@@ -317,7 +319,8 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
             if (j >= n_cols || (self_exclude && j == i)) key[u] = __uint_as_float(0x7fc00000u);
         }
     }
-    const float m = min32(key);
+    float m = min32(key);
+    if (!own) m = __uint_as_float(0x7fc00000u);
     // "<=": a key equal to the current k-th may still win on the global id
     const bool any = __any_sync(0xffffffffu, m <= s.tau);
     if (PROF) {
@@ -331,7 +334,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
     if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
     quarter_lock(s);
-    int c = s.cnt[s.row];
+    int c = own ? s.cnt[s.row] : 0;
     s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -340,14 +343,14 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
         for (int uu = 0; uu < 16; ++uu) {
             const int u = half * 16 + uu;
             const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
-            if (key[u] <= s.tau) {
+            if (own && key[u] <= s.tau) {
                 s.B[c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
                 ++c;
                 if (PROF) ++s.c_app;
             }
         }
     }
-    s.cnt[s.row] = c;
+    if (own) s.cnt[s.row] = c;
     quarter_unlock(s);
     if (PROF) s.c_append += clock64() - f0;
 }
@@ -435,6 +438,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (lane == 0) {
             ((int*)(base + L.locks))[warp & 3] = 0;
             ((int*)(base + L.locks))[4 + (warp & 3)] = 0;
+            ((int*)(base + L.locks))[8 + (warp & 3)] = 0;
         }
     }
     tc_fence_before();
@@ -613,39 +617,36 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
             // The first WARM tiles (the row block's own cell, where most chunks hold
-            // survivors) are handled by warp h = 0 alone and without locking; after
-            // that the two warps take one column half each.
+            // survivors) are split by rows: each warp of the quarter sweeps all
+            // columns for its 16 rows, no locks.  After that the two warps take
+            // one column half each and share the rows under the quarter lock.
             const bool warm = tt < kt::WARM;
             if (tt == kt::WARM) {
-                // hand-over: warp h = 1 starts only after h = 0 has finished the
-                // lock-free warm-up tiles (bounded wait on a shared-memory flag)
-                volatile int* done = (volatile int*)(base + L.locks) + 4 + q;
-                if (h == 0) {
-                    __syncwarp();
-                    if (lane == 0) {
-                        __threadfence_block();
-                        *done = 1;
-                    }
-                } else {
-                    if (lane == 0) {
-                        const uint64_t wt = globaltimer();
-                        while (*done == 0) {
-                            if (*abort_flag) { ok = false; break; }
-                            if (globaltimer() - wt > 2000000000ull) {
-                                *abort_flag = 1;
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(128);
+                // hand-over: both warps finish the warm-up before either takes a
+                // column half (bounded waits on shared-memory flags)
+                volatile int* flags = (volatile int*)(base + L.locks) + 4;
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    flags[4 * h + q] = 1;
+                    const uint64_t wt = globaltimer();
+                    while (flags[4 * (1 - h) + q] == 0) {
+                        if (*abort_flag) { ok = false; break; }
+                        if (globaltimer() - wt > 2000000000ull) {
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
                         }
-                        __threadfence_block();
+                        __nanosleep(128);
                     }
-                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                    if (!ok) break;
+                    __threadfence_block();
                 }
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
                 s.shared = true;
             }
-            for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
+            const bool own = warm ? ((lane >> 4) == h) : true;
+            for (int hh = warm ? 0 : h; hh < (warm ? 2 : h + 1); ++hh) {
                 const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * HALF;
                 const int jt = t * kt::BN + hh * HALF;
                 const bool edge = (jt + HALF > pr.n_cols) ||
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     tmem_ld32(tb + (c + 1) * 32, vb);
                     if (jt + c * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge,
-                                        gidrow);
+                                        own, gidrow);
                     __syncwarp();
                     if (PROF) l0 = clock64();
                     tmem_wait_ld32(vb);
@@ -670,7 +671,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (c + 2 < HALF / 32) tmem_ld32(tb + (c + 2) * 32, va);
                     if (jt + (c + 1) * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
-                                        edge, gidrow);
+                                        edge, own, gidrow);
                     __syncwarp();
                 }
             }
