@@ -150,23 +150,33 @@ __device__ __forceinline__ uint64_t heap_init_val() {
     return ((uint64_t)f2ord(INFINITY) << 32) | 0xFFFFFFFFull;
 }
 
-// Replace the root of the max-heap of `row` (entries strided by BM) by x and sift down.
-__device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, uint64_t x) {
+// Replace the root of the max-heap of `row` (entries strided by BM) by x and sift
+// down: a fixed number of levels (depth = levels below the root for n entries),
+// predicated instead of branching, so the 32 rows of a warp stay in step.
+__device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, int depth,
+                                                  uint64_t x) {
     int e = 0;
-    for (;;) {
+    bool done = false;
+    for (int lvl = 0; lvl < depth; ++lvl) {
         const int l = 2 * e + 1;
-        if (l >= n) break;
-        uint64_t hc = H[l * kt::BM + row];
-        int c = l;
-        if (l + 1 < n) {
-            const uint64_t hr = H[(l + 1) * kt::BM + row];
-            if (hr > hc) { c = l + 1; hc = hr; }
-        }
-        if (hc <= x) break;
-        H[e * kt::BM + row] = hc;
-        e = c;
+        const bool has_l = !done && l < n, has_r = !done && l + 1 < n;
+        uint64_t hl = 0, hr = 0;
+        if (has_l) hl = H[l * kt::BM + row];
+        if (has_r) hr = H[(l + 1) * kt::BM + row];
+        const bool right = has_r && hr > hl;
+        const uint64_t hc = right ? hr : hl;
+        const bool go = has_l && hc > x;
+        if (go) H[e * kt::BM + row] = hc;
+        e = go ? (right ? l + 1 : l) : e;
+        done = !go;
     }
     H[e * kt::BM + row] = x;
+}
+
+__host__ __device__ inline int heap_depth(int n) {
+    int d = 0;
+    while ((1 << (d + 1)) - 1 < n) ++d;  // levels below the root
+    return d;
 }
 
 __device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
@@ -238,7 +248,7 @@ struct EpiState {
     int* cnt;
     int* lock;
     volatile int* abort;
-    int row, kp;
+    int row, kp, depth;
     bool shared;  // false while the partner warp is idle: no lock needed
     float tau;
     // counters (used only by the profiling instantiation)
@@ -282,7 +292,7 @@ __device__ __forceinline__ int epi_flush(EpiState& s, int c) {
         if (q < c) {
             const uint64_t x = s.B[q * kt::BM + s.row];
             if (x < s.H[s.row]) {
-                heap_replace_root(s.H, s.row, s.kp, x);
+                heap_replace_root(s.H, s.row, s.kp, s.depth, x);
                 if (PROF) ++s.c_ins;
             }
         }
@@ -595,6 +605,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.lock = (int*)(base + L.locks) + q;
         s.abort = abort_flag;
         s.kp = P.kprime;
+        s.depth = heap_depth(P.kprime);
         s.shared = false;
         s.tau = INFINITY;
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
