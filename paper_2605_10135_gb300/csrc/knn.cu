@@ -134,8 +134,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     o += kt::CAP * kt::BM * 8;
     L.cnt = o;
     o += kt::BM * 4;
-    L.locks = o;  // 4 quarter locks, then 8 "warm-up done" flags (one per warp)
-    o += 12 * 4;
+    L.locks = o;  // 4 quarter locks, then 4 "warm-up done" flags
+    o += 8 * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -150,33 +150,23 @@ __device__ __forceinline__ uint64_t heap_init_val() {
     return ((uint64_t)f2ord(INFINITY) << 32) | 0xFFFFFFFFull;
 }
 
-// Replace the root of the max-heap of `row` (entries strided by BM) by x and sift
-// down: a fixed number of levels (depth = levels below the root for n entries),
-// predicated instead of branching, so the 32 rows of a warp stay in step.
-__device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, int depth,
-                                                  uint64_t x) {
+// Replace the root of the max-heap of `row` (entries strided by BM) by x and sift down.
+__device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, uint64_t x) {
     int e = 0;
-    bool done = false;
-    for (int lvl = 0; lvl < depth; ++lvl) {
+    for (;;) {
         const int l = 2 * e + 1;
-        const bool has_l = !done && l < n, has_r = !done && l + 1 < n;
-        uint64_t hl = 0, hr = 0;
-        if (has_l) hl = H[l * kt::BM + row];
-        if (has_r) hr = H[(l + 1) * kt::BM + row];
-        const bool right = has_r && hr > hl;
-        const uint64_t hc = right ? hr : hl;
-        const bool go = has_l && hc > x;
-        if (go) H[e * kt::BM + row] = hc;
-        e = go ? (right ? l + 1 : l) : e;
-        done = !go;
+        if (l >= n) break;
+        uint64_t hc = H[l * kt::BM + row];
+        int c = l;
+        if (l + 1 < n) {
+            const uint64_t hr = H[(l + 1) * kt::BM + row];
+            if (hr > hc) { c = l + 1; hc = hr; }
+        }
+        if (hc <= x) break;
+        H[e * kt::BM + row] = hc;
+        e = c;
     }
     H[e * kt::BM + row] = x;
-}
-
-__host__ __device__ inline int heap_depth(int n) {
-    int d = 0;
-    while ((1 << (d + 1)) - 1 < n) ++d;  // levels below the root
-    return d;
 }
 
 __device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
@@ -248,7 +238,7 @@ struct EpiState {
     int* cnt;
     int* lock;
     volatile int* abort;
-    int row, kp, depth;
+    int row, kp;
     bool shared;  // false while the partner warp is idle: no lock needed
     float tau;
     // counters (used only by the profiling instantiation)
@@ -292,7 +282,7 @@ __device__ __forceinline__ int epi_flush(EpiState& s, int c) {
         if (q < c) {
             const uint64_t x = s.B[q * kt::BM + s.row];
             if (x < s.H[s.row]) {
-                heap_replace_root(s.H, s.row, s.kp, s.depth, x);
+                heap_replace_root(s.H, s.row, s.kp, x);
                 if (PROF) ++s.c_ins;
             }
         }
@@ -308,11 +298,9 @@ __device__ __forceinline__ int epi_flush(EpiState& s, int c) {
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
 // (every comparison with NaN is false, and the minimum skips NaN).
-// own == false: the row belongs to the partner warp in this phase; the lane only
-// takes part in the warp-wide steps.
 template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], int j0, int i,
-                                          int n_cols, int self_exclude, bool edge, bool own,
+                                          int n_cols, int self_exclude, bool edge,
                                           const uint32_t* __restrict__ gidrow) {
     long long f0 = 0;
     if (PROF) {
@@ -329,8 +317,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
             if (j >= n_cols || (self_exclude && j == i)) key[u] = __uint_as_float(0x7fc00000u);
         }
     }
-    float m = min32(key);
-    if (!own) m = __uint_as_float(0x7fc00000u);
+    const float m = min32(key);
     // "<=": a key equal to the current k-th may still win on the global id
     const bool any = __any_sync(0xffffffffu, m <= s.tau);
     if (PROF) {
@@ -344,7 +331,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
     if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
     quarter_lock(s);
-    int c = own ? s.cnt[s.row] : 0;
+    int c = s.cnt[s.row];
     s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -353,14 +340,14 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
         for (int uu = 0; uu < 16; ++uu) {
             const int u = half * 16 + uu;
             const uint32_t g = __shfl_sync(0xffffffffu, g_l, u);
-            if (own && key[u] <= s.tau) {
+            if (key[u] <= s.tau) {
                 s.B[c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | g;
                 ++c;
                 if (PROF) ++s.c_app;
             }
         }
     }
-    if (own) s.cnt[s.row] = c;
+    s.cnt[s.row] = c;
     quarter_unlock(s);
     if (PROF) s.c_append += clock64() - f0;
 }
@@ -448,7 +435,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (lane == 0) {
             ((int*)(base + L.locks))[warp & 3] = 0;
             ((int*)(base + L.locks))[4 + (warp & 3)] = 0;
-            ((int*)(base + L.locks))[8 + (warp & 3)] = 0;
         }
     }
     tc_fence_before();
@@ -605,7 +591,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.lock = (int*)(base + L.locks) + q;
         s.abort = abort_flag;
         s.kp = P.kprime;
-        s.depth = heap_depth(P.kprime);
         s.shared = false;
         s.tau = INFINITY;
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
@@ -628,36 +613,39 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
             // The first WARM tiles (the row block's own cell, where most chunks hold
-            // survivors) are split by rows: each warp of the quarter sweeps all
-            // columns for its 16 rows, no locks.  After that the two warps take
-            // one column half each and share the rows under the quarter lock.
+            // survivors) are handled by warp h = 0 alone and without locking; after
+            // that the two warps take one column half each.
             const bool warm = tt < kt::WARM;
             if (tt == kt::WARM) {
-                // hand-over: both warps finish the warm-up before either takes a
-                // column half (bounded waits on shared-memory flags)
-                volatile int* flags = (volatile int*)(base + L.locks) + 4;
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence_block();
-                    flags[4 * h + q] = 1;
-                    const uint64_t wt = globaltimer();
-                    while (flags[4 * (1 - h) + q] == 0) {
-                        if (*abort_flag) { ok = false; break; }
-                        if (globaltimer() - wt > 2000000000ull) {
-                            *abort_flag = 1;
-                            ok = false;
-                            break;
-                        }
-                        __nanosleep(128);
+                // hand-over: warp h = 1 starts only after h = 0 has finished the
+                // lock-free warm-up tiles (bounded wait on a shared-memory flag)
+                volatile int* done = (volatile int*)(base + L.locks) + 4 + q;
+                if (h == 0) {
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        *done = 1;
                     }
-                    __threadfence_block();
+                } else {
+                    if (lane == 0) {
+                        const uint64_t wt = globaltimer();
+                        while (*done == 0) {
+                            if (*abort_flag) { ok = false; break; }
+                            if (globaltimer() - wt > 2000000000ull) {
+                                *abort_flag = 1;
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(128);
+                        }
+                        __threadfence_block();
+                    }
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
                 }
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (!ok) break;
                 s.shared = true;
             }
-            const bool own = warm ? ((lane >> 4) == h) : true;
-            for (int hh = warm ? 0 : h; hh < (warm ? 2 : h + 1); ++hh) {
+            for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
                 const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * HALF;
                 const int jt = t * kt::BN + hh * HALF;
                 const bool edge = (jt + HALF > pr.n_cols) ||
@@ -674,7 +662,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     tmem_ld32(tb + (c + 1) * 32, vb);
                     if (jt + c * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge,
-                                        own, gidrow);
+                                        gidrow);
                     __syncwarp();
                     if (PROF) l0 = clock64();
                     tmem_wait_ld32(vb);
@@ -682,7 +670,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (c + 2 < HALF / 32) tmem_ld32(tb + (c + 2) * 32, va);
                     if (jt + (c + 1) * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
-                                        edge, own, gidrow);
+                                        edge, gidrow);
                     __syncwarp();
                 }
             }
