@@ -32,6 +32,25 @@ if ROOT not in sys.path:
 METRIC = "index-build vectors/s at recall@10>=0.95; distance TFLOP/s as % of GB300 peak"
 
 
+def _kernel_traffic():
+    """DRAM bytes per distance-tile launch from the committed ncu capture, or None
+    when the kernel source has changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "k_knn_tiles_sift1m_u8.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        j = json.load(f)
+    h = hashlib.sha256()
+    for rel in ("paper_2605_10135_gb300/csrc/knn.cu", "paper_2605_10135_gb300/csrc/common.cuh",
+                "paper_2605_10135_gb300/csrc/stages.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != j.get("kernel_source_sha256"):
+        return None
+    return int(j["dram_bytes_read_per_launch"] + j["dram_bytes_write_per_launch"])
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -296,7 +315,8 @@ def main():
         },
         "roofline": {
             "kernel": "k_knn_tiles", "bound": "tensor", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": _kernel_traffic() if w.name == "sift1m_d128_u8" else None,
             "peak_source": f"{src} bf16_tflops_sustained",
             "algorithmic_flops_per_launch": flops, "kernel_ms": tile_avg_ms,
         },
