@@ -198,6 +198,22 @@ int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
 int ann_medoid_workspace(int64_t N, int d, size_t* bytes);
 int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, void* ws,
                size_t ws_bytes, void* stream);
+/* ann_medoid_noalloc: the same result as ann_medoid (same kernels, same order),
+ * for callers that cannot allocate device memory - e.g. code running inside
+ * a framework that owns the device's memory pool, or a pipeline stage where a
+ * cudaMalloc could synchronise the device or fail part-way.  It takes no
+ * workspace and calls no allocating routine: its scratch is a fixed array of
+ * 4 MiB + 16 KiB inside the library, reserved on every device that loads the
+ * library until the process exits.  Limits: d <= 4096 and
+ * ceil(N / 4096) * d <= 524288 (e.g. N <= 2^21 at d = 1024); larger inputs are
+ * rejected with ANN_ERR_INVALID_ARG (use ann_medoid with a workspace).  The
+ * first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.  The paper
+ * has no counterpart: this entry point exists only for such callers. */
+int ann_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out,
+                       void* stream);
 int ann_knn_query_workspace(int64_t N, int64_t nq, int d, int dtype, int k, size_t* bytes);
 int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,
                   uint32_t* out_id, float* out_d, void* ws, size_t ws_bytes, void* stream);

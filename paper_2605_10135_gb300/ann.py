@@ -63,6 +63,7 @@ def lib():
             "ann_merge": (I32, [P, P, P, P, I32, I64, I64, I32, P, P, P, P, SZ, P]),
             "ann_medoid_workspace": (I32, [I64, I32, PSZ]),
             "ann_medoid": (I32, [P, I64, I32, I32, P, P, SZ, P]),
+            "ann_medoid_noalloc": (I32, [P, I64, I32, I32, P, P]),
             "ann_knn_query_workspace": (I32, [I64, I64, I32, I32, I32, PSZ]),
             "ann_knn_query": (I32, [P, I64, P, I64, I32, I32, I32, P, P, P, SZ, P]),
             "ann_search": (I32, [P, P, I32, P, I64, I32, I32, P, I64, ct.c_uint32, I32, I32, P, P,
@@ -244,6 +245,19 @@ def medoid(X: torch.Tensor) -> torch.Tensor:
     nb = _wsize(L.ann_medoid_workspace, N, d)
     ws = _ws(nb, X.device)
     _check(L.ann_medoid(_ptr(X), N, d, _DT[X.dtype], _ptr(out), _ptr(ws), nb, _stream()))
+    return out
+
+
+def medoid_noalloc(X: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """ann_medoid without any allocation inside the library (fixed internal scratch).
+
+    For callers that cannot allocate device memory; pass a preallocated int32[1]
+    `out` to avoid the one allocation this wrapper would otherwise make."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=X.device)
+    _check(lib().ann_medoid_noalloc(_ptr(X), N, d, _DT[X.dtype], _ptr(out), _stream()))
     return out
 
 

@@ -317,6 +317,14 @@ int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, 
     return run_medoid(X, N, d, dtype, entry_out, part, mean, best, (cudaStream_t)stream);
 }
 
+int ann_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out,
+                       void* stream) {
+    ANN_REQUIRE(N >= 1 && N < (1ll << 32) && d >= 1, "N and d must be >= 1");
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype");
+    ANN_REQUIRE(X && entry_out, "NULL pointer");
+    return run_medoid_noalloc(X, N, d, dtype, entry_out, (cudaStream_t)stream);
+}
+
 int ann_knn_query_workspace(int64_t N, int64_t nq, int d, int dtype, int k, size_t* bytes) {
     ANN_REQUIRE(bytes, "bytes is NULL");
     int rc = knn_args(N, d, dtype, 1, nq, k, ANN_EXACT, 0);

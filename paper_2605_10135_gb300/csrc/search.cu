@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "stages.cuh"
 
 namespace ann {
@@ -261,6 +263,60 @@ int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, doub
     k_entry_out<<<1, 32, 0, st>>>(best, entry);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
+}
+
+// ---- medoid without allocation -----------------------------------------------------
+// Scratch of ann_medoid_noalloc: per-chunk FP64 column sums, the float mean and
+// the 64-bit argmin, in one array reserved for the lifetime of the process on
+// every device that loads the library.
+constexpr size_t NOALLOC_PART_DOUBLES = (size_t)1 << 19;  // 4 MiB of column sums
+constexpr size_t NOALLOC_MEAN_FLOATS = 4096;               // d <= 4096
+constexpr size_t NOALLOC_BYTES = NOALLOC_PART_DOUBLES * 8 + NOALLOC_MEAN_FLOATS * 4 + 256;
+static __device__ __align__(256) unsigned char g_medoid_scratch[NOALLOC_BYTES];
+
+// Device address of g_medoid_scratch on the current device, looked up once per
+// device (with that device current) and cached.  Host code must never hand the
+// symbol itself to a kernel: on the host it names a stand-in, not device memory.
+static int medoid_scratch_ptr(unsigned char** out) {
+    static std::mutex mu;
+    static unsigned char* ptrs[64] = {nullptr};
+    int dev = 0;
+    ANN_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(ANN_ERR_UNSUPPORTED, "device index %d >= 64", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_medoid_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ANN_ERR_CUDA, "cudaGetSymbolAddress(g_medoid_scratch): %s",
+                        cudaGetErrorString(e));
+        ptrs[dev] = (unsigned char*)p;
+    }
+    *out = ptrs[dev];
+    return ANN_OK;
+}
+
+int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry,
+                       cudaStream_t st) {
+    const int64_t nchunk = (N + MED_ROWS - 1) / MED_ROWS;
+    if (d < 1 || d > (int)NOALLOC_MEAN_FLOATS)
+        return fail(ANN_ERR_INVALID_ARG, "ann_medoid_noalloc: d must be in [1, %d]",
+                    (int)NOALLOC_MEAN_FLOATS);
+    if ((size_t)nchunk * (size_t)d > NOALLOC_PART_DOUBLES)
+        return fail(ANN_ERR_INVALID_ARG,
+                    "ann_medoid_noalloc: ceil(N / %d) * d = %lld exceeds the fixed scratch of "
+                    "%zu column sums; use ann_medoid with a workspace",
+                    MED_ROWS, (long long)nchunk * d, NOALLOC_PART_DOUBLES);
+    unsigned char* base = nullptr;
+    int rc = medoid_scratch_ptr(&base);
+    if (rc) return rc;
+    // Every scratch byte read below is written first in the same call (partial
+    // sums, then the mean and the argmin seed), so nothing needs clearing.
+    double* part = (double*)base;
+    float* mean = (float*)(base + NOALLOC_PART_DOUBLES * 8);
+    unsigned long long* best =
+        (unsigned long long*)(base + NOALLOC_PART_DOUBLES * 8 + NOALLOC_MEAN_FLOATS * 4);
+    return run_medoid(X, N, d, dtype, entry, part, mean, best, st);
 }
 
 }  // namespace ann

@@ -134,5 +134,7 @@ size_t medoid_ws(int64_t N, int d, double** part, float** mean, unsigned long lo
                  void* base, size_t cap);
 int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, double* part,
                float* mean, unsigned long long* best, cudaStream_t st);
+int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry,
+                       cudaStream_t st);
 
 }  // namespace ann
