@@ -206,7 +206,7 @@ static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int
     ANN_REQUIRE(k >= 1 && k <= 96, "k must be in [1, 96]");
     ANN_REQUIRE(d >= 1, "d < 1");
     ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 128), "rerank_k must be 0 or in [k, 128]");
-    if (precision != ANN_EXACT)
+    if (precision != ANN_EXACT && precision != ANN_BF16_RERANK && precision != ANN_FP8_RERANK)
         return fail(ANN_ERR_UNSUPPORTED, "precision %d is not built in this version", precision);
     if (d > 256) return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d > 256 not built in this version");
     return ANN_OK;
@@ -218,7 +218,7 @@ int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, in
     int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
     if (rc) return rc;
     KnnPlan pl;
-    if ((rc = knn_plan(d, dtype, k, rerank_k, &pl))) return rc;
+    if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
     *bytes = knn_ws(C, rows, pl, nullptr, nullptr, 0);
     return ANN_OK;
 }
@@ -233,7 +233,7 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     ANN_REQUIRE(offsets, "offsets is NULL");
     ANN_REQUIRE(rows == 0 || (X && members && knn_id && knn_d), "NULL pointer");
     KnnPlan pl;
-    if ((rc = knn_plan(d, dtype, k, rerank_k, &pl))) return rc;
+    if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
     size_t need = knn_ws(C, rows, pl, nullptr, nullptr, 0);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
     if (rows == 0) return ANN_OK;
@@ -331,7 +331,7 @@ int ann_knn_query_workspace(int64_t N, int64_t nq, int d, int dtype, int k, size
     if (rc) return rc;
     ANN_REQUIRE(N < (1 << 24) && nq < (1 << 24), "N and nq must be < 2^24");
     KnnPlan pl;
-    if ((rc = knn_plan(d, dtype, k, 0, &pl))) return rc;
+    if ((rc = knn_plan(d, dtype, k, ANN_EXACT, 0, &pl))) return rc;
     *bytes = query_ws(N, nq, pl, nullptr, nullptr, 0);
     return ANN_OK;
 }
@@ -345,7 +345,7 @@ int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
     if (nq == 0) return ANN_OK;
     KnnPlan pl;
-    knn_plan(d, dtype, k, 0, &pl);
+    knn_plan(d, dtype, k, ANN_EXACT, 0, &pl);
     QueryWs w;
     query_ws(N, nq, pl, &w, ws, ws_bytes);
     return run_knn_query(X, N, Q, nq, d, dtype, k, pl, w, out_id, out_d, (cudaStream_t)stream);

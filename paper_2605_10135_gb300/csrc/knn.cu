@@ -41,6 +41,7 @@
 //           screen a widened list that k_rerank re-scores in FP32.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "stages.cuh"
 
@@ -48,20 +49,19 @@ namespace ann {
 
 namespace kt {
 constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int KB = 64;                  // K elements per 128-byte block
+constexpr int BNMAX = 256;              // widest tile (N of one MMA)
+constexpr int KB = 64;                  // 16-bit elements per 128-byte K block
+constexpr int KB8 = 128;                // 8-bit elements per 128-byte K block
 constexpr int KAUG = 16;                // norm block: 16 elements (32 bytes)
 constexpr int A_BLK_BYTES = BM * 128;   // one K block of the 128 A rows
-constexpr int B_BLK_BYTES = BN * 128;   // one K block of the 256 B rows
 constexpr int A_AUG_BYTES = BM * 32;
-constexpr int B_AUG_BYTES = BN * 32;
 constexpr int NAUG = 1;                 // norm-block slots (loaded first in each tile)
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
 constexpr int CAP = 16;                 // survivor buffer entries per row
 constexpr int WARM = 6;                 // leading tiles handled by one warp per quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t TMEM_COLS = NACC * BN;
+constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
 constexpr int CELL = 1024;              // rows per pivot cell
 }  // namespace kt
@@ -107,6 +107,8 @@ struct KnnParams {
     int kprime;    // heap entries per row
     int k_out;     // entries written per row
     int nst;       // main pipeline stages
+    int kbe;       // elements per 128-byte K block (64 for 16-bit, 128 for 8-bit operands)
+    int kind8;     // 1: E4M3 operands (tcgen05.mma kind::f8f6f4, K = 32 per MMA)
     uint32_t idesc_neg, idesc_aug;
     uint32_t* out_id;
     float* out_d;
@@ -117,7 +119,7 @@ struct KnnSmemLayout {
     uint32_t a, aaug, b, baug, heap, buf, cnt, locks, bars, tmem_slot, abort_flag, total;
 };
 
-__host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int kprime) {
+__host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int kprime) {
     KnnSmemLayout L;
     uint32_t o = 0;
     L.a = o;
@@ -125,9 +127,9 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int nkb_a, int nst, int
     L.aaug = o;
     o += 1024 * ((kt::A_AUG_BYTES + 1023) / 1024);
     L.b = o;
-    o += nst * kt::B_BLK_BYTES;
+    o += nst * bn * 128;
     L.baug = o;
-    o += kt::NAUG * kt::B_AUG_BYTES;
+    o += kt::NAUG * bn * 32;
     L.heap = o;
     o += kprime * kt::BM * 8;
     L.buf = o;
@@ -360,7 +362,18 @@ __device__ __forceinline__ void prof_add_warp(int which, unsigned long long v) {
     if ((threadIdx.x & 31) == 0) prof_add(which, v);
 }
 
-template <bool PROF>
+// D (+)= A * B^T with E4M3 operands (kind::f8f6f4), FP32 accumulator.
+__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+template <int BN, bool PROF>
 __global__ void __launch_bounds__(kt::THREADS, 1)
     k_knn_tiles(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmAaug,
@@ -376,18 +389,19 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     }
     const KnnProblem pr = P.probs[lo];
     const int rb = (int)(bid - P.blk_off[lo]);
-    const int ntiles = (pr.n_cols + kt::BN - 1) / kt::BN;
+    const int ntiles = (pr.n_cols + BN - 1) / BN;
+    constexpr int B_BLK_BYTES = BN * 128, B_AUG_BYTES = BN * 32;
     // Sweep order: tile t0, t0+1, ... wrapping around.  With local_first the sweep
     // starts near the block's own rows (rows are ordered by cell), so each row's
     // k-th key tightens early.
     int t0 = 0;
     if (P.local_first) {
-        t0 = (rb * kt::BM - 512) / kt::BN;
+        t0 = (rb * kt::BM - 512) / BN;
         if (t0 < 0 || t0 >= ntiles) t0 = 0;
     }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const KnnSmemLayout L = knn_smem_layout(P.nkb_a, P.nst, P.kprime);
+    const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.kprime);
     const uint32_t sA = smem_u32(base + L.a);
     const uint32_t sAaug = smem_u32(base + L.aaug);
     const uint32_t sB = smem_u32(base + L.b);
@@ -452,7 +466,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             const int a_y = (int)(pr.a_row0 + (int64_t)rb * kt::BM);
             mbar_expect_tx(a_bar, P.nkb_a * kt::A_BLK_BYTES + kt::A_AUG_BYTES);
             for (int b = 0; b < P.nkb_a; ++b)
-                tma_load_2d(sA + b * kt::A_BLK_BYTES, &tmA, a_bar, b * kt::KB, a_y);
+                tma_load_2d(sA + b * kt::A_BLK_BYTES, &tmA, a_bar, b * P.kbe, a_y);
             tma_load_2d(sAaug, &tmAaug, a_bar, 0, 0);
             uint32_t last_par = 0, used = 0, alast_par = 0, aused = 0;
             int st = 0, sa = 0;
@@ -461,11 +475,11 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             unsigned long long prod_wait = 0;
             for (int tt = 0; tt < ntiles && ok; ++tt) {
                 const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
-                const int b_y = (int)(pr.b_row0 + (int64_t)t * kt::BN);
+                const int b_y = (int)(pr.b_row0 + (int64_t)t * BN);
                 // the norm block first: its MMA opens the tile, so the slot frees early
                 if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
-                mbar_expect_tx(afull_bar + 8 * sa, kt::B_AUG_BYTES);
-                tma_load_2d(sBaug + sa * kt::B_AUG_BYTES, &tmBaug, afull_bar + 8 * sa, 0, b_y);
+                mbar_expect_tx(afull_bar + 8 * sa, B_AUG_BYTES);
+                tma_load_2d(sBaug + sa * B_AUG_BYTES, &tmBaug, afull_bar + 8 * sa, 0, b_y);
                 aused |= 1u << sa;
                 alast_par = (alast_par & ~(1u << sa)) | (aph << sa);
                 if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
@@ -474,8 +488,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
                     if (PROF) prod_wait += clock64() - w0;
-                    mbar_expect_tx(full_bar + 8 * st, kt::B_BLK_BYTES);
-                    tma_load_2d(sB + st * kt::B_BLK_BYTES, &tmB, full_bar + 8 * st, j * kt::KB, b_y);
+                    mbar_expect_tx(full_bar + 8 * st, B_BLK_BYTES);
+                    tma_load_2d(sB + st * B_BLK_BYTES, &tmB, full_bar + 8 * st, j * P.kbe, b_y);
                     used |= 1u << st;
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
@@ -514,13 +528,13 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 }
                 if (PROF) w_acc += clock64() - w0;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + a * kt::BN;
+                const uint32_t d_tmem = tmem + a * BN;
                 // D = [1,1,1,0..] . [h,m,l,0..] (= |y|^2 / 2), then D -= x . y
                 if (PROF) w0 = clock64();
                 if (!mbar_wait(afull_bar + 8 * sa, aph, abort_flag)) { ok = false; break; }
                 if (PROF) w_full += clock64() - w0;
                 tc_fence_after();
-                umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(sBaug + sa * kt::B_AUG_BYTES),
+                umma_f16(d_tmem, sdesc_sw32(sAaug), sdesc_sw32(sBaug + sa * B_AUG_BYTES),
                          P.idesc_aug, 0);
                 umma_commit(aempty_bar + 8 * sa);
                 if (++sa == kt::NAUG) { sa = 0; aph ^= 1; }
@@ -531,7 +545,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) w_full += clock64() - w0;
                     tc_fence_after();
                     if (PROF) w0 = clock64();
-                    const uint32_t bsm = sB + st * kt::B_BLK_BYTES;
+                    const uint32_t bsm = sB + st * B_BLK_BYTES;
                     int ablk[2];
                     int na = 1;
                     if (P.mode == 0) {
@@ -545,10 +559,16 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     }
                     for (int q = 0; q < na; ++q) {
                         const uint32_t asm_ = sA + ablk[q] * kt::A_BLK_BYTES;
+                        // four K steps of 32 bytes per 128-byte block (K = 16 for 16-bit
+                        // operands, K = 32 for E4M3)
 #pragma unroll
-                        for (int s = 0; s < kt::KB / 16; ++s) {
-                            umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
-                                     P.idesc_neg, accum);
+                        for (int s = 0; s < 4; ++s) {
+                            if (P.kind8)
+                                umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
+                                        P.idesc_neg, accum);
+                            else
+                                umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                         sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
                         }
                     }
                     long long w1 = 0;
@@ -603,7 +623,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
-        constexpr int HALF = kt::BN / 2;
+        constexpr int HALF = BN / 2;
         for (int tt = 0; tt < ntiles; ++tt) {
             const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
             const int a = tt % kt::NACC;
@@ -646,8 +666,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 s.shared = true;
             }
             for (int hh = warm ? 0 : h; hh < (warm ? (h == 0 ? 2 : 0) : h + 1); ++hh) {
-                const uint32_t tb = tmem + lane_addr + a * kt::BN + hh * HALF;
-                const int jt = t * kt::BN + hh * HALF;
+                const uint32_t tb = tmem + lane_addr + a * BN + hh * HALF;
+                const int jt = t * BN + hh * HALF;
                 const bool edge = (jt + HALF > pr.n_cols) ||
                                   (P.self_exclude && i0 + 32 > jt && i0 < jt + HALF);
                 uint32_t va[32], vb[32];
@@ -782,16 +802,43 @@ template <>
 __device__ __forceinline__ __nv_bfloat16 cvt_from_float(float v) { return __float2bfloat16_rn(v); }
 template <>
 __device__ __forceinline__ __half cvt_from_float(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 cvt_from_float(float v) {
+    __nv_fp8_e4m3 r;
+    r.__x = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);  // round to nearest even
+    return r;
+}
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_float(__nv_fp8_e4m3 v) { return (float)v; }
+
+// Largest |x| over n elements (for the E4M3 scale), as float bits in *out (init 0).
+__global__ void k_absmax(const void* X, int dtype, int64_t n, unsigned int* out) {
+    float m = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(load_elem(X, dtype, i)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
 
 // Gather rows into the tile layout: row p' of G (pitch Kp elements) holds the
 // operand copy of vector src[p'] (zeros when src[p'] < 0); norms[p'] = |x|^2
 // and aug[p'] = |x|^2 / 2 split exactly into three BF16 values (hi, mid, lo)
 // followed by zeros.
 // mode 0: element t = cvt(x_t).  mode 1: [hi | lo] sections of Kh elements.
+// scale (E4M3 only): every element is multiplied by 448 / *amax_bits, and the
+// norms by its square, so keys keep their order.
 template <typename T>
 __global__ void k_gather(const void* X, int dtype, int d, const int64_t* __restrict__ srcrow,
                          int64_t rows_cap, int mode, int Kp, int Kh, T* __restrict__ G,
-                         float* __restrict__ norms, __nv_bfloat16* __restrict__ aug) {
+                         float* __restrict__ norms, __nv_bfloat16* __restrict__ aug,
+                         const unsigned int* __restrict__ amax_bits) {
+    float scale = 1.0f;
+    if (amax_bits) {
+        const float am = __uint_as_float(*amax_bits);
+        if (am > 0.0f) scale = 448.0f / am;
+    }
     const int lane = threadIdx.x & 31;
     const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -803,7 +850,7 @@ __global__ void k_gather(const void* X, int dtype, int d, const int64_t* __restr
             float v = 0.0f;
             if (mode == 0) {
                 if (src >= 0 && t < d) {
-                    v = load_elem(X, dtype, src * d + t);
+                    v = load_elem(X, dtype, src * d + t) * scale;
                     nrm = fmaf(v, v, nrm);
                 }
                 g[t] = cvt_from_float<T>(v);
@@ -817,7 +864,7 @@ __global__ void k_gather(const void* X, int dtype, int d, const int64_t* __restr
                         out = h;
                         nrm = fmaf(v, v, nrm);
                     } else {
-                        out = cvt_from_float<T>(v - (float)h);
+                        out = cvt_from_float<T>(v - to_float(h));
                     }
                 }
                 g[t] = out;
@@ -1077,25 +1124,49 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// 2-D tensor map over a [rows x inner] 16-bit matrix with box {box_inner, box_rows}.
+// 2-D tensor map over a [rows x inner] matrix of 16-bit (esize 2) or 8-bit (esize 1)
+// elements with box {box_inner, box_rows}.
 static int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int box_inner,
-                     int box_rows, CUtensorMapSwizzle swz) {
+                     int box_rows, CUtensorMapSwizzle swz, int esize = 2) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return fail(ANN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * esize};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)G, dims, strides, box, es,
+    const CUtensorMapDataType dt =
+        esize == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(m, dt, 2, (void*)G, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ANN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return ANN_OK;
 }
 
-int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl) {
+// Operand layout, tile width and pipeline depth for a dtype / precision.
+//   ANN_EXACT      : uint8 -> BF16 copy (exact integer keys, no re-rank);
+//                    float -> BF16 hi/lo split (FP32 data) or the data's own
+//                    16-bit type, screening k + 16 (or rerank_k) for the re-rank.
+//   ANN_BF16_RERANK: one BF16 copy, screening rerank_k (default 128).
+//   ANN_FP8_RERANK : one E4M3 copy (all values scaled by 448 / max|x|), screening
+//                    rerank_k (default 128).
+int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) {
     KnnPlan p;
-    if (dtype == ANN_F32) {
+    p.elem8 = 0;
+    if (precision == ANN_FP8_RERANK) {
+        p.mode = 0;
+        p.Kh = 0;
+        p.elem8 = 1;
+        p.Kp = (int)align_up((size_t)d, kt::KB8);
+        p.ab_fmt = 0;  // E4M3
+        p.rerank = true;
+    } else if (precision == ANN_BF16_RERANK) {
+        p.mode = 0;
+        p.Kh = 0;
+        p.Kp = (int)align_up((size_t)d, kt::KB);
+        p.ab_fmt = 1;
+        p.rerank = true;
+    } else if (dtype == ANN_F32) {
         p.mode = 1;
         p.Kh = (int)align_up((size_t)d, kt::KB);
         p.Kp = 2 * p.Kh;
@@ -1108,32 +1179,45 @@ int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl) {
         p.ab_fmt = dtype == ANN_F16 ? 0 : 1;
         p.rerank = dtype != ANN_U8;
     }
-    p.nkb_a = p.Kp / kt::KB;
+    p.kbe = p.elem8 ? kt::KB8 : kt::KB;
+    p.nkb_a = p.Kp / p.kbe;
     p.nkb_b = p.nkb_a;
-    p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : k + 16) : k;
+    const int wide = precision == ANN_EXACT ? k + 16 : 128;
+    p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : wide) : k;
     if (p.kprime < k) p.kprime = k;
     if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
+    // Widest tile with a 3-stage ring, else the narrow one, else 2 stages.
     const size_t cap = 227 * 1024;
     p.nst = 0;
-    for (int nst = kt::MAX_NST; nst >= 2; --nst) {
-        if (knn_smem_layout(p.nkb_a, nst, p.kprime).total <= cap) { p.nst = nst; break; }
+    const int tries[4][2] = {{256, 3}, {128, 3}, {256, 2}, {128, 2}};
+    for (int q = 0; q < 4 && !p.nst; ++q) {
+        const int bn = tries[q][0];
+        for (int nst = kt::MAX_NST; nst >= tries[q][1]; --nst)
+            if (knn_smem_layout(bn, p.nkb_a, nst, p.kprime).total <= cap) {
+                p.nst = nst;
+                p.bn = bn;
+                break;
+            }
     }
     if (!p.nst)
         return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory", d,
                     p.kprime);
-    p.smem = knn_smem_layout(p.nkb_a, p.nst, p.kprime).total;
+    p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.kprime).total;
     *pl = p;
     return ANN_OK;
 }
 
+// Operand bytes per gathered row.
+static inline size_t row_bytes(const KnnPlan& pl) { return (size_t)pl.Kp * (pl.elem8 ? 1 : 2); }
+
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap) {
     Carver cv(base, cap);
     KnnWs w;
-    w.rows_cap = rows + (int64_t)kt::BM * C + kt::BN;
+    w.rows_cap = rows + (int64_t)kt::BM * C + kt::BNMAX;
     w.blk_off = cv.take<int64_t>(C + 1);
     w.pad_off = cv.take<int64_t>(C + 1);
     w.probs = cv.take<KnnProblem>(C);
-    w.G = cv.take<__nv_bfloat16>((size_t)w.rows_cap * pl.Kp);
+    w.G = (__nv_bfloat16*)cv.take<uint8_t>((size_t)w.rows_cap * row_bytes(pl));
     w.aug = cv.take<__nv_bfloat16>((size_t)w.rows_cap * kt::KAUG);
     w.ones = cv.take<__nv_bfloat16>((size_t)128 * kt::KAUG);
     w.norms = cv.take<float>((size_t)w.rows_cap + 512);
@@ -1142,17 +1226,18 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.src = cv.take<int64_t>((size_t)w.rows_cap);
     w.gid = cv.take<uint32_t>((size_t)w.rows_cap);
     w.outrow = cv.take<int64_t>((size_t)w.rows_cap);
-    w.prows_cap = rows / kt::CELL + (int64_t)(kt::BM + 1) * C + kt::BN;
+    w.prows_cap = rows / kt::CELL + (int64_t)(kt::BM + 1) * C + kt::BNMAX;
     w.ppad_off = cv.take<int64_t>(C + 1);
     w.npiv = cv.take<int32_t>(C);
     w.pprobs = cv.take<KnnProblem>(C);
     w.psrc = cv.take<int64_t>((size_t)w.prows_cap);
-    w.GP = cv.take<__nv_bfloat16>((size_t)w.prows_cap * pl.Kp);
+    w.GP = (__nv_bfloat16*)cv.take<uint8_t>((size_t)w.prows_cap * row_bytes(pl));
     w.paug = cv.take<__nv_bfloat16>((size_t)w.prows_cap * kt::KAUG);
     w.pnorms = cv.take<float>((size_t)w.prows_cap + 512);
     w.cell = cv.take<uint32_t>((size_t)rows);
     w.cell_d = cv.take<float>((size_t)rows);
     w.perm = cv.take<uint32_t>((size_t)rows);
+    w.amax = cv.take<float>(4);
     if (out) *out = w;
     return cv.used + 256;
 }
@@ -1161,14 +1246,16 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
                         const void* GB, const void* augB, int64_t rowsB, const KnnParams& P,
                         int64_t grid, cudaStream_t st, bool timed) {
     CUtensorMap ta, tb, taa, tba;
-    int rc = make_tmap(&ta, GA, rowsA, pl.Kp, kt::KB, kt::BM, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (!rc) rc = make_tmap(&tb, GB, rowsB, pl.Kp, kt::KB, kt::BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    const int es = pl.elem8 ? 1 : 2;
+    int rc = make_tmap(&ta, GA, rowsA, pl.Kp, pl.kbe, kt::BM, CU_TENSOR_MAP_SWIZZLE_128B, es);
+    if (!rc) rc = make_tmap(&tb, GB, rowsB, pl.Kp, pl.kbe, pl.bn, CU_TENSOR_MAP_SWIZZLE_128B, es);
     if (!rc) rc = make_tmap(&taa, ones, 128, kt::KAUG, kt::KAUG, kt::BM, CU_TENSOR_MAP_SWIZZLE_32B);
     if (!rc)
-        rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, kt::BN, CU_TENSOR_MAP_SWIZZLE_32B);
+        rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, pl.bn, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
     const bool prof = timed && tile_counters_on();
-    auto kern = prof ? k_knn_tiles<true> : k_knn_tiles<false>;
+    auto kern = pl.bn == 256 ? (prof ? k_knn_tiles<256, true> : k_knn_tiles<256, false>)
+                             : (prof ? k_knn_tiles<128, true> : k_knn_tiles<128, false>);
     ANN_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
     if (grid <= 0) return ANN_OK;
@@ -1222,8 +1309,11 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.kprime = pl.kprime;
     P.k_out = pl.rerank ? pl.kprime : k;
     P.nst = pl.nst;
-    P.idesc_neg = idesc_f16(kt::BM, kt::BN, pl.ab_fmt) | (1u << 13);  // negate A
-    P.idesc_aug = idesc_f16(kt::BM, kt::BN, 1);                       // BF16 norm step
+    P.kbe = pl.kbe;
+    P.kind8 = pl.elem8;
+    // same descriptor layout for kind::f16 and kind::f8f6f4 (format 0 = FP16 / E4M3)
+    P.idesc_neg = idesc_f16(kt::BM, pl.bn, pl.ab_fmt) | (1u << 13);  // negate A
+    P.idesc_aug = idesc_f16(kt::BM, pl.bn, 1);                       // BF16 norm step
     P.out_id = out_id;
     P.out_d = out_d;
     P.status = device_status_ptr();
@@ -1232,18 +1322,35 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
 
 static int launch_gather(const void* X, int dtype, int d, const int64_t* src, int64_t rows_cap,
                          const KnnPlan& pl, void* G, float* norms, __nv_bfloat16* aug,
-                         cudaStream_t st) {
+                         const unsigned int* amax, cudaStream_t st) {
     const int threads = 256;
     const int64_t want = (rows_cap * 32 + threads - 1) / threads;
     const unsigned grid = (unsigned)(want < 152 * 64 ? want : 152 * 64);
-    if (pl.ab_fmt == 1)
+    if (pl.elem8)
+        k_gather<__nv_fp8_e4m3><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode,
+                                                          pl.Kp, pl.Kh, (__nv_fp8_e4m3*)G, norms,
+                                                          aug, amax);
+    else if (pl.ab_fmt == 1)
         k_gather<__nv_bfloat16><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode,
                                                           pl.Kp, pl.Kh, (__nv_bfloat16*)G, norms,
-                                                          aug);
+                                                          aug, nullptr);
     else
         k_gather<__half><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode, pl.Kp,
-                                                  pl.Kh, (__half*)G, norms, aug);
+                                                  pl.Kh, (__half*)G, norms, aug, nullptr);
     ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+// E4M3 plans: the largest |x| over the given arrays into amax (float bits).
+static int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,
+                         unsigned int* amax, cudaStream_t st) {
+    ANN_CHECK_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned int), st));
+    k_absmax<<<152 * 8, 256, 0, st>>>(X, dtype, n, amax);
+    ANN_CHECK_LAUNCH();
+    if (Q && nq_elems > 0) {
+        k_absmax<<<152 * 2, 256, 0, st>>>(Q, dtype, nq_elems, amax);
+        ANN_CHECK_LAUNCH();
+    }
     return ANN_OK;
 }
 
@@ -1270,7 +1377,13 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnPlan pp = pl;
     pp.kprime = 1;
     pp.rerank = false;
-    pp.smem = knn_smem_layout(pp.nkb_a, pp.nst, 1).total;
+    pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, 1).total;
+    const unsigned int* amax = nullptr;
+    if (pl.elem8) {
+        int rc8 = launch_absmax(X, dtype, N * d, nullptr, 0, (unsigned int*)w.amax, st);
+        if (rc8) return rc8;
+        amax = (const unsigned int*)w.amax;
+    }
     k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, kt::CELL, w.pad_off, w.ppad_off, w.npiv, w.pprobs);
     ANN_CHECK_LAUNCH();
     k_rowmap_plain<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, C,
@@ -1279,8 +1392,10 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     k_rowmap_pivots<<<grid_rows(w.prows_cap, 256), 256, 0, st>>>(members, offsets, w.ppad_off,
                                                                  w.npiv, C, w.prows_cap, w.psrc);
     ANN_CHECK_LAUNCH();
-    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, st))) return rc;
-    if ((rc = launch_gather(X, dtype, d, w.psrc, w.prows_cap, pl, w.GP, w.pnorms, w.paug, st)))
+    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, amax, st)))
+        return rc;
+    if ((rc = launch_gather(X, dtype, d, w.psrc, w.prows_cap, pl, w.GP, w.pnorms, w.paug, amax,
+                            st)))
         return rc;
     KnnParams PP = base_params(pp, 1, w.blk_off, w.pprobs, C, w.norms, nullptr, nullptr, 0, 0,
                                w.cell, w.cell_d);
@@ -1295,7 +1410,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                                                                C, w.rows_cap, w.src, w.gid,
                                                                w.outrow);
     ANN_CHECK_LAUNCH();
-    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, st))) return rc;
+    if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, amax, st)))
+        return rc;
     // 3. the kNN sweep
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
@@ -1312,14 +1428,14 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
 size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* base, size_t cap) {
     Carver cv(base, cap);
     QueryWs w;
-    w.capA = nq + kt::BM + kt::BN;
-    w.capB = N + kt::BM + kt::BN;
+    w.capA = nq + kt::BM + kt::BNMAX;
+    w.capB = N + kt::BM + kt::BNMAX;
     w.blk_off = cv.take<int64_t>(4);
     w.pad_off = cv.take<int64_t>(4);
     w.offs = cv.take<int64_t>(4);
     w.prob = cv.take<KnnProblem>(1);
-    w.GA = cv.take<__nv_bfloat16>((size_t)w.capA * pl.Kp);
-    w.GB = cv.take<__nv_bfloat16>((size_t)w.capB * pl.Kp);
+    w.GA = (__nv_bfloat16*)cv.take<uint8_t>((size_t)w.capA * row_bytes(pl));
+    w.GB = (__nv_bfloat16*)cv.take<uint8_t>((size_t)w.capB * row_bytes(pl));
     w.augA = cv.take<__nv_bfloat16>((size_t)w.capA * kt::KAUG);
     w.augB = cv.take<__nv_bfloat16>((size_t)w.capB * kt::KAUG);
     w.ones = cv.take<__nv_bfloat16>((size_t)128 * kt::KAUG);
@@ -1329,6 +1445,7 @@ size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* ba
     w.cand_d = pl.rerank ? cv.take<float>((size_t)nq * pl.kprime) : nullptr;
     w.srcA = cv.take<int64_t>((size_t)w.capA);
     w.srcB = cv.take<int64_t>((size_t)w.capB);
+    w.amax = cv.take<float>(4);
     if (out) *out = w;
     return cv.used + 256;
 }
@@ -1369,8 +1486,14 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     k_rowmap_plain<<<grid_rows(w.capB, 256), 256, 0, st>>>(nullptr, w.offs + 2, w.pad_off + 2, 1,
                                                            w.capB, w.srcB);
     ANN_CHECK_LAUNCH();
-    int rc = launch_gather(Q, dtype, d, w.srcA, w.capA, pl, w.GA, w.na, w.augA, st);
-    if (!rc) rc = launch_gather(X, dtype, d, w.srcB, w.capB, pl, w.GB, w.nb, w.augB, st);
+    const unsigned int* amax = nullptr;
+    if (pl.elem8) {
+        int rc8 = launch_absmax(X, dtype, N * d, Q, nq * d, (unsigned int*)w.amax, st);
+        if (rc8) return rc8;
+        amax = (const unsigned int*)w.amax;
+    }
+    int rc = launch_gather(Q, dtype, d, w.srcA, w.capA, pl, w.GA, w.na, w.augA, amax, st);
+    if (!rc) rc = launch_gather(X, dtype, d, w.srcB, w.capB, pl, w.GB, w.nb, w.augB, amax, st);
     if (rc) return rc;
     KnnParams P = base_params(pl, k, w.blk_off, w.prob, 1, w.na, nullptr, nullptr, 0, 0,
                               pl.rerank ? w.cand_id : out_id, pl.rerank ? w.cand_d : out_d);

@@ -42,13 +42,16 @@ struct KnnPlan {
     int Kp;           // elements per gathered row
     int Kh;           // split: elements per section
     int nkb_a, nkb_b;
-    uint32_t ab_fmt;  // 0 fp16, 1 bf16
+    int elem8;        // 1: E4M3 operands (kind::f8f6f4)
+    int kbe;          // elements per 128-byte K block
+    int bn;           // tile width (N of one MMA): 256 or 128
+    uint32_t ab_fmt;  // 16-bit operands: 0 fp16, 1 bf16 (E4M3: 0)
     bool rerank;
     int kprime;
     int nst;
     size_t smem;
 };
-int knn_plan(int d, int dtype, int k, int rerank_k, KnnPlan* pl);
+int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl);
 
 struct KnnWs {
     int64_t* blk_off;
@@ -76,6 +79,7 @@ struct KnnWs {
     uint32_t* cell;     // [rows] nearest pivot of each member row
     float* cell_d;
     uint32_t* perm;     // [rows] local index of the row at each cell-ordered position
+    float* amax;        // E4M3 plans: largest |x| (float bits)
 };
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
@@ -99,6 +103,7 @@ struct QueryWs {
     int64_t capA, capB;
     int64_t* srcA;
     int64_t* srcB;
+    float* amax;
 };
 size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* base, size_t cap);
 int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, int dtype, int k,

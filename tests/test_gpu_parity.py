@@ -252,3 +252,41 @@ def test_end_to_end_gauss10k():
     check_float_lists(X, mem_o, out["knn_id"].cpu().numpy(), out["knn_d"].cpu().numpy(), oid, od)
     g, deg = as_u32(out["graph"]), as_u32(out["degree"])
     assert np.all(deg <= w.R) and not np.any(g == np.arange(w.N)[:, None])
+
+
+# ------------------------------------------------------------ precision forms
+
+def _recall10(gid, oid):
+    hit = 0
+    for g, o in zip(gid[:, :10], oid[:, :10]):
+        hit += len(set(g.tolist()) & set(o.tolist()) - {PAD})
+    return hit / (10 * len(gid))
+
+
+@pytest.mark.parametrize("prec,bar", [(ann.BF16_RERANK, 0.995), (ann.FP8_RERANK, 0.95)])
+def test_precision_forms_rerank_exact_distances_and_recall(prec, bar):
+    """BF16 / E4M3 screening tiles, FP32 re-rank of the top 128 (Deep-like unit vectors)."""
+    X = datagen.anisotropic_mixture(12000, 96, 64, 0.25, True, np.float32, seed=101)
+    mem, off = _oracle_shards(X, 4, 2, seed=102)
+    k = 64
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), k, precision=prec, rerank_k=128)
+    gid, gd = as_u32(gid), gd.cpu().numpy().astype(np.float64)
+    oid, od = oracle.shard_knn(X, mem, off, k)
+    for q in range(0, len(mem), 97):  # every returned distance is the exact FP32 one
+        u = mem[q]
+        ok = gid[q] != PAD
+        true_d = ((X[gid[q][ok]].astype(np.float64) - X[u].astype(np.float64)) ** 2).sum(1)
+        assert np.all(np.abs(gd[q][ok] - true_d) <= 1e-5 * true_d + 1e-12)
+        key = list(zip(gd[q][ok].tolist(), gid[q][ok].tolist()))
+        assert key == sorted(key) and u not in gid[q]
+    rec = _recall10(gid, oid)
+    assert rec >= bar, rec
+
+
+def test_bf16_precision_form_is_exact_on_uint8():
+    X = datagen.clustered_u8(4000, 128, 16, seed=103)
+    mem, off = _oracle_shards(X, 3, 2, seed=104)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 32, precision=ann.BF16_RERANK, rerank_k=64)
+    oid, od = oracle.shard_knn(X, mem, off, 32)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
