@@ -55,7 +55,17 @@ enum ann_dtype { ANN_F32 = 0, ANN_F16 = 1, ANN_BF16 = 2, ANN_U8 = 3 };
  *  ANN_EXACT: uint8 -> BF16 tiles with FP32 accumulation (exact integers);
  *             float -> BF16 hi/lo split tiles (three products) screening a
  *             widened list, then an FP32 direct-form re-rank.
- *  ANN_BF16_RERANK / ANN_FP8_RERANK / ANN_LEARNED: reserved (not built yet). */
+ *  ANN_BF16_RERANK: float vectors rounded once to BF16 (one product per
+ *             pair, FP32 accumulation) screen a list of rerank_k (default
+ *             128) candidates per row, then the FP32 direct-form re-rank
+ *             picks the k of smallest (distance, id); on uint8 it equals
+ *             ANN_EXACT (BF16 holds 0..255 exactly).
+ *  ANN_FP8_RERANK: as ANN_BF16_RERANK with E4M3 screening tiles
+ *             (tcgen05 kind::f8f6f4): every element is multiplied by one
+ *             global scale 448 / max|x| before rounding, and the norm terms
+ *             use the same scaled values.  E4M3 keeps 3 mantissa bits, so
+ *             the screened list misses more true neighbours than BF16's.
+ *  ANN_LEARNED: reserved (not built yet; returns ANN_ERR_UNSUPPORTED). */
 enum ann_precision { ANN_EXACT = 0, ANN_BF16_RERANK = 1, ANN_FP8_RERANK = 2, ANN_LEARNED = 3 };
 
 /* Prune rule for L -> R (Sec. III, Sec. VI-B2 use L = 2R; the rule itself is
@@ -137,10 +147,13 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
  *  members, offsets  as produced by ann_partition (C shards, rows = offsets[C]
  *                    total members; each shard's ids sorted increasingly).
  *  knn_id / knn_d    [rows x k] output, row p for members[p].
- *  precision         ANN_EXACT only (see enum).  uint8 results are bit-exact;
- *                    float results carry FP32 direct-form distances.
- *  rerank_k          width of the screened list for float data before the
- *                    re-rank (0 = k + 16); ignored for uint8.
+ *  precision         ANN_EXACT, ANN_BF16_RERANK or ANN_FP8_RERANK (see
+ *                    enum).  uint8 results are bit-exact under ANN_EXACT and
+ *                    ANN_BF16_RERANK; float results carry FP32 direct-form
+ *                    distances of the ids returned.
+ *  rerank_k          width of the screened list before the re-rank: 0 =
+ *                    k + 16 (ANN_EXACT) or 128 (the screening forms); else
+ *                    k <= rerank_k <= 128.  Ignored for uint8 under ANN_EXACT.
  *  model             reserved, must be NULL.
  * Limits: d <= 256 (uint8: d <= 258 keeps the integer tiles exact),
  * 1 <= k <= 96, every shard smaller than 2^24 members.
