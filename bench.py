@@ -149,6 +149,26 @@ def oracle_sample(w, X, budget_rows=48):
     return w.N / total, oracle.num_threads(), desc, total
 
 
+# ------------------------------------------------------------------ multi-rank helpers
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of per-rank values over all ranks of the default
+    process group (the values themselves when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, timed by the slowest rank (weak scaling:
+    every rank builds its own replica of the workload)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -279,12 +299,7 @@ def main():
         counters = ann.tile_counters_read()
         ann.tile_counters_enable(False)
 
-    if dist is not None:
-        t = torch.tensor([ms, float(np.mean(e2e_ms))], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_mean = t.tolist()
-    else:
-        e2e_mean = float(np.mean(e2e_ms))
+    ms, e2e_mean = max_over_ranks([ms, float(np.mean(e2e_ms))], dev)
 
     off = out["offsets"].cpu().numpy()
     sizes = np.diff(off).astype(np.float64)
@@ -313,7 +328,7 @@ def main():
         return
     line = {
         "metric": METRIC,
-        "value": world * w.N / (ms * 1e-3),
+        "value": whole_job_rate(w.N, world, ms),
         "unit": "vectors/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -351,7 +366,7 @@ def main():
             "algorithmic_flops_per_launch": flops, "kernel_ms": tile_avg_ms,
         },
         "e2e": {
-            "value": world * w.N / (e2e_mean * 1e-3), "unit": "vectors/s",
+            "value": whole_job_rate(w.N, world, e2e_mean), "unit": "vectors/s",
             "h2d_bytes_per_step": int(X.nbytes),
             "d2h_bytes_per_step": int(graph_h.numel() * 4 + gdist_h.numel() * 4 + deg_h.numel() * 4),
             "ms_per_step": e2e_mean,
