@@ -761,32 +761,79 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
 
 // ---- problem tables, gather and norms ------------------------------------------
 // probs[s] for the C shards: a/b rows at the 128-padded offsets, out rows at offsets.
-__global__ void k_shard_tables(const int64_t* __restrict__ offsets, int C, int64_t rows,
-                               int64_t* __restrict__ blk_off, int64_t* __restrict__ pad_off,
-                               KnnProblem* __restrict__ probs, int* status) {
-    if (threadIdx.x || blockIdx.x) return;
-    int64_t b = 0, p = 0;
-    bool bad = offsets[0] != 0 || offsets[C] != rows;
-    for (int s = 0; s < C; ++s) {
-        int64_t n = offsets[s + 1] - offsets[s];
-        if (n < 0 || n >= (1ll << 24)) { bad = true; n = 0; }
-        blk_off[s] = b;
-        pad_off[s] = p;
-        KnnProblem pr;
-        pr.a_row0 = p;
-        pr.b_row0 = p;
-        pr.out_row0 = offsets[s];
-        pr.mem_row0 = offsets[s];
-        pr.n_rows = (int32_t)n;
-        pr.n_cols = (int32_t)n;
-        probs[s] = pr;
-        const int64_t nbk = (n + kt::BM - 1) / kt::BM;
-        b += nbk;
-        p += nbk * kt::BM;
+// One block of 1024 threads, thread s = shard s (C <= 1024).  Gathered rows stay
+// in shard order (pad_off: 128-padded row offsets); the problem table lists the
+// shards by decreasing size (order[j] = shard of problem j), so the CTAs of the
+// largest shards start first and the launch ends on short CTAs.
+__global__ void __launch_bounds__(1024)
+    k_shard_tables(const int64_t* __restrict__ offsets, int C, int64_t rows,
+                   int64_t* __restrict__ blk_off, int64_t* __restrict__ pad_off,
+                   KnnProblem* __restrict__ probs, int32_t* __restrict__ order_out, int* status) {
+    __shared__ int64_t nbk[1024], scan[1024], psh[1024];
+    __shared__ int order[1024];
+    __shared__ int bad;
+    const int s = threadIdx.x;
+    if (blockIdx.x) return;
+    if (s == 0) bad = (offsets[0] != 0 || offsets[C] != rows) ? 1 : 0;
+    __syncthreads();
+    int64_t n = 0;
+    if (s < C) {
+        n = offsets[s + 1] - offsets[s];
+        if (n < 0 || n >= (1ll << 24)) {
+            bad = 1;
+            n = 0;
+        }
     }
-    blk_off[C] = bad ? 0 : b;  // nothing runs on inconsistent input
-    pad_off[C] = p;
-    if (bad) atomicOr(status, DEV_BAD_INPUT);
+    nbk[s] = (n + kt::BM - 1) / kt::BM;
+    scan[s] = nbk[s];
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive prefix sum (Hillis-Steele)
+        const int64_t v = s >= o ? scan[s - o] : 0;
+        __syncthreads();
+        scan[s] += v;
+        __syncthreads();
+    }
+    psh[s] = (scan[s] - nbk[s]) * kt::BM;
+    if (s < C) pad_off[s] = psh[s];
+    if (s == C - 1) pad_off[C] = scan[s] * kt::BM;
+    if (s < C) {  // rank by (size descending, shard ascending)
+        int r = 0;
+        for (int t = 0; t < C; ++t) {
+            int64_t m = offsets[t + 1] - offsets[t];
+            if (m < 0 || m >= (1ll << 24)) m = 0;
+            r += (m > n || (m == n && t < s)) ? 1 : 0;
+        }
+        order[r] = s;
+    }
+    __syncthreads();
+    const int sh = s < C ? order[s] : 0;
+    const int64_t mine = s < C ? nbk[sh] : 0;
+    __syncthreads();
+    scan[s] = mine;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = s >= o ? scan[s - o] : 0;
+        __syncthreads();
+        scan[s] += v;
+        __syncthreads();
+    }
+    if (s < C) {
+        const int64_t ns = nbk[sh] ? offsets[sh + 1] - offsets[sh] : 0;
+        blk_off[s] = scan[s] - mine;
+        order_out[s] = sh;
+        KnnProblem q;
+        q.a_row0 = psh[sh];
+        q.b_row0 = psh[sh];
+        q.out_row0 = offsets[sh];
+        q.mem_row0 = offsets[sh];
+        q.n_rows = (int32_t)ns;
+        q.n_cols = (int32_t)ns;
+        probs[s] = q;
+    }
+    if (s == C - 1) {
+        blk_off[C] = bad ? 0 : scan[s];  // nothing runs on inconsistent input
+        if (bad) atomicOr(status, DEV_BAD_INPUT);
+    }
 }
 
 // [1, 1, 1, 0 x 13] in every one of 128 rows: the A side of the norm K step.
@@ -920,9 +967,13 @@ __global__ void k_rowmap_plain(const uint32_t* __restrict__ members,
 // Pivots of every shard: P_s = ceil(n_s / cell) evenly spaced members (cells of
 // about `cell` rows).  Tables for the pivot-assignment launch: A = the shard's
 // rows, B = its pivots.
+// Pivot problems (a shard's rows against its pivots), listed in the same order as
+// the shard problems (order[j] = shard of problem j) so that both launches share
+// blk_off.
 __global__ void k_pivot_tables(const int64_t* __restrict__ offsets, int C, int cell,
-                               const int64_t* __restrict__ pad_off, int64_t* __restrict__ ppad_off,
-                               int32_t* __restrict__ npiv, KnnProblem* __restrict__ pprobs) {
+                               const int64_t* __restrict__ pad_off, const int32_t* __restrict__ order,
+                               int64_t* __restrict__ ppad_off, int32_t* __restrict__ npiv,
+                               KnnProblem* __restrict__ pprobs) {
     if (threadIdx.x || blockIdx.x) return;
     int64_t p = 0;
     for (int s = 0; s < C; ++s) {
@@ -933,17 +984,22 @@ __global__ void k_pivot_tables(const int64_t* __restrict__ offsets, int C, int c
         if (P > 1024) P = 1024;
         npiv[s] = (int32_t)P;
         ppad_off[s] = p;
-        KnnProblem pr;
-        pr.a_row0 = pad_off[s];
-        pr.b_row0 = p;
-        pr.out_row0 = offsets[s];
-        pr.mem_row0 = 0;
-        pr.n_rows = (int32_t)n;
-        pr.n_cols = n > 0 ? (int32_t)P : 0;
-        pprobs[s] = pr;
         p += (P + kt::BM - 1) / kt::BM * kt::BM;
     }
     ppad_off[C] = p;
+    for (int j = 0; j < C; ++j) {
+        const int s = order[j];
+        int64_t n = offsets[s + 1] - offsets[s];
+        if (n < 0) n = 0;
+        KnnProblem pr;
+        pr.a_row0 = pad_off[s];
+        pr.b_row0 = ppad_off[s];
+        pr.out_row0 = offsets[s];
+        pr.mem_row0 = 0;
+        pr.n_rows = (int32_t)n;
+        pr.n_cols = n > 0 ? npiv[s] : 0;
+        pprobs[j] = pr;
+    }
 }
 
 __global__ void k_rowmap_pivots(const uint32_t* __restrict__ members,
@@ -1228,6 +1284,7 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.prows_cap = rows / kt::CELL + (int64_t)(kt::BM + 1) * C + kt::BNMAX;
     w.ppad_off = cv.take<int64_t>(C + 1);
     w.npiv = cv.take<int32_t>(C);
+    w.order = cv.take<int32_t>(C);
     w.pprobs = cv.take<KnnProblem>(C);
     w.psrc = cv.take<int64_t>((size_t)w.prows_cap);
     w.GP = (__nv_bfloat16*)cv.take<uint8_t>((size_t)w.prows_cap * row_bytes(pl));
@@ -1367,7 +1424,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                   const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st) {
     (void)N;
     int* status = device_status_ptr();
-    k_shard_tables<<<1, 32, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs, status);
+    k_shard_tables<<<1, 1024, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs, w.order,
+                                       status);
     ANN_CHECK_LAUNCH();
     k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
     ANN_CHECK_LAUNCH();
@@ -1383,7 +1441,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         if (rc8) return rc8;
         amax = (const unsigned int*)w.amax;
     }
-    k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, kt::CELL, w.pad_off, w.ppad_off, w.npiv, w.pprobs);
+    k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, kt::CELL, w.pad_off, w.order, w.ppad_off, w.npiv,
+                                     w.pprobs);
     ANN_CHECK_LAUNCH();
     k_rowmap_plain<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, C,
                                                                w.rows_cap, w.src);

@@ -71,6 +71,7 @@ struct KnnWs {
     int64_t prows_cap;  // pivot rows (padded per shard)
     int64_t* ppad_off;  // [C+1]
     int32_t* npiv;      // [C]
+    int32_t* order;     // [C] shard of problem j (shards by decreasing size)
     KnnProblem* pprobs; // [C]
     int64_t* psrc;      // [prows_cap]
     __nv_bfloat16* GP;  // [prows_cap x Kp]
