@@ -181,9 +181,9 @@ def main():
     ap.add_argument("--nq", type=int, default=1000)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
-    ap.add_argument("--precision", default="exact", choices=["exact", "bf16", "fp8"],
-                    help="distance-tile form: exact (uint8 / FP32 split), or BF16 / E4M3 "
-                         "screening with an FP32 re-rank of the top 128")
+    ap.add_argument("--precision", default="exact", choices=["exact", "bf16", "f16", "fp8"],
+                    help="distance-tile form: exact (uint8 / FP32 split), or BF16 / scaled "
+                         "FP16 / E4M3 screening with an FP32 re-rank of the top 128")
     ap.add_argument("--tile-counters", action="store_true",
                     help="after timing, run one step with the counting kernel variant and "
                          "report its per-role cycle counters")
@@ -223,7 +223,8 @@ def main():
     Xd = Xh.to(dev)
     init_d = torch.from_numpy(init).to(dev)
     samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
-    prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "fp8": ann.FP8_RERANK}[args.precision]
+    prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "f16": ann.F16_RERANK,
+            "fp8": ann.FP8_RERANK}[args.precision]
     cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R, iters=10, precision=prec)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
@@ -320,6 +321,9 @@ def main():
         products = 3
     elif prec == ann.BF16_RERANK:
         dtype, operands, products = "bf16", "bf16, fp32 accumulate; fp32 re-rank of top 128", 1
+    elif prec == ann.F16_RERANK:
+        dtype, operands, products = ("f16", "fp16 (power-of-two global scale), fp32 accumulate; "
+                                     "fp32 re-rank of top 128", 1)
     else:
         dtype, operands, products = "fp8", "e4m3 (one global scale), fp32 accumulate; fp32 re-rank of top 128", 1
     if rank != 0:

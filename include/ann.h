@@ -65,8 +65,18 @@ enum ann_dtype { ANN_F32 = 0, ANN_F16 = 1, ANN_BF16 = 2, ANN_U8 = 3 };
  *             global scale 448 / max|x| before rounding, and the norm terms
  *             use the same scaled values.  E4M3 keeps 3 mantissa bits, so
  *             the screened list misses more true neighbours than BF16's.
+ *  ANN_F16_RERANK: as ANN_BF16_RERANK with FP16 screening tiles: every
+ *             element is multiplied by the power of two that puts max|x| in
+ *             [2^13, 2^14) (exact), then rounded to FP16 (11 significant bits
+ *             against BF16's 8, same tensor-core rate).  Exact on uint8.
  *  ANN_LEARNED: reserved (not built yet; returns ANN_ERR_UNSUPPORTED). */
-enum ann_precision { ANN_EXACT = 0, ANN_BF16_RERANK = 1, ANN_FP8_RERANK = 2, ANN_LEARNED = 3 };
+enum ann_precision {
+    ANN_EXACT = 0,
+    ANN_BF16_RERANK = 1,
+    ANN_FP8_RERANK = 2,
+    ANN_LEARNED = 3,
+    ANN_F16_RERANK = 4
+};
 
 /* Prune rule for L -> R (Sec. III, Sec. VI-B2 use L = 2R; the rule itself is
  * not printed in the paper).  ANN_PRUNE_RANK: rank-based detour count
@@ -147,16 +157,17 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
  *  members, offsets  as produced by ann_partition (C shards, rows = offsets[C]
  *                    total members; each shard's ids sorted increasingly).
  *  knn_id / knn_d    [rows x k] output, row p for members[p].
- *  precision         ANN_EXACT, ANN_BF16_RERANK or ANN_FP8_RERANK (see
- *                    enum).  uint8 results are bit-exact under ANN_EXACT and
- *                    ANN_BF16_RERANK; float results carry FP32 direct-form
- *                    distances of the ids returned.
+ *  precision         ANN_EXACT, ANN_BF16_RERANK, ANN_F16_RERANK or
+ *                    ANN_FP8_RERANK (see enum).  uint8 results are bit-exact
+ *                    under ANN_EXACT, ANN_BF16_RERANK and ANN_F16_RERANK; float
+ *                    results carry FP32 direct-form distances of the ids
+ *                    returned.
  *  rerank_k          width of the screened list before the re-rank: 0 =
  *                    k + 16 (ANN_EXACT) or 128 (the screening forms); else
  *                    k <= rerank_k <= 128.  Ignored for uint8 under ANN_EXACT.
  *  model             reserved, must be NULL.
  * Limits: d <= 256 (uint8: d <= 258 keeps the integer tiles exact),
- * 1 <= k <= 96, every shard smaller than 2^24 members.
+ * 1 <= k <= 96, 1 <= C <= 1024, every shard smaller than 2^24 members.
  * ------------------------------------------------------------------------- */
 int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
                             int precision, int rerank_k, size_t* bytes);

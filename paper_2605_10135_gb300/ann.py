@@ -16,7 +16,7 @@ import torch
 from . import build as _build
 
 PAD = 0xFFFFFFFF
-EXACT, BF16_RERANK, FP8_RERANK, LEARNED = 0, 1, 2, 3
+EXACT, BF16_RERANK, FP8_RERANK, LEARNED, F16_RERANK = 0, 1, 2, 3, 4
 PRUNE_RANK, PRUNE_TRUNC = 0, 1
 _DT = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2, torch.uint8: 3}
 

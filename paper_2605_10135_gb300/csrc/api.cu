@@ -201,12 +201,13 @@ static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int
                     int rerank_k) {
     ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
     ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
-    ANN_REQUIRE(C >= 1 && C <= (1 << 20), "C out of range");
+    ANN_REQUIRE(C >= 1 && C <= 1024, "C must be in [1, 1024]");
     ANN_REQUIRE(rows >= 0 && rows < (1ll << 40), "rows out of range");
     ANN_REQUIRE(k >= 1 && k <= 96, "k must be in [1, 96]");
     ANN_REQUIRE(d >= 1, "d < 1");
     ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 128), "rerank_k must be 0 or in [k, 128]");
-    if (precision != ANN_EXACT && precision != ANN_BF16_RERANK && precision != ANN_FP8_RERANK)
+    if (precision != ANN_EXACT && precision != ANN_BF16_RERANK && precision != ANN_FP8_RERANK &&
+        precision != ANN_F16_RERANK)
         return fail(ANN_ERR_UNSUPPORTED, "precision %d is not built in this version", precision);
     if (d > 256) return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d > 256 not built in this version");
     return ANN_OK;

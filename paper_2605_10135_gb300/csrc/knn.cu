@@ -880,10 +880,21 @@ __global__ void k_gather(const void* X, int dtype, int d, const int64_t* __restr
                          int64_t rows_cap, int mode, int Kp, int Kh, T* __restrict__ G,
                          float* __restrict__ norms, __nv_bfloat16* __restrict__ aug,
                          const unsigned int* __restrict__ amax_bits) {
+    // Global operand scale: E4M3 maps max|x| to 448 (the largest finite value);
+    // scaled FP16 multiplies by the power of two that puts max|x| in [2^13, 2^14)
+    // (exact, and far from both overflow and the subnormal range).
     float scale = 1.0f;
     if (amax_bits) {
         const float am = __uint_as_float(*amax_bits);
-        if (am > 0.0f) scale = 448.0f / am;
+        if (am > 0.0f && am <= 3.0e38f) {
+            if (sizeof(T) == 1) {
+                scale = 448.0f / am;
+            } else {
+                int ex;
+                frexpf(am, &ex);
+                scale = ldexpf(1.0f, 14 - ex);
+            }
+        }
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -966,10 +977,8 @@ __global__ void k_rowmap_plain(const uint32_t* __restrict__ members,
 
 // Pivots of every shard: P_s = ceil(n_s / cell) evenly spaced members (cells of
 // about `cell` rows).  Tables for the pivot-assignment launch: A = the shard's
-// rows, B = its pivots.
-// Pivot problems (a shard's rows against its pivots), listed in the same order as
-// the shard problems (order[j] = shard of problem j) so that both launches share
-// blk_off.
+// rows, B = its pivots, listed in the same order as the shard problems
+// (order[j] = shard of problem j) so that both launches share blk_off.
 __global__ void k_pivot_tables(const int64_t* __restrict__ offsets, int C, int cell,
                                const int64_t* __restrict__ pad_off, const int32_t* __restrict__ order,
                                int64_t* __restrict__ ppad_off, int32_t* __restrict__ npiv,
@@ -1208,12 +1217,21 @@ static int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int
 int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) {
     KnnPlan p;
     p.elem8 = 0;
+    p.scaled = 0;
     if (precision == ANN_FP8_RERANK) {
         p.mode = 0;
         p.Kh = 0;
         p.elem8 = 1;
+        p.scaled = 1;
         p.Kp = (int)align_up((size_t)d, kt::KB8);
         p.ab_fmt = 0;  // E4M3
+        p.rerank = true;
+    } else if (precision == ANN_F16_RERANK) {
+        p.mode = 0;
+        p.Kh = 0;
+        p.scaled = 1;
+        p.Kp = (int)align_up((size_t)d, kt::KB);
+        p.ab_fmt = 0;  // FP16
         p.rerank = true;
     } else if (precision == ANN_BF16_RERANK) {
         p.mode = 0;
@@ -1392,12 +1410,14 @@ static int launch_gather(const void* X, int dtype, int d, const int64_t* src, in
                                                           aug, nullptr);
     else
         k_gather<__half><<<grid, threads, 0, st>>>(X, dtype, d, src, rows_cap, pl.mode, pl.Kp,
-                                                  pl.Kh, (__half*)G, norms, aug, nullptr);
+                                                  pl.Kh, (__half*)G, norms, aug,
+                                                  pl.scaled ? amax : nullptr);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }
 
-// E4M3 plans: the largest |x| over the given arrays into amax (float bits).
+// Scaled plans (E4M3, FP16): the largest |x| over the given arrays into amax
+// (float bits).
 static int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,
                          unsigned int* amax, cudaStream_t st) {
     ANN_CHECK_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned int), st));
@@ -1436,7 +1456,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     pp.rerank = false;
     pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, 1).total;
     const unsigned int* amax = nullptr;
-    if (pl.elem8) {
+    if (pl.scaled) {
         int rc8 = launch_absmax(X, dtype, N * d, nullptr, 0, (unsigned int*)w.amax, st);
         if (rc8) return rc8;
         amax = (const unsigned int*)w.amax;
@@ -1545,7 +1565,7 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
                                                            w.capB, w.srcB);
     ANN_CHECK_LAUNCH();
     const unsigned int* amax = nullptr;
-    if (pl.elem8) {
+    if (pl.scaled) {
         int rc8 = launch_absmax(X, dtype, N * d, Q, nq * d, (unsigned int*)w.amax, st);
         if (rc8) return rc8;
         amax = (const unsigned int*)w.amax;

@@ -43,6 +43,7 @@ struct KnnPlan {
     int Kh;           // split: elements per section
     int nkb_a, nkb_b;
     int elem8;        // 1: E4M3 operands (kind::f8f6f4)
+    int scaled;       // 1: operands carry one global scale from max|x| (E4M3, scaled FP16)
     int kbe;          // elements per 128-byte K block
     int bn;           // tile width (N of one MMA): 256 or 128
     uint32_t ab_fmt;  // 16-bit operands: 0 fp16, 1 bf16 (E4M3: 0)

@@ -47,6 +47,8 @@ def test_workspace_queries_validate_on_host(L):
     assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 0, 0, 0, ct.byref(n)) == 1  # k = 0
     assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 1, 0, ct.byref(n)) == 0  # BF16 form
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 2, 0, ct.byref(n)) == 0  # E4M3 form
+    assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 4, 0, ct.byref(n)) == 0  # FP16 form
+    assert L.ann_shard_knn_workspace(1000, 128, 0, 2000, 2000, 64, 0, 0, ct.byref(n)) == 1  # C
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 2, 32, ct.byref(n)) == 1  # < k
     assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 3, 0, ct.byref(n)) == 2  # reserved
     assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256

@@ -265,7 +265,8 @@ def _recall10(gid, oid):
 
 # E4M3 keeps 3 mantissa bits: on unit vectors at d = 96 its screening list of 128
 # holds about 79% of the exact top 10 (measured); BF16's holds all but a few.
-@pytest.mark.parametrize("prec,bar", [(ann.BF16_RERANK, 0.995), (ann.FP8_RERANK, 0.75)])
+@pytest.mark.parametrize("prec,bar", [(ann.BF16_RERANK, 0.995), (ann.F16_RERANK, 0.995),
+                                      (ann.FP8_RERANK, 0.75)])
 def test_precision_forms_rerank_exact_distances_and_recall(prec, bar):
     """BF16 / E4M3 screening tiles, FP32 re-rank of the top 128 (Deep-like unit vectors)."""
     X = datagen.anisotropic_mixture(12000, 96, 64, 0.25, True, np.float32, seed=101)
@@ -285,10 +286,12 @@ def test_precision_forms_rerank_exact_distances_and_recall(prec, bar):
     assert rec >= bar, rec
 
 
-def test_bf16_precision_form_is_exact_on_uint8():
+@pytest.mark.parametrize("prec", [ann.BF16_RERANK, ann.F16_RERANK])
+def test_16bit_precision_forms_are_exact_on_uint8(prec):
+    """0..255 and their products are exact in BF16 and in power-of-two-scaled FP16."""
     X = datagen.clustered_u8(4000, 128, 16, seed=103)
     mem, off = _oracle_shards(X, 3, 2, seed=104)
-    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 32, precision=ann.BF16_RERANK, rerank_k=64)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 32, precision=prec, rerank_k=64)
     oid, od = oracle.shard_knn(X, mem, off, 32)
     assert np.array_equal(as_u32(gid), oid)
     assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
