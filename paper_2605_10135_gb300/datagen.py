@@ -30,6 +30,9 @@ __all__ = [
     "powerlaw_gaussian",
     "kmeans_sample",
     "uneven_shards",
+    "mlp_init",
+    "triplet_draws",
+    "row_sample",
 ]
 
 
@@ -187,3 +190,28 @@ def uneven_shards(n: int, n_shards: int, r: int, lo: int, hi: int, seed: int
             members[fill[c]] = g
             fill[c] += 1
     return members, offsets
+
+
+def mlp_init(d: int, hidden: int = 256, out: int = 32, seed: int = 1006) -> np.ndarray:
+    """Initial parameters of the d -> hidden -> out projection MLP as one float32
+    array [W1 (hidden x d) | b1 | W2 (out x hidden) | b2]: W1 ~ N(0, 2/d) (He),
+    W2 ~ N(0, 1/hidden), biases zero."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, np.sqrt(2.0 / d), size=(hidden, d))
+    W2 = rng.normal(0.0, np.sqrt(1.0 / hidden), size=(out, hidden))
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(out)]
+                          ).astype(np.float32)
+
+
+def triplet_draws(steps: int, batch: int, seed: int = 1007) -> np.ndarray:
+    """Uniform uint32 draws [steps, batch, 3] for the triplet picks (anchor slot,
+    positive rank, negative row), reduced modulo their ranges by the method."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 2**32, size=(steps, batch, 3), dtype=np.uint64).astype(np.uint32)
+
+
+def row_sample(n: int, frac: float = 0.01, minimum: int = 256, seed: int = 1008) -> np.ndarray:
+    """Sorted uint32 sample of max(minimum, frac * n) distinct rows (at most n)."""
+    rng = np.random.default_rng(seed)
+    s = min(n, max(minimum, int(frac * n)))
+    return np.sort(rng.choice(n, size=s, replace=False)).astype(np.uint32)
