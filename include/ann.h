@@ -69,7 +69,8 @@ enum ann_dtype { ANN_F32 = 0, ANN_F16 = 1, ANN_BF16 = 2, ANN_U8 = 3 };
  *             element is multiplied by the power of two that puts max|x| in
  *             [2^13, 2^14) (exact), then rounded to FP16 (11 significant bits
  *             against BF16's 8, same tensor-core rate).  Exact on uint8.
- *  ANN_LEARNED: reserved (not built yet; returns ANN_ERR_UNSUPPORTED). */
+ *  ANN_LEARNED: candidates proposed by a learned 32-dimensional embedding,
+ *             re-ranked exactly (see ann_learned_train below). */
 enum ann_precision {
     ANN_EXACT = 0,
     ANN_BF16_RERANK = 1,
@@ -165,8 +166,9 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
  *  rerank_k          width of the screened list before the re-rank: 0 =
  *                    k + 16 (ANN_EXACT) or 128 (the screening forms); else
  *                    k <= rerank_k <= 128.  Ignored for uint8 under ANN_EXACT.
- *  model             reserved, must be NULL.
- * Limits: d <= 256 (uint8: d <= 258 keeps the integer tiles exact),
+ *  model             ANN_LEARNED: the device parameter array of the MLP (see
+ *                    ann_learned_train); otherwise NULL.
+ * Limits: d <= 256 (ANN_LEARNED: d <= 4096; uint8: d <= 258 keeps the integer tiles exact),
  * 1 <= k <= 96, 1 <= C <= 1024, every shard smaller than 2^24 members.
  * ------------------------------------------------------------------------- */
 int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
@@ -253,6 +255,50 @@ int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const 
                     int64_t N, int d, int dtype, const void* Q, int64_t nq, const uint32_t* gt,
                     uint32_t entry, int Ls, uint32_t* out_id, float* recall_out,
                     uint32_t* dist_count_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned candidate form (ANN_LEARNED).  Not part of the paper, which builds
+ * every shard graph from exact distances (Sec. II-B, Sec. IV Workflow (2)): a
+ * small MLP embeds every vector in 32 dimensions, each shard row's nearest
+ * members in that space are its candidates, and the candidates are re-ranked
+ * with exact FP32 distances in the original space (the kernel of
+ * ANN_F16_RERANK screens the FP32 embeddings).  Its error is its recall against
+ * the exact graph; the plain exact ann_shard_knn is the fallback.
+ *
+ * model (parameters): one device float32 array of 256 d + 256 + 32 * 256 + 32
+ *   values [W1 (256 x d, row-major) | b1 | W2 (32 x 256, row-major) | b2];
+ *   f(x) = W2 relu(W1 (x / s) + b1) + b2 with s = max |x| over all N vectors.
+ *
+ * ann_learned_train: Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected, FP32)
+ *   on the triplet margin loss (1/B) sum_i max(0, |f(a)-f(p)|^2 - |f(a)-f(n)|^2
+ *   + margin), `steps` steps of `batch` triplets.  First the exact kk nearest
+ *   vectors (all N, by (distance, id), the row itself excluded) of each of the
+ *   S rows sample[] are found with the tile query kernel.  Triplet i of step t
+ *   takes draws[(t * batch + i) * 3 + {0, 1, 2}] = (u, r1, r2): anchor
+ *   a = sample[u mod S] with list L, positive L[r1 mod kpos], negative
+ *   L[kpos + (r2 >> 1) mod (kk - kpos)] for even r2, else row (r2 >> 1) mod N.
+ *   params: in = initial parameters, out = trained (updated in place).
+ *   losses: NULL or device float[steps], the mean loss of each step.
+ *   recall_est: NULL or device float[1]: the fraction of each sampled row's
+ *   exact 10 nearest vectors found among its 64 nearest in embedding space
+ *   (all N) - an estimate of the form's recall@10 before any shard is built.
+ *   Ids in sample[] at or above N are replaced by 0 and set status bit 2.
+ *   Limits: d <= 256 (the exact sample search), 2 <= kk <= 95,
+ *   1 <= kpos < kk, N >= kk + 2, 1 <= S <= N, batch <= 65536.
+ * ann_learned_embed: E [N x 32] float32 = f(X) for all rows (FP32 GEMMs).
+ *   Limits: d <= 4096.
+ * ann_shard_knn with precision ANN_LEARNED: model = the parameters; the
+ *   screened list has rerank_k (0 = 128) entries; any d <= 4096.
+ * ------------------------------------------------------------------------- */
+int ann_learned_train_workspace(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
+                                size_t* bytes);
+int ann_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t* sample,
+                      int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
+                      float lr, float margin, float* params, float* losses, float* recall_est,
+                      void* ws, size_t ws_bytes, void* stream);
+int ann_learned_embed_workspace(int64_t N, int d, size_t* bytes);
+int ann_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
+                      void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

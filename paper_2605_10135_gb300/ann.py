@@ -71,6 +71,11 @@ def lib():
             "ann_recall": (I32, [P, I32, P, I32, I64, I32, P, P]),
             "ann_search_eval": (I32, [P, P, I32, P, I64, I32, I32, P, I64, P, ct.c_uint32, I32, P,
                                       P, P, P]),
+            "ann_learned_train_workspace": (I32, [I64, I32, I32, I64, I32, I32, PSZ]),
+            "ann_learned_train": (I32, [P, I64, I32, I32, P, I64, I32, I32, P, I32, I32,
+                                        ct.c_float, ct.c_float, P, P, P, P, SZ, P]),
+            "ann_learned_embed_workspace": (I32, [I64, I32, PSZ]),
+            "ann_learned_embed": (I32, [P, I64, I32, I32, P, P, P, SZ, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -176,8 +181,9 @@ def partition(X: torch.Tensor, C: int, r: int, init_centroids: torch.Tensor,
 
 
 def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: int,
-              precision: int = EXACT, rerank_k: int = 0):
-    """Exact kNN inside every shard: (knn_id [rows, k] int32, knn_d [rows, k] float32)."""
+              precision: int = EXACT, rerank_k: int = 0, model: torch.Tensor | None = None):
+    """kNN inside every shard: (knn_id [rows, k] int32, knn_d [rows, k] float32).
+    model: the MLP parameters (float32, on the device) for precision=LEARNED."""
     X = _cuda(X, "X")
     N, d = X.shape
     members = _cuda(members, "members")
@@ -190,10 +196,51 @@ def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: 
     L = lib()
     nb = _wsize(L.ann_shard_knn_workspace, N, d, _DT[X.dtype], C, rows, k, precision, rerank_k)
     ws = _ws(nb, dev)
+    if model is not None:
+        model = _cuda(model, "model")
     _check(L.ann_shard_knn(_ptr(X), N, d, _DT[X.dtype], _ptr(members), _ptr(offsets), C, rows, k,
-                           precision, rerank_k, None, _ptr(knn_id), _ptr(knn_d), _ptr(ws), nb,
-                           _stream()))
+                           precision, rerank_k, _ptr(model), _ptr(knn_id), _ptr(knn_d), _ptr(ws),
+                           nb, _stream()))
     return knn_id, knn_d
+
+
+def learned_train(X: torch.Tensor, sample: torch.Tensor, draws: torch.Tensor,
+                  params: torch.Tensor, kk: int = 40, kpos: int = 10, lr: float = 1e-3,
+                  margin: float = 1e-3, estimate: bool = True):
+    """Train the projection MLP in place (params: float32 device array).
+    draws: uint32 bit patterns [steps, batch, 3] (int32 tensor).
+    Returns (losses [steps] float32, recall estimate [1] float32 or None)."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    sample = _cuda(sample, "sample")
+    draws = _cuda(draws, "draws")
+    params = _cuda(params, "params")
+    steps, batch = int(draws.shape[0]), int(draws.shape[1])
+    S = sample.numel()
+    dev = X.device
+    losses = torch.empty(max(steps, 1), dtype=torch.float32, device=dev)
+    est = torch.empty(1, dtype=torch.float32, device=dev) if estimate else None
+    L = lib()
+    nb = _wsize(L.ann_learned_train_workspace, N, d, _DT[X.dtype], S, kk, batch)
+    ws = _ws(nb, dev)
+    _check(L.ann_learned_train(_ptr(X), N, d, _DT[X.dtype], _ptr(sample), S, kk, kpos,
+                               _ptr(draws), steps, batch, lr, margin, _ptr(params),
+                               _ptr(losses), _ptr(est), _ptr(ws), nb, _stream()))
+    return losses[:steps], est
+
+
+def learned_embed(X: torch.Tensor, params: torch.Tensor) -> torch.Tensor:
+    """E [N, 32] float32 = the MLP embedding of every row."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    params = _cuda(params, "params")
+    E = torch.empty((N, 32), dtype=torch.float32, device=X.device)
+    L = lib()
+    nb = _wsize(L.ann_learned_embed_workspace, N, d)
+    ws = _ws(nb, X.device)
+    _check(L.ann_learned_embed(_ptr(X), N, d, _DT[X.dtype], _ptr(params), _ptr(E), _ptr(ws), nb,
+                               _stream()))
+    return E
 
 
 def prune(knn_id: torch.Tensor, knn_d: torch.Tensor, members: torch.Tensor,

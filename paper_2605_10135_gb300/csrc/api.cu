@@ -207,10 +207,24 @@ static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int
     ANN_REQUIRE(d >= 1, "d < 1");
     ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 128), "rerank_k must be 0 or in [k, 128]");
     if (precision != ANN_EXACT && precision != ANN_BF16_RERANK && precision != ANN_FP8_RERANK &&
-        precision != ANN_F16_RERANK)
-        return fail(ANN_ERR_UNSUPPORTED, "precision %d is not built in this version", precision);
+        precision != ANN_F16_RERANK && precision != ANN_LEARNED)
+        return fail(ANN_ERR_INVALID_ARG, "bad precision %d", precision);
+    if (precision == ANN_LEARNED) {
+        ANN_REQUIRE(d <= 4096, "learned form: d must be <= 4096");
+        return ANN_OK;
+    }
     if (d > 256) return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d > 256 not built in this version");
     return ANN_OK;
+}
+
+// The learned form screens 32-dimensional FP32 embeddings with scaled FP16 tiles.
+static int learned_plan(int k, int rerank_k, KnnPlan* pl) {
+    return knn_plan(ml::OUT, ANN_F32, k, ANN_F16_RERANK, rerank_k, pl);
+}
+
+static size_t learned_knn_bytes(int64_t N, int d, int C, int64_t rows, const KnnPlan& pl) {
+    return knn_ws(C, rows, pl, nullptr, nullptr, 0) + align_up((size_t)N * ml::OUT * 4, 256) +
+           learned_embed_ws(N, d) + 512;
 }
 
 int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
@@ -219,6 +233,11 @@ int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, in
     int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
     if (rc) return rc;
     KnnPlan pl;
+    if (precision == ANN_LEARNED) {
+        if ((rc = learned_plan(k, rerank_k, &pl))) return rc;
+        *bytes = learned_knn_bytes(N, d, C, rows, pl);
+        return ANN_OK;
+    }
     if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
     *bytes = knn_ws(C, rows, pl, nullptr, nullptr, 0);
     return ANN_OK;
@@ -230,10 +249,30 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                   void* stream) {
     int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
     if (rc) return rc;
-    ANN_REQUIRE(model == nullptr, "model must be NULL in this version");
     ANN_REQUIRE(offsets, "offsets is NULL");
     ANN_REQUIRE(rows == 0 || (X && members && knn_id && knn_d), "NULL pointer");
     KnnPlan pl;
+    if (precision == ANN_LEARNED) {
+        ANN_REQUIRE(model, "the learned form needs model (its parameters)");
+        if ((rc = learned_plan(k, rerank_k, &pl))) return rc;
+        if ((rc = check_ws(ws, ws_bytes, learned_knn_bytes(N, d, C, rows, pl)))) return rc;
+        if (rows == 0) return ANN_OK;
+        Carver cv(ws, ws_bytes);
+        const size_t kb = knn_ws(C, rows, pl, nullptr, nullptr, 0);
+        uint8_t* kbase = cv.take<uint8_t>(kb);
+        float* E = cv.take<float>((size_t)N * ml::OUT);
+        const size_t eb = learned_embed_ws(N, d);
+        uint8_t* ebase = cv.take<uint8_t>(eb);
+        if (!cv.ok) return fail(ANN_ERR_WORKSPACE, "workspace too small");
+        cudaStream_t st = (cudaStream_t)stream;
+        if ((rc = run_learned_embed(X, N, d, dtype, (const float*)model, E, ebase, eb, st)))
+            return rc;
+        KnnWs w;
+        knn_ws(C, rows, pl, &w, kbase, kb);
+        return run_shard_knn(E, N, ml::OUT, ANN_F32, members, offsets, C, rows, k, pl, w, knn_id,
+                             knn_d, st, X, d, dtype);
+    }
+    ANN_REQUIRE(model == nullptr, "model must be NULL unless precision is ANN_LEARNED");
     if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
     size_t need = knn_ws(C, rows, pl, nullptr, nullptr, 0);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
@@ -242,6 +281,59 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     knn_ws(C, rows, pl, &w, ws, ws_bytes);
     return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, knn_id, knn_d,
                          (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- learned form
+static int learned_args(int64_t N, int d, int dtype, int64_t S, int kk, int kpos, int batch) {
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(d >= 1 && d <= 256, "learned training: d must be in [1, 256]");
+    ANN_REQUIRE(kk >= 2 && kk <= 95, "kk must be in [2, 95]");
+    ANN_REQUIRE(N >= kk + 2 && N < (1ll << 32), "N must be in [kk + 2, 2^32)");
+    ANN_REQUIRE(kpos >= 1 && kpos < kk, "kpos must be in [1, kk)");
+    ANN_REQUIRE(S >= 1 && S <= N, "S must be in [1, N]");
+    ANN_REQUIRE(batch >= 1 && batch <= (1 << 16), "batch must be in [1, 65536]");
+    return ANN_OK;
+}
+
+int ann_learned_train_workspace(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
+                                size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    int rc = learned_args(N, d, dtype, S, kk, 1, batch);
+    if (rc) return rc;
+    *bytes = learned_train_ws(N, d, dtype, S, kk, batch, nullptr, nullptr, 0);
+    return *bytes ? ANN_OK : fail(ANN_ERR_UNSUPPORTED, "learned training: no plan for d=%d", d);
+}
+
+int ann_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t* sample,
+                      int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
+                      float lr, float margin, float* params, float* losses, float* recall_est,
+                      void* ws, size_t ws_bytes, void* stream) {
+    int rc = learned_args(N, d, dtype, S, kk, kpos, batch);
+    if (rc) return rc;
+    ANN_REQUIRE(steps >= 0, "steps < 0");
+    ANN_REQUIRE(X && sample && params && (steps == 0 || draws), "NULL pointer");
+    ANN_REQUIRE(lr > 0.0f && margin >= 0.0f, "lr must be > 0 and margin >= 0");
+    const size_t need = learned_train_ws(N, d, dtype, S, kk, batch, nullptr, nullptr, 0);
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    return run_learned_train(X, N, d, dtype, sample, S, kk, kpos, draws, steps, batch, lr, margin,
+                             params, losses, recall_est, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int ann_learned_embed_workspace(int64_t N, int d, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 0 && d >= 1 && d <= 4096, "N / d out of range");
+    *bytes = learned_embed_ws(N, d);
+    return ANN_OK;
+}
+
+int ann_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
+                      void* ws, size_t ws_bytes, void* stream) {
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32) && d >= 1 && d <= 4096, "N / d out of range");
+    ANN_REQUIRE(N == 0 || (X && params && E), "NULL pointer");
+    int rc = check_ws(ws, ws_bytes, learned_embed_ws(N, d));
+    if (rc) return rc;
+    return run_learned_embed(X, N, d, dtype, params, E, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- prune / merge

@@ -1418,8 +1418,8 @@ static int launch_gather(const void* X, int dtype, int d, const int64_t* src, in
 
 // Scaled plans (E4M3, FP16): the largest |x| over the given arrays into amax
 // (float bits).
-static int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,
-                         unsigned int* amax, cudaStream_t st) {
+int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,
+                  unsigned int* amax, cudaStream_t st) {
     ANN_CHECK_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned int), st));
     k_absmax<<<152 * 8, 256, 0, st>>>(X, dtype, n, amax);
     ANN_CHECK_LAUNCH();
@@ -1441,7 +1441,13 @@ static unsigned grid_rows(int64_t rows, int threads) {
 // order (ties are broken by global id), only the amount of top-k work does.
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
-                  const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st) {
+                  const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st,
+                  const void* Xr, int dr, int dtype_r) {
+    if (!Xr) {
+        Xr = X;
+        dr = d;
+        dtype_r = dtype;
+    }
     (void)N;
     int* status = device_status_ptr();
     k_shard_tables<<<1, 1024, 0, st>>>(offsets, C, rows, w.blk_off, w.pad_off, w.probs, w.order,
@@ -1497,7 +1503,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                       rows / kt::BM + C + 1, st, true);
     if (rc) return rc;
     if (pl.rerank)
-        return launch_rerank(X, X, dtype, d, members, rows, w.cand_id, pl.kprime, k, knn_id,
+        return launch_rerank(Xr, Xr, dtype_r, dr, members, rows, w.cand_id, pl.kprime, k, knn_id,
                              knn_d, st);
     return ANN_OK;
 }

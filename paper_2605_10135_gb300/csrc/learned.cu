@@ -1,0 +1,518 @@
+// Learned candidate form: a d -> 256 -> 32 projection MLP proposes each shard
+// row's candidate neighbours in embedding space; the candidates are re-ranked
+// with exact FP32 distances in the original space.  The paper builds shard graphs
+// from exact distances only (Sec. II-B, Sec. IV Workflow (2)); this form is an
+// addition beside it, judged by its recall against the exact graph.
+//
+// Model    f(x) = W2 relu(W1 (x / s) + b1) + b2, s = max |x| over all vectors;
+//          parameters are one FP32 array [W1 (256 x d) | b1 | W2 (32 x 256) | b2].
+// Training triplet margin loss (1/B) sum max(0, |f(a)-f(p)|^2 - |f(a)-f(n)|^2 + m)
+//          with Adam (0.9, 0.999, 1e-8, bias-corrected), FP32 master weights.
+//          Anchors come from a sample of the vectors; their exact kk nearest
+//          vectors (tile query kernel over all N) give positives (first kpos)
+//          and near-miss negatives (the rest), half the negatives are uniform
+//          rows.  The random picks are caller inputs.
+// Kernels  plain FP32 tiled GEMMs (64 x 64 x 16 tiles, 4 x 4 outputs a thread,
+//          every output summed over k in increasing order, so results are
+//          deterministic) with fused bias / ReLU / mask epilogues, and small
+//          element-wise kernels for the loss, Adam and the triplet picks.
+#include "stages.cuh"
+
+namespace ann {
+
+// A matrix operand read element by element: logical (r, c) is stored at row r,
+// column c (trans = 0) or row c, column r (trans = 1); the stored row index goes
+// through an optional gather map, then row0 is added; the value is converted from
+// dtype and multiplied by *sp (a device scalar) when sp is set.
+struct Mat {
+    const void* p;
+    int dtype;
+    const uint32_t* gather;
+    int64_t row0;
+    int64_t ld;
+    int trans;
+    const float* sp;
+};
+
+__device__ __forceinline__ float mat_at(const Mat& m, int64_t r, int64_t c, float s) {
+    const int64_t sr = m.trans ? c : r, sc = m.trans ? r : c;
+    const int64_t row = (m.gather ? (int64_t)m.gather[sr] : sr) + m.row0;
+    return load_elem(m.p, m.dtype, row * m.ld + sc) * s;
+}
+
+// C[M x N] = A[M x K] . B[K x N], ep(i, j, acc) stores each output.
+template <class EP>
+__global__ void __launch_bounds__(256) k_sgemm(int64_t M, int N, int K, Mat A, Mat B, EP ep) {
+    __shared__ float As[16][68];
+    __shared__ float Bs[16][68];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    const float sa = A.sp ? *A.sp : 1.0f, sb = B.sp ? *B.sp : 1.0f;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + q * 256;
+            const int r = A.trans ? (e & 63) : (e >> 4);  // consecutive threads follow
+            const int c = A.trans ? (e >> 6) : (e & 15);  // the stored rows
+            const int64_t gi = m0 + r;
+            const int gk = k0 + c;
+            As[c][r] = (gi < M && gk < K) ? mat_at(A, gi, gk, sa) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + q * 256;
+            const int r = B.trans ? (e & 15) : (e >> 6);
+            const int c = B.trans ? (e >> 4) : (e & 63);
+            const int gk = k0 + r, gj = n0 + c;
+            Bs[r][c] = (gk < K && gj < N) ? mat_at(B, gk, gj, sb) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gi = m0 + ty * 4 + i;
+            const int gj = n0 + tx * 4 + j;
+            if (gi < M && gj < N) ep(gi, gj, acc[i][j]);
+        }
+}
+
+// ---- epilogues ---------------------------------------------------------------
+struct EpHidden {  // U = acc + b1 (kept for the backward pass if U is set), H = relu(U)
+    float* U;
+    float* H;
+    const float* b;
+    int ld;
+    __device__ void operator()(int64_t i, int j, float acc) const {
+        const float u = acc + b[j];
+        if (U) U[i * ld + j] = u;
+        H[i * ld + j] = u > 0.0f ? u : 0.0f;
+    }
+};
+struct EpBias {  // C = acc + b
+    float* C;
+    const float* b;
+    int ld;
+    __device__ void operator()(int64_t i, int j, float acc) const { C[i * ld + j] = acc + b[j]; }
+};
+struct EpStore {  // C = acc
+    float* C;
+    int ld;
+    __device__ void operator()(int64_t i, int j, float acc) const { C[i * ld + j] = acc; }
+};
+struct EpReluMask {  // C = acc where U > 0, else 0 (back through the ReLU)
+    float* C;
+    const float* U;
+    int ld;
+    __device__ void operator()(int64_t i, int j, float acc) const {
+        C[i * ld + j] = U[i * ld + j] > 0.0f ? acc : 0.0f;
+    }
+};
+
+template <class EP>
+static int gemm(int64_t M, int N, int K, const Mat& A, const Mat& B, const EP& ep,
+                cudaStream_t st) {
+    if (M <= 0 || N <= 0) return ANN_OK;
+    const dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+    k_sgemm<EP><<<grid, 256, 0, st>>>(M, N, K, A, B, ep);
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+static Mat mat(const void* p, int dtype, int64_t ld, int trans = 0, const uint32_t* gather = nullptr,
+               int64_t row0 = 0, const float* sp = nullptr) {
+    Mat m;
+    m.p = p;
+    m.dtype = dtype;
+    m.gather = gather;
+    m.row0 = row0;
+    m.ld = ld;
+    m.trans = trans;
+    m.sp = sp;
+    return m;
+}
+
+// ---- small kernels -----------------------------------------------------------
+// 1 / max|x| (1 when every element is 0).
+__global__ void k_inv_scale(const unsigned int* amax_bits, float* inv) {
+    if (threadIdx.x || blockIdx.x) return;
+    const float a = __uint_as_float(*amax_bits);
+    *inv = a > 0.0f ? __frcp_rn(a) : 1.0f;
+}
+
+// Triplet rows of one step: idx[i] = anchor, idx[B + i] = positive, idx[2B + i] =
+// negative, from draws [B x 3] (anchor slot, r1, r2).
+// Ids at or above N (bad input) are replaced by 0 and reported in the status word.
+__device__ __forceinline__ uint32_t safe_id(uint32_t v, int64_t N, int* status) {
+    if ((int64_t)v < N) return v;
+    atomicOr(status, DEV_BAD_INPUT);
+    return 0;
+}
+
+__global__ void k_triplets(const uint32_t* __restrict__ sample, int64_t S,
+                           const uint32_t* __restrict__ knn, int kk, int kpos,
+                           const uint32_t* __restrict__ draws, int B, int64_t N,
+                           uint32_t* __restrict__ idx, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const uint32_t* dr = draws + (int64_t)i * 3;
+    const int64_t j = (int64_t)(dr[0] % (uint64_t)S);
+    const uint32_t* L = knn + j * kk;
+    const uint32_t r2 = dr[2];
+    idx[i] = safe_id(sample[j], N, status);
+    idx[B + i] = safe_id(L[dr[1] % (uint32_t)kpos], N, status);
+    idx[2 * B + i] = (r2 & 1u) ? (uint32_t)((uint64_t)(r2 >> 1) % (uint64_t)N)
+                               : safe_id(L[kpos + (r2 >> 1) % (uint32_t)(kk - kpos)], N, status);
+}
+
+// Per triplet: loss term and the gradient of the batch loss w.r.t. the three
+// embeddings (rows i, B + i, 2B + i of Z / dZ).
+__global__ void k_triplet_loss(const float* __restrict__ Z, int B, float margin,
+                               float* __restrict__ dZ, float* __restrict__ li) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const float* za = Z + (int64_t)i * ml::OUT;
+    const float* zp = Z + (int64_t)(B + i) * ml::OUT;
+    const float* zn = Z + (int64_t)(2 * B + i) * ml::OUT;
+    float dp = 0.0f, dn = 0.0f;
+    for (int c = 0; c < ml::OUT; ++c) {
+        const float u = za[c] - zp[c], v = za[c] - zn[c];
+        dp = fmaf(u, u, dp);
+        dn = fmaf(v, v, dn);
+    }
+    const float h = dp - dn + margin;
+    const bool act = h > 0.0f;
+    li[i] = act ? h : 0.0f;
+    const float g = act ? 2.0f / (float)B : 0.0f;
+    float* ga = dZ + (int64_t)i * ml::OUT;
+    float* gp = dZ + (int64_t)(B + i) * ml::OUT;
+    float* gn = dZ + (int64_t)(2 * B + i) * ml::OUT;
+    for (int c = 0; c < ml::OUT; ++c) {
+        ga[c] = g * (zn[c] - zp[c]);
+        gp[c] = g * (zp[c] - za[c]);
+        gn[c] = g * (za[c] - zn[c]);
+    }
+}
+
+// out[j] = sum over rows of A[row * cols + j], rows in increasing order.
+__global__ void k_colsum(const float* __restrict__ A, int64_t rows, int cols,
+                         float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    float s = 0.0f;
+    for (int64_t r = 0; r < rows; ++r) s += A[r * cols + j];
+    out[j] = s;
+}
+
+// Mean of li[0..B) into *out (fixed tree order, one block).
+__global__ void k_mean(const float* __restrict__ li, int B, float* out) {
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < B; i += 256) s += li[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (float)B;
+}
+
+// One Adam step on n parameters; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t).
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+// Copy rows sample[j] of X (esize bytes per element) into Q row j.
+__global__ void k_gather_rows(const uint8_t* __restrict__ X, int64_t row_bytes,
+                              const uint32_t* __restrict__ rows, int64_t n, int64_t N,
+                              uint8_t* __restrict__ Q, int* status) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const uint8_t* s = X + (int64_t)safe_id(rows[w], N, status) * row_bytes;
+    uint8_t* q = Q + w * row_bytes;
+    for (int64_t b = lane; b < row_bytes; b += 32) q[b] = s[b];
+}
+
+// The kk nearest other vectors of sample row j: its kk+1 list without itself
+// (without the last entry if the row itself is not listed).
+__global__ void k_drop_self(const uint32_t* __restrict__ ids, int kq,
+                            const uint32_t* __restrict__ sample, int64_t S,
+                            uint32_t* __restrict__ knn) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= S) return;
+    const uint32_t self = sample[j];
+    int o = 0;
+    for (int e = 0; e < kq && o < kq - 1; ++e) {
+        const uint32_t v = ids[j * kq + e];
+        if (v != self) knn[j * (kq - 1) + o++] = v;
+    }
+    for (; o < kq - 1; ++o) knn[j * (kq - 1) + o] = ANN_PAD;
+}
+
+// hits += |truth[j][0..tk) intersect found[j][0..fk)| over rows j.
+__global__ void k_cover(const uint32_t* __restrict__ found, int fs, int fk,
+                        const uint32_t* __restrict__ truth, int ts, int tk, int64_t n,
+                        unsigned long long* hits) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long h = 0;
+    if (j < n) {
+        for (int a = 0; a < tk; ++a) {
+            const uint32_t t = truth[j * ts + a];
+            if (t == ANN_PAD) continue;
+            for (int b = 0; b < fk; ++b)
+                if (found[j * fs + b] == t) {
+                    ++h;
+                    break;
+                }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0 && h) atomicAdd(hits, h);
+}
+
+__global__ void k_hits_to_recall(const unsigned long long* hits, int64_t denom, float* out) {
+    if (threadIdx.x || blockIdx.x) return;
+    *out = denom > 0 ? (float)((double)*hits / (double)denom) : 0.0f;
+}
+
+// ---- embedding ---------------------------------------------------------------
+static constexpr int64_t EMB_CHUNK = 65536;
+
+size_t learned_embed_ws(int64_t N, int d) {
+    (void)d;
+    Carver cv(nullptr, ~(size_t)0);
+    cv.take<unsigned int>(4);
+    cv.take<float>(4);
+    cv.take<float>((size_t)(N < EMB_CHUNK ? N : EMB_CHUNK) * ml::HID + 1);
+    return cv.used + 256;
+}
+
+static int embed_rows(const void* X, int dtype, int d, const uint32_t* rows, int64_t row0,
+                      int64_t n, const float* params, const float* inv_s, float* U, float* H,
+                      float* Z, cudaStream_t st) {
+    const float* W1 = params;
+    const float* b1 = W1 + (int64_t)ml::HID * d;
+    const float* W2 = b1 + ml::HID;
+    const float* b2 = W2 + (int64_t)ml::OUT * ml::HID;
+    int rc = gemm(n, ml::HID, d, mat(X, dtype, d, 0, rows, row0, inv_s),
+                  mat(W1, ANN_F32, d, 1), EpHidden{U, H, b1, ml::HID}, st);
+    if (rc) return rc;
+    return gemm(n, ml::OUT, ml::HID, mat(H, ANN_F32, ml::HID), mat(W2, ANN_F32, ml::HID, 1),
+                EpBias{Z, b2, ml::OUT}, st);
+}
+
+int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
+                      void* ws, size_t ws_bytes, cudaStream_t st) {
+    Carver cv(ws, ws_bytes);
+    unsigned int* amax = cv.take<unsigned int>(4);
+    float* inv_s = cv.take<float>(4);
+    float* H = cv.take<float>((size_t)(N < EMB_CHUNK ? N : EMB_CHUNK) * ml::HID + 1);
+    if (!cv.ok) return fail(ANN_ERR_WORKSPACE, "learned embed: workspace too small");
+    if (N == 0) return ANN_OK;
+    int rc = launch_absmax(X, dtype, N * d, nullptr, 0, amax, st);
+    if (rc) return rc;
+    k_inv_scale<<<1, 32, 0, st>>>(amax, inv_s);
+    ANN_CHECK_LAUNCH();
+    for (int64_t r0 = 0; r0 < N; r0 += EMB_CHUNK) {
+        const int64_t n = N - r0 < EMB_CHUNK ? N - r0 : EMB_CHUNK;
+        if ((rc = embed_rows(X, dtype, d, nullptr, r0, n, params, inv_s, nullptr, H,
+                             E + r0 * ml::OUT, st)))
+            return rc;
+    }
+    return ANN_OK;
+}
+
+// ---- training ----------------------------------------------------------------
+static constexpr int EST_K = 64;  // embedding-space list width of the recall estimate
+
+struct LearnTrainWs {
+    uint8_t* Q;          // [S x d] sample rows, X's type
+    uint32_t* kq_id;     // [S x (kk+1)]
+    float* kq_d;
+    uint32_t* knn;       // [S x kk]
+    void* qws;           // query workspace (exact, original space; then embedding space)
+    size_t qws_bytes;
+    uint32_t* idx;       // [3B]
+    float *U, *H, *Z, *dZ, *dU;
+    float *G, *m, *v;    // [P]
+    float* li;           // [B]
+    float* E;            // [N x 32]
+    float* QE;           // [S x 32]
+    uint32_t* eid;       // [S x EST_K]
+    float* ed;
+    unsigned long long* hits;
+    void* ews;           // embedding workspace
+    size_t ews_bytes;
+};
+
+size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
+                        LearnTrainWs* out, void* base, size_t cap) {
+    KnnPlan p1, p2;
+    if (knn_plan(d, dtype, kk + 1, ANN_EXACT, 0, &p1) || knn_plan(ml::OUT, ANN_F32, EST_K, ANN_EXACT, 0, &p2))
+        return 0;
+    const size_t q1 = query_ws(N, S, p1, nullptr, nullptr, 0);
+    const size_t q2 = query_ws(N, S, p2, nullptr, nullptr, 0);
+    Carver cv(base, cap);
+    LearnTrainWs w;
+    const int64_t R = 3 * (int64_t)batch;
+    const int64_t P = ml::n_params(d);
+    w.Q = cv.take<uint8_t>((size_t)S * d * dtype_bytes(dtype));
+    w.kq_id = cv.take<uint32_t>((size_t)S * (kk + 1));
+    w.kq_d = cv.take<float>((size_t)S * (kk + 1));
+    w.knn = cv.take<uint32_t>((size_t)S * kk);
+    w.qws_bytes = q1 > q2 ? q1 : q2;
+    w.qws = cv.take<uint8_t>(w.qws_bytes);
+    w.idx = cv.take<uint32_t>((size_t)R);
+    w.U = cv.take<float>((size_t)R * ml::HID);
+    w.H = cv.take<float>((size_t)R * ml::HID);
+    w.Z = cv.take<float>((size_t)R * ml::OUT);
+    w.dZ = cv.take<float>((size_t)R * ml::OUT);
+    w.dU = cv.take<float>((size_t)R * ml::HID);
+    w.G = cv.take<float>((size_t)P);
+    w.m = cv.take<float>((size_t)P);
+    w.v = cv.take<float>((size_t)P);
+    w.li = cv.take<float>((size_t)batch);
+    w.E = cv.take<float>((size_t)N * ml::OUT);
+    w.QE = cv.take<float>((size_t)S * ml::OUT);
+    w.eid = cv.take<uint32_t>((size_t)S * EST_K);
+    w.ed = cv.take<float>((size_t)S * EST_K);
+    w.hits = cv.take<unsigned long long>(1);
+    w.ews_bytes = learned_embed_ws(N, d);
+    w.ews = cv.take<uint8_t>(w.ews_bytes);
+    if (out) *out = w;
+    if (!base) return cv.used + 256;  // size query
+    return cv.ok ? cv.used + 256 : 0;
+}
+
+int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t* sample,
+                      int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
+                      float lr, float margin, float* params, float* losses, float* recall_est,
+                      void* ws, size_t ws_bytes, cudaStream_t st) {
+    LearnTrainWs w;
+    const size_t need = learned_train_ws(N, d, dtype, S, kk, batch, &w, ws, ws_bytes);
+    if (!need || need > ws_bytes) return fail(ANN_ERR_WORKSPACE, "learned train: workspace too small");
+    int rc;
+    const int64_t P = ml::n_params(d);
+    const int64_t R = 3 * (int64_t)batch;
+    // 1. exact kk nearest vectors of every sampled row (tile query kernel, all N)
+    const int64_t rb = (int64_t)d * dtype_bytes(dtype);
+    int* status = device_status_ptr();
+    k_gather_rows<<<(unsigned)((S * 32 + 255) / 256), 256, 0, st>>>((const uint8_t*)X, rb, sample,
+                                                                   S, N, w.Q, status);
+    ANN_CHECK_LAUNCH();
+    KnnPlan p1;
+    if ((rc = knn_plan(d, dtype, kk + 1, ANN_EXACT, 0, &p1))) return rc;
+    QueryWs q1;
+    query_ws(N, S, p1, &q1, w.qws, w.qws_bytes);
+    if ((rc = run_knn_query(X, N, w.Q, S, d, dtype, kk + 1, p1, q1, w.kq_id, w.kq_d, st)))
+        return rc;
+    k_drop_self<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(w.kq_id, kk + 1, sample, S, w.knn);
+    ANN_CHECK_LAUNCH();
+    // 2. input scale
+    Carver ec(w.ews, w.ews_bytes);
+    unsigned int* amax = ec.take<unsigned int>(4);
+    float* inv_s = ec.take<float>(4);
+    if ((rc = launch_absmax(X, dtype, N * d, nullptr, 0, amax, st))) return rc;
+    k_inv_scale<<<1, 32, 0, st>>>(amax, inv_s);
+    ANN_CHECK_LAUNCH();
+    // 3. Adam steps
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.m, 0, (size_t)P * sizeof(float), st));
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.v, 0, (size_t)P * sizeof(float), st));
+    float* gW1 = w.G;
+    float* gb1 = gW1 + (int64_t)ml::HID * d;
+    float* gW2 = gb1 + ml::HID;
+    float* gb2 = gW2 + (int64_t)ml::OUT * ml::HID;
+    const float* W2 = params + (int64_t)ml::HID * d + ml::HID;
+    double b1t = 1.0, b2t = 1.0;
+    for (int t = 0; t < steps; ++t) {
+        k_triplets<<<(batch + 255) / 256, 256, 0, st>>>(sample, S, w.knn, kk, kpos,
+                                                       draws + (int64_t)t * batch * 3, batch, N,
+                                                       w.idx, status);
+        ANN_CHECK_LAUNCH();
+        if ((rc = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, st)))
+            return rc;
+        k_triplet_loss<<<(batch + 127) / 128, 128, 0, st>>>(w.Z, batch, margin, w.dZ, w.li);
+        ANN_CHECK_LAUNCH();
+        if (losses) {
+            k_mean<<<1, 256, 0, st>>>(w.li, batch, losses + t);
+            ANN_CHECK_LAUNCH();
+        }
+        // dW2 = dZ^T H, db2 = column sums of dZ
+        if ((rc = gemm(ml::OUT, ml::HID, (int)R, mat(w.dZ, ANN_F32, ml::OUT, 1),
+                       mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, st)))
+            return rc;
+        k_colsum<<<1, 32, 0, st>>>(w.dZ, R, ml::OUT, gb2);
+        ANN_CHECK_LAUNCH();
+        // dU = (dZ W2) where U > 0
+        if ((rc = gemm(R, ml::HID, ml::OUT, mat(w.dZ, ANN_F32, ml::OUT),
+                       mat(W2, ANN_F32, ml::HID), EpReluMask{w.dU, w.U, ml::HID}, st)))
+            return rc;
+        // dW1 = dU^T (X / s), db1 = column sums of dU
+        if ((rc = gemm(ml::HID, d, (int)R, mat(w.dU, ANN_F32, ml::HID, 1),
+                       mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, st)))
+            return rc;
+        k_colsum<<<1, 256, 0, st>>>(w.dU, R, ml::HID, gb1);
+        ANN_CHECK_LAUNCH();
+        b1t *= 0.9;
+        b2t *= 0.999;
+        k_adam<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(params, w.G, w.m, w.v, P, lr,
+                                                           (float)(1.0 / (1.0 - b1t)),
+                                                           (float)(1.0 / (1.0 - b2t)));
+        ANN_CHECK_LAUNCH();
+    }
+    // 4. recall estimate: the sample's exact top 10 within its top EST_K in
+    //    embedding space (all N)
+    if (recall_est) {
+        if ((rc = run_learned_embed(X, N, d, dtype, params, w.E, w.ews, w.ews_bytes, st)))
+            return rc;
+        k_gather_rows<<<(unsigned)((S * 32 + 255) / 256), 256, 0, st>>>(
+            (const uint8_t*)w.E, ml::OUT * 4, sample, S, N, (uint8_t*)w.QE, status);
+        ANN_CHECK_LAUNCH();
+        KnnPlan p2;
+        if ((rc = knn_plan(ml::OUT, ANN_F32, EST_K, ANN_EXACT, 0, &p2))) return rc;
+        QueryWs q2;
+        query_ws(N, S, p2, &q2, w.qws, w.qws_bytes);
+        if ((rc = run_knn_query(w.E, N, w.QE, S, ml::OUT, ANN_F32, EST_K, p2, q2, w.eid, w.ed, st)))
+            return rc;
+        ANN_CHECK_CUDA(cudaMemsetAsync(w.hits, 0, sizeof(unsigned long long), st));
+        const int tk = kk < 10 ? kk : 10;
+        k_cover<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(w.eid, EST_K, EST_K, w.knn, kk, tk,
+                                                            S, w.hits);
+        ANN_CHECK_LAUNCH();
+        k_hits_to_recall<<<1, 32, 0, st>>>(w.hits, S * tk, recall_est);
+        ANN_CHECK_LAUNCH();
+    }
+    return ANN_OK;
+}
+
+}  // namespace ann

@@ -84,9 +84,12 @@ struct KnnWs {
     float* amax;        // E4M3 plans: largest |x| (float bits)
 };
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
+// X [N x d] screens the candidates; the re-rank (float plans) scores them on Xr
+// [N x dr] (type dtype_r), which defaults to X itself.
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
-                  const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st);
+                  const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st,
+                  const void* Xr = nullptr, int dr = 0, int dtype_r = 0);
 
 struct QueryWs {
     int64_t* blk_off;
@@ -137,6 +140,28 @@ int run_search(const uint32_t* graph, const uint32_t* degree, int R, const void*
                uint32_t* out_id, uint32_t* out_count, cudaStream_t st);
 int run_recall(const uint32_t* found, int fs, const uint32_t* truth, int ts, int64_t nq, int kk,
                float* recall_out, unsigned long long* hits, cudaStream_t st);
+
+// max |x| over X [n elements] and, if given, Q [nq_elems] into *amax (float bits;
+// the word is zeroed first).
+int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,
+                  unsigned int* amax, cudaStream_t st);
+
+// ---- learned candidate form ---------------------------------------------------------
+namespace ml {
+constexpr int HID = 256;  // hidden width
+constexpr int OUT = 32;   // embedding width
+inline int64_t n_params(int d) { return (int64_t)HID * d + HID + (int64_t)OUT * HID + OUT; }
+}  // namespace ml
+struct LearnTrainWs;
+size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
+                        LearnTrainWs* out, void* base, size_t cap);
+int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t* sample,
+                      int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
+                      float lr, float margin, float* params, float* losses, float* recall_est,
+                      void* ws, size_t ws_bytes, cudaStream_t st);
+size_t learned_embed_ws(int64_t N, int d);
+int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params,
+                      float* E, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t medoid_ws(int64_t N, int d, double** part, float** mean, unsigned long long** best,
                  void* base, size_t cap);
 int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, double* part,

@@ -50,7 +50,21 @@ def test_workspace_queries_validate_on_host(L):
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 4, 0, ct.byref(n)) == 0  # FP16 form
     assert L.ann_shard_knn_workspace(1000, 128, 0, 2000, 2000, 64, 0, 0, ct.byref(n)) == 1  # C
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 2, 32, ct.byref(n)) == 1  # < k
-    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 3, 0, ct.byref(n)) == 2  # reserved
+    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 3, 0, ct.byref(n)) == 0  # learned
+    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256
+    assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 5, 0, ct.byref(n)) == 1  # bad
+
+
+def test_learned_workspace_queries_validate_on_host(L):
+    n = ct.c_size_t(0)
+    assert L.ann_learned_train_workspace(10000, 96, 0, 100, 40, 256, ct.byref(n)) == 0
+    assert n.value > 10000 * 32 * 4
+    assert L.ann_learned_train_workspace(10000, 300, 0, 100, 40, 256, ct.byref(n)) == 1  # d
+    assert L.ann_learned_train_workspace(30, 96, 0, 10, 40, 256, ct.byref(n)) == 1       # N < kk+2
+    assert L.ann_learned_embed_workspace(10000, 1024, ct.byref(n)) == 0 and n.value > 0
+    f = ct.c_float
+    assert L.ann_learned_train(None, 10000, 96, 0, None, 100, 40, 40, None, 1, 256, f(1e-3),
+                               f(1e-3), None, None, None, None, 0, None) == 1  # kpos = kk
     assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256
     assert L.ann_merge_workspace(1000, 2000, ct.byref(n)) == 0 and n.value > 0
     assert L.ann_prune(None, None, None, None, 4, 10, 100, 0, 8, 0, None, None, None, 0,
