@@ -181,9 +181,18 @@ def main():
     ap.add_argument("--nq", type=int, default=1000)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
-    ap.add_argument("--precision", default="exact", choices=["exact", "bf16", "f16", "fp8"],
-                    help="distance-tile form: exact (uint8 / FP32 split), or BF16 / scaled "
-                         "FP16 / E4M3 screening with an FP32 re-rank of the top 128")
+    ap.add_argument("--precision", default="exact",
+                    choices=["exact", "bf16", "f16", "fp8", "learned"],
+                    help="distance-tile form: exact (uint8 / FP32 split), BF16 / scaled FP16 / "
+                         "E4M3 screening with an FP32 re-rank of the top 128, or learned "
+                         "(32-d MLP embedding screened, re-ranked exactly)")
+    ap.add_argument("--rerank-k", type=int, default=0, help="screened list width (0: default)")
+    ap.add_argument("--learn-steps", type=int, default=300)
+    ap.add_argument("--learn-batch", type=int, default=512)
+    ap.add_argument("--sample-frac", type=float, default=0.01)
+    ap.add_argument("--learn-lr", type=float, default=1e-3)
+    ap.add_argument("--min-recall", type=float, default=0.9,
+                    help="learned form: recall estimate below which the exact form is used")
     ap.add_argument("--tile-counters", action="store_true",
                     help="after timing, run one step with the counting kernel variant and "
                          "report its per-role cycle counters")
@@ -224,12 +233,23 @@ def main():
     init_d = torch.from_numpy(init).to(dev)
     samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
     prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "f16": ann.F16_RERANK,
-            "fp8": ann.FP8_RERANK}[args.precision]
-    cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R, iters=10, precision=prec)
+            "fp8": ann.FP8_RERANK, "learned": ann.LEARNED}[args.precision]
+    cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R, iters=10, precision=prec,
+                          rerank_k=args.rerank_k)
+    learned = None
+    if prec == ann.LEARNED:
+        from paper_2605_10135_gb300 import datagen
+        ls = datagen.row_sample(w.N, args.sample_frac, 256, seed=w.seed + 11)
+        learned = ann.LearnedInputs(
+            sample=torch.from_numpy(ls.view(np.int32)).to(dev),
+            draws=torch.from_numpy(datagen.triplet_draws(args.learn_steps, args.learn_batch,
+                                                         seed=w.seed + 12).view(np.int32)).to(dev),
+            params0=torch.from_numpy(datagen.mlp_init(w.d, seed=w.seed + 13)).to(dev),
+            lr=args.learn_lr, min_recall=args.min_recall)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
 
     def step(x):
-        return ann.build_index(x, cfg, init_d, samp_d)
+        return ann.build_index(x, cfg, init_d, samp_d, learned)
 
     for _ in range(max(args.warmup, 3)):
         out = step(Xd)
@@ -280,7 +300,7 @@ def main():
     # quality: the exact form gives the exact graph by construction; a screening form
     # is scored against the exact form's lists on the same partition
     graph_recall = 1.0
-    if prec != ann.EXACT:
+    if out.get("precision", prec) != ann.EXACT:
         ex_id, _ = ann.shard_knn(Xd, out["members"], out["offsets"], w.k, ann.EXACT)
         graph_recall = float(ann.recall(out["knn_id"], ex_id, 10).item())
         del ex_id
@@ -304,7 +324,8 @@ def main():
 
     off = out["offsets"].cpu().numpy()
     sizes = np.diff(off).astype(np.float64)
-    flops = float(np.sum(sizes ** 2) * 2 * w.d)
+    d_tile = 32 if out.get("precision") == ann.LEARNED else w.d
+    flops = float(np.sum(sizes ** 2) * 2 * d_tile)
     tile_avg_ms = tile_ms / max(tile_n, 1)
     achieved = flops / (tile_avg_ms * 1e-3) / 1e12
     peaks, src = _peaks()
@@ -313,7 +334,7 @@ def main():
     if prec == ann.FP8_RERANK:
         peak *= 2.0  # nominal dense E4M3 / BF16 ratio (4.5 / 2.25 PFLOP/s)
         peak_note += " x 2 (nominal fp8/bf16 ratio)"
-    if w.dtype == "u8" and prec != ann.FP8_RERANK:
+    if w.dtype == "u8" and prec not in (ann.FP8_RERANK, ann.LEARNED):
         dtype, operands, products = "u8", "bf16 (exact for uint8), fp32 accumulate", 1
     elif prec == ann.EXACT:
         dtype = "f32"
@@ -324,8 +345,12 @@ def main():
     elif prec == ann.F16_RERANK:
         dtype, operands, products = ("f16", "fp16 (power-of-two global scale), fp32 accumulate; "
                                      "fp32 re-rank of top 128", 1)
-    else:
+    elif prec == ann.FP8_RERANK:
         dtype, operands, products = "fp8", "e4m3 (one global scale), fp32 accumulate; fp32 re-rank of top 128", 1
+    else:
+        dtype, operands, products = ("learned32-f16", "32-d MLP embedding (fp32 GEMMs) screened "
+                                     "with scaled fp16, fp32 accumulate; fp32 re-rank in the "
+                                     "original space", 1)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -347,6 +372,12 @@ def main():
             "workload": w.name, "N": w.N, "d": w.d, "elem": w.dtype, "shards": w.C,
             "replicas": w.r, "k": w.k, "R": w.R, "kmeans_iters": 10,
             "precision": args.precision,
+            "learned": (None if prec != ann.LEARNED else {
+                "steps": args.learn_steps, "batch": args.learn_batch,
+                "sample_rows": int(learned.sample.numel()),
+                "recall_estimate": out.get("recall_estimate"),
+                "fell_back_to_exact": out.get("precision") != ann.LEARNED,
+                "timed_step_includes_training": True}),
             "tile_operands": operands, "tensor_products_per_pair": products,
             "l2": "flushed (512 MB write) before every timed step",
             "recall_at_10": graph_recall,

@@ -348,6 +348,20 @@ def recall(found: torch.Tensor, truth: torch.Tensor, kk: int = 10) -> torch.Tens
 
 
 @dataclass
+class LearnedInputs:
+    """Seeded inputs of the learned form (see datagen): sample rows [S] (int32 bit
+    patterns of uint32), triplet draws [steps, batch, 3] and initial parameters."""
+    sample: torch.Tensor
+    draws: torch.Tensor
+    params0: torch.Tensor
+    kk: int = 40
+    kpos: int = 10
+    lr: float = 1e-3
+    margin: float = 1e-3
+    min_recall: float = 0.9   # estimate below this: fall back to the exact form
+
+
+@dataclass
 class BuildConfig:
     """Parameters of one divide-and-merge build (k = intermediate degree L)."""
     C: int
@@ -361,11 +375,26 @@ class BuildConfig:
 
 
 def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
-                sample_idx: torch.Tensor) -> dict:
-    """The whole hot path: partition -> per-shard kNN -> prune -> merge (all on the GPU)."""
+                sample_idx: torch.Tensor, learned: LearnedInputs | None = None) -> dict:
+    """The whole hot path: partition -> per-shard kNN -> prune -> merge (all on the GPU).
+
+    With precision LEARNED the projection MLP is trained first (learned.params0 is
+    not modified); when its recall estimate is below learned.min_recall the shard
+    graphs are built with the exact form instead (out["precision"] says which)."""
     cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
-    knn_id, knn_d = shard_knn(X, members, offsets, cfg.k, cfg.precision, cfg.rerank_k)
+    precision, model, est = cfg.precision, None, None
+    if precision == LEARNED:
+        if learned is None:
+            raise ValueError("precision LEARNED needs LearnedInputs")
+        model = learned.params0.clone()
+        _, est_t = learned_train(X, learned.sample, learned.draws, model, learned.kk,
+                                 learned.kpos, learned.lr, learned.margin)
+        est = float(est_t.item())
+        if est < learned.min_recall:
+            precision, model = EXACT, None
+    knn_id, knn_d = shard_knn(X, members, offsets, cfg.k, precision, cfg.rerank_k, model)
     pr_id, pr_d = prune(knn_id, knn_d, members, offsets, cfg.R, cfg.rule, N=X.shape[0])
     graph, gdist, degree = merge(pr_id, pr_d, members, offsets, X.shape[0])
     return dict(centroids=cent, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
-                pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree)
+                pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree,
+                precision=precision, recall_estimate=est, model=model)
