@@ -213,7 +213,9 @@ static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int
         ANN_REQUIRE(d <= 4096, "learned form: d must be <= 4096");
         return ANN_OK;
     }
-    if (d > 256) return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d > 256 not built in this version");
+    ANN_REQUIRE(d <= 4096, "shard_knn: d must be <= 4096");
+    if (dtype == ANN_U8 && d > 258)
+        return fail(ANN_ERR_UNSUPPORTED, "uint8 with d > 258: the integer tiles are not exact");
     return ANN_OK;
 }
 
@@ -286,7 +288,7 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
 // ---------------------------------------------------------------- learned form
 static int learned_args(int64_t N, int d, int dtype, int64_t S, int kk, int kpos, int batch) {
     ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
-    ANN_REQUIRE(d >= 1 && d <= 256, "learned training: d must be in [1, 256]");
+    ANN_REQUIRE(d >= 1 && d <= 4096, "learned training: d must be in [1, 4096]");
     ANN_REQUIRE(kk >= 2 && kk <= 95, "kk must be in [2, 95]");
     ANN_REQUIRE(N >= kk + 2 && N < (1ll << 32), "N must be in [kk + 2, 2^32)");
     ANN_REQUIRE(kpos >= 1 && kpos < kk, "kpos must be in [1, kk)");

@@ -103,7 +103,8 @@ struct KnnParams {
     int self_exclude;
     int local_first;          // sweep the columns near the row block first
     int mode;      // 0 plain, 1 split
-    int nkb_a;     // resident A k-blocks
+    int nkb_a;     // A k-blocks (resident unless a_stream)
+    int a_stream;  // 1: A blocks stream through the ring with the B blocks (large d)
     int nkb_b;     // B k-blocks per tile
     int kprime;    // heap entries per row
     int k_out;     // entries written per row
@@ -120,15 +121,23 @@ struct KnnSmemLayout {
     uint32_t a, aaug, b, baug, heap, buf, locks, bars, tmem_slot, abort_flag, total;
 };
 
-__host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int kprime) {
+// a_stream = 0: the CTA's A rows stay resident (nkb_a K blocks) and a ring stage
+// holds one B block; a_stream = 1 (large d): nothing resident, a stage holds one
+// B block followed by the matching A block.
+__host__ __device__ inline uint32_t knn_stage_bytes(int bn, int a_stream) {
+    return (uint32_t)bn * 128 + (a_stream ? kt::A_BLK_BYTES : 0);
+}
+
+__host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int kprime,
+                                                         int a_stream) {
     KnnSmemLayout L;
     uint32_t o = 0;
     L.a = o;
-    o += nkb_a * kt::A_BLK_BYTES;
+    o += (a_stream ? 0 : nkb_a) * kt::A_BLK_BYTES;
     L.aaug = o;
     o += 1024 * ((kt::A_AUG_BYTES + 1023) / 1024);
     L.b = o;
-    o += nst * bn * 128;
+    o += nst * knn_stage_bytes(bn, a_stream);
     L.baug = o;
     o += kt::NAUG * bn * 32;
     L.heap = o;
@@ -428,7 +437,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.kprime);
+    const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.kprime, P.a_stream);
+    const uint32_t STG = knn_stage_bytes(BN, P.a_stream);
     const uint32_t sA = smem_u32(base + L.a);
     const uint32_t sAaug = smem_u32(base + L.aaug);
     const uint32_t sB = smem_u32(base + L.b);
@@ -489,8 +499,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             tma_prefetch_desc(&tmAaug);
             tma_prefetch_desc(&tmBaug);
             const int a_y = (int)(pr.a_row0 + (int64_t)rb * kt::BM);
-            mbar_expect_tx(a_bar, P.nkb_a * kt::A_BLK_BYTES + kt::A_AUG_BYTES);
-            for (int b = 0; b < P.nkb_a; ++b)
+            const int nres = P.a_stream ? 0 : P.nkb_a;
+            mbar_expect_tx(a_bar, nres * kt::A_BLK_BYTES + kt::A_AUG_BYTES);
+            for (int b = 0; b < nres; ++b)
                 tma_load_2d(sA + b * kt::A_BLK_BYTES, &tmA, a_bar, b * P.kbe, a_y);
             tma_load_2d(sAaug, &tmAaug, a_bar, 0, 0);
             uint32_t last_par = 0, used = 0, alast_par = 0, aused = 0;
@@ -513,8 +524,12 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
                     if (PROF) prod_wait += clock64() - w0;
-                    mbar_expect_tx(full_bar + 8 * st, B_BLK_BYTES);
-                    tma_load_2d(sB + st * B_BLK_BYTES, &tmB, full_bar + 8 * st, j * P.kbe, b_y);
+                    mbar_expect_tx(full_bar + 8 * st,
+                                   B_BLK_BYTES + (P.a_stream ? kt::A_BLK_BYTES : 0));
+                    tma_load_2d(sB + st * STG, &tmB, full_bar + 8 * st, j * P.kbe, b_y);
+                    if (P.a_stream)
+                        tma_load_2d(sB + st * STG + B_BLK_BYTES, &tmA, full_bar + 8 * st,
+                                    j * P.kbe, a_y);
                     used |= 1u << st;
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
@@ -570,7 +585,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) w_full += clock64() - w0;
                     tc_fence_after();
                     if (PROF) w0 = clock64();
-                    const uint32_t bsm = sB + st * B_BLK_BYTES;
+                    const uint32_t bsm = sB + st * STG;
                     int ablk[2];
                     int na = 1;
                     if (P.mode == 0) {
@@ -583,7 +598,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                         ablk[0] = j - H2;  // hi . lo
                     }
                     for (int q = 0; q < na; ++q) {
-                        const uint32_t asm_ = sA + ablk[q] * kt::A_BLK_BYTES;
+                        const uint32_t asm_ =
+                            P.a_stream ? bsm + B_BLK_BYTES : sA + ablk[q] * kt::A_BLK_BYTES;
                         // four K steps of 32 bytes per 128-byte block (K = 16 for 16-bit
                         // operands, K = 32 for E4M3)
 #pragma unroll
@@ -1259,23 +1275,31 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
     p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : wide) : k;
     if (p.kprime < k) p.kprime = k;
     if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
-    // Widest tile with a 3-stage ring, else the narrow one, else 2 stages.
+    // Resident A rows if they fit: the widest tile with a 3-stage ring, else the
+    // narrow one, else 2 stages.  Otherwise (large d, single-product operands)
+    // the A blocks stream through the ring beside the B blocks.
     const size_t cap = 227 * 1024;
     p.nst = 0;
+    p.a_stream = 0;
     const int tries[4][2] = {{256, 3}, {128, 3}, {256, 2}, {128, 2}};
-    for (int q = 0; q < 4 && !p.nst; ++q) {
-        const int bn = tries[q][0];
-        for (int nst = kt::MAX_NST; nst >= tries[q][1]; --nst)
-            if (knn_smem_layout(bn, p.nkb_a, nst, p.kprime).total <= cap) {
-                p.nst = nst;
-                p.bn = bn;
-                break;
-            }
+    for (int as = 0; as < 2 && !p.nst; ++as) {
+        if (as && p.mode != 0) break;
+        for (int q = 0; q < 4 && !p.nst; ++q) {
+            const int bn = tries[q][0];
+            for (int nst = kt::MAX_NST; nst >= tries[q][1]; --nst)
+                if (knn_smem_layout(bn, p.nkb_a, nst, p.kprime, as).total <= cap) {
+                    p.nst = nst;
+                    p.bn = bn;
+                    p.a_stream = as;
+                    break;
+                }
+        }
     }
     if (!p.nst)
-        return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory", d,
-                    p.kprime);
-    p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.kprime).total;
+        return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory%s",
+                    d, p.kprime,
+                    p.mode ? " (FP32 at this d: use a screening precision)" : "");
+    p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.kprime, p.a_stream).total;
     *pl = p;
     return ANN_OK;
 }
@@ -1379,6 +1403,7 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.local_first = local_first;
     P.mode = pl.mode;
     P.nkb_a = pl.nkb_a;
+    P.a_stream = pl.a_stream;
     P.nkb_b = pl.nkb_b;
     P.kprime = pl.kprime;
     P.k_out = pl.rerank ? pl.kprime : k;
@@ -1460,7 +1485,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnPlan pp = pl;
     pp.kprime = 1;
     pp.rerank = false;
-    pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, 1).total;
+    pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, 1, pp.a_stream).total;
     const unsigned int* amax = nullptr;
     if (pl.scaled) {
         int rc8 = launch_absmax(X, dtype, N * d, nullptr, 0, (unsigned int*)w.amax, st);

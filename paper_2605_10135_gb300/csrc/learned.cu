@@ -375,10 +375,17 @@ struct LearnTrainWs {
     size_t ews_bytes;
 };
 
+// The sample's neighbour lists: the exact plan when it fits shared memory, else
+// (FP32 at large d) scaled-FP16 screening of 128 candidates with the FP32 re-rank.
+static int sample_plan(int d, int dtype, int kq, KnnPlan* p) {
+    if (knn_plan(d, dtype, kq, ANN_EXACT, 0, p) == ANN_OK) return ANN_OK;
+    return knn_plan(d, dtype, kq, ANN_F16_RERANK, 0, p);
+}
+
 size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
                         LearnTrainWs* out, void* base, size_t cap) {
     KnnPlan p1, p2;
-    if (knn_plan(d, dtype, kk + 1, ANN_EXACT, 0, &p1) || knn_plan(ml::OUT, ANN_F32, EST_K, ANN_EXACT, 0, &p2))
+    if (sample_plan(d, dtype, kk + 1, &p1) || knn_plan(ml::OUT, ANN_F32, EST_K, ANN_EXACT, 0, &p2))
         return 0;
     const size_t q1 = query_ws(N, S, p1, nullptr, nullptr, 0);
     const size_t q2 = query_ws(N, S, p2, nullptr, nullptr, 0);
@@ -431,7 +438,7 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
                                                                    S, N, w.Q, status);
     ANN_CHECK_LAUNCH();
     KnnPlan p1;
-    if ((rc = knn_plan(d, dtype, kk + 1, ANN_EXACT, 0, &p1))) return rc;
+    if ((rc = sample_plan(d, dtype, kk + 1, &p1))) return rc;
     QueryWs q1;
     query_ws(N, S, p1, &q1, w.qws, w.qws_bytes);
     if ((rc = run_knn_query(X, N, w.Q, S, d, dtype, kk + 1, p1, q1, w.kq_id, w.kq_d, st)))

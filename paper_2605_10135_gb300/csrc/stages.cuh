@@ -46,6 +46,7 @@ struct KnnPlan {
     int scaled;       // 1: operands carry one global scale from max|x| (E4M3, scaled FP16)
     int kbe;          // elements per 128-byte K block
     int bn;           // tile width (N of one MMA): 256 or 128
+    int a_stream;     // 1: A blocks stream through the ring (d too large to keep resident)
     uint32_t ab_fmt;  // 16-bit operands: 0 fp16, 1 bf16 (E4M3: 0)
     bool rerank;
     int kprime;

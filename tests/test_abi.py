@@ -51,7 +51,10 @@ def test_workspace_queries_validate_on_host(L):
     assert L.ann_shard_knn_workspace(1000, 128, 0, 2000, 2000, 64, 0, 0, ct.byref(n)) == 1  # C
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 2, 32, ct.byref(n)) == 1  # < k
     assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 3, 0, ct.byref(n)) == 0  # learned
-    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # d > 256
+    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # f32 split
+    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 4, 0, ct.byref(n)) == 0  # streamed
+    assert L.ann_shard_knn_workspace(1000, 1024, 1, 16, 2000, 64, 0, 0, ct.byref(n)) == 0  # f16
+    assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # u8
     assert L.ann_shard_knn_workspace(1000, 128, 3, 16, 2000, 64, 5, 0, ct.byref(n)) == 1  # bad
 
 
@@ -59,7 +62,7 @@ def test_learned_workspace_queries_validate_on_host(L):
     n = ct.c_size_t(0)
     assert L.ann_learned_train_workspace(10000, 96, 0, 100, 40, 256, ct.byref(n)) == 0
     assert n.value > 10000 * 32 * 4
-    assert L.ann_learned_train_workspace(10000, 300, 0, 100, 40, 256, ct.byref(n)) == 1  # d
+    assert L.ann_learned_train_workspace(10000, 5000, 0, 100, 40, 256, ct.byref(n)) == 1  # d
     assert L.ann_learned_train_workspace(30, 96, 0, 10, 40, 256, ct.byref(n)) == 1       # N < kk+2
     assert L.ann_learned_embed_workspace(10000, 1024, ct.byref(n)) == 0 and n.value > 0
     f = ct.c_float

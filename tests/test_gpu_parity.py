@@ -185,6 +185,38 @@ def test_knn_query_and_medoid_u8():
     assert int(ann.medoid(T(X)).item()) == oracle.medoid(X)
 
 
+@pytest.mark.parametrize("kind,d,prec", [("f16", 768, ann.EXACT), ("bf16", 1024, ann.EXACT),
+                                         ("f32", 640, ann.F16_RERANK)])
+def test_large_d_streamed_tiles_float_rule(kind, d, prec):
+    """128 rows of d >= 640 do not fit shared memory: their K blocks stream
+    through the ring beside the B blocks (one launch, several shards)."""
+    N = 2500
+    if kind == "f16":
+        X = datagen.anisotropic_mixture(N, d, 32, 0.25, False, np.float16, seed=151)
+        Xt = T(X)
+    elif kind == "bf16":
+        Xt = T(datagen.gaussian_mixture_f32(N, d, 8, seed=152)).to(torch.bfloat16)
+        X = Xt.float().cpu().numpy()
+    else:
+        X = datagen.powerlaw_gaussian(N, d, 0.8, seed=153)
+        Xt = T(X)
+    mem, off = _oracle_shards(X, 3, 2, seed=154)
+    gid, gd = ann.shard_knn(Xt, T(mem), T(off), 16, precision=prec,
+                            rerank_k=64 if prec != ann.EXACT else 0)
+    oid, od = oracle.shard_knn(X, mem, off, 16)
+    check_float_lists(X, mem, gid.cpu().numpy(), gd.cpu().numpy(), oid, od)
+
+
+def test_knn_query_large_d_f16():
+    X = datagen.anisotropic_mixture(3000, 1024, 16, 0.25, False, np.float16, seed=155)
+    Q = datagen.anisotropic_mixture(100, 1024, 16, 0.25, False, np.float16, seed=156)
+    gid, gd = ann.knn_query(T(X), T(Q), 10)
+    oid, od = oracle.bruteforce(X, Q, 10)
+    Xq = np.vstack([X, Q])
+    check_float_lists(Xq, np.arange(len(X), len(X) + len(Q)), gid.cpu().numpy(),
+                      gd.cpu().numpy(), oid, od)
+
+
 def test_knn_query_f32_rule():
     X = datagen.gaussian_mixture_f32(3000, 48, seed=63)
     Q = datagen.gaussian_mixture_f32(200, 48, seed=64)
