@@ -312,6 +312,38 @@ def main():
     recall = float(ann.recall(ids, gt, 10).item())
     status = ann.device_status()
 
+    # one more step with events between the stages (not timed above)
+    torch.cuda.synchronize()
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    sev[0].record(st)
+    cent_s, mem_s, off_s = ann.partition(Xd, cfg.C, cfg.r, init_d, samp_d, cfg.iters)
+    sev[1].record(st)
+    prec_s, model_s = cfg.precision, None
+    if prec_s == ann.LEARNED:
+        model_s = learned.params0.clone()
+        _, est_s = ann.learned_train(Xd, learned.sample, learned.draws, model_s, learned.kk,
+                                     learned.kpos, learned.lr, learned.margin)
+        if float(est_s.item()) < learned.min_recall:
+            prec_s, model_s = ann.EXACT, None
+    sev[2].record(st)
+    kid_s, kd_s = ann.shard_knn(Xd, mem_s, off_s, cfg.k, prec_s, cfg.rerank_k, model_s)
+    sev[3].record(st)
+    pid_s, pd_s = ann.prune(kid_s, kd_s, mem_s, off_s, cfg.R, cfg.rule, N=w.N)
+    sev[4].record(st)
+    ann.merge(pid_s, pd_s, mem_s, off_s, w.N)
+    sev[5].record(st)
+    torch.cuda.synchronize()
+    stages_ms = {name: sev[i].elapsed_time(sev[i + 1]) for i, name in
+                 enumerate(["partition", "learn", "shard_knn", "prune", "merge"])}
+    if model_s is not None:  # the embedding alone (part of the learned shard_knn)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ann.learned_embed(Xd, model_s)
+        e1.record(st)
+        torch.cuda.synchronize()
+        stages_ms["of_which_embed"] = e0.elapsed_time(e1)
+    del kid_s, kd_s, pid_s, pd_s
+
     counters = None
     if args.tile_counters:
         ann.tile_counters_read()
@@ -390,6 +422,7 @@ def main():
             "mean_dist_count": float(cnt.float().mean().item()),
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
             "distance_tflops": achieved,
+            "stages_ms": stages_ms,
             "device_status": status,
         },
         "roofline": {

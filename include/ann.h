@@ -168,12 +168,10 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
  *                    k <= rerank_k <= 128.  Ignored for uint8 under ANN_EXACT.
  *  model             ANN_LEARNED: the device parameter array of the MLP (see
  *                    ann_learned_train); otherwise NULL.
- * Limits: d <= 4096 (uint8: d <= 258, which keeps the integer tiles exact;
- * FP32 under ANN_EXACT: the split operands of a row block must fit shared memory,
- * about d <= 384 - larger d takes a screening precision), 1 <= k <= 96,
- * 1 <= C <= 1024, every shard smaller than 2^24 members.  When the 128 rows of a
- * block do not fit shared memory (large d) their K blocks stream through the
- * ring beside the B blocks instead of staying resident.
+ * Limits: d <= 4096 (uint8: d <= 258, which keeps the integer tiles exact),
+ * 1 <= k <= 96, 1 <= C <= 1024, every shard smaller than 2^24 members.  When
+ * the 128 rows of a block do not fit shared memory (large d) their K blocks
+ * stream through the ring beside the B blocks instead of staying resident.
  * ------------------------------------------------------------------------- */
 int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, int k,
                             int precision, int rerank_k, size_t* bytes);
@@ -287,8 +285,6 @@ int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const 
  *   exact 10 nearest vectors found among its 64 nearest in embedding space
  *   (all N) - an estimate of the form's recall@10 before any shard is built.
  *   Ids in sample[] at or above N are replaced by 0 and set status bit 2.
- *   The sample search is exact where the exact plan fits shared memory, else
- *   (FP32 at large d) it screens 128 candidates in scaled FP16 and re-ranks.
  *   Limits: d <= 4096, 2 <= kk <= 95,
  *   1 <= kpos < kk, N >= kk + 2, 1 <= S <= N, batch <= 65536.
  * ann_learned_embed: E [N x 32] float32 = f(X) for all rows (FP32 GEMMs).

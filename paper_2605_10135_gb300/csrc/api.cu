@@ -36,6 +36,7 @@ int fail(int code, const char* fmt, ...) {
 // ---- launch counter and tile timing --------------------------------------------
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static std::mutex g_timing_mu;
 static bool g_timing = false;

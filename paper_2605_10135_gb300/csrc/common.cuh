@@ -28,6 +28,7 @@ int fail(int code, const char* fmt, ...);
 // Every kernel launch of the library is followed by ANN_CHECK_LAUNCH(), which
 // also counts it (ann_launch_count).
 void count_launch();
+void count_launches(unsigned long long n);  // kernels run by graph replays
 #define ANN_CHECK_LAUNCH()                \
     do {                                  \
         ::ann::count_launch();            \

@@ -104,7 +104,7 @@ struct KnnParams {
     int local_first;          // sweep the columns near the row block first
     int mode;      // 0 plain, 1 split
     int nkb_a;     // A k-blocks (resident unless a_stream)
-    int a_stream;  // 1: A blocks stream through the ring with the B blocks (large d)
+    int a_stream;  // A blocks per ring stage (0: A resident; large d: 1, or 2 for split)
     int nkb_b;     // B k-blocks per tile
     int kprime;    // heap entries per row
     int k_out;     // entries written per row
@@ -122,10 +122,11 @@ struct KnnSmemLayout {
 };
 
 // a_stream = 0: the CTA's A rows stay resident (nkb_a K blocks) and a ring stage
-// holds one B block; a_stream = 1 (large d): nothing resident, a stage holds one
-// B block followed by the matching A block.
+// holds one B block; a_stream > 0 (large d): nothing resident, a stage holds one
+// B block followed by the a_stream A blocks it multiplies (split operands: the hi
+// and lo blocks against a hi B block, the hi block against a lo B block).
 __host__ __device__ inline uint32_t knn_stage_bytes(int bn, int a_stream) {
-    return (uint32_t)bn * 128 + (a_stream ? kt::A_BLK_BYTES : 0);
+    return (uint32_t)bn * 128 + a_stream * kt::A_BLK_BYTES;
 }
 
 __host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int kprime,
@@ -524,12 +525,23 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) w0 = clock64();
                     if (!mbar_wait(empty_bar + 8 * st, ph ^ 1, abort_flag)) { ok = false; break; }
                     if (PROF) prod_wait += clock64() - w0;
-                    mbar_expect_tx(full_bar + 8 * st,
-                                   B_BLK_BYTES + (P.a_stream ? kt::A_BLK_BYTES : 0));
+                    // streamed A blocks of this B block (see knn_stage_bytes)
+                    int as0 = j, na = 0;
+                    if (P.a_stream) {
+                        na = 1;
+                        if (P.mode == 1) {
+                            const int H2 = P.nkb_b >> 1;
+                            if (j < H2) na = 2; else as0 = j - H2;
+                        }
+                    }
+                    mbar_expect_tx(full_bar + 8 * st, B_BLK_BYTES + na * kt::A_BLK_BYTES);
                     tma_load_2d(sB + st * STG, &tmB, full_bar + 8 * st, j * P.kbe, b_y);
-                    if (P.a_stream)
+                    if (na >= 1)
                         tma_load_2d(sB + st * STG + B_BLK_BYTES, &tmA, full_bar + 8 * st,
-                                    j * P.kbe, a_y);
+                                    as0 * P.kbe, a_y);
+                    if (na == 2)  // the lo block of the same columns
+                        tma_load_2d(sB + st * STG + B_BLK_BYTES + kt::A_BLK_BYTES, &tmA,
+                                    full_bar + 8 * st, (as0 + (P.nkb_b >> 1)) * P.kbe, a_y);
                     used |= 1u << st;
                     last_par = (last_par & ~(1u << st)) | (ph << st);
                     if (++st == P.nst) { st = 0; ph ^= 1; }
@@ -598,8 +610,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                         ablk[0] = j - H2;  // hi . lo
                     }
                     for (int q = 0; q < na; ++q) {
-                        const uint32_t asm_ =
-                            P.a_stream ? bsm + B_BLK_BYTES : sA + ablk[q] * kt::A_BLK_BYTES;
+                        const uint32_t asm_ = P.a_stream
+                                                  ? bsm + B_BLK_BYTES + q * kt::A_BLK_BYTES
+                                                  : sA + ablk[q] * kt::A_BLK_BYTES;
                         // four K steps of 32 bytes per 128-byte block (K = 16 for 16-bit
                         // operands, K = 32 for E4M3)
 #pragma unroll
@@ -1185,6 +1198,100 @@ __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
     }
 }
 
+// The same re-rank with 16-byte loads (rows 16-byte aligned, d * element size a
+// multiple of 16): lane l sums the squared differences of 16-byte chunks
+// l, l + 32, ... in order, then a fixed xor tree adds the 32 partial sums.  Two
+// candidates are scored per pass so that their loads overlap.
+template <int DT>
+struct Chunk16 {
+    static constexpr int V = DT == ANN_F32 ? 4 : (DT == ANN_U8 ? 16 : 8);
+    __device__ static void unpack(const uint4& w, float (&f)[V]) {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (DT == ANN_F32) {
+                f[i] = __uint_as_float(u[i]);
+            } else if (DT == ANN_F16) {
+                const float2 t = __half22float2(*(const __half2*)&u[i]);
+                f[2 * i] = t.x;
+                f[2 * i + 1] = t.y;
+            } else if (DT == ANN_BF16) {
+                const float2 t = __bfloat1622float2(*(const __nv_bfloat162*)&u[i]);
+                f[2 * i] = t.x;
+                f[2 * i + 1] = t.y;
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) f[4 * i + b] = (float)((u[i] >> (8 * b)) & 0xFFu);
+            }
+        }
+    }
+};
+
+template <int E, int DT>
+__global__ void k_rerank_vec(const void* X, const void* Xrow, int d,
+                             const uint32_t* __restrict__ row_ids, int64_t nrows,
+                             const uint32_t* __restrict__ cand, int kc, int k,
+                             uint32_t* __restrict__ out_id, float* __restrict__ out_d) {
+    constexpr int V = Chunk16<DT>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= nrows) return;
+    const int64_t u = row_ids ? (int64_t)row_ids[p] : p;
+    const int nch = d / V;
+    const uint4* xu = (const uint4*)Xrow + u * nch;
+    uint64_t keys[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) keys[e] = ~0ull;
+    for (int c = 0; c < kc; c += 2) {
+        const uint32_t v0 = cand[p * kc + c];
+        const uint32_t v1 = c + 1 < kc ? cand[p * kc + c + 1] : ANN_PAD;
+        if (v0 == ANN_PAD && v1 == ANN_PAD) continue;  // uniform
+        const uint4* x0 = (const uint4*)X + (int64_t)(v0 == ANN_PAD ? 0 : v0) * nch;
+        const uint4* x1 = (const uint4*)X + (int64_t)(v1 == ANN_PAD ? 0 : v1) * nch;
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int q = lane; q < nch; q += 32) {
+            const uint4 wa = __ldg(xu + q), w0 = __ldg(x0 + q), w1 = __ldg(x1 + q);
+            float fa[V], f0[V], f1[V];
+            Chunk16<DT>::unpack(wa, fa);
+            Chunk16<DT>::unpack(w0, f0);
+            Chunk16<DT>::unpack(w1, f1);
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const float d0 = __fsub_rn(fa[t], f0[t]), d1 = __fsub_rn(fa[t], f1[t]);
+                s0 = __fadd_rn(s0, __fmul_rn(d0, d0));
+                s1 = __fadd_rn(s1, __fmul_rn(d1, d1));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 = __fadd_rn(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+            s1 = __fadd_rn(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cc = c + h;
+            const uint32_t v = h ? v1 : v0;
+            if (v != ANN_PAD && (cc & 31) == lane) {
+                const int e = cc >> 5;
+#pragma unroll
+                for (int q = 0; q < E; ++q)
+                    if (q == e) keys[q] = ((uint64_t)f2ord(h ? s1 : s0) << 32) | v;
+            }
+        }
+    }
+    warp_bitonic_u64<E>(keys);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = lane * E + e;
+        if (idx < k) {
+            const uint64_t x = keys[e];
+            const bool pad = (x == ~0ull);
+            out_id[p * k + idx] = pad ? ANN_PAD : (uint32_t)x;
+            out_d[p * k + idx] = pad ? INFINITY : ord2f((uint32_t)(x >> 32));
+        }
+    }
+}
+
 // ---- host side -------------------------------------------------------------------
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -1282,8 +1389,7 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
     p.nst = 0;
     p.a_stream = 0;
     const int tries[4][2] = {{256, 3}, {128, 3}, {256, 2}, {128, 2}};
-    for (int as = 0; as < 2 && !p.nst; ++as) {
-        if (as && p.mode != 0) break;
+    for (int as = 0; as <= (p.mode ? 2 : 1) && !p.nst; as += (p.mode ? 2 : 1)) {
         for (int q = 0; q < 4 && !p.nst; ++q) {
             const int bn = tries[q][0];
             for (int nst = kt::MAX_NST; nst >= tries[q][1]; --nst)
@@ -1296,9 +1402,8 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
         }
     }
     if (!p.nst)
-        return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory%s",
-                    d, p.kprime,
-                    p.mode ? " (FP32 at this d: use a screening precision)" : "");
+        return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory",
+                    d, p.kprime);
     p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.kprime, p.a_stream).total;
     *pl = p;
     return ANN_OK;
@@ -1378,12 +1483,28 @@ static int launch_rerank(const void* X, const void* Xrow, int dtype, int d, cons
     const int threads = 128;
     const unsigned grid = (unsigned)((nrows * 32 + threads - 1) / threads);
     if (nrows == 0) return ANN_OK;
-    if (kc <= 64)
+    const int es = dtype_bytes(dtype);
+    const bool vec = ((size_t)d * es) % 16 == 0 && (uintptr_t)X % 16 == 0 &&
+                     (uintptr_t)Xrow % 16 == 0;
+#define ANN_RERANK_VEC(E, DT)                                                                  \
+    k_rerank_vec<E, DT><<<grid, threads, 0, st>>>(X, Xrow, d, row_ids, nrows, cand, kc, k,     \
+                                                  out_id, out_d)
+    if (vec) {
+        const bool w = kc > 64;
+        switch (dtype) {
+        case ANN_F32: if (w) ANN_RERANK_VEC(4, ANN_F32); else ANN_RERANK_VEC(2, ANN_F32); break;
+        case ANN_F16: if (w) ANN_RERANK_VEC(4, ANN_F16); else ANN_RERANK_VEC(2, ANN_F16); break;
+        case ANN_BF16: if (w) ANN_RERANK_VEC(4, ANN_BF16); else ANN_RERANK_VEC(2, ANN_BF16); break;
+        default: if (w) ANN_RERANK_VEC(4, ANN_U8); else ANN_RERANK_VEC(2, ANN_U8); break;
+        }
+    } else if (kc <= 64) {
         k_rerank<2><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
                                               out_id, out_d);
-    else
+    } else {
         k_rerank<4><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
                                               out_id, out_d);
+    }
+#undef ANN_RERANK_VEC
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }

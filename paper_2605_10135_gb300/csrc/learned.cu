@@ -171,11 +171,11 @@ __device__ __forceinline__ uint32_t safe_id(uint32_t v, int64_t N, int* status) 
 
 __global__ void k_triplets(const uint32_t* __restrict__ sample, int64_t S,
                            const uint32_t* __restrict__ knn, int kk, int kpos,
-                           const uint32_t* __restrict__ draws, int B, int64_t N,
-                           uint32_t* __restrict__ idx, int* status) {
+                           const uint32_t* __restrict__ draws, const int* __restrict__ step,
+                           int B, int64_t N, uint32_t* __restrict__ idx, int* status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
-    const uint32_t* dr = draws + (int64_t)i * 3;
+    const uint32_t* dr = draws + ((int64_t)*step * B + i) * 3;
     const int64_t j = (int64_t)(dr[0] % (uint64_t)S);
     const uint32_t* L = knn + j * kk;
     const uint32_t r2 = dr[2];
@@ -224,8 +224,9 @@ __global__ void k_colsum(const float* __restrict__ A, int64_t rows, int cols,
     out[j] = s;
 }
 
-// Mean of li[0..B) into *out (fixed tree order, one block).
-__global__ void k_mean(const float* __restrict__ li, int B, float* out) {
+// Mean of li[0..B) into out[*step] (fixed tree order, one block).
+__global__ void k_mean(const float* __restrict__ li, int B, const int* __restrict__ step,
+                       float* out) {
     __shared__ float red[256];
     float s = 0.0f;
     for (int i = threadIdx.x; i < B; i += 256) s += li[i];
@@ -235,20 +236,28 @@ __global__ void k_mean(const float* __restrict__ li, int B, float* out) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = red[0] / (float)B;
+    if (threadIdx.x == 0) out[*step] = red[0] / (float)B;
 }
 
-// One Adam step on n parameters; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t).
+// One Adam step on n parameters, t = *step + 1; c1 = 1 / (1 - beta1^t),
+// c2 = 1 / (1 - beta2^t) (in double, rounded once).
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
+                       float* __restrict__ v, int64_t n, float lr, const int* __restrict__ step) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double t = (double)(*step + 1);
+    const float c1 = (float)(1.0 / (1.0 - pow(0.9, t)));
+    const float c2 = (float)(1.0 / (1.0 - pow(0.999, t)));
     const float gi = g[i];
     const float mi = 0.9f * m[i] + 0.1f * gi;
     const float vi = 0.999f * v[i] + 0.001f * gi * gi;
     m[i] = mi;
     v[i] = vi;
     p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+}
+
+__global__ void k_step_advance(int* step) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ++*step;
 }
 
 // Copy rows sample[j] of X (esize bytes per element) into Q row j.
@@ -371,6 +380,7 @@ struct LearnTrainWs {
     uint32_t* eid;       // [S x EST_K]
     float* ed;
     unsigned long long* hits;
+    int* step;           // device step counter (read by the captured step)
     void* ews;           // embedding workspace
     size_t ews_bytes;
 };
@@ -414,6 +424,7 @@ size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batc
     w.eid = cv.take<uint32_t>((size_t)S * EST_K);
     w.ed = cv.take<float>((size_t)S * EST_K);
     w.hits = cv.take<unsigned long long>(1);
+    w.step = cv.take<int>(4);
     w.ews_bytes = learned_embed_ws(N, d);
     w.ews = cv.take<uint8_t>(w.ews_bytes);
     if (out) *out = w;
@@ -460,42 +471,82 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
     float* gW2 = gb1 + ml::HID;
     float* gb2 = gW2 + (int64_t)ml::OUT * ml::HID;
     const float* W2 = params + (int64_t)ml::HID * d + ml::HID;
-    double b1t = 1.0, b2t = 1.0;
-    for (int t = 0; t < steps; ++t) {
-        k_triplets<<<(batch + 255) / 256, 256, 0, st>>>(sample, S, w.knn, kk, kpos,
-                                                       draws + (int64_t)t * batch * 3, batch, N,
-                                                       w.idx, status);
+    // One training step; every step-dependent value is read from w.step on the
+    // device, so the step can be captured once as a CUDA graph and replayed.
+    auto one_step = [&](cudaStream_t q) -> int {
+        int r;
+        k_triplets<<<(batch + 255) / 256, 256, 0, q>>>(sample, S, w.knn, kk, kpos, draws,
+                                                       w.step, batch, N, w.idx, status);
         ANN_CHECK_LAUNCH();
-        if ((rc = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, st)))
-            return rc;
-        k_triplet_loss<<<(batch + 127) / 128, 128, 0, st>>>(w.Z, batch, margin, w.dZ, w.li);
+        if ((r = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, q)))
+            return r;
+        k_triplet_loss<<<(batch + 127) / 128, 128, 0, q>>>(w.Z, batch, margin, w.dZ, w.li);
         ANN_CHECK_LAUNCH();
         if (losses) {
-            k_mean<<<1, 256, 0, st>>>(w.li, batch, losses + t);
+            k_mean<<<1, 256, 0, q>>>(w.li, batch, w.step, losses);
             ANN_CHECK_LAUNCH();
         }
         // dW2 = dZ^T H, db2 = column sums of dZ
-        if ((rc = gemm(ml::OUT, ml::HID, (int)R, mat(w.dZ, ANN_F32, ml::OUT, 1),
-                       mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, st)))
-            return rc;
-        k_colsum<<<1, 32, 0, st>>>(w.dZ, R, ml::OUT, gb2);
+        if ((r = gemm(ml::OUT, ml::HID, (int)R, mat(w.dZ, ANN_F32, ml::OUT, 1),
+                      mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, q)))
+            return r;
+        k_colsum<<<1, 32, 0, q>>>(w.dZ, R, ml::OUT, gb2);
         ANN_CHECK_LAUNCH();
         // dU = (dZ W2) where U > 0
-        if ((rc = gemm(R, ml::HID, ml::OUT, mat(w.dZ, ANN_F32, ml::OUT),
-                       mat(W2, ANN_F32, ml::HID), EpReluMask{w.dU, w.U, ml::HID}, st)))
-            return rc;
+        if ((r = gemm(R, ml::HID, ml::OUT, mat(w.dZ, ANN_F32, ml::OUT),
+                      mat(W2, ANN_F32, ml::HID), EpReluMask{w.dU, w.U, ml::HID}, q)))
+            return r;
         // dW1 = dU^T (X / s), db1 = column sums of dU
-        if ((rc = gemm(ml::HID, d, (int)R, mat(w.dU, ANN_F32, ml::HID, 1),
-                       mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, st)))
-            return rc;
-        k_colsum<<<1, 256, 0, st>>>(w.dU, R, ml::HID, gb1);
+        if ((r = gemm(ml::HID, d, (int)R, mat(w.dU, ANN_F32, ml::HID, 1),
+                      mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, q)))
+            return r;
+        k_colsum<<<1, 256, 0, q>>>(w.dU, R, ml::HID, gb1);
         ANN_CHECK_LAUNCH();
-        b1t *= 0.9;
-        b2t *= 0.999;
-        k_adam<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(params, w.G, w.m, w.v, P, lr,
-                                                           (float)(1.0 / (1.0 - b1t)),
-                                                           (float)(1.0 / (1.0 - b2t)));
+        k_adam<<<(unsigned)((P + 255) / 256), 256, 0, q>>>(params, w.G, w.m, w.v, P, lr,
+                                                           w.step);
         ANN_CHECK_LAUNCH();
+        k_step_advance<<<1, 32, 0, q>>>(w.step);
+        ANN_CHECK_LAUNCH();
+        return ANN_OK;
+    };
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.step, 0, sizeof(int), st));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    ANN_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (steps > 1 && cs == cudaStreamCaptureStatusNone) {
+        // Capture on a private stream ordered after st (the legacy default stream
+        // cannot be captured), replay there, and order st after the replays.
+        cudaStream_t q = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ANN_CHECK_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+        ANN_CHECK_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+        ANN_CHECK_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+        ANN_CHECK_CUDA(cudaEventRecord(e0, st));
+        ANN_CHECK_CUDA(cudaStreamWaitEvent(q, e0, 0));
+        const unsigned long long l0 = ann_launch_count();  // counts the captured launches
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t ec = cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal);
+        if (ec == cudaSuccess) {
+            rc = one_step(q);
+            ec = cudaStreamEndCapture(q, &g);
+        }
+        const unsigned long long per_step = ann_launch_count() - l0;
+        if (!rc && ec == cudaSuccess) ec = cudaGraphInstantiate(&ge, g, 0);
+        for (int t = 0; !rc && ec == cudaSuccess && t < steps; ++t) ec = cudaGraphLaunch(ge, q);
+        if (!rc && ec == cudaSuccess) ec = cudaEventRecord(e1, q);
+        if (!rc && ec == cudaSuccess) ec = cudaStreamWaitEvent(st, e1, 0);
+        if (ge) cudaGraphExecDestroy(ge);  // freed once the queued launches finish
+        if (g) cudaGraphDestroy(g);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(q);  // released once its work completes
+        if (rc) return rc;
+        if (ec != cudaSuccess)
+            return fail(ANN_ERR_CUDA, "training step graph: %s", cudaGetErrorString(ec));
+        count_launches(per_step * (unsigned long long)(steps - 1));
+    } else {
+        for (int t = 0; t < steps; ++t)
+            if ((rc = one_step(st))) return rc;
     }
     // 4. recall estimate: the sample's exact top 10 within its top EST_K in
     //    embedding space (all N)

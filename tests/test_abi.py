@@ -51,7 +51,7 @@ def test_workspace_queries_validate_on_host(L):
     assert L.ann_shard_knn_workspace(1000, 128, 0, 2000, 2000, 64, 0, 0, ct.byref(n)) == 1  # C
     assert L.ann_shard_knn_workspace(1000, 128, 0, 16, 2000, 64, 2, 32, ct.byref(n)) == 1  # < k
     assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 3, 0, ct.byref(n)) == 0  # learned
-    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # f32 split
+    assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 0, 0, ct.byref(n)) == 0  # f32 split
     assert L.ann_shard_knn_workspace(1000, 768, 0, 16, 2000, 64, 4, 0, ct.byref(n)) == 0  # streamed
     assert L.ann_shard_knn_workspace(1000, 1024, 1, 16, 2000, 64, 0, 0, ct.byref(n)) == 0  # f16
     assert L.ann_shard_knn_workspace(1000, 512, 3, 16, 2000, 64, 0, 0, ct.byref(n)) == 2  # u8

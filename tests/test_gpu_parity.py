@@ -186,7 +186,7 @@ def test_knn_query_and_medoid_u8():
 
 
 @pytest.mark.parametrize("kind,d,prec", [("f16", 768, ann.EXACT), ("bf16", 1024, ann.EXACT),
-                                         ("f32", 640, ann.F16_RERANK)])
+                                         ("f32", 640, ann.F16_RERANK), ("f32", 768, ann.EXACT)])
 def test_large_d_streamed_tiles_float_rule(kind, d, prec):
     """128 rows of d >= 640 do not fit shared memory: their K blocks stream
     through the ring beside the B blocks (one launch, several shards)."""
