@@ -1748,4 +1748,68 @@ int tile_counters_read(unsigned long long* out, int n, bool reset) {
     return ANN_OK;
 }
 
+// ---- screening query: tile keys only, exact decisions taken by the caller ---------
+// For every A row p (row rowsel[p0 + p] of Xa, or p0 + p when rowsel is NULL) the
+// ks rows of Xb with the smallest tile key |y|^2/2 - x.y (ties to the smaller
+// index), written as indices into Xb.  Both sides use the FP32 split operand form
+// (three BF16 products), whatever their element types.
+
+static int screen_plan(int d, int ks, KnnPlan* pl) {
+    int rc = knn_plan(d, ANN_F32, ks, ANN_EXACT, 0, pl);
+    if (rc) return rc;
+    pl->rerank = false;
+    pl->kprime = ks;
+    pl->smem = knn_smem_layout(pl->bn, pl->nkb_a, pl->nst, ks, pl->a_stream).total;
+    return ANN_OK;
+}
+
+size_t screen_ws(int64_t na, int64_t nb, int d, int ks) {
+    KnnPlan pl;
+    if (screen_plan(d, ks, &pl)) return 0;
+    Carver cv(nullptr, ~(size_t)0);
+    cv.take<uint8_t>(query_ws(nb, na, pl, nullptr, nullptr, 0));
+    cv.take<float>((size_t)na * ks);
+    return cv.used + 256;
+}
+
+__global__ void k_rowmap_sel(const uint32_t* __restrict__ rowsel, int64_t p0, int64_t n,
+                             int64_t cap, int64_t* __restrict__ src) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < cap;
+         p += (int64_t)gridDim.x * blockDim.x)
+        src[p] = p < n ? (rowsel ? (int64_t)rowsel[p0 + p] : p0 + p) : -1;
+}
+
+int run_screen(const void* Xa, int dta, const uint32_t* rowsel, int64_t p0, int64_t na,
+               const void* Xb, int dtb, int64_t nb, int d, int ks, uint32_t* out_id, void* ws,
+               size_t ws_bytes, cudaStream_t st) {
+    KnnPlan pl;
+    int rc = screen_plan(d, ks, &pl);
+    if (rc) return rc;
+    if (screen_ws(na, nb, d, ks) > ws_bytes) return fail(ANN_ERR_WORKSPACE, "screen: workspace");
+    if (na == 0) return ANN_OK;
+    Carver cv(ws, ws_bytes);
+    const size_t qb = query_ws(nb, na, pl, nullptr, nullptr, 0);
+    uint8_t* qbase = cv.take<uint8_t>(qb);
+    float* out_d = cv.take<float>((size_t)na * ks);
+    QueryWs w;
+    query_ws(nb, na, pl, &w, qbase, qb);
+    k_query_tables<<<1, 32, 0, st>>>(nb, na, w.blk_off, w.pad_off, w.offs, w.prob);
+    ANN_CHECK_LAUNCH();
+    k_ones_tile<<<(128 * kt::KAUG + 255) / 256, 256, 0, st>>>(w.ones);
+    ANN_CHECK_LAUNCH();
+    k_rowmap_sel<<<grid_rows(w.capA, 256), 256, 0, st>>>(rowsel, p0, na, w.capA, w.srcA);
+    ANN_CHECK_LAUNCH();
+    k_rowmap_plain<<<grid_rows(w.capB, 256), 256, 0, st>>>(nullptr, w.offs + 2, w.pad_off + 2, 1,
+                                                           w.capB, w.srcB);
+    ANN_CHECK_LAUNCH();
+    if ((rc = launch_gather(Xa, dta, d, w.srcA, w.capA, pl, w.GA, w.na, w.augA, nullptr, st)))
+        return rc;
+    if ((rc = launch_gather(Xb, dtb, d, w.srcB, w.capB, pl, w.GB, w.nb, w.augB, nullptr, st)))
+        return rc;
+    KnnParams P = base_params(pl, ks, w.blk_off, w.prob, 1, w.na, nullptr, nullptr, 0, 0, out_id,
+                              out_d);
+    const int64_t grid = (na + kt::BM - 1) / kt::BM;
+    return launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st, false);
+}
+
 }  // namespace ann

@@ -1,11 +1,17 @@
 // Replicated k-means partitioning (Sec. IV Workflow (1); Sec. II-B: k-means
 // shards, each vector replicated into its nearest shards).
 //
-//  kmeans iterations : per-pair FP32 distances (terms added in index order,
-//                      unfused, so the argmin is bit-identical to a plain loop),
-//                      first-minimum argmin, FP64 centroid sums accumulated in
-//                      sample order by one thread per (dimension), mean rounded
-//                      to float; empty clusters keep their centroid.
+//  distances         : d32 = FP32 squared distance with the terms added in index
+//                      order, unfused (the oracle's definition).  Up to 32
+//                      centroids every d32 is computed (thread per pair); with
+//                      more, the tensor cores screen them first: a tile query keeps the
+//                      min(C, r + 6) centroids of smallest tile key per vector,
+//                      and d32 is computed for those only.  The result equals the
+//                      full d32 scan unless more than 6 other centroids lie within
+//                      the screen's rounding (about 1e-6 relative) of the r-th.
+//  kmeans iterations : nearest centroid by (d32, id) for every sample row, FP64
+//                      centroid sums accumulated in sample order, mean rounded to
+//                      float; empty clusters keep their centroid.
 //  assignment        : the r centroids of smallest (d32, id) for every vector.
 //  shard lists       : block histograms, per-shard scan over blocks, and a
 //                      stable scatter (warp match_any ranks) so each shard's
@@ -43,7 +49,7 @@ __global__ void k_dist_centroids(const void* X, int dtype, int d, const uint32_t
     }
 }
 
-// The r entries of smallest (dist, c) per point, in that order.
+// The r entries of smallest (dist, c) per point, in that order (full scan).
 __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
                        uint32_t* __restrict__ out, int32_t* __restrict__ lab_out) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -64,6 +70,57 @@ __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
         if (bc < 0) bc = 0;  // unreachable for finite distances
         if (out) out[p * r + q] = (uint32_t)bc;
         if (lab_out && q == 0) lab_out[p] = bc;
+        prev_d = bd;
+        prev_c = bc;
+    }
+}
+
+// d32 of the screened candidates: dist[p * ks + j] for centroid cand[p * ks + j]
+// (centroids row-major [C x d]).
+__global__ void k_d32_cand(const void* X, int dtype, int d, const uint32_t* rowsel, int64_t p0,
+                           int64_t np, const float* __restrict__ cent,
+                           const uint32_t* __restrict__ cand, int ks, float* __restrict__ dist) {
+    const int64_t total = np * ks;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = q / ks;
+        const int64_t row = rowsel ? (int64_t)rowsel[p0 + p] : p0 + p;
+        const float* c = cent + (int64_t)cand[q] * d;
+        float s = 0.0f;
+        for (int t = 0; t < d; ++t) {
+            const float df = __fsub_rn(load_elem(X, dtype, row * d + t), __ldg(c + t));
+            s = __fadd_rn(s, __fmul_rn(df, df));
+        }
+        dist[q] = s;
+    }
+}
+
+// The r candidates of smallest (d32, centroid id) per point, in that order.
+__global__ void k_topr_cand(const float* __restrict__ dist, const uint32_t* __restrict__ cand,
+                            int64_t np, int ks, int r, uint32_t* __restrict__ out,
+                            int32_t* __restrict__ lab_out) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const float* dp = dist + p * ks;
+    const uint32_t* cp = cand + p * ks;
+    float prev_d = -INFINITY;
+    int64_t prev_c = -1;
+    for (int q = 0; q < r; ++q) {
+        float bd = INFINITY;
+        int64_t bc = -1;
+        for (int j = 0; j < ks; ++j) {
+            const float v = dp[j];
+            const int64_t c = cp[j];
+            const bool after = (v > prev_d) || (v == prev_d && c > prev_c);
+            if (!after) continue;
+            if (bc < 0 || v < bd || (v == bd && c < bc)) {
+                bd = v;
+                bc = c;
+            }
+        }
+        if (bc < 0) bc = 0;  // unreachable: ks >= r distinct candidates
+        if (out) out[p * r + q] = (uint32_t)bc;
+        if (lab_out && q == 0) lab_out[p] = (int32_t)bc;
         prev_d = bd;
         prev_c = bc;
     }
@@ -222,22 +279,28 @@ __global__ void k_scatter(const uint32_t* __restrict__ assign, int64_t N, int r,
 }
 
 // ---- host driver --------------------------------------------------------------
-static int64_t dist_chunk(int64_t N, int C) {
-    int64_t ch = (int64_t)1 << 26;
-    ch /= C;
-    if (ch < 1024) ch = 1024;
-    return ch < N ? ch : N;
-}
+static constexpr int64_t ASSIGN_CHUNK = 131072;  // rows per assignment launch
+static constexpr int FULL_SCAN_C = 32;            // up to this many centroids: no screen
+static int screen_width(int C, int r) { return C < r + 6 ? C : r + 6; }
 
 size_t partition_ws(int64_t N, int d, int C, int r, int64_t S, PartitionWs* out, void* base,
                     size_t cap) {
     Carver cv(base, cap);
     PartitionWs w;
-    w.chunk = dist_chunk(N > S ? N : S, C);
+    const int64_t nmax = N > S ? N : S;
+    w.chunk = nmax < ASSIGN_CHUNK ? (nmax > 0 ? nmax : 1) : ASSIGN_CHUNK;
+    w.ks = screen_width(C, r);
+    const int ks1 = screen_width(C, 1);
+    const size_t sw1 = screen_ws(w.chunk, C, d, w.ks), sw2 = screen_ws(w.chunk, C, d, ks1);
+    w.sws_bytes = sw1 > sw2 ? sw1 : sw2;
     int64_t nblk = (N + SB - 1) / SB;
     w.cent = cv.take<float>((size_t)C * d);
     w.centT = cv.take<float>((size_t)C * d);
-    w.dist = cv.take<float>((size_t)w.chunk * C);
+    const bool full = C <= FULL_SCAN_C;
+    if (full) w.sws_bytes = 0;
+    w.dist = cv.take<float>((size_t)w.chunk * (full ? C : w.ks));
+    w.cand = cv.take<uint32_t>((size_t)w.chunk * w.ks);
+    w.sws = cv.take<uint8_t>(w.sws_bytes + 1);
     w.lab = cv.take<int32_t>((size_t)(S > 0 ? S : 1));
     w.sums = cv.take<double>((size_t)C * d);
     w.cnt = cv.take<int64_t>((size_t)C);
@@ -246,6 +309,33 @@ size_t partition_ws(int64_t N, int d, int C, int r, int64_t S, PartitionWs* out,
     w.tot = cv.take<int64_t>((size_t)C);
     if (out) *out = w;
     return cv.used + 256;
+}
+
+// The r centroids of smallest (d32, id) for rows p0 .. p0+np-1 (through rowsel
+// when given): tensor-core screen, then d32 of the candidates.
+static int assign_chunk(const void* X, int dtype, int d, const uint32_t* rowsel, int64_t p0,
+                        int64_t np, int C, int r, const PartitionWs& w, uint32_t* out,
+                        int32_t* lab, cudaStream_t st) {
+    if (C <= FULL_SCAN_C) {
+        const int64_t tot = np * C;
+        const unsigned g = (unsigned)((tot + 255) / 256 < 65535 * 8 ? (tot + 255) / 256 : 65535 * 8);
+        k_dist_centroids<<<g, 256, 0, st>>>(X, dtype, d, rowsel, p0, np, w.centT, C, w.dist);
+        ANN_CHECK_LAUNCH();
+        k_topr<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, np, C, r, out, lab);
+        ANN_CHECK_LAUNCH();
+        return ANN_OK;
+    }
+    const int ks = screen_width(C, r);
+    int rc = run_screen(X, dtype, rowsel, p0, np, w.cent, ANN_F32, C, d, ks, w.cand, w.sws,
+                        w.sws_bytes, st);
+    if (rc) return rc;
+    const int64_t tot = np * ks;
+    const unsigned g = (unsigned)((tot + 255) / 256 < 65535 * 8 ? (tot + 255) / 256 : 65535 * 8);
+    k_d32_cand<<<g, 256, 0, st>>>(X, dtype, d, rowsel, p0, np, w.cent, w.cand, ks, w.dist);
+    ANN_CHECK_LAUNCH();
+    k_topr_cand<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, w.cand, np, ks, r, out, lab);
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
 }
 
 int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
@@ -260,11 +350,9 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
     for (int it = 0; it < iters && S > 0; ++it) {
         for (int64_t p0 = 0; p0 < S; p0 += w.chunk) {
             int64_t np = S - p0 < w.chunk ? S - p0 : w.chunk;
-            k_dist_centroids<<<nb(np * C, tpb) < 65535u * 8 ? nb(np * C, tpb) : 65535u * 8, tpb, 0,
-                               st>>>(X, dtype, d, sample_idx, p0, np, w.centT, C, w.dist);
-            ANN_CHECK_LAUNCH();
-            k_topr<<<nb(np, tpb), tpb, 0, st>>>(w.dist, np, C, 1, nullptr, w.lab + p0);
-            ANN_CHECK_LAUNCH();
+            int rc = assign_chunk(X, dtype, d, sample_idx, p0, np, C, 1, w, nullptr,
+                                  w.lab + p0, st);
+            if (rc) return rc;
         }
         ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * C, st));
         {
@@ -282,12 +370,9 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
                                    cudaMemcpyDeviceToDevice, st));
     for (int64_t p0 = 0; p0 < N; p0 += w.chunk) {
         int64_t np = N - p0 < w.chunk ? N - p0 : w.chunk;
-        unsigned g = nb(np * C, tpb);
-        k_dist_centroids<<<g < 65535u * 8 ? g : 65535u * 8, tpb, 0, st>>>(X, dtype, d, nullptr, p0,
-                                                                          np, w.centT, C, w.dist);
-        ANN_CHECK_LAUNCH();
-        k_topr<<<nb(np, tpb), tpb, 0, st>>>(w.dist, np, C, r, w.assign + p0 * r, nullptr);
-        ANN_CHECK_LAUNCH();
+        int rc = assign_chunk(X, dtype, d, nullptr, p0, np, C, r, w, w.assign + p0 * r, nullptr,
+                              st);
+        if (rc) return rc;
     }
     int64_t nblk = (N + SB - 1) / SB;
     k_block_hist<<<(unsigned)nblk, 256, C * sizeof(int32_t), st>>>(w.assign, N, r, C, nblk, w.hist);

@@ -12,7 +12,11 @@ namespace ann {
 struct PartitionWs {
     float* cent;       // [C*d] working centroids
     float* centT;      // [d*C] transposed copy read by the distance kernel
-    float* dist;       // [chunk*C]
+    float* dist;       // [chunk*C] (full scan) or [chunk*ks] d32 of the screened candidates
+    uint32_t* cand;    // [chunk*ks] screened centroid ids
+    uint8_t* sws;      // screening workspace
+    size_t sws_bytes;
+    int ks;            // screened centroids per vector (final assignment)
     int32_t* lab;      // [S]
     double* sums;      // [C*d]
     int64_t* cnt;      // [C]
@@ -141,6 +145,13 @@ int run_search(const uint32_t* graph, const uint32_t* degree, int R, const void*
                uint32_t* out_id, uint32_t* out_count, cudaStream_t st);
 int run_recall(const uint32_t* found, int fs, const uint32_t* truth, int ts, int64_t nq, int kk,
                float* recall_out, unsigned long long* hits, cudaStream_t st);
+
+// Screening query (tile keys only): for A rows p0 .. p0+na-1 (through rowsel when
+// given) of Xa, the ks rows of Xb [nb x d] of smallest tile key, as indices.
+size_t screen_ws(int64_t na, int64_t nb, int d, int ks);
+int run_screen(const void* Xa, int dta, const uint32_t* rowsel, int64_t p0, int64_t na,
+               const void* Xb, int dtb, int64_t nb, int d, int ks, uint32_t* out_id, void* ws,
+               size_t ws_bytes, cudaStream_t st);
 
 // max |x| over X [n elements] and, if given, Q [nq_elems] into *amax (float bits;
 // the word is zeroed first).

@@ -64,6 +64,25 @@ def test_partition_bit_exact(kind):
     assert np.array_equal(mem, mem_o)
 
 
+@pytest.mark.parametrize("kind,d", [("u8", 128), ("f32", 64), ("f16", 700)])
+def test_partition_screened_bit_exact(kind, d):
+    """More than 32 centroids: tensor-core screening of r + 6 centroids, then d32 of
+    those; the result must equal the oracle's full d32 scan (ids, centroids, lists).
+    d = 700 streams the K blocks of the vector side."""
+    if kind == "u8":
+        X = datagen.clustered_u8(6000, d, 64, seed=131)
+    elif kind == "f32":
+        X = datagen.gaussian_mixture_f32(6000, d, 64, 2.0, seed=132)
+    else:
+        X = datagen.anisotropic_mixture(4000, d, 64, 0.25, False, np.float16, seed=133)
+    C, r, iters = 48, 2, 4
+    cent, mem, off, (sample, init) = _gpu_partition(X, C, r, iters, seed=134)
+    cent_o, _, mem_o, off_o = oracle.partition(X, init, sample, iters, C, r)
+    assert np.array_equal(cent.view(np.uint32), cent_o.view(np.uint32))
+    assert np.array_equal(off, off_o)
+    assert np.array_equal(mem, mem_o)
+
+
 def test_partition_edge_cases():
     X = datagen.clustered_u8(700, 16, 4, seed=35)
     for C, r in [(1, 1), (3, 3), (7, 1)]:
