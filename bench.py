@@ -187,6 +187,8 @@ def main():
                          "E4M3 screening with an FP32 re-rank of the top 128, or learned "
                          "(32-d MLP embedding screened, re-ranked exactly)")
     ap.add_argument("--rerank-k", type=int, default=0, help="screened list width (0: default)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the candidate tile plans during the first warm-up step")
     ap.add_argument("--learn-steps", type=int, default=300)
     ap.add_argument("--learn-batch", type=int, default=512)
     ap.add_argument("--sample-frac", type=float, default=0.01)
@@ -251,9 +253,14 @@ def main():
     def step(x):
         return ann.build_index(x, cfg, init_d, samp_d, learned)
 
+    if args.autotune:
+        ann.autotune(1)
     for _ in range(max(args.warmup, 3)):
         out = step(Xd)
     torch.cuda.synchronize()
+    ann.autotune(0)
+    tuned = (ann.autotune_lookup(w.d, Xd.dtype, w.k, out.get("precision", prec), args.rerank_k,
+                                 int(out["members"].numel()), w.C) if args.autotune else None)
 
     uuid = str(torch.cuda.get_device_properties(dev).uuid)
     clocks = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
@@ -423,6 +430,7 @@ def main():
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
             "distance_tflops": achieved,
             "stages_ms": stages_ms,
+            "tile_plan_autotuned": tuned,
             "device_status": status,
         },
         "roofline": {

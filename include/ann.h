@@ -114,6 +114,22 @@ int ann_timing_read(double* tile_ms, int* launches);
 int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 
+/* Autotuner of the distance-tile plan.  ann_autotune(1): every later
+ * ann_shard_knn call (not ANN_LEARNED) whose key (d, dtype, k, precision,
+ * rerank_k, floor(log2(rows / C))) has no decision yet runs the whole shard kNN
+ * once with each candidate plan - tile width 256 or 128, the two deepest TMA
+ * rings that fit shared memory - timing each with CUDA events on its stream
+ * (the call synchronises that stream), and keeps the fastest for the key.  The
+ * lists do not depend on the plan, so the call's output is the same as
+ * untuned.  Decided keys use their plan whether tuning is on or off.
+ * ann_autotune(0) stops tuning new keys; ann_autotune(-1) also forgets every
+ * decision.  ann_autotune_lookup: host out found (0/1) and, if found, the
+ * chosen tile width bn, ring depth nst, streamed-A flag, its time in ms and the
+ * number of plans tried. */
+int ann_autotune(int on);
+int ann_autotune_lookup(int d, int dtype, int k, int precision, int rerank_k, int64_t rows, int C,
+                        int* found, int* bn, int* nst, int* a_stream, float* ms, int* tried);
+
 /* Reads (host out) and clears the device status word of the current device:
  * bit 1 = a bounded device wait gave up, bit 2 = inconsistent input found on
  * the device (e.g. offsets[C] != rows), bit 4 = a fixed-capacity buffer

@@ -75,6 +75,8 @@ def lib():
             "ann_learned_train": (I32, [P, I64, I32, I32, P, I64, I32, I32, P, I32, I32,
                                         ct.c_float, ct.c_float, P, P, P, P, SZ, P]),
             "ann_learned_embed_workspace": (I32, [I64, I32, PSZ]),
+            "ann_autotune": (I32, [I32]),
+            "ann_autotune_lookup": (I32, [I32, I32, I32, I32, I32, I64, I32, P, P, P, P, P, P]),
             "ann_learned_embed": (I32, [P, I64, I32, I32, P, P, P, SZ, P]),
         }
         for name, (res, args) in sigs.items():
@@ -149,6 +151,24 @@ def tile_counters_read() -> dict:
     arr = (ct.c_ulonglong * len(TILE_COUNTERS))()
     _check(lib().ann_tile_counters_read(arr, len(TILE_COUNTERS)))
     return dict(zip(TILE_COUNTERS, [int(v) for v in arr]))
+
+
+def autotune(on: int = 1):
+    """1: time the candidate tile plans of every new shard-kNN key and keep the
+    fastest; 0: stop tuning new keys; -1: also forget every decision."""
+    _check(lib().ann_autotune(int(on)))
+
+
+def autotune_lookup(d: int, dtype: torch.dtype, k: int, precision: int, rerank_k: int, rows: int,
+                    C: int):
+    """The tuned plan of a key as a dict, or None."""
+    vals = [ct.c_int(0) for _ in range(4)] + [ct.c_float(0.0), ct.c_int(0)]
+    _check(lib().ann_autotune_lookup(d, _DT[dtype], k, precision, rerank_k, rows, C,
+                                     *[ct.byref(v) for v in vals]))
+    if not vals[0].value:
+        return None
+    return dict(bn=vals[1].value, nst=vals[2].value, a_stream=vals[3].value, ms=vals[4].value,
+                tried=vals[5].value)
 
 
 def device_status() -> int:

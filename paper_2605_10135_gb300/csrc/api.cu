@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -197,6 +199,74 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
                          members_out, offsets_out, w, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------- autotuner
+// Plans chosen by timing, per (d, dtype, k, precision, rerank_k, shard-size
+// bucket = floor(log2(rows / C))); process-wide, guarded by a mutex.
+struct TuneKey {
+    int d, dtype, k, precision, rerank_k, bucket;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(d, dtype, k, precision, rerank_k, bucket) <
+               std::tie(o.d, o.dtype, o.k, o.precision, o.rerank_k, o.bucket);
+    }
+};
+struct TuneEntry {
+    KnnPlan plan;
+    float ms;
+    int tried;
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneEntry> g_tuned;
+static std::atomic<bool> g_autotune{false};
+
+static TuneKey tune_key(int d, int dtype, int k, int precision, int rerank_k, int64_t rows, int C) {
+    int64_t per = rows / (C > 0 ? C : 1);
+    int b = 0;
+    while (per > 1) {
+        per >>= 1;
+        ++b;
+    }
+    return TuneKey{d, dtype, k, precision, rerank_k, b};
+}
+
+static bool tuned_plan(const TuneKey& key, KnnPlan* pl) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it == g_tuned.end()) return false;
+    *pl = it->second.plan;
+    return true;
+}
+
+static void store_tuned(const TuneKey& key, const KnnPlan& pl, float ms, int tried) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = TuneEntry{pl, ms, tried};
+}
+
+int ann_autotune(int on) {
+    g_autotune.store(on != 0);
+    if (on < 0) {  // forget every decision
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned.clear();
+        g_autotune.store(false);
+    }
+    return ANN_OK;
+}
+
+int ann_autotune_lookup(int d, int dtype, int k, int precision, int rerank_k, int64_t rows, int C,
+                        int* found, int* bn, int* nst, int* a_stream, float* ms, int* tried) {
+    ANN_REQUIRE(found && bn && nst && a_stream && ms && tried, "NULL pointer");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(d, dtype, k, precision, rerank_k, rows, C));
+    *found = it != g_tuned.end();
+    if (*found) {
+        *bn = it->second.plan.bn;
+        *nst = it->second.plan.nst;
+        *a_stream = it->second.plan.a_stream;
+        *ms = it->second.ms;
+        *tried = it->second.tried;
+    }
+    return ANN_OK;
+}
+
 // ---------------------------------------------------------------- shard kNN
 static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int precision,
                     int rerank_k) {
@@ -282,8 +352,44 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     if (rows == 0) return ANN_OK;
     KnnWs w;
     knn_ws(C, rows, pl, &w, ws, ws_bytes);
-    return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, knn_id, knn_d,
-                         (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    const TuneKey key = tune_key(d, dtype, k, precision, rerank_k, rows, C);
+    if (tuned_plan(key, &pl)) {
+        return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, knn_id, knn_d,
+                             st);
+    }
+    if (!g_autotune.load()) {
+        return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, knn_id, knn_d,
+                             st);
+    }
+    // Autotune: run the whole shard kNN once per plan, timed with events on the
+    // stream; every run writes the same lists, so the last one is the result.
+    KnnPlan vars[8];
+    const int nv = knn_plan_variants(d, dtype, k, precision, rerank_k, vars, 8);
+    if (nv <= 0) return -nv;
+    cudaEvent_t e0, e1;
+    ANN_CHECK_CUDA(cudaEventCreate(&e0));
+    ANN_CHECK_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int v = 0; v < nv && !rc; ++v) {
+        ANN_CHECK_CUDA(cudaEventRecord(e0, st));
+        rc = run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, vars[v], w, knn_id, knn_d,
+                           st);
+        ANN_CHECK_CUDA(cudaEventRecord(e1, st));
+        ANN_CHECK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        ANN_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (v == 0 || ms < best_ms) {
+            best = v;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    store_tuned(key, vars[best], best_ms, nv);
+    return ANN_OK;
 }
 
 // ---------------------------------------------------------------- learned form

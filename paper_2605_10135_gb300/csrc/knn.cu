@@ -1409,6 +1409,36 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
     return ANN_OK;
 }
 
+// Every shared-memory plan of the same problem (same operand form and list width)
+// that the autotuner may time: for each tile width the two deepest rings that
+// fit, A resident if any plan with resident A fits, else streamed.  out[0] is
+// the default plan.  Results never depend on the plan (same per-pair arithmetic,
+// ties by id), only the speed does.
+int knn_plan_variants(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* out,
+                      int max_out) {
+    KnnPlan base;
+    int rc = knn_plan(d, dtype, k, precision, rerank_k, &base);
+    if (rc) return -rc;
+    int n = 0;
+    out[n++] = base;
+    const size_t cap = 227 * 1024;
+    for (int bn = 256; bn >= 128 && n < max_out; bn -= 128) {
+        int found = 0;
+        for (int nst = kt::MAX_NST; nst >= 2 && found < 2 && n < max_out; --nst) {
+            if (knn_smem_layout(bn, base.nkb_a, nst, base.kprime, base.a_stream).total > cap)
+                continue;
+            ++found;
+            if (bn == base.bn && nst == base.nst) continue;
+            KnnPlan v = base;
+            v.bn = bn;
+            v.nst = nst;
+            v.smem = knn_smem_layout(bn, base.nkb_a, nst, base.kprime, base.a_stream).total;
+            out[n++] = v;
+        }
+    }
+    return n;
+}
+
 // Operand bytes per gathered row.
 static inline size_t row_bytes(const KnnPlan& pl) { return (size_t)pl.Kp * (pl.elem8 ? 1 : 2); }
 

@@ -58,6 +58,10 @@ struct KnnPlan {
     size_t smem;
 };
 int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl);
+// Plans the autotuner may time (default first); returns their number, or minus
+// the error code when no plan exists.
+int knn_plan_variants(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* out,
+                      int max_out);
 
 struct KnnWs {
     int64_t* blk_off;

@@ -346,3 +346,29 @@ def test_16bit_precision_forms_are_exact_on_uint8(prec):
     oid, od = oracle.shard_knn(X, mem, off, 32)
     assert np.array_equal(as_u32(gid), oid)
     assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_autotuner_keeps_the_lists_and_records_a_plan(kind):
+    """Tuning runs every candidate plan; the lists must be bit-identical to the
+    untuned call, and the decision is used by the next call."""
+    if kind == "u8":
+        X = datagen.clustered_u8(9000, 128, 32, seed=171)
+    else:
+        X = datagen.gaussian_mixture_f32(9000, 96, 16, seed=172)
+    mem, off = _oracle_shards(X, 3, 2, seed=173)
+    k = 24
+    ann.autotune(-1)
+    ref_id, ref_d = ann.shard_knn(T(X), T(mem), T(off), k)
+    ann.autotune(1)
+    try:
+        got_id, got_d = ann.shard_knn(T(X), T(mem), T(off), k)
+    finally:
+        ann.autotune(0)
+    rows = len(mem)
+    plan = ann.autotune_lookup(X.shape[1], T(X).dtype, k, ann.EXACT, 0, rows, 3)
+    assert plan is not None and plan["tried"] >= 2 and plan["bn"] in (128, 256)
+    assert torch.equal(got_id, ref_id) and torch.equal(got_d, ref_d)
+    again_id, again_d = ann.shard_knn(T(X), T(mem), T(off), k)   # uses the tuned plan
+    assert torch.equal(again_id, ref_id) and torch.equal(again_d, ref_d)
+    ann.autotune(-1)
