@@ -372,3 +372,28 @@ def test_autotuner_keeps_the_lists_and_records_a_plan(kind):
     again_id, again_d = ann.shard_knn(T(X), T(mem), T(off), k)   # uses the tuned plan
     assert torch.equal(again_id, ref_id) and torch.equal(again_d, ref_d)
     ann.autotune(-1)
+
+
+def test_captured_build_replays_match_eager():
+    """The whole build captured as one CUDA graph: replays give the eager result,
+    also after new vectors are copied into the captured input."""
+    from paper_2605_10135_gb300 import configs
+    w = configs.GAUSS_10K
+    X = w.vectors()
+    sample, init_rows = w.kmeans_inputs()
+    init = X[init_rows].astype(np.float32)
+    cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R)
+    Xd, init_d, samp_d = T(X), T(init), T(sample)
+    eager = ann.build_index(Xd.clone(), cfg, init_d, samp_d)
+    cap = ann.CapturedBuild(Xd, cfg, init_d, samp_d)
+    out = cap.replay()
+    torch.cuda.synchronize()
+    for key in ("members", "offsets", "knn_id", "graph", "degree"):
+        assert torch.equal(out[key], eager[key]), key
+    X2 = w.vectors(seed_offset=5)
+    eager2 = ann.build_index(T(X2), cfg, init_d, samp_d)
+    cap.X.copy_(T(X2))
+    out2 = cap.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out2["graph"], eager2["graph"])
+    assert cap.kernels > 10
