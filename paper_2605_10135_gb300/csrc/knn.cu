@@ -410,6 +410,19 @@ __device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+// The tt-th tile of a sweep that starts at t0 and moves outward: t0, t0+1, t0-1,
+// t0+2, t0-2, ... while both sides have tiles, then the rest of the longer side.
+__device__ __forceinline__ int tile_at(int tt, int t0, int ntiles) {
+    const int left = t0, right = ntiles - 1 - t0;
+    const int m = left < right ? left : right;
+    if (tt <= 2 * m) {
+        const int k = (tt + 1) >> 1;
+        return (tt & 1) ? t0 + k : t0 - k;
+    }
+    const int extra = tt - 2 * m;
+    return right > left ? t0 + m + extra : t0 - m - extra;
+}
+
 template <int BN, bool PROF>
 __global__ void __launch_bounds__(kt::THREADS, 1)
     k_knn_tiles(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -428,13 +441,14 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     const int rb = (int)(bid - P.blk_off[lo]);
     const int ntiles = (pr.n_cols + BN - 1) / BN;
     constexpr int B_BLK_BYTES = BN * 128, B_AUG_BYTES = BN * 32;
-    // Sweep order: tile t0, t0+1, ... wrapping around.  With local_first the sweep
-    // starts near the block's own rows (rows are ordered by cell), so each row's
-    // k-th key tightens early.
+    // Sweep order (tile_at): with local_first the sweep starts at the tile holding
+    // the block's first row and moves outward, alternating forward and backward;
+    // rows are ordered by cell and cells along a chain of nearby pivots, so each
+    // row's k-th key tightens early and far cells come last.
     int t0 = 0;
     if (P.local_first) {
-        t0 = (rb * kt::BM - 512) / BN;
-        if (t0 < 0 || t0 >= ntiles) t0 = 0;
+        t0 = rb * kt::BM / BN;
+        if (t0 >= ntiles) t0 = ntiles - 1;
     }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             bool ok = true;
             unsigned long long prod_wait = 0;
             for (int tt = 0; tt < ntiles && ok; ++tt) {
-                const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
+                const int t = tile_at(tt, t0, ntiles);
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * BN);
                 // the norm block first: its MMA opens the tile, so the slot frees early
                 if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
@@ -679,7 +693,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
         constexpr int HALF = BN / 2;
         for (int tt = 0; tt < ntiles; ++tt) {
-            const int t = tt + t0 < ntiles ? tt + t0 : tt + t0 - ntiles;
+            const int t = tile_at(tt, t0, ntiles);
             const int a = tt % kt::NACC;
             long long w0 = 0;
             if (PROF) w0 = clock64();
@@ -1058,11 +1072,151 @@ __global__ void k_rowmap_pivots(const uint32_t* __restrict__ members,
     }
 }
 
-// Counting sort of each shard's rows by cell (the nearest pivot): perm[off_s + pos]
-// = local index.  The order inside a cell does not affect any result.
+// 16 bytes of a row as floats (V elements of type DT).
+template <int DT>
+struct Chunk16 {
+    static constexpr int V = DT == ANN_F32 ? 4 : (DT == ANN_U8 ? 16 : 8);
+    __device__ static void unpack(const uint4& w, float (&f)[V]) {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (DT == ANN_F32) {
+                f[i] = __uint_as_float(u[i]);
+            } else if (DT == ANN_F16) {
+                const float2 t = __half22float2(*(const __half2*)&u[i]);
+                f[2 * i] = t.x;
+                f[2 * i + 1] = t.y;
+            } else if (DT == ANN_BF16) {
+                const float2 t = __bfloat1622float2(*(const __nv_bfloat162*)&u[i]);
+                f[2 * i] = t.x;
+                f[2 * i + 1] = t.y;
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) f[4 * i + b] = (float)((u[i] >> (8 * b)) & 0xFFu);
+            }
+        }
+    }
+};
+
+// Order the pivots of each shard along a greedy chain (start at pivot 0, always
+// step to the nearest pivot not yet taken; FP32 distances from the vectors), so
+// that cells adjacent in the row order are near in space.  crank[ppad_off[s] + q]
+// = chain position of pivot q.  One block per shard: the current pivot's row is
+// staged in shared memory, every thread scores its pivots with 16-byte loads
+// (VEC) or element loads, and warp shuffles plus one shared-memory pass pick the
+// nearest.  Only the sweep order depends on it, never a result.
+template <int DT, bool VEC>
+__global__ void __launch_bounds__(256)
+    k_pivot_chain(const void* X, int d, const int64_t* __restrict__ psrc,
+                  const int64_t* __restrict__ ppad_off, const int32_t* __restrict__ npiv,
+                  uint32_t* __restrict__ crank) {
+    extern __shared__ float cur_row[];  // d floats
+    __shared__ uint8_t taken[1024];
+    __shared__ float wbd[8];
+    __shared__ int wbq[8];
+    __shared__ int cur;
+    constexpr int V = Chunk16<DT>::V;
+    const int s = blockIdx.x;
+    const int P = npiv[s];
+    const int64_t base = ppad_off[s];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) taken[q] = 0;
+    if (threadIdx.x == 0) {
+        cur = 0;
+        taken[0] = 1;
+        crank[base] = 0;
+    }
+    __syncthreads();
+    for (int step = 1; step < P; ++step) {
+        const int64_t rc = psrc[base + cur];
+        for (int t = threadIdx.x; t < d; t += blockDim.x)
+            cur_row[t] = rc >= 0 ? load_elem(X, DT, rc * d + t) : 0.0f;
+        __syncthreads();
+        float best = INFINITY;
+        int bi = P;
+        for (int q = threadIdx.x; q < P; q += blockDim.x) {
+            if (taken[q]) continue;
+            const int64_t rq = psrc[base + q];
+            float acc = 0.0f;
+            if (rq >= 0) {
+                if (VEC) {
+                    const uint4* row = (const uint4*)X + rq * (d / V);
+                    for (int c = 0; c < d / V; ++c) {
+                        float f[V];
+                        Chunk16<DT>::unpack(__ldg(row + c), f);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const float df = f[e] - cur_row[c * V + e];
+                            acc = fmaf(df, df, acc);
+                        }
+                    }
+                } else {
+                    for (int t = 0; t < d; ++t) {
+                        const float df = load_elem(X, DT, rq * d + t) - cur_row[t];
+                        acc = fmaf(df, df, acc);
+                    }
+                }
+            }
+            if (acc < best || (acc == best && q < bi)) {
+                best = acc;
+                bi = q;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float a = __shfl_xor_sync(0xffffffffu, best, o);
+            const int aq = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (a < best || (a == best && aq < bi)) {
+                best = a;
+                bi = aq;
+            }
+        }
+        if (lane == 0) {
+            wbd[wid] = best;
+            wbq[wid] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float b0 = wbd[0];
+            int nx = wbq[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (wbd[w] < b0 || (wbd[w] == b0 && wbq[w] < nx)) {
+                    b0 = wbd[w];
+                    nx = wbq[w];
+                }
+            if (nx >= P) nx = 0;  // unreachable while pivots remain
+            taken[nx] = 1;
+            crank[base + nx] = (uint32_t)step;
+            cur = nx;
+        }
+        __syncthreads();
+    }
+}
+
+static int launch_pivot_chain(const void* X, int dtype, int d, const KnnWs& w, int C,
+                              cudaStream_t st) {
+    const bool vec = ((size_t)d * dtype_bytes(dtype)) % 16 == 0 && (uintptr_t)X % 16 == 0;
+    const size_t sm = (size_t)d * sizeof(float);
+#define ANN_CHAIN(DT)                                                                          \
+    (vec ? k_pivot_chain<DT, true><<<C, 256, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank)  \
+         : k_pivot_chain<DT, false><<<C, 256, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank))
+    switch (dtype) {
+    case ANN_F32: ANN_CHAIN(ANN_F32); break;
+    case ANN_F16: ANN_CHAIN(ANN_F16); break;
+    case ANN_BF16: ANN_CHAIN(ANN_BF16); break;
+    default: ANN_CHAIN(ANN_U8); break;
+    }
+#undef ANN_CHAIN
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+// Counting sort of each shard's rows by cell (the nearest pivot), cells taken in
+// chain order (crank): perm[off_s + pos] = local index.  The order inside a cell
+// does not affect any result.
 __global__ void k_cell_sort(const uint32_t* __restrict__ cellid,
                             const int64_t* __restrict__ offsets, const int32_t* __restrict__ npiv,
-                            uint32_t* __restrict__ perm) {
+                            const uint32_t* __restrict__ crank,
+                            const int64_t* __restrict__ ppad_off, uint32_t* __restrict__ perm) {
     __shared__ int32_t cnt[1024];
     __shared__ int32_t base[1024];
     const int s = blockIdx.x;
@@ -1070,8 +1224,10 @@ __global__ void k_cell_sort(const uint32_t* __restrict__ cellid,
     const int P = npiv[s];
     for (int c = threadIdx.x; c < P; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
+    const uint32_t* rk = crank + ppad_off[s];
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         uint32_t c = cellid[o + i];
+        c = c < (uint32_t)P ? rk[c] : 0;
         if (c >= (uint32_t)P) c = 0;
         atomicAdd(&cnt[c], 1);
     }
@@ -1086,6 +1242,7 @@ __global__ void k_cell_sort(const uint32_t* __restrict__ cellid,
     __syncthreads();
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         uint32_t c = cellid[o + i];
+        c = c < (uint32_t)P ? rk[c] : 0;
         if (c >= (uint32_t)P) c = 0;
         const int32_t pos = atomicAdd(&base[c], 1);
         perm[o + pos] = (uint32_t)i;
@@ -1202,31 +1359,6 @@ __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
 // multiple of 16): lane l sums the squared differences of 16-byte chunks
 // l, l + 32, ... in order, then a fixed xor tree adds the 32 partial sums.  Two
 // candidates are scored per pass so that their loads overlap.
-template <int DT>
-struct Chunk16 {
-    static constexpr int V = DT == ANN_F32 ? 4 : (DT == ANN_U8 ? 16 : 8);
-    __device__ static void unpack(const uint4& w, float (&f)[V]) {
-        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (DT == ANN_F32) {
-                f[i] = __uint_as_float(u[i]);
-            } else if (DT == ANN_F16) {
-                const float2 t = __half22float2(*(const __half2*)&u[i]);
-                f[2 * i] = t.x;
-                f[2 * i + 1] = t.y;
-            } else if (DT == ANN_BF16) {
-                const float2 t = __bfloat1622float2(*(const __nv_bfloat162*)&u[i]);
-                f[2 * i] = t.x;
-                f[2 * i + 1] = t.y;
-            } else {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) f[4 * i + b] = (float)((u[i] >> (8 * b)) & 0xFFu);
-            }
-        }
-    }
-};
-
 template <int E, int DT>
 __global__ void k_rerank_vec(const void* X, const void* Xrow, int d,
                              const uint32_t* __restrict__ row_ids, int64_t nrows,
@@ -1470,6 +1602,7 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.cell = cv.take<uint32_t>((size_t)rows);
     w.cell_d = cv.take<float>((size_t)rows);
     w.perm = cv.take<uint32_t>((size_t)rows);
+    w.crank = cv.take<uint32_t>((size_t)w.prows_cap);
     w.amax = cv.take<float>(4);
     if (out) *out = w;
     return cv.used + 256;
@@ -1664,7 +1797,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                       rows / kt::BM + C + 1, st, false);
     if (rc) return rc;
     // 2. cell order
-    k_cell_sort<<<C, 512, 0, st>>>(w.cell, offsets, w.npiv, w.perm);
+    if ((rc = launch_pivot_chain(X, dtype, d, w, C, st))) return rc;
+    k_cell_sort<<<C, 512, 0, st>>>(w.cell, offsets, w.npiv, w.crank, w.ppad_off, w.perm);
     ANN_CHECK_LAUNCH();
     k_rowmap_cells<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, w.perm,
                                                                C, w.rows_cap, w.src, w.gid,

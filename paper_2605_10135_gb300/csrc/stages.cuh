@@ -90,6 +90,7 @@ struct KnnWs {
     uint32_t* cell;     // [rows] nearest pivot of each member row
     float* cell_d;
     uint32_t* perm;     // [rows] local index of the row at each cell-ordered position
+    uint32_t* crank;    // [prows_cap] chain position of each pivot (cell order)
     float* amax;        // E4M3 plans: largest |x| (float bits)
 };
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
