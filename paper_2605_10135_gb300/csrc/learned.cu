@@ -129,12 +129,127 @@ struct EpReluMask {  // C = acc where U > 0, else 0 (back through the ReLU)
     }
 };
 
+// Split-K: slice z of the K range [z * ks, (z + 1) * ks) into part[z][M x N].
+struct EpPart {
+    float* part;
+    int64_t M;
+    int N;
+    __device__ void operator()(int64_t i, int j, float acc) const { part[i * N + j] = acc; }
+};
+
+__global__ void __launch_bounds__(256)
+    k_sgemm_split(int64_t M, int N, int K, int kslice, Mat A, Mat B, float* part) {
+    // shift the K window of this slice into the operands' row / column offsets
+    const int z = blockIdx.z;
+    const int k0 = z * kslice;
+    const int kn = K - k0 < kslice ? K - k0 : kslice;
+    Mat a = A, b = B;
+    // A is logical M x K: K is its column (trans 0) or stored row (trans 1)
+    if (a.trans) {
+        if (a.gather) a.gather += k0; else a.row0 += k0;
+    } else {
+        a.p = (const char*)a.p + (int64_t)k0 * (a.dtype == ANN_F32 ? 4 : (a.dtype == ANN_U8 ? 1 : 2));
+    }
+    // B is logical K x N: K is its stored row (trans 0) or column (trans 1)
+    if (!b.trans) {
+        if (b.gather) b.gather += k0; else b.row0 += k0;
+    } else {
+        b.p = (const char*)b.p + (int64_t)k0 * (b.dtype == ANN_F32 ? 4 : (b.dtype == ANN_U8 ? 1 : 2));
+    }
+    EpPart ep{part + (int64_t)z * M * N, M, N};
+    // same tile loop as k_sgemm on the slice
+    __shared__ float As[16][68];
+    __shared__ float Bs[16][68];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * 64;
+    const int n0 = blockIdx.y * 64;
+    const float sa = a.sp ? *a.sp : 1.0f, sb = b.sp ? *b.sp : 1.0f;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int kk0 = 0; kk0 < kn; kk0 += 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + q * 256;
+            const int r = a.trans ? (e & 63) : (e >> 4);
+            const int c = a.trans ? (e >> 6) : (e & 15);
+            const int64_t gi = m0 + r;
+            const int gk = kk0 + c;
+            As[c][r] = (gi < M && gk < kn) ? mat_at(a, gi, gk, sa) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + q * 256;
+            const int r = b.trans ? (e & 15) : (e >> 6);
+            const int c = b.trans ? (e >> 4) : (e & 63);
+            const int gk = kk0 + r, gj = n0 + c;
+            Bs[r][c] = (gk < kn && gj < N) ? mat_at(b, gk, gj, sb) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gi = m0 + ty * 4 + i;
+            const int gj = n0 + tx * 4 + j;
+            if (gi < M && gj < N) ep(gi, gj, acc[i][j]);
+        }
+}
+
+// Sum of the slices in slice order, then the real epilogue.
+template <class EP>
+__global__ void k_split_reduce(const float* __restrict__ part, int nz, int64_t M, int N, EP ep) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= M * N) return;
+    float s = 0.0f;
+    for (int z = 0; z < nz; ++z) s += part[(int64_t)z * M * N + q];
+    ep(q / N, (int)(q % N), s);
+}
+
+// Grids that would leave most of the 152 SMs idle with long K loops (the weight
+// gradients: M x N small, K = 3 x batch) are split along K into slices whose
+// partial products are summed in slice order; part must hold nz * M * N floats.
+static constexpr int64_t SPLIT_PART_FLOATS = (int64_t)1 << 22;
+
 template <class EP>
 static int gemm(int64_t M, int N, int K, const Mat& A, const Mat& B, const EP& ep,
-                cudaStream_t st) {
+                cudaStream_t st, float* part = nullptr) {
     if (M <= 0 || N <= 0) return ANN_OK;
     const dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
-    k_sgemm<EP><<<grid, 256, 0, st>>>(M, N, K, A, B, ep);
+    const int64_t blocks = (int64_t)grid.x * grid.y;
+    int nz = 1;
+    if (part && blocks < 304 && K >= 256) {
+        nz = (int)((304 + blocks - 1) / blocks);
+        if (nz > K / 64) nz = K / 64;
+        while (nz > 1 && (int64_t)nz * M * N > SPLIT_PART_FLOATS) --nz;
+    }
+    if (nz <= 1) {
+        k_sgemm<EP><<<grid, 256, 0, st>>>(M, N, K, A, B, ep);
+        ANN_CHECK_LAUNCH();
+        return ANN_OK;
+    }
+    int kslice = (K + nz - 1) / nz;
+    kslice = (kslice + 15) / 16 * 16;
+    nz = (K + kslice - 1) / kslice;
+    k_sgemm_split<<<dim3(grid.x, grid.y, nz), 256, 0, st>>>(M, N, K, kslice, A, B, part);
+    ANN_CHECK_LAUNCH();
+    k_split_reduce<EP><<<(unsigned)((M * N + 255) / 256), 256, 0, st>>>(part, nz, M, N, ep);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }
@@ -328,16 +443,16 @@ size_t learned_embed_ws(int64_t N, int d) {
 
 static int embed_rows(const void* X, int dtype, int d, const uint32_t* rows, int64_t row0,
                       int64_t n, const float* params, const float* inv_s, float* U, float* H,
-                      float* Z, cudaStream_t st) {
+                      float* Z, cudaStream_t st, float* part = nullptr) {
     const float* W1 = params;
     const float* b1 = W1 + (int64_t)ml::HID * d;
     const float* W2 = b1 + ml::HID;
     const float* b2 = W2 + (int64_t)ml::OUT * ml::HID;
     int rc = gemm(n, ml::HID, d, mat(X, dtype, d, 0, rows, row0, inv_s),
-                  mat(W1, ANN_F32, d, 1), EpHidden{U, H, b1, ml::HID}, st);
+                  mat(W1, ANN_F32, d, 1), EpHidden{U, H, b1, ml::HID}, st, part);
     if (rc) return rc;
     return gemm(n, ml::OUT, ml::HID, mat(H, ANN_F32, ml::HID), mat(W2, ANN_F32, ml::HID, 1),
-                EpBias{Z, b2, ml::OUT}, st);
+                EpBias{Z, b2, ml::OUT}, st, part);
 }
 
 int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
@@ -381,6 +496,7 @@ struct LearnTrainWs {
     float* ed;
     unsigned long long* hits;
     int* step;           // device step counter (read by the captured step)
+    float* part;         // split-K partial products
     void* ews;           // embedding workspace
     size_t ews_bytes;
 };
@@ -425,6 +541,7 @@ size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batc
     w.ed = cv.take<float>((size_t)S * EST_K);
     w.hits = cv.take<unsigned long long>(1);
     w.step = cv.take<int>(4);
+    w.part = cv.take<float>((size_t)SPLIT_PART_FLOATS);
     w.ews_bytes = learned_embed_ws(N, d);
     w.ews = cv.take<uint8_t>(w.ews_bytes);
     if (out) *out = w;
@@ -478,7 +595,7 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
         k_triplets<<<(batch + 255) / 256, 256, 0, q>>>(sample, S, w.knn, kk, kpos, draws,
                                                        w.step, batch, N, w.idx, status);
         ANN_CHECK_LAUNCH();
-        if ((r = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, q)))
+        if ((r = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, q, w.part)))
             return r;
         k_triplet_loss<<<(batch + 127) / 128, 128, 0, q>>>(w.Z, batch, margin, w.dZ, w.li);
         ANN_CHECK_LAUNCH();
@@ -488,7 +605,7 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
         }
         // dW2 = dZ^T H, db2 = column sums of dZ
         if ((r = gemm(ml::OUT, ml::HID, (int)R, mat(w.dZ, ANN_F32, ml::OUT, 1),
-                      mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, q)))
+                      mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, q, w.part)))
             return r;
         k_colsum<<<1, 32, 0, q>>>(w.dZ, R, ml::OUT, gb2);
         ANN_CHECK_LAUNCH();
@@ -498,7 +615,7 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
             return r;
         // dW1 = dU^T (X / s), db1 = column sums of dU
         if ((r = gemm(ml::HID, d, (int)R, mat(w.dU, ANN_F32, ml::HID, 1),
-                      mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, q)))
+                      mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, q, w.part)))
             return r;
         k_colsum<<<1, 256, 0, q>>>(w.dU, R, ml::HID, gb1);
         ANN_CHECK_LAUNCH();
