@@ -109,9 +109,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_sample(w, X, budget_rows=48):
+def oracle_sample(w, X, budget_rows=1500):
     """Time the plain oracle on a bounded sample of the workload and extrapolate
-    to the whole build; returns (vectors/s, threads, description)."""
+    to the whole build; returns (vectors/s, threads, description, seconds)."""
     import oracle
 
     sample, init_rows = w.kmeans_inputs()
@@ -119,20 +119,14 @@ def oracle_sample(w, X, budget_rows=48):
     t0 = time.perf_counter()
     cent, _ = oracle.kmeans(X, init, sample, 10)
     t_kmeans = time.perf_counter() - t0
-    n_asg = 20000
     t0 = time.perf_counter()
-    a = oracle.assign(X[:n_asg], cent, w.r)
-    t_assign = (time.perf_counter() - t0) * (w.N / n_asg)
-    # shard 0 of a partition of the first 200k vectors, scaled to the full shard size
-    sub = X[:200_000]
-    members, offsets = oracle.shards(oracle.assign(sub, cent, w.r), w.C)
-    n0 = int(offsets[1] - offsets[0])
-    rows = np.linspace(0, max(n0 - 1, 0), budget_rows).astype(np.int64)
+    members, offsets = oracle.shards(oracle.assign(X, cent, w.r), w.C)
+    t_assign = time.perf_counter() - t0
+    rows_total = int(offsets[-1])
+    rows = np.linspace(0, max(rows_total - 1, 0), budget_rows).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.shard_knn(sub, members, offsets, w.k, rows=rows)
-    t_rows = time.perf_counter() - t0
-    full_shard = w.r * w.N / w.C
-    t_knn = t_rows / budget_rows * (full_shard / max(n0, 1)) * (w.r * w.N)
+    oracle.shard_knn(X, members, offsets, w.k, rows=rows)
+    t_knn = (time.perf_counter() - t0) / budget_rows * rows_total
     # prune + merge: per-row cost on a small graph of the same degrees
     Xs = X[:6000]
     ms_, os_ = oracle.shards(oracle.assign(Xs, cent, w.r), w.C)
@@ -142,10 +136,10 @@ def oracle_sample(w, X, budget_rows=48):
     oracle.merge(pid, pd, ms_, os_, Xs.shape[0])
     t_pm = (time.perf_counter() - t0) * (w.N / Xs.shape[0])
     total = t_kmeans + t_assign + t_knn + t_pm
-    desc = (f"oracle: k-means 10 iters on the full sample, assignment of {n_asg} vectors, "
-            f"exact kNN of {budget_rows} rows of one shard of a 200k-vector partition, "
-            f"prune+merge of a 6000-vector graph; each extrapolated to N={w.N} "
-            f"(kNN by rows x shard size)")
+    desc = (f"oracle: k-means (10 iterations) and the replicated assignment of all "
+            f"{w.N} vectors run in full; the exact kNN of {budget_rows} shard rows spread "
+            f"evenly over all {rows_total} rows, scaled by rows; prune+merge of a "
+            f"6000-vector graph, scaled by N")
     return w.N / total, oracle.num_threads(), desc, total
 
 
@@ -493,10 +487,10 @@ def run_reference(args, w, world, rank):
         return
     X = w.vectors()
     for _ in range(max(args.warmup, 3) and 1):
-        oracle_sample(w, X, budget_rows=8)
+        oracle_sample(w, X, budget_rows=64)
     vals, tms = [], []
     for _ in range(args.steps):
-        v, cores, desc, total = oracle_sample(w, X, budget_rows=16)
+        v, cores, desc, total = oracle_sample(w, X, budget_rows=800)
         vals.append(v)
         tms.append(total * 1e3)
     v = float(np.mean(vals))
