@@ -183,7 +183,8 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
  *                    k + 16 (ANN_EXACT) or 128 (the screening forms); else
  *                    k <= rerank_k <= 128.  Ignored for uint8 under ANN_EXACT.
  *  model             ANN_LEARNED: the device parameter array of the MLP (see
- *                    ann_learned_train); otherwise NULL.
+ *                    ann_learned_train); NULL makes ANN_LEARNED the exact form
+ *                    (ANN_EXACT).  Other precisions: NULL.
  * Limits: d <= 4096 (uint8: d <= 258, which keeps the integer tiles exact),
  * 1 <= k <= 96, 1 <= C <= 1024, every shard smaller than 2^24 members.  When
  * the 128 rows of a block do not fit shared memory (large d) their K blocks

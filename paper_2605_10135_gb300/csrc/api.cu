@@ -306,9 +306,15 @@ int ann_shard_knn_workspace(int64_t N, int d, int dtype, int C, int64_t rows, in
     int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
     if (rc) return rc;
     KnnPlan pl;
-    if (precision == ANN_LEARNED) {
+    if (precision == ANN_LEARNED) {  // enough for the exact form too (no model given)
         if ((rc = learned_plan(k, rerank_k, &pl))) return rc;
-        *bytes = learned_knn_bytes(N, d, C, rows, pl);
+        size_t b = learned_knn_bytes(N, d, C, rows, pl);
+        KnnPlan pe;
+        if (knn_plan(d, dtype, k, ANN_EXACT, rerank_k, &pe) == ANN_OK) {
+            const size_t be = knn_ws(C, rows, pe, nullptr, nullptr, 0);
+            if (be > b) b = be;
+        }
+        *bytes = b;
         return ANN_OK;
     }
     if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
@@ -325,8 +331,11 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     ANN_REQUIRE(offsets, "offsets is NULL");
     ANN_REQUIRE(rows == 0 || (X && members && knn_id && knn_d), "NULL pointer");
     KnnPlan pl;
+    if (precision == ANN_LEARNED && !model) {  // no model: the exact form
+        precision = ANN_EXACT;
+        if ((rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k))) return rc;
+    }
     if (precision == ANN_LEARNED) {
-        ANN_REQUIRE(model, "the learned form needs model (its parameters)");
         if ((rc = learned_plan(k, rerank_k, &pl))) return rc;
         if ((rc = check_ws(ws, ws_bytes, learned_knn_bytes(N, d, C, rows, pl)))) return rc;
         if (rows == 0) return ANN_OK;

@@ -142,3 +142,11 @@ def test_trained_model_lists_are_exactly_scored_and_close_to_the_oracle():
     r_gpu = oracle.recall_at(gid[rows], eid, 10)
     r_or = oracle.recall_at(oid[rows], eid, 10)
     assert abs(r_gpu - r_or) <= 0.02 and r_gpu > 0.7
+
+
+def test_learned_without_model_is_the_exact_form():
+    X = datagen.clustered_u8(3000, 64, 16, seed=111)
+    mem, off = _shards(X, 3, 2, seed=112)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 12, precision=ann.LEARNED)
+    eid, ed = ann.shard_knn(T(X), T(mem), T(off), 12)
+    assert torch.equal(gid, eid) and torch.equal(gd, ed)
