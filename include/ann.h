@@ -304,7 +304,9 @@ int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const 
  *   Ids in sample[] at or above N are replaced by 0 and set status bit 2.
  *   Limits: d <= 4096, 2 <= kk <= 95,
  *   1 <= kpos < kk, N >= kk + 2, 1 <= S <= N, batch <= 65536.
- * ann_learned_embed: E [N x 32] float32 = f(X) for all rows (FP32 GEMMs).
+ * ann_learned_embed: E [N x 32] float32 = f(X) for all rows.  Layer 1 runs on
+ *   the tensor cores with FP16 operands (x / s and W1 rounded to FP16, FP32
+ *   accumulation), layer 2 in FP32; training uses FP32 throughout.
  *   Limits: d <= 4096.
  * ann_shard_knn with precision ANN_LEARNED: model = the parameters; the
  *   screened list has rerank_k (0 = 128) entries; any d <= 4096.

@@ -1445,8 +1445,8 @@ static PFN_encodeTiled get_encode() {
 
 // 2-D tensor map over a [rows x inner] matrix of 16-bit (esize 2) or 8-bit (esize 1)
 // elements with box {box_inner, box_rows}.
-static int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int box_inner,
-                     int box_rows, CUtensorMapSwizzle swz, int esize = 2) {
+int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int box_inner, int box_rows,
+              CUtensorMapSwizzle swz, int esize) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return fail(ANN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};

@@ -429,15 +429,190 @@ __global__ void k_hits_to_recall(const unsigned long long* hits, int64_t denom, 
     *out = denom > 0 ? (float)((double)*hits / (double)denom) : 0.0f;
 }
 
-// ---- embedding ---------------------------------------------------------------
+// ---- embedding of all rows on the tensor cores ------------------------------------
+// Layer 1 (x/s . W1^T, K = d) runs as tcgen05.mma (M=128, N=256, K=16) on FP16
+// operands: the scaled inputs lie in [-1, 1] and the weights are small, so FP16
+// keeps 11 significant bits where BF16 would keep 8.  One CTA per 128 rows: warp 0
+// feeds a 3-stage TMA ring (the rows' 64-element K block and W1's), warp 1 issues
+// the MMAs into 256 TMEM columns, then all four warps read their 32 rows back,
+// add b1, apply ReLU and do layer 2 (256 -> 32) in FP32 from shared memory.
+namespace emb {
+constexpr int BM = 128;
+constexpr int KB = 64;
+constexpr int NST = 3;
+constexpr int A_BYTES = BM * 128;
+constexpr int B_BYTES = ml::HID * 128;
+constexpr int STAGE = A_BYTES + B_BYTES;
+constexpr int THREADS = 128;
+constexpr int W2T_FLOATS = ml::HID * ml::OUT;
+constexpr size_t SMEM = 1024 + (size_t)NST * STAGE + (size_t)(W2T_FLOATS + ml::HID + ml::OUT) * 4 +
+                        (2 * NST + 1) * 8 + 16;
+}  // namespace emb
+
+__global__ void __launch_bounds__(emb::THREADS, 1)
+    k_embed_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+               int64_t n, int nkb, uint32_t idesc, const float* __restrict__ b1,
+               const float* __restrict__ W2, const float* __restrict__ b2, float* __restrict__ E,
+               int* status) {
+    using namespace emb;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring = smem_u32(base);
+    float* w2t = (float*)(base + NST * STAGE);  // [h][o]
+    float* sb1 = w2t + W2T_FLOATS;
+    float* sb2 = sb1 + ml::HID;
+    uint8_t* tail = (uint8_t*)(sb2 + ml::OUT);
+    const uint32_t bars = smem_u32(tail);
+    const uint32_t full = bars, empty = bars + NST * 8, done = bars + 2 * NST * 8;
+    volatile uint32_t* tslot = (volatile uint32_t*)(tail + (2 * NST + 1) * 8);
+    volatile int* abort_flag = (volatile int*)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(full + 8 * s, 1);
+            mbar_init(empty + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32((const void*)tslot), ml::HID);
+        tmem_relinquish();
+    }
+    for (int i = threadIdx.x; i < W2T_FLOATS; i += THREADS)
+        w2t[i] = W2[(i % ml::OUT) * ml::HID + i / ml::OUT];
+    for (int i = threadIdx.x; i < ml::HID; i += THREADS) sb1[i] = b1[i];
+    if (threadIdx.x < ml::OUT) sb2[threadIdx.x] = b2[threadIdx.x];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // producer
+        tma_prefetch_desc(&tmX);
+        tma_prefetch_desc(&tmW);
+        uint32_t used = 0, last_par = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % NST;
+            const uint32_t ph = (uint32_t)(kb / NST) & 1u;
+            if (!mbar_wait(empty + 8 * s, ph ^ 1u, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(full + 8 * s, STAGE);
+            tma_load_2d(ring + s * STAGE, &tmX, full + 8 * s, kb * KB, (int)row0);
+            tma_load_2d(ring + s * STAGE + A_BYTES, &tmW, full + 8 * s, kb * KB, 0);
+            used |= 1u << s;
+            last_par = (last_par & ~(1u << s)) | (ph << s);
+        }
+        int dummy = 0;  // every issued copy lands before the CTA may exit
+        for (int s = 0; s < NST; ++s)
+            if (used >> s & 1) mbar_wait(full + 8 * s, (last_par >> s) & 1u, &dummy, 200000000ull);
+        if (!ok) atomicOr(status, DEV_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issue
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % NST;
+            const uint32_t ph = (uint32_t)(kb / NST) & 1u;
+            if (!mbar_wait(full + 8 * s, ph, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a = ring + s * STAGE, b = a + A_BYTES;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                umma_f16(tmem, sdesc_sw128(a + q * 32), sdesc_sw128(b + q * 32), idesc,
+                         (kb | q) != 0 ? 1u : 0u);
+            umma_commit(empty + 8 * s);
+        }
+        umma_commit(done);  // also after a timeout: every issued MMA completes first
+        if (!ok) atomicOr(status, DEV_TIMEOUT);
+    }
+    __syncwarp();
+    // epilogue: thread = row (TMEM lane)
+    const bool got = mbar_wait(done, 0, abort_flag);
+    tc_fence_after();
+    if (got && !*abort_flag) {
+        float z[ml::OUT];
+#pragma unroll
+        for (int o = 0; o < ml::OUT; ++o) z[o] = sb2[o];
+        const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+        for (int c = 0; c < ml::HID / 32; ++c) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lane_addr + c * 32, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int h = c * 32 + j;
+                float hv = __uint_as_float(v[j]) + sb1[h];
+                hv = hv > 0.0f ? hv : 0.0f;
+                const float4* w = (const float4*)(w2t + h * ml::OUT);
+#pragma unroll
+                for (int q = 0; q < ml::OUT / 4; ++q) {
+                    const float4 ww = w[q];
+                    z[4 * q] = fmaf(hv, ww.x, z[4 * q]);
+                    z[4 * q + 1] = fmaf(hv, ww.y, z[4 * q + 1]);
+                    z[4 * q + 2] = fmaf(hv, ww.z, z[4 * q + 2]);
+                    z[4 * q + 3] = fmaf(hv, ww.w, z[4 * q + 3]);
+                }
+            }
+        }
+        const int64_t row = row0 + warp * 32 + lane;
+        if (row < n) {
+            float4* out = (float4*)(E + row * ml::OUT);
+#pragma unroll
+            for (int q = 0; q < ml::OUT / 4; ++q)
+                out[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(status, DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, ml::HID);
+    }
+}
+
+// FP16 operands: out[i][t] = half(in(row r0 + i, t) * scale) for i < n and t < d,
+// 0 elsewhere (rows up to n_pad, columns up to Kp).
+__global__ void k_to_half_rows(const void* X, int dtype, int d, int64_t r0, int64_t n,
+                               int64_t n_pad, int Kp, const float* __restrict__ inv_s,
+                               __half* __restrict__ out) {
+    const float sc = inv_s ? *inv_s : 1.0f;
+    const int64_t total = n_pad * Kp;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / Kp;
+        const int t = (int)(q - i * Kp);
+        out[q] = __float2half_rn(i < n && t < d ? load_elem(X, dtype, (r0 + i) * d + t) * sc
+                                                : 0.0f);
+    }
+}
+
 static constexpr int64_t EMB_CHUNK = 65536;
 
+static int64_t emb_chunk(int d) {
+    const int64_t Kp = (d + emb::KB - 1) / emb::KB * emb::KB;
+    int64_t ch = ((int64_t)256 << 20) / (Kp * 2);  // at most 256 MB of FP16 rows
+    if (ch > EMB_CHUNK) ch = EMB_CHUNK;
+    return ch / emb::BM * emb::BM > 0 ? ch / emb::BM * emb::BM : emb::BM;
+}
+
+// Rows of one embedding launch, rounded up to whole 128-row blocks.
+static int64_t emb_rows_buf(int64_t N, int d) {
+    const int64_t ch = N < emb_chunk(d) ? N : emb_chunk(d);
+    return (ch + emb::BM - 1) / emb::BM * emb::BM > 0 ? (ch + emb::BM - 1) / emb::BM * emb::BM
+                                                      : emb::BM;
+}
+
 size_t learned_embed_ws(int64_t N, int d) {
-    (void)d;
+    const int64_t Kp = (d + emb::KB - 1) / emb::KB * emb::KB;
     Carver cv(nullptr, ~(size_t)0);
     cv.take<unsigned int>(4);
     cv.take<float>(4);
-    cv.take<float>((size_t)(N < EMB_CHUNK ? N : EMB_CHUNK) * ml::HID + 1);
+    cv.take<__half>((size_t)emb_rows_buf(N, d) * Kp);
+    cv.take<__half>((size_t)ml::HID * Kp);
     return cv.used + 256;
 }
 
@@ -457,21 +632,46 @@ static int embed_rows(const void* X, int dtype, int d, const uint32_t* rows, int
 
 int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
                       void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int Kp = (d + emb::KB - 1) / emb::KB * emb::KB;
+    const int64_t chunk = emb_chunk(d);
     Carver cv(ws, ws_bytes);
     unsigned int* amax = cv.take<unsigned int>(4);
     float* inv_s = cv.take<float>(4);
-    float* H = cv.take<float>((size_t)(N < EMB_CHUNK ? N : EMB_CHUNK) * ml::HID + 1);
+    __half* XB = cv.take<__half>((size_t)emb_rows_buf(N, d) * Kp);
+    __half* WB = cv.take<__half>((size_t)ml::HID * Kp);
     if (!cv.ok) return fail(ANN_ERR_WORKSPACE, "learned embed: workspace too small");
     if (N == 0) return ANN_OK;
     int rc = launch_absmax(X, dtype, N * d, nullptr, 0, amax, st);
     if (rc) return rc;
     k_inv_scale<<<1, 32, 0, st>>>(amax, inv_s);
     ANN_CHECK_LAUNCH();
-    for (int64_t r0 = 0; r0 < N; r0 += EMB_CHUNK) {
-        const int64_t n = N - r0 < EMB_CHUNK ? N - r0 : EMB_CHUNK;
-        if ((rc = embed_rows(X, dtype, d, nullptr, r0, n, params, inv_s, nullptr, H,
-                             E + r0 * ml::OUT, st)))
+    const float* W1 = params;
+    const float* b1 = W1 + (int64_t)ml::HID * d;
+    const float* W2 = b1 + ml::HID;
+    const float* b2 = W2 + (int64_t)ml::OUT * ml::HID;
+    k_to_half_rows<<<(unsigned)(((int64_t)ml::HID * Kp + 255) / 256), 256, 0, st>>>(
+        W1, ANN_F32, d, 0, ml::HID, ml::HID, Kp, nullptr, WB);
+    ANN_CHECK_LAUNCH();
+    CUtensorMap tw;
+    if ((rc = make_tmap(&tw, WB, ml::HID, Kp, emb::KB, ml::HID, CU_TENSOR_MAP_SWIZZLE_128B)))
+        return rc;
+    ANN_CHECK_CUDA(cudaFuncSetAttribute(k_embed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)emb::SMEM));
+    const uint32_t idesc = idesc_f16(emb::BM, ml::HID, 0);  // FP16 x FP16 -> FP32
+    int* status = device_status_ptr();
+    for (int64_t r0 = 0; r0 < N; r0 += chunk) {
+        const int64_t n = N - r0 < chunk ? N - r0 : chunk;
+        const int64_t n_pad = (n + emb::BM - 1) / emb::BM * emb::BM;  // <= emb_rows_buf
+        const int64_t tot = n_pad * Kp;
+        const unsigned g = (unsigned)((tot + 255) / 256 < 152 * 64 ? (tot + 255) / 256 : 152 * 64);
+        k_to_half_rows<<<g, 256, 0, st>>>(X, dtype, d, r0, n, n_pad, Kp, inv_s, XB);
+        ANN_CHECK_LAUNCH();
+        CUtensorMap tx;
+        if ((rc = make_tmap(&tx, XB, n_pad, Kp, emb::KB, emb::BM, CU_TENSOR_MAP_SWIZZLE_128B)))
             return rc;
+        k_embed_tc<<<(unsigned)((n + emb::BM - 1) / emb::BM), emb::THREADS, emb::SMEM, st>>>(
+            tx, tw, n, Kp / emb::KB, idesc, b1, W2, b2, E + r0 * ml::OUT, status);
+        ANN_CHECK_LAUNCH();
     }
     return ANN_OK;
 }

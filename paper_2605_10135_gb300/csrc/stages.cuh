@@ -158,6 +158,11 @@ int run_screen(const void* Xa, int dta, const uint32_t* rowsel, int64_t p0, int6
                const void* Xb, int dtb, int64_t nb, int d, int ks, uint32_t* out_id, void* ws,
                size_t ws_bytes, cudaStream_t st);
 
+// 2-D tensor map over a [rows x inner] matrix of 16-bit (esize 2) or 8-bit
+// (esize 1) elements, box {box_inner, box_rows}.
+int make_tmap(CUtensorMap* m, const void* G, int64_t rows, int inner, int box_inner, int box_rows,
+              CUtensorMapSwizzle swz, int esize = 2);
+
 // max |x| over X [n elements] and, if given, Q [nq_elems] into *amax (float bits;
 // the word is zeroed first).
 int launch_absmax(const void* X, int dtype, int64_t n, const void* Q, int64_t nq_elems,

@@ -35,17 +35,34 @@ def _lib():
     assert ann.device_status() == 0
 
 
-@pytest.mark.parametrize("kind", ["f32", "u8"])
-def test_embedding_matches_oracle(kind):
+def _fp16_operands(X, p):
+    """What the tensor-core layer 1 multiplies: FP16(x * (1 / max|x|)) and FP16(W1)."""
+    d = X.shape[1]
+    inv = np.float32(1.0) / np.float32(np.abs(X.astype(np.float32)).max())
+    xs = (X.astype(np.float32) * inv).astype(np.float16).astype(np.float64)
+    q = np.asarray(p, dtype=np.float64).copy()
+    q[:OL.HIDDEN * d] = np.asarray(p[:OL.HIDDEN * d], dtype=np.float32).astype(np.float16)
+    return xs, q
+
+
+@pytest.mark.parametrize("kind,d", [("f32", 96), ("u8", 64), ("f16", 1000)])
+def test_embedding_matches_oracle(kind, d):
+    """Layer 1 on the tensor cores (FP16 operands, FP32 accumulation), layer 2 in
+    FP32: against the FP64 forward pass of the same FP16-rounded operands."""
     if kind == "f32":
-        X = datagen.anisotropic_mixture(5000, 96, 32, 0.25, True, np.float32, seed=61)
+        X = datagen.anisotropic_mixture(5000, d, 32, 0.25, True, np.float32, seed=61)
+    elif kind == "u8":
+        X = datagen.clustered_u8(70000, d, 64, seed=62)   # more than one 65536-row chunk
     else:
-        X = datagen.clustered_u8(70000, 64, 64, seed=62)   # more than one 65536-row chunk
+        X = datagen.anisotropic_mixture(3000, d, 16, 0.25, False, np.float16, seed=64)
     p = datagen.mlp_init(X.shape[1], seed=63)
     E = ann.learned_embed(T(X), T(p)).cpu().numpy().astype(np.float64)
-    ref = OL.embed(X, p)
+    xs, q = _fp16_operands(X, p)
+    ref = OL.forward(q, xs, X.shape[1])[2]
     # FP32 sums of d + 256 products: error well below 1e-4 of the embedding scale
     assert np.abs(E - ref).max() <= 1e-4 * np.abs(ref).max()
+    # and the FP16 rounding itself moves the embedding by well under 1% of its scale
+    assert np.abs(E - OL.embed(X, p)).max() <= 1e-2 * np.abs(ref).max()
 
 
 def _train_case(steps, batch, seed):
