@@ -114,6 +114,14 @@ int ann_timing_read(double* tile_ms, int* launches);
 int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 
+/* Self-test of the bounded device waits (no fault, no hang): one warp waits on
+ * an mbarrier that nothing completes, through the bounded wait that every
+ * pipelined kernel uses; mode 0 lets the limit (limit_us microseconds, at most
+ * 2 s) run out, mode 1 starts with the abort flag set.  The kernel records the
+ * timeout bit in the device status word and returns, so a following
+ * ann_device_status() returns ANN_ERR_TIMEOUT and the context stays usable. */
+int ann_wait_selftest(int mode, int64_t limit_us, void* stream);
+
 /* Autotuner of the distance-tile plan.  ann_autotune(1): every later
  * ann_shard_knn call (not ANN_LEARNED) whose key (d, dtype, k, precision,
  * rerank_k, floor(log2(rows / C))) has no decision yet runs the whole shard kNN

@@ -76,6 +76,7 @@ def lib():
                                         ct.c_float, ct.c_float, P, P, P, P, SZ, P]),
             "ann_learned_embed_workspace": (I32, [I64, I32, PSZ]),
             "ann_autotune": (I32, [I32]),
+            "ann_wait_selftest": (I32, [I32, I64, P]),
             "ann_autotune_lookup": (I32, [I32, I32, I32, I32, I32, I64, I32, P, P, P, P, P, P]),
             "ann_learned_embed": (I32, [P, I64, I32, I32, P, P, P, SZ, P]),
         }
@@ -151,6 +152,11 @@ def tile_counters_read() -> dict:
     arr = (ct.c_ulonglong * len(TILE_COUNTERS))()
     _check(lib().ann_tile_counters_read(arr, len(TILE_COUNTERS)))
     return dict(zip(TILE_COUNTERS, [int(v) for v in arr]))
+
+
+def wait_selftest(mode: int = 0, limit_us: int = 20000):
+    """Run the bounded-wait self-test (see ann.h); read the outcome with device_status()."""
+    _check(lib().ann_wait_selftest(mode, limit_us, _stream()))
 
 
 def autotune(on: int = 1):

@@ -163,6 +163,37 @@ int ann_device_status(int* out) {
     return ANN_OK;
 }
 
+// ---------------------------------------------------------------- wait self-test
+// One warp waits on an mbarrier that nothing arrives on, through the same bounded
+// wait the pipelined kernels use (globaltimer limit, abort flag).  mode 0: the
+// limit runs out; mode 1: the abort flag is already set.  Either way the wait
+// gives up, the kernel records DEV_TIMEOUT and returns.
+__global__ void k_wait_selftest(int mode, uint64_t limit_ns, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = mode == 1 ? 1 : 0;
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        // phase 0 never completes: no thread arrives and no copy is pending
+        const bool ok = mbar_wait(smem_u32(&bar), 0, (volatile int*)&abort_flag, limit_ns);
+        if (!ok) atomicOr(status, DEV_TIMEOUT);
+    }
+    __syncwarp();
+}
+
+int ann_wait_selftest(int mode, int64_t limit_us, void* stream) {
+    ANN_REQUIRE(mode == 0 || mode == 1, "mode must be 0 or 1");
+    ANN_REQUIRE(limit_us >= 1 && limit_us <= 2000000, "limit_us must be in [1, 2e6]");
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(mode, (uint64_t)limit_us * 1000ull,
+                                                         device_status_ptr());
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
 // ---------------------------------------------------------------- partition
 int ann_partition_workspace(int64_t N, int d, int C, int r, int64_t S, size_t* bytes) {
     ANN_REQUIRE(bytes, "bytes is NULL");

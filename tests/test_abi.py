@@ -82,3 +82,16 @@ def test_null_workspace_is_rejected(L):
     rc = L.ann_merge(ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), 4, 2000,
                      1000, 8, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(16), None, 0, None)
     assert rc == 5 and b"workspace" in L.ann_last_error()
+
+
+def test_host_side_failures_return_status_codes(L):
+    """Argument and workspace failures are caught on the host before any launch."""
+    n = ct.c_size_t(0)
+    assert L.ann_wait_selftest(2, 100, None) == 1
+    assert L.ann_wait_selftest(0, 0, None) == 1
+    dummy = ct.c_void_p(16)  # never dereferenced: the calls fail before using it
+    buf = (ct.c_int64 * 3)(0, 1000, 2000)
+    assert L.ann_shard_knn_workspace(1000, 64, 3, 2, 2000, 16, 0, 0, ct.byref(n)) == 0
+    rc = L.ann_shard_knn(dummy, 1000, 64, 3, dummy, ct.cast(buf, ct.c_void_p), 2, 2000, 16, 0, 0,
+                         None, dummy, dummy, None, 0, None)
+    assert rc == 5 and b"workspace" in L.ann_last_error().lower()

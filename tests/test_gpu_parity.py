@@ -397,3 +397,22 @@ def test_captured_build_replays_match_eager():
     torch.cuda.synchronize()
     assert torch.equal(out2["graph"], eager2["graph"])
     assert cap.kernels > 10
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A wait on an mbarrier that nothing completes gives up at its limit (or at
+    once when the abort flag is set), records the timeout bit and returns."""
+    import time
+    ann.device_status()
+    ann.wait_selftest(0, 20000)
+    assert ann.device_status() & 1
+    t0 = time.time()
+    ann.wait_selftest(1, 2000000)   # abort flag set: no need to wait 2 s
+    assert ann.device_status() & 1
+    assert time.time() - t0 < 1.0
+    X = datagen.clustered_u8(1500, 32, 8, seed=181)
+    mem, off = _oracle_shards(X, 2, 1, seed=182)
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), 8)
+    oid, od = oracle.shard_knn(X, mem, off, 8)
+    assert np.array_equal(as_u32(gid), oid)
+    assert ann.device_status() == 0
