@@ -126,15 +126,16 @@ __global__ void k_topr_cand(const float* __restrict__ dist, const uint32_t* __re
     }
 }
 
-// FP64 sums in sample order.  One warp per (centroid c, 32 consecutive
-// dimensions): every lane keeps its own register accumulator and adds the
-// samples labelled c in sample order, so each (c, t) sum is the plain sequential
-// one; the C x d/32 warps are independent, which hides the FP64 add latency.
-// Labels and rows of 32 consecutive samples come in one coalesced load each; a
-// ballot picks the samples of label c.
-__global__ void k_kmeans_sums(const void* X, int dtype, int d, const uint32_t* __restrict__ sample,
-                              int64_t S, const int32_t* __restrict__ lab, int C,
-                              double* __restrict__ sums) {
+// FP64 centroid sums in sample order (so each (c, t) sum is the plain sequential
+// one).  list[off[c] .. off[c] + cnt[c]) holds the rows of the samples labelled c
+// in sample order; one warp per (c, 32 consecutive dimensions) keeps a register
+// accumulator per lane, visits only its own samples, loads 8 rows ahead, and only
+// the FP64 adds are serial.  The C x d/32 warps are independent.
+__global__ void k_kmeans_sums_lists(const void* X, int dtype, int d,
+                                    const uint32_t* __restrict__ list,
+                                    const int64_t* __restrict__ off,
+                                    const int64_t* __restrict__ cnt, int C,
+                                    double* __restrict__ sums) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int nt = (d + 31) / 32;
@@ -142,20 +143,59 @@ __global__ void k_kmeans_sums(const void* X, int dtype, int d, const uint32_t* _
     const int c = (int)(w / nt);
     const int t = (int)(w % nt) * 32 + lane;
     const bool active = t < d;
+    const uint32_t* lc = list + off[c];
+    const int64_t n = cnt[c];
     double acc = 0.0;
-    for (int64_t s0 = 0; s0 < S; s0 += 32) {
-        const int64_t sl = s0 + lane;
-        const int myc = sl < S ? __ldg(lab + sl) : -1;
-        const uint32_t myr = sl < S ? __ldg(sample + sl) : 0u;
-        uint32_t m = __ballot_sync(0xffffffffu, myc == c);
-        while (m) {
-            const int u = __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t r = __shfl_sync(0xffffffffu, myr, u);
-            if (active) acc = __dadd_rn(acc, (double)load_elem(X, dtype, (int64_t)r * d + t));
-        }
+    for (int64_t i0 = 0; i0 < n; i0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = (active && i0 + u < n) ? load_elem(X, dtype, (int64_t)__ldg(lc + i0 + u) * d + t)
+                                          : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (i0 + u < n) acc = __dadd_rn(acc, (double)v[u]);
     }
     if (active) sums[(int64_t)c * d + t] = acc;
+}
+
+// Exclusive prefix of the label counts (C <= 1024; one thread).
+__global__ void k_label_offsets(const int64_t* __restrict__ cnt, int C, int64_t* __restrict__ off) {
+    if (threadIdx.x || blockIdx.x) return;
+    int64_t a = 0;
+    for (int c = 0; c < C; ++c) {
+        off[c] = a;
+        a += cnt[c];
+    }
+    off[C] = a;
+}
+
+// Rows of the samples labelled c in sample order (one block of 256 per c).
+__global__ void __launch_bounds__(256)
+    k_label_lists(const int32_t* __restrict__ lab, const uint32_t* __restrict__ sample,
+                  int64_t S, const int64_t* __restrict__ off, uint32_t* __restrict__ list) {
+    __shared__ int wcnt[8];
+    __shared__ int64_t run;
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    for (int64_t s0 = 0; s0 < S; s0 += 256) {
+        const int64_t s = s0 + threadIdx.x;
+        const bool f = s < S && lab[s] == c;
+        const uint32_t b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wcnt[wid] = __popc(b);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int q = 0; q < 8; ++q) {
+            if (q < wid) before += wcnt[q];
+            total += wcnt[q];
+        }
+        if (f) list[off[c] + run + before + __popc(b & ((1u << lane) - 1))] = sample[s];
+        __syncthreads();
+        if (threadIdx.x == 0) run += total;
+        __syncthreads();
+    }
 }
 
 __global__ void k_count_labels(const int32_t* __restrict__ lab, int64_t S, int64_t* cnt) {
@@ -304,6 +344,8 @@ size_t partition_ws(int64_t N, int d, int C, int r, int64_t S, PartitionWs* out,
     w.lab = cv.take<int32_t>((size_t)(S > 0 ? S : 1));
     w.sums = cv.take<double>((size_t)C * d);
     w.cnt = cv.take<int64_t>((size_t)C);
+    w.loff = cv.take<int64_t>((size_t)C + 1);
+    w.llist = cv.take<uint32_t>((size_t)(S > 0 ? S : 1));
     w.assign = cv.take<uint32_t>((size_t)N * r);
     w.hist = cv.take<int32_t>((size_t)C * nblk);
     w.tot = cv.take<int64_t>((size_t)C);
@@ -355,13 +397,17 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
             if (rc) return rc;
         }
         ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int64_t) * C, st));
+        k_count_labels<<<nb(S, tpb) < 4096u ? nb(S, tpb) : 4096u, tpb, 0, st>>>(w.lab, S, w.cnt);
+        ANN_CHECK_LAUNCH();
+        k_label_offsets<<<1, 32, 0, st>>>(w.cnt, C, w.loff);
+        ANN_CHECK_LAUNCH();
+        k_label_lists<<<C, 256, 0, st>>>(w.lab, sample_idx, S, w.loff, w.llist);
+        ANN_CHECK_LAUNCH();
         {
             const int64_t warps = (int64_t)C * ((d + 31) / 32);
-            k_kmeans_sums<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(X, dtype, d, sample_idx, S,
-                                                                     w.lab, C, w.sums);
+            k_kmeans_sums_lists<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(
+                X, dtype, d, w.llist, w.loff, w.cnt, C, w.sums);
         }
-        ANN_CHECK_LAUNCH();
-        k_count_labels<<<nb(S, tpb) < 4096u ? nb(S, tpb) : 4096u, tpb, 0, st>>>(w.lab, S, w.cnt);
         ANN_CHECK_LAUNCH();
         k_kmeans_update<<<nb(cd, tpb), tpb, 0, st>>>(w.sums, w.cnt, C, d, w.cent, w.centT);
         ANN_CHECK_LAUNCH();

@@ -20,6 +20,8 @@ struct PartitionWs {
     int32_t* lab;      // [S]
     double* sums;      // [C*d]
     int64_t* cnt;      // [C]
+    int64_t* loff;     // [C+1] offsets of the per-label sample lists
+    uint32_t* llist;   // [S] sample rows grouped by label, sample order inside a label
     uint32_t* assign;  // [N*r]
     int32_t* hist;     // [C*nblk]
     int64_t* tot;      // [C]
