@@ -130,6 +130,10 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
     uint8_t* ovf_pos = tpos + TS;                // [KM]
     const uint32_t lt = (1u << lane) - 1;
     const bool vec = (k & 3) == 0;
+    // the table starts empty once; after each row only the slots its ids used are
+    // emptied again
+    for (int h = lane; h < TS; h += 32) tkey[h] = ANN_PAD;
+    __syncwarp();
 
     for (int64_t p = blockIdx.x * (int64_t)nwb + wib; p < rows; p += (int64_t)gridDim.x * nwb) {
         const int s = shard_of(offsets, C, p);
@@ -149,7 +153,6 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 sel[e] = j < m ? (uint32_t)j : 0xFFFFFFFFu;
             }
         } else {
-            for (int h = lane; h < TS; h += 32) tkey[h] = ANN_PAD;
             for (int j = lane; j < KM; j += 32) cnt[j] = 0;
             if (lane == 0) *novf_p = 0;
             __syncwarp();
@@ -168,8 +171,17 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
             const int novf = *novf_p;
             // Lane-parallel over the neighbours v_i: each lane reads whole lists
             // (16-byte loads), so all of a row's list reads are in flight at once.
-            for (int i = lane; i < m; i += 32) {
-                const int64_t w = row_in_range(start, rowlist, list[i], m0, m1);
+            // The neighbours' rows are looked up first, all lanes' loads together.
+            int64_t wrow[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                wrow[e] = i < m ? row_in_range(start, rowlist, list[i], m0, m1) : -1;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                const int64_t w = wrow[e];
                 if (w < 0) continue;
                 const uint32_t* Lw = knn_id + w * k;
                 if (vec) {
@@ -203,6 +215,7 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 const int j = lane * E + e;
                 sel[e] = j < m ? (((uint32_t)cnt[j] << 16) | (uint32_t)j) : 0xFFFFFFFFu;
             }
+            for (int j = lane; j < m; j += 32) tkey[tslot(list[j])] = ANN_PAD;
             warp_sort<E, uint32_t>(sel);
         }
         // sel[] (element index lane*E+e) now ranks positions; keep the first min(R, m).
