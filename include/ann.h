@@ -88,7 +88,8 @@ enum ann_prune_rule { ANN_PRUNE_RANK = 0, ANN_PRUNE_TRUNC = 1 };
 /* Message of the last failed call on this host thread ("" if none). */
 const char* ann_last_error(void);
 
-/* Library ABI version (major*100 + minor). */
+/* Library ABI version (major*100 + minor); 103 adds ANN_F16_RERANK, the learned
+ * form, the autotuner and the wait self-test to 100. */
 int ann_version(void);
 
 /* Number of kernels this library has launched in this process (host counter). */

@@ -104,7 +104,7 @@ extern "C" {
 
 const char* ann_last_error(void) { return ann::g_err; }
 
-int ann_version(void) { return 100; }
+int ann_version(void) { return 103; }  // 1.03: learned form, autotuner, wait self-test
 
 unsigned long long ann_launch_count(void) { return g_launches.load(); }
 
