@@ -32,21 +32,28 @@ if ROOT not in sys.path:
 METRIC = "index-build vectors/s at recall@10>=0.95; distance TFLOP/s as % of GB300 peak"
 
 
+def _kernel_source_sha256():
+    """Hash of the distance-tile kernel's device code: knn.cu up to the host-side
+    tables (the kernel and its device helpers) and the shared device helpers."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2605_10135_gb300/csrc/knn.cu")) as f:
+        src = f.read()
+    cut = src.index("// ---- problem tables, gather and norms")
+    h = hashlib.sha256(src[:cut].encode())
+    with open(os.path.join(ROOT, "paper_2605_10135_gb300/csrc/common.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
 def _kernel_traffic():
     """DRAM bytes per distance-tile launch from the committed ncu capture, or None
     when the kernel source has changed since the counters were taken."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "k_knn_tiles_sift1m_u8.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
-    h = hashlib.sha256()
-    for rel in ("paper_2605_10135_gb300/csrc/knn.cu", "paper_2605_10135_gb300/csrc/common.cuh",
-                "paper_2605_10135_gb300/csrc/stages.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != j.get("kernel_source_sha256"):
+    if _kernel_source_sha256() != j.get("kernel_source_sha256"):
         return None
     return int(j["dram_bytes_read_per_launch"] + j["dram_bytes_write_per_launch"])
 
