@@ -64,7 +64,7 @@ constexpr int CAP = 8;                  // survivor buffer entries per row and e
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
-constexpr int CELL = 1024;              // rows per pivot cell
+constexpr int CELL = 256;               // rows per pivot cell (at most 1024 cells a shard)
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -1106,14 +1106,14 @@ struct Chunk16 {
 // (VEC) or element loads, and warp shuffles plus one shared-memory pass pick the
 // nearest.  Only the sweep order depends on it, never a result.
 template <int DT, bool VEC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     k_pivot_chain(const void* X, int d, const int64_t* __restrict__ psrc,
                   const int64_t* __restrict__ ppad_off, const int32_t* __restrict__ npiv,
                   uint32_t* __restrict__ crank) {
     extern __shared__ float cur_row[];  // d floats
     __shared__ uint8_t taken[1024];
-    __shared__ float wbd[8];
-    __shared__ int wbq[8];
+    __shared__ float wbd[32];
+    __shared__ int wbq[32];
     __shared__ int cur;
     constexpr int V = Chunk16<DT>::V;
     const int s = blockIdx.x;
@@ -1197,8 +1197,8 @@ static int launch_pivot_chain(const void* X, int dtype, int d, const KnnWs& w, i
     const bool vec = ((size_t)d * dtype_bytes(dtype)) % 16 == 0 && (uintptr_t)X % 16 == 0;
     const size_t sm = (size_t)d * sizeof(float);
 #define ANN_CHAIN(DT)                                                                          \
-    (vec ? k_pivot_chain<DT, true><<<C, 256, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank)  \
-         : k_pivot_chain<DT, false><<<C, 256, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank))
+    (vec ? k_pivot_chain<DT, true><<<C, 1024, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank)  \
+         : k_pivot_chain<DT, false><<<C, 1024, sm, st>>>(X, d, w.psrc, w.ppad_off, w.npiv, w.crank))
     switch (dtype) {
     case ANN_F32: ANN_CHAIN(ANN_F32); break;
     case ANN_F16: ANN_CHAIN(ANN_F16); break;
@@ -1748,6 +1748,31 @@ static unsigned grid_rows(int64_t rows, int threads) {
 // members (the pivot assignment is itself a k = 1 launch of the tile kernel), so
 // that each row block sweeps its own cell first; results do not depend on the
 // order (ties are broken by global id), only the amount of top-k work does.
+// One non-blocking side stream and a pair of fork / join events per device and
+// host thread, created on first use and kept for the life of the process (so that
+// a build can also be captured as a CUDA graph: the fork and join are events).
+static int side_stream(cudaStream_t* s, cudaEvent_t* fork_ev, cudaEvent_t* join_ev) {
+    struct Side {
+        int dev = -1;
+        cudaStream_t s = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+    };
+    static thread_local Side cache[8];
+    int dev = 0;
+    ANN_CHECK_CUDA(cudaGetDevice(&dev));
+    Side& c = cache[dev & 7];
+    if (c.dev != dev) {
+        ANN_CHECK_CUDA(cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking));
+        ANN_CHECK_CUDA(cudaEventCreateWithFlags(&c.a, cudaEventDisableTiming));
+        ANN_CHECK_CUDA(cudaEventCreateWithFlags(&c.b, cudaEventDisableTiming));
+        c.dev = dev;
+    }
+    *s = c.s;
+    *fork_ev = c.a;
+    *join_ev = c.b;
+    return ANN_OK;
+}
+
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
                   const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st,
@@ -1785,6 +1810,15 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     k_rowmap_pivots<<<grid_rows(w.prows_cap, 256), 256, 0, st>>>(members, offsets, w.ppad_off,
                                                                  w.npiv, C, w.prows_cap, w.psrc);
     ANN_CHECK_LAUNCH();
+    // The pivot chain needs only the pivots and runs on one SM per shard: it goes
+    // to a side stream, beside the gathers and the pivot-assignment launch.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    if ((rc = side_stream(&side, &fork_ev, &join_ev))) return rc;
+    ANN_CHECK_CUDA(cudaEventRecord(fork_ev, st));
+    ANN_CHECK_CUDA(cudaStreamWaitEvent(side, fork_ev, 0));
+    if ((rc = launch_pivot_chain(X, dtype, d, w, C, side))) return rc;
+    ANN_CHECK_CUDA(cudaEventRecord(join_ev, side));
     if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, amax, st)))
         return rc;
     if ((rc = launch_gather(X, dtype, d, w.psrc, w.prows_cap, pl, w.GP, w.pnorms, w.paug, amax,
@@ -1797,7 +1831,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                       rows / kt::BM + C + 1, st, false);
     if (rc) return rc;
     // 2. cell order
-    if ((rc = launch_pivot_chain(X, dtype, d, w, C, st))) return rc;
+    ANN_CHECK_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
     k_cell_sort<<<C, 512, 0, st>>>(w.cell, offsets, w.npiv, w.crank, w.ppad_off, w.perm);
     ANN_CHECK_LAUNCH();
     k_rowmap_cells<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, w.perm,
