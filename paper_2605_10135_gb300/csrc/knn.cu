@@ -64,7 +64,7 @@ constexpr int CAP = 8;                  // survivor buffer entries per row and e
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
-constexpr int CELL = 256;               // rows per pivot cell (at most 1024 cells a shard)
+constexpr int CELL = 128;               // rows per pivot cell (at most 1024 cells a shard)
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
