@@ -34,14 +34,21 @@ METRIC = "index-build vectors/s at recall@10>=0.95; distance TFLOP/s as % of GB3
 
 def _kernel_source_sha256():
     """Hash of the distance-tile kernel's device code: knn.cu up to the host-side
-    tables (the kernel and its device helpers) and the shared device helpers."""
+    tables (the kernel and its device helpers) and the shared device helpers, with
+    // comments and blank lines left out."""
     import hashlib
+    import re
+
+    def code(text):
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+        return "\n".join(ln for ln in lines if ln)
+
     with open(os.path.join(ROOT, "paper_2605_10135_gb300/csrc/knn.cu")) as f:
         src = f.read()
     cut = src.index("// ---- problem tables, gather and norms")
-    h = hashlib.sha256(src[:cut].encode())
-    with open(os.path.join(ROOT, "paper_2605_10135_gb300/csrc/common.cuh"), "rb") as f:
-        h.update(f.read())
+    h = hashlib.sha256(code(src[:cut]).encode())
+    with open(os.path.join(ROOT, "paper_2605_10135_gb300/csrc/common.cuh")) as f:
+        h.update(code(f.read()).encode())
     return h.hexdigest()
 
 

@@ -10,15 +10,18 @@
 // is |y_j|^2 / 2 split exactly into three BF16 values.
 //
 // Kernel k_knn_tiles: one CTA per 128-row block of one problem (a shard, or a
-// query batch against all vectors).  Warp roles:
+// query batch against all vectors); all problems in one launch, largest first.
+// Warp roles:
 //   warp 0   : TMA producer.  The CTA's A rows (all K) stay resident in shared
-//              memory; B tiles of 256 rows stream through a ring of 32 KB stages
-//              (one 64-element K block, 128-byte swizzle) and their 16-element
-//              norm blocks through a second, small ring (32-byte swizzle).
-//   warp 1   : allocates 512 TMEM columns (two 128x256 FP32 accumulators) and
-//              issues tcgen05.mma (M=128, N=256, K=16) from one thread.  The issue
-//              of an MMA waits for room in the tensor pipe, so the thread does
-//              little else: one commit per stage and one per tile.
+//              memory when they fit, else their K blocks stream beside the B
+//              blocks (large d); B tiles of 256 (or 128) rows stream through a
+//              ring of stages (one 128-byte K block, 128-byte swizzle) and their
+//              16-element norm blocks through a second, small ring (32-byte
+//              swizzle).
+//   warp 1   : allocates 512 TMEM columns (two FP32 accumulators) and issues
+//              tcgen05.mma (M=128, N=256 or 128, K=16; K=32 for E4M3) from one
+//              thread.  The issue of an MMA waits for room in the tensor pipe, so
+//              the thread does little else: one commit per stage and one per tile.
 //   warps 2-9: epilogue, two warps per TMEM lane quarter (one thread per row,
 //              one column half per warp).  32-column chunks are read with
 //              tcgen05.ld (the next chunk's load overlaps the current chunk's
@@ -28,9 +31,10 @@
 //              a full buffer is emptied into the row's max-heap in shared memory
 //              under the quarter lock, all 32 rows of the warp in lockstep
 //              (composite (key, global id) order, so ties go to the smaller id).
-// Rows are ordered by cell (see run_shard_knn) and each sweep starts near the
-// block's own rows, so the k-th key is tight after the first few tiles and
-// later chunks are almost always skipped.
+// Rows are ordered by cell, cells along a chain of nearby pivots (see
+// run_shard_knn), and each sweep starts at the block's own tile and moves
+// outward, so the k-th key is tight after the first few tiles and later chunks
+// are almost always skipped.
 // Every wait is bounded; on a timeout the CTA records DEV_TIMEOUT, drains its
 // copies, frees TMEM and returns.
 //
