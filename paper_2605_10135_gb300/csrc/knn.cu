@@ -68,7 +68,8 @@ constexpr int CAP = 8;                  // survivor buffer entries per row and e
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
-constexpr int CELL = 128;               // rows per pivot cell (at most 1024 cells a shard)
+constexpr int CELL = 128;               // rows per pivot cell, short rows (at most 1024 a shard)
+constexpr int CELL_WIDE = 1024;         // rows per pivot cell, rows over 512 bytes
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -1805,7 +1806,11 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         if (rc8) return rc8;
         amax = (const unsigned int*)w.amax;
     }
-    k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, kt::CELL, w.pad_off, w.order, w.ppad_off, w.npiv,
+    // Fine cells pay off where the top-k epilogue bounds the sweep (short rows);
+    // with long rows the contraction dominates and coarse cells keep the pivot
+    // launch (rows x pivots x d) and the chain (pivots^2 x d) cheap.
+    const int cell = row_bytes(pl) <= 512 ? kt::CELL : kt::CELL_WIDE;
+    k_pivot_tables<<<1, 32, 0, st>>>(offsets, C, cell, w.pad_off, w.order, w.ppad_off, w.npiv,
                                      w.pprobs);
     ANN_CHECK_LAUNCH();
     k_rowmap_plain<<<grid_rows(w.rows_cap, 256), 256, 0, st>>>(members, offsets, w.pad_off, C,
