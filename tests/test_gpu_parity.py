@@ -337,6 +337,27 @@ def test_precision_forms_rerank_exact_distances_and_recall(prec, bar):
     assert rec >= bar, rec
 
 
+@pytest.mark.parametrize("prec,bar", [(ann.BF16_RERANK, 0.99), (ann.F16_RERANK, 0.995),
+                                      (ann.FP8_RERANK, 0.8)])
+def test_precision_forms_with_streamed_tiles(prec, bar):
+    """d = 768: the screening tiles stream their A blocks too (E4M3 blocks hold 128
+    elements); the re-rank still returns exact FP32 distances, sorted."""
+    X = datagen.powerlaw_gaussian(3000, 768, 0.8, seed=105)
+    mem, off = _oracle_shards(X, 3, 2, seed=106)
+    k = 16
+    gid, gd = ann.shard_knn(T(X), T(mem), T(off), k, precision=prec, rerank_k=96)
+    gid, gd = as_u32(gid), gd.cpu().numpy().astype(np.float64)
+    oid, od = oracle.shard_knn(X, mem, off, k)
+    for q in range(0, len(mem), 53):
+        u = mem[q]
+        ok = gid[q] != PAD
+        true_d = ((X[gid[q][ok]].astype(np.float64) - X[u].astype(np.float64)) ** 2).sum(1)
+        assert np.all(np.abs(gd[q][ok] - true_d) <= 1e-5 * true_d + 1e-12)
+        key = list(zip(gd[q][ok].tolist(), gid[q][ok].tolist()))
+        assert key == sorted(key) and u not in gid[q]
+    assert _recall10(gid, oid) >= bar
+
+
 @pytest.mark.parametrize("prec", [ann.BF16_RERANK, ann.F16_RERANK])
 def test_16bit_precision_forms_are_exact_on_uint8(prec):
     """0..255 and their products are exact in BF16 and in power-of-two-scaled FP16."""
