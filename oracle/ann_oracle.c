@@ -172,14 +172,126 @@ void or_assign(const void* X, int64_t N, int d, int dtype, const float* cent, in
  * in increasing id order (Sec. V-C: merging needs the original vector order). */
 void or_shards(const uint32_t* assign, int64_t N, int r, int C, uint32_t* members,
                int64_t* offsets) {
+    /* OR_PAD entries (a vector held by fewer than r shards, Sec. V-B) are skipped. */
     int64_t* fill = (int64_t*)calloc((size_t)C + 1, sizeof(int64_t));
-    for (int64_t i = 0; i < N * r; i++) fill[assign[i] + 1]++;
+    for (int64_t i = 0; i < N * r; i++)
+        if (assign[i] != OR_PAD) fill[assign[i] + 1]++;
     offsets[0] = 0;
     for (int c = 0; c < C; c++) offsets[c + 1] = offsets[c] + fill[c + 1];
     for (int c = 0; c < C; c++) fill[c] = offsets[c];
     for (int64_t g = 0; g < N; g++)
-        for (int q = 0; q < r; q++) members[fill[assign[g * r + q]]++] = (uint32_t)g;
+        for (int q = 0; q < r; q++)
+            if (assign[g * r + q] != OR_PAD) members[fill[assign[g * r + q]]++] = (uint32_t)g;
     free(fill);
+}
+
+/* ---- blockwise-adaptive assignment with selective replication (Sec. V-A,
+ * Sec. V-B, Algorithm 1) -------------------------------------------------
+ * Vectors are read once, in id order, in blocks of `block` vectors.  Per
+ * vector v, its candidate centroids are the M first in the order (d32(v, c), c)
+ * (M = C considers every centroid).  State per cluster c: tot (members so far),
+ * org (originals so far), rep (replicas so far), rad2 (largest d32 of its
+ * originals so far: the squared radius).
+ *
+ * For block b (1-based), in this order (Sec. V-A):
+ *  1. originals: each v of the block, in id order, goes to its nearest
+ *     available candidate, i.e. the first one with tot < cap (cap = 0: no
+ *     limit); if none of the M has room it goes to its nearest one anyway and
+ *     is counted as an overflow;
+ *  2. statistics: rad2 takes the block's originals in; the replica threshold
+ *     theta_c = max(0, cap - ceil(org_c * N / processed)) leaves room for the
+ *     originals still to come, extrapolated from the rate seen so far
+ *     (processed = vectors in blocks 1..b); cap = 0: no threshold;
+ *  3. replicas (Algorithm 1): each v of the block, in id order, walks its
+ *     candidates in order; with its original c at distance dd (squared), a
+ *     candidate c' != c at squared distance dd' is taken while v is in fewer
+ *     than omega shards, if rep_c' < theta_c' and tot_c' < cap (size check) and
+ *        dd' < (eps * eps) * dd                      (distance constraint)
+ *        dd' < ((eps * tau) * (eps * tau)) * rad2_c'  (radius constraint),
+ *     tau = 1 + (tau0 - 1) / b; these are the paper's d' < eps d and
+ *     d' < eps tau R[c'] on squared distances, evaluated in FP64 on the d32
+ *     values exactly as written.  An infinite eps skips both constraints.
+ *
+ * assign_out [N x omega]: the original first, then replicas in candidate
+ * order, then OR_PAD.  stats_out[0] = replicas, stats_out[1] = overflows. */
+void or_selective(const void* X, int64_t N, int d, int dtype, const float* cent, int C,
+                  int omega, int M, double eps, double tau0, int64_t block, int64_t cap,
+                  uint32_t* assign_out, int64_t* stats_out) {
+    uint32_t* cand = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(N > 0 ? N : 1) * M);
+    float* cdd = (float*)malloc(sizeof(float) * (size_t)(N > 0 ? N : 1) * M);
+    /* candidate lists: the M first centroids in (d32, id) order */
+    #pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < N; v++) {
+        float* dist = (float*)malloc(sizeof(float) * (size_t)C);
+        char* taken = (char*)calloc((size_t)C, 1);
+        for (int c = 0; c < C; c++) dist[c] = or_d32(X, dtype, v, cent, 0, c, d);
+        for (int j = 0; j < M; j++) {
+            int best = -1;
+            for (int c = 0; c < C; c++) {
+                if (taken[c]) continue;
+                if (best < 0 || dist[c] < dist[best]) best = c;
+            }
+            taken[best] = 1;
+            cand[v * M + j] = (uint32_t)best;
+            cdd[v * M + j] = dist[best];
+        }
+        free(dist); free(taken);
+    }
+    int64_t* tot = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+    int64_t* org = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+    int64_t* rep = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+    int64_t* theta = (int64_t*)calloc((size_t)C, sizeof(int64_t));
+    float* rad2 = (float*)calloc((size_t)C, sizeof(float));
+    int* orig_j = (int*)malloc(sizeof(int) * (size_t)(block > 0 ? block : 1));
+    const int test = !isinf(eps);
+    int64_t nrep = 0, novf = 0;
+    for (int64_t i = 0; i < N * omega; i++) assign_out[i] = OR_PAD;
+    for (int64_t b0 = 0, beta = 1; b0 < N; b0 += block, beta++) {
+        const int64_t b1 = N - b0 < block ? N : b0 + block;
+        /* 1. originals */
+        for (int64_t v = b0; v < b1; v++) {
+            int jj = -1;
+            for (int j = 0; j < M; j++)
+                if (cap == 0 || tot[cand[v * M + j]] < cap) { jj = j; break; }
+            if (jj < 0) { jj = 0; novf++; }
+            const uint32_t c = cand[v * M + jj];
+            orig_j[v - b0] = jj;
+            assign_out[v * omega] = c;
+            tot[c]++;
+            org[c]++;
+            if (cdd[v * M + jj] > rad2[c]) rad2[c] = cdd[v * M + jj];
+        }
+        /* 2. thresholds */
+        for (int c = 0; c < C; c++) {
+            if (cap == 0) continue;
+            const int64_t proj = (org[c] * N + b1 - 1) / b1;
+            theta[c] = cap - proj > 0 ? cap - proj : 0;
+        }
+        const double tau = 1.0 + (tau0 - 1.0) / (double)beta;
+        const double e2 = eps * eps, et = eps * tau, et2 = et * et;
+        /* 3. replicas */
+        for (int64_t v = b0; v < b1; v++) {
+            const int jo = orig_j[v - b0];
+            const uint32_t c = cand[v * M + jo];
+            const double dd = (double)cdd[v * M + jo];
+            int assigned = 1;
+            for (int j = 0; j < M; j++) {
+                if (assigned >= omega) break;
+                const uint32_t c2 = cand[v * M + j];
+                if (c2 == c) continue;
+                if (cap != 0 && (rep[c2] >= theta[c2] || tot[c2] >= cap)) continue;
+                const double dd2 = (double)cdd[v * M + j];
+                if (test && !(dd2 < e2 * dd && dd2 < et2 * (double)rad2[c2])) continue;
+                assign_out[v * omega + assigned] = c2;
+                assigned++;
+                rep[c2]++;
+                tot[c2]++;
+                nrep++;
+            }
+        }
+    }
+    if (stats_out) { stats_out[0] = nrep; stats_out[1] = novf; }
+    free(cand); free(cdd); free(tot); free(org); free(rep); free(theta); free(rad2); free(orig_j);
 }
 
 /* ---- exact per-shard kNN (Sec. IV Workflow step 2; the shard graph of

@@ -29,6 +29,7 @@ def lib():
             "or_kmeans": (None, [P, I64, I32, I32, I32, P, P, I64, I32, P, P]),
             "or_assign": (None, [P, I64, I32, I32, P, I32, I32, I32, P]),
             "or_shards": (None, [P, I64, I32, I32, P, P]),
+            "or_selective": (None, [P, I64, I32, I32, P, I32, I32, I32, D, D, I64, I64, P, P]),
             "or_shard_knn_rows": (None, [P, I32, I32, P, P, I32, I32, P, I64, P, P]),
             "or_prune": (None, [P, P, P, P, I32, I32, I32, I32, P, P]),
             "or_merge": (None, [P, P, P, P, I32, I64, I32, P, I64, P, P, P]),
@@ -102,6 +103,24 @@ def shards(assign_: np.ndarray, C: int):
     offsets = np.empty(C + 1, np.int64)
     lib().or_shards(_p(a), N, r, C, _p(members), _p(offsets))
     return members, offsets
+
+
+def selective(X, cent, omega, M=None, eps=float("inf"), tau0=1.0, block=None, cap=0):
+    """Blockwise-adaptive assignment with selective replication (Sec. V).
+
+    Returns (assign [N, omega] uint32 with PAD for unused slots, stats [2] int64 =
+    (replicas, overflowed originals))."""
+    X = _c(X)
+    cent = _c(cent, np.float32)
+    C = cent.shape[0]
+    N = X.shape[0]
+    M = C if M is None else M
+    block = max(N, 1) if block is None else block
+    out = np.empty((N, omega), np.uint32)
+    stats = np.zeros(2, np.int64)
+    lib().or_selective(_p(X), N, X.shape[1], dtype_code(X), _p(cent), C, omega, M, float(eps),
+                       float(tau0), int(block), int(cap), _p(out), _p(stats))
+    return out, stats
 
 
 def partition(X, init, sample_idx, iters, C, r):
