@@ -177,6 +177,35 @@ def whole_job_rate(units_per_rank, world, ms):
     return world * units_per_rank / (ms * 1e-3)
 
 
+def union_recall_at_10(ann, Xd, out, N, nq, seed):
+    """Mean over nq sampled vectors of |10 nearest in the union of the vector's
+    shard kNN lists  intersect  its exact 10 nearest over all N| / 10."""
+    import torch
+    rng = np.random.default_rng(seed)
+    vs = np.sort(rng.choice(N, min(nq, N), replace=False))
+    q = Xd[torch.from_numpy(vs).to(Xd.device)]
+    gt_id, _ = ann.knn_query(Xd, q, 11)
+    gt = gt_id.cpu().numpy().view(np.uint32)
+    members = out["members"].cpu().numpy().view(np.uint32)
+    kid = out["knn_id"].cpu().numpy().view(np.uint32)
+    kd = out["knn_d"].cpu().numpy()
+    order = np.argsort(members, kind="stable")
+    ms = members[order]
+    lo, hi = np.searchsorted(ms, vs, "left"), np.searchsorted(ms, vs, "right")
+    hit = 0
+    for i, v in enumerate(vs):
+        truth = [int(t) for t in gt[i] if int(t) != int(v)][:10]
+        cand = {}
+        for p in order[lo[i]:hi[i]]:
+            for t, dd in zip(kid[p], kd[p]):
+                t = int(t)
+                if t != 0xFFFFFFFF and (t not in cand or dd < cand[t]):
+                    cand[t] = float(dd)
+        top = sorted(cand.items(), key=lambda e: (e[1], e[0]))[:10]
+        hit += len({t for t, _ in top} & set(truth))
+    return hit / (10.0 * len(vs))
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -205,6 +234,13 @@ def main():
     ap.add_argument("--learn-lr", type=float, default=1e-3)
     ap.add_argument("--min-recall", type=float, default=0.9,
                     help="learned form: recall estimate below which the exact form is used")
+    ap.add_argument("--epsilon", type=float, default=None,
+                    help="selective replication (Sec. V) with this eps; default: every vector "
+                         "in its r nearest shards")
+    ap.add_argument("--tau0", type=float, default=2.0)
+    ap.add_argument("--sel-block", type=int, default=65536, help="vectors per assignment block")
+    ap.add_argument("--capacity", type=int, default=0, help="members per shard, 0 = no limit")
+    ap.add_argument("--cand", type=int, default=16, help="candidate centroids per vector")
     ap.add_argument("--tile-counters", action="store_true",
                     help="after timing, run one step with the counting kernel variant and "
                          "report its per-role cycle counters")
@@ -246,8 +282,12 @@ def main():
     samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
     prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "f16": ann.F16_RERANK,
             "fp8": ann.FP8_RERANK, "learned": ann.LEARNED}[args.precision]
+    sel = None
+    if args.epsilon is not None:
+        sel = ann.SelectiveConfig(epsilon=args.epsilon, tau0=args.tau0, block=args.sel_block,
+                                  capacity=args.capacity, cand=args.cand)
     cfg = ann.BuildConfig(C=w.C, r=w.r, k=w.k, R=w.R, iters=10, precision=prec,
-                          rerank_k=args.rerank_k)
+                          rerank_k=args.rerank_k, selective=sel)
     learned = None
     if prec == ann.LEARNED:
         from paper_2605_10135_gb300 import datagen
@@ -343,6 +383,7 @@ def main():
         ex_id, _ = ann.shard_knn(Xd, out["members"], out["offsets"], w.k, ann.EXACT)
         graph_recall = float(ann.recall(out["knn_id"], ex_id, 10).item())
         del ex_id
+    union_recall = union_recall_at_10(ann, Xd, out, w.N, args.nq, w.seed + 21)
     # search recall@10 from the medoid
     Q = torch.from_numpy(Qn).to(dev)
     gt, _ = ann.knn_query(Xd, Q, 10)
@@ -355,7 +396,11 @@ def main():
     torch.cuda.synchronize()
     sev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     sev[0].record(st)
-    cent_s, mem_s, off_s = ann.partition(Xd, cfg.C, cfg.r, init_d, samp_d, cfg.iters)
+    if sel is None:
+        cent_s, mem_s, off_s = ann.partition(Xd, cfg.C, cfg.r, init_d, samp_d, cfg.iters)
+    else:
+        cent_s, mem_s, off_s, _, _ = ann.partition_selective(Xd, cfg.C, cfg.r, init_d, samp_d,
+                                                             cfg.iters, sel)
     sev[1].record(st)
     prec_s, model_s = cfg.precision, None
     if prec_s == ann.LEARNED:
@@ -457,6 +502,16 @@ def main():
                                   if prec == ann.EXACT else
                                   "graph recall@10 of the shard kNN lists vs the exact form's "
                                   "lists on the same partition"),
+            "union_recall_at_10": union_recall,
+            "union_recall_definition": ("for nq sampled vectors: the 10 nearest of the union of "
+                                        "the vector's shard kNN lists vs its exact 10 nearest "
+                                        "over all N (partition locality)"),
+            "selective": (None if sel is None else {
+                "epsilon": sel.epsilon, "tau0": sel.tau0, "block": sel.block,
+                "capacity": sel.capacity, "cand": sel.cand,
+                "replicated_share": float(out["selective_stats"][0].item()) / w.N,
+                "overflowed_originals": int(out["selective_stats"][1].item()),
+                "member_rows": int(out["offsets"][-1].item())}),
             "search_recall_at_10": recall, "search_Ls": 64, "queries": args.nq,
             "mean_dist_count": float(cnt.float().mean().item()),
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],

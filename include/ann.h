@@ -175,6 +175,61 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
                   size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * ann_partition_selective - Sec. V: k-means centroids as in ann_partition,
+ * then the blockwise-adaptive assignment with selective replication (Sec.
+ * V-A, Sec. V-B, Algorithm 1).  Vectors are taken once, in id order, in blocks
+ * of `block` vectors.  Vector v considers its `cand` (M) centroids of smallest
+ * (d32, id).  Per cluster c the call tracks its members (tot), originals,
+ * replicas, and squared radius rad2 = the largest d32 of its originals so far.
+ * For block b (1-based):
+ *   1. originals: each v, in id order, joins its nearest candidate with
+ *      tot < capacity (capacity 0: no limit); with none of the M free it
+ *      joins its nearest one anyway (counted in stats_out[1]);
+ *   2. per cluster, replica threshold theta = max(0, capacity -
+ *      ceil(originals * N / processed)), processed = vectors in blocks 1..b
+ *      (room kept for the originals still to come; no threshold without a
+ *      capacity), and rad2 updated with the block's originals;
+ *   3. replicas: each v, in id order, walks its candidates nearest first and
+ *      joins c' (not its original c) while it is in fewer than omega shards,
+ *      if replicas(c') < theta(c'), tot(c') < capacity, and
+ *         d32(v,c') < (eps*eps) * d32(v,c)                 (distance test)
+ *         d32(v,c') < ((eps*tau)*(eps*tau)) * rad2(c')     (radius test),
+ *      tau = 1 + (tau0 - 1) / b, both right-hand sides in FP64 (the paper's
+ *      d' < eps d and d' < eps tau R[c'] on squared distances).  epsilon =
+ *      +INFINITY drops both tests.
+ * With epsilon = +INFINITY and capacity 0 the result is ann_partition's with
+ * r = omega.
+ *
+ *  params        host pointer to the parameters below.
+ *  assign_out    [N x omega] uint32 or NULL: v's original shard first, then
+ *                its replicas nearest first, then ANN_PAD.
+ *  members_out   room for N*omega uint32; shard c's members (ids ascending)
+ *                are members_out[offsets_out[c] .. offsets_out[c+1]).
+ *  offsets_out   [C+1] int64; offsets_out[C] = N + replicas.
+ *  stats_out     [2] int64 or NULL: replicas, originals that found no room.
+ * Limits: 1 <= omega <= cand <= min(C, 32), C <= 1024, epsilon >= 0 (or
+ * +inf), tau0 finite >= 0, block >= 1, capacity < 2^40.  Without a capacity
+ * every stage runs over all vectors in parallel; with one, the dependence of
+ * each vector on the earlier ones is resolved by one thread block.
+ * ------------------------------------------------------------------------- */
+typedef struct ann_selective_params {
+    double epsilon;    /* eps of Sec. V-B (Table 4: 1.1 .. 1.5); +inf: no test */
+    double tau0;       /* tau of the first block (Sec. V-B: large, then falling) */
+    int64_t block;     /* vectors per block (Sec. V-A) */
+    int64_t capacity;  /* members per shard, 0 = unlimited */
+    int omega;         /* most shards a vector joins (omega = 2: one replica) */
+    int cand;          /* candidate centroids per vector (M) */
+} ann_selective_params;
+
+int ann_partition_selective_workspace(int64_t N, int d, int C, int64_t S,
+                                      const ann_selective_params* params, size_t* bytes);
+int ann_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
+                            const float* init_centroids, const uint32_t* sample_idx, int64_t S,
+                            int iters, const ann_selective_params* params, float* centroids_out,
+                            uint32_t* assign_out, uint32_t* members_out, int64_t* offsets_out,
+                            int64_t* stats_out, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
  * ann_shard_knn - Sec. IV Workflow (2): the graph of every shard, built
  * independently.  For shard member u (row p = its position in members), the
  * k other members of the same shard with the smallest (distance, id), self

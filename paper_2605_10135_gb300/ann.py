@@ -54,6 +54,9 @@ def lib():
             "ann_device_status": (I32, [ct.POINTER(ct.c_int)]),
             "ann_partition_workspace": (I32, [I64, I32, I32, I32, I64, PSZ]),
             "ann_partition": (I32, [P, I64, I32, I32, I32, I32, P, P, I64, I32, P, P, P, P, SZ, P]),
+            "ann_partition_selective_workspace": (I32, [I64, I32, I32, I64, P, PSZ]),
+            "ann_partition_selective": (I32, [P, I64, I32, I32, I32, P, P, I64, I32, P, P, P, P,
+                                              P, P, P, SZ, P]),
             "ann_shard_knn_workspace": (I32, [I64, I32, I32, I32, I64, I32, I32, I32, PSZ]),
             "ann_shard_knn": (I32, [P, I64, I32, I32, P, P, I32, I64, I32, I32, I32, P, P, P, P, SZ,
                                     P]),
@@ -204,6 +207,50 @@ def partition(X: torch.Tensor, C: int, r: int, init_centroids: torch.Tensor,
     _check(L.ann_partition(_ptr(X), N, d, _DT[X.dtype], C, r, _ptr(init), _ptr(sample), S, iters,
                            _ptr(cent), _ptr(members), _ptr(offsets), _ptr(ws), nb, _stream()))
     return cent, members, offsets
+
+
+class _SelectiveParams(ct.Structure):
+    _fields_ = [("epsilon", ct.c_double), ("tau0", ct.c_double), ("block", ct.c_int64),
+                ("capacity", ct.c_int64), ("omega", ct.c_int), ("cand", ct.c_int)]
+
+
+@dataclass
+class SelectiveConfig:
+    """Blockwise-adaptive assignment with selective replication (Sec. V)."""
+    epsilon: float = 1.2
+    tau0: float = 2.0
+    block: int = 65536
+    capacity: int = 0
+    cand: int = 16
+
+
+def partition_selective(X: torch.Tensor, C: int, omega: int, init_centroids: torch.Tensor,
+                        sample_idx: torch.Tensor, iters: int, sel: SelectiveConfig,
+                        with_assign: bool = False):
+    """k-means shards + selective replication: (centroids, members [rows], offsets,
+    stats [2] = (replicas, overflowed originals), assign [N, omega] or None).
+    Reads offsets[C] back to the host (the number of member rows)."""
+    X = _cuda(X, "X")
+    N, d = X.shape
+    init = _cuda(init_centroids.to(torch.float32), "init_centroids")
+    sample = _cuda(sample_idx.to(torch.int32), "sample_idx")
+    S = sample.numel()
+    dev = X.device
+    p = _SelectiveParams(float(sel.epsilon), float(sel.tau0), int(sel.block), int(sel.capacity),
+                         int(omega), int(min(sel.cand, C)))
+    cent = torch.empty((C, d), dtype=torch.float32, device=dev)
+    members = torch.empty(N * omega, dtype=torch.int32, device=dev)
+    offsets = torch.empty(C + 1, dtype=torch.int64, device=dev)
+    stats = torch.empty(2, dtype=torch.int64, device=dev)
+    assign = torch.empty((N, omega), dtype=torch.int32, device=dev) if with_assign else None
+    L = lib()
+    nb = _wsize(L.ann_partition_selective_workspace, N, d, C, S, ct.byref(p))
+    ws = _ws(nb, dev)
+    _check(L.ann_partition_selective(_ptr(X), N, d, _DT[X.dtype], C, _ptr(init), _ptr(sample), S,
+                                     iters, ct.byref(p), _ptr(cent), _ptr(assign), _ptr(members),
+                                     _ptr(offsets), _ptr(stats), _ptr(ws), nb, _stream()))
+    rows = int(offsets[C].item())
+    return cent, members[:rows], offsets, stats, assign
 
 
 def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: int,
@@ -398,6 +445,7 @@ class BuildConfig:
     rule: int = PRUNE_RANK
     precision: int = EXACT
     rerank_k: int = 0
+    selective: SelectiveConfig | None = None  # None: every vector in its r nearest shards
 
 
 def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
@@ -407,7 +455,12 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
     With precision LEARNED the projection MLP is trained first (learned.params0 is
     not modified); when its recall estimate is below learned.min_recall the shard
     graphs are built with the exact form instead (out["precision"] says which)."""
-    cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
+    sel_stats = None
+    if cfg.selective is None:
+        cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
+    else:
+        cent, members, offsets, sel_stats, _ = partition_selective(
+            X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters, cfg.selective)
     precision, model, est = cfg.precision, None, None
     if precision == LEARNED:
         if learned is None:
@@ -423,7 +476,7 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
     graph, gdist, degree = merge(pr_id, pr_d, members, offsets, X.shape[0])
     return dict(centroids=cent, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
                 pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree,
-                precision=precision, recall_estimate=est, model=model)
+                precision=precision, recall_estimate=est, model=model, selective_stats=sel_stats)
 
 
 class CapturedBuild:
@@ -438,6 +491,9 @@ class CapturedBuild:
                  sample_idx: torch.Tensor):
         if cfg.precision == LEARNED:
             raise ValueError("the learned form is not capturable")
+        if cfg.selective is not None:
+            raise ValueError("selective replication is not capturable (its row count is read "
+                             "back to the host)")
         self.X, self.cfg = X, cfg
         self.init, self.sample = init_centroids, sample_idx
         side = torch.cuda.Stream(device=X.device)

@@ -230,6 +230,66 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
                          members_out, offsets_out, w, (cudaStream_t)stream);
 }
 
+static int check_selective(int64_t N, int d, int C, int64_t S, const ann_selective_params* p) {
+    ANN_REQUIRE(p, "params is NULL");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
+    ANN_REQUIRE(d >= 1 && d <= 4096, "d out of range");
+    ANN_REQUIRE(C >= 1 && C <= 1024, "need 1 <= C <= 1024");
+    ANN_REQUIRE(S >= 0 && S <= N, "S out of range");
+    ANN_REQUIRE(p->cand >= 1 && p->cand <= (C < 32 ? C : 32), "need 1 <= cand <= min(C, 32)");
+    ANN_REQUIRE(p->omega >= 1 && p->omega <= p->cand, "need 1 <= omega <= cand");
+    ANN_REQUIRE(p->epsilon >= 0.0 && !isnan(p->epsilon), "epsilon must be >= 0 or +inf");
+    ANN_REQUIRE(p->tau0 >= 0.0 && isfinite(p->tau0), "tau0 must be finite and >= 0");
+    ANN_REQUIRE(p->block >= 1, "block must be >= 1");
+    ANN_REQUIRE(p->capacity >= 0 && p->capacity < (1ll << 40), "capacity out of range");
+    return ANN_OK;
+}
+
+int ann_partition_selective_workspace(int64_t N, int d, int C, int64_t S,
+                                      const ann_selective_params* p, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    int rc = check_selective(N, d, C, S, p);
+    if (rc) return rc;
+    *bytes = selective_ws(N, d, C, S, p->cand, p->omega, p->block, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
+                            const float* init_centroids, const uint32_t* sample_idx, int64_t S,
+                            int iters, const ann_selective_params* p, float* centroids_out,
+                            uint32_t* assign_out, uint32_t* members_out, int64_t* offsets_out,
+                            int64_t* stats_out, void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_partition_selective_workspace(N, d, C, S, p, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(iters >= 0, "iters < 0");
+    ANN_REQUIRE(init_centroids && centroids_out && offsets_out, "NULL pointer");
+    ANN_REQUIRE(N == 0 || (X && members_out), "NULL pointer");
+    ANN_REQUIRE(S == 0 || iters == 0 || sample_idx, "sample_idx is NULL");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    SelectiveWs w;
+    selective_ws(N, d, C, S, p->cand, p->omega, p->block, &w, ws, ws_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (N == 0) {
+        ANN_CHECK_CUDA(cudaMemsetAsync(offsets_out, 0, sizeof(int64_t) * (C + 1), st));
+        if (stats_out) ANN_CHECK_CUDA(cudaMemsetAsync(stats_out, 0, 2 * sizeof(int64_t), st));
+        ANN_CHECK_CUDA(cudaMemcpyAsync(centroids_out, init_centroids, sizeof(float) * C * d,
+                                       cudaMemcpyDeviceToDevice, st));
+        return ANN_OK;
+    }
+    SelectiveArgs a;
+    a.eps = p->epsilon;
+    a.tau0 = p->tau0;
+    a.block = p->block;
+    a.cap = p->capacity;
+    a.omega = p->omega;
+    a.M = p->cand;
+    return run_partition_selective(X, N, d, dtype, C, init_centroids, sample_idx, S, iters, a,
+                                   centroids_out, assign_out, members_out, offsets_out, stats_out,
+                                   w, st);
+}
+
 // ---------------------------------------------------------------- autotuner
 // Plans chosen by timing, per (d, dtype, k, precision, rerank_k, shard-size
 // bucket = floor(log2(rows / C))); process-wide, guarded by a mutex.

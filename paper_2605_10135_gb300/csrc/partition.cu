@@ -51,7 +51,8 @@ __global__ void k_dist_centroids(const void* X, int dtype, int d, const uint32_t
 
 // The r entries of smallest (dist, c) per point, in that order (full scan).
 __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
-                       uint32_t* __restrict__ out, int32_t* __restrict__ lab_out) {
+                       uint32_t* __restrict__ out, int32_t* __restrict__ lab_out,
+                       float* __restrict__ dout) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
     const float* dp = dist + p * C;
@@ -69,6 +70,7 @@ __global__ void k_topr(const float* __restrict__ dist, int64_t np, int C, int r,
         }
         if (bc < 0) bc = 0;  // unreachable for finite distances
         if (out) out[p * r + q] = (uint32_t)bc;
+        if (dout) dout[p * r + q] = bd;
         if (lab_out && q == 0) lab_out[p] = bc;
         prev_d = bd;
         prev_c = bc;
@@ -98,7 +100,7 @@ __global__ void k_d32_cand(const void* X, int dtype, int d, const uint32_t* rows
 // The r candidates of smallest (d32, centroid id) per point, in that order.
 __global__ void k_topr_cand(const float* __restrict__ dist, const uint32_t* __restrict__ cand,
                             int64_t np, int ks, int r, uint32_t* __restrict__ out,
-                            int32_t* __restrict__ lab_out) {
+                            int32_t* __restrict__ lab_out, float* __restrict__ dout) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= np) return;
     const float* dp = dist + p * ks;
@@ -120,6 +122,7 @@ __global__ void k_topr_cand(const float* __restrict__ dist, const uint32_t* __re
         }
         if (bc < 0) bc = 0;  // unreachable: ks >= r distinct candidates
         if (out) out[p * r + q] = (uint32_t)bc;
+        if (dout) dout[p * r + q] = bd;
         if (lab_out && q == 0) lab_out[p] = (int32_t)bc;
         prev_d = bd;
         prev_c = bc;
@@ -236,7 +239,10 @@ __global__ void k_block_hist(const uint32_t* __restrict__ assign, int64_t N, int
     int64_t g0 = blockIdx.x * (int64_t)SB;
     for (int i = threadIdx.x; i < SB * r; i += blockDim.x) {
         int64_t g = g0 + i / r;
-        if (g < N) atomicAdd(&h[assign[g * r + (i % r)]], 1);
+        if (g < N) {
+            const uint32_t c = assign[g * r + (i % r)];
+            if (c < (uint32_t)C) atomicAdd(&h[c], 1);  // ANN_PAD: unused slot
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) hist[(int64_t)c * nblk + blockIdx.x] = h[c];
@@ -303,8 +309,9 @@ __global__ void k_scatter(const uint32_t* __restrict__ assign, int64_t N, int r,
     const int64_t nent = (min((int64_t)SB, N - g0)) * r;
     for (int64_t e0 = 0; e0 < nent; e0 += 32) {
         int64_t e = e0 + lane;
-        bool valid = e < nent;
-        uint32_t c = valid ? assign[g0 * r + e] : 0xFFFFFFFFu;
+        uint32_t c = e < nent ? assign[g0 * r + e] : 0xFFFFFFFFu;
+        if (c >= (uint32_t)C) c = 0xFFFFFFFFu;  // past the end, or an unused slot
+        const bool valid = c != 0xFFFFFFFFu;
         uint32_t peers = __match_any_sync(0xffffffffu, c);
         int rank = __popc(peers & ((1u << lane) - 1));
         int r0 = valid ? run[c] : 0;
@@ -357,13 +364,13 @@ size_t partition_ws(int64_t N, int d, int C, int r, int64_t S, PartitionWs* out,
 // when given): tensor-core screen, then d32 of the candidates.
 static int assign_chunk(const void* X, int dtype, int d, const uint32_t* rowsel, int64_t p0,
                         int64_t np, int C, int r, const PartitionWs& w, uint32_t* out,
-                        int32_t* lab, cudaStream_t st) {
+                        int32_t* lab, cudaStream_t st, float* dout = nullptr) {
     if (C <= FULL_SCAN_C) {
         const int64_t tot = np * C;
         const unsigned g = (unsigned)((tot + 255) / 256 < 65535 * 8 ? (tot + 255) / 256 : 65535 * 8);
         k_dist_centroids<<<g, 256, 0, st>>>(X, dtype, d, rowsel, p0, np, w.centT, C, w.dist);
         ANN_CHECK_LAUNCH();
-        k_topr<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, np, C, r, out, lab);
+        k_topr<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, np, C, r, out, lab, dout);
         ANN_CHECK_LAUNCH();
         return ANN_OK;
     }
@@ -375,15 +382,17 @@ static int assign_chunk(const void* X, int dtype, int d, const uint32_t* rowsel,
     const unsigned g = (unsigned)((tot + 255) / 256 < 65535 * 8 ? (tot + 255) / 256 : 65535 * 8);
     k_d32_cand<<<g, 256, 0, st>>>(X, dtype, d, rowsel, p0, np, w.cent, w.cand, ks, w.dist);
     ANN_CHECK_LAUNCH();
-    k_topr_cand<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, w.cand, np, ks, r, out, lab);
+    k_topr_cand<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(w.dist, w.cand, np, ks, r, out, lab,
+                                                               dout);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }
 
-int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
-                  const float* init_centroids, const uint32_t* sample_idx, int64_t S, int iters,
-                  float* centroids_out, uint32_t* members_out, int64_t* offsets_out,
-                  const PartitionWs& w, cudaStream_t st) {
+// Lloyd iterations on the sample rows (centroids left in w.cent / w.centT and
+// copied to centroids_out).
+static int kmeans_stage(const void* X, int d, int dtype, int C, const float* init_centroids,
+                        const uint32_t* sample_idx, int64_t S, int iters, float* centroids_out,
+                        const PartitionWs& w, cudaStream_t st) {
     const int64_t cd = (int64_t)C * d;
     const int tpb = 256;
     auto nb = [](int64_t n, int t) { return (unsigned)((n + t - 1) / t); };
@@ -414,23 +423,371 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
     }
     ANN_CHECK_CUDA(cudaMemcpyAsync(centroids_out, w.cent, sizeof(float) * cd,
                                    cudaMemcpyDeviceToDevice, st));
-    for (int64_t p0 = 0; p0 < N; p0 += w.chunk) {
-        int64_t np = N - p0 < w.chunk ? N - p0 : w.chunk;
-        int rc = assign_chunk(X, dtype, d, nullptr, p0, np, C, r, w, w.assign + p0 * r, nullptr,
-                              st);
-        if (rc) return rc;
-    }
+    return ANN_OK;
+}
+
+// Member lists from assign [N x r] (ANN_PAD slots skipped): ids ascending per shard.
+static int shard_lists(const uint32_t* assign, int64_t N, int r, int C, const PartitionWs& w,
+                       uint32_t* members_out, int64_t* offsets_out, cudaStream_t st) {
     int64_t nblk = (N + SB - 1) / SB;
-    k_block_hist<<<(unsigned)nblk, 256, C * sizeof(int32_t), st>>>(w.assign, N, r, C, nblk, w.hist);
+    k_block_hist<<<(unsigned)nblk, 256, C * sizeof(int32_t), st>>>(assign, N, r, C, nblk, w.hist);
     ANN_CHECK_LAUNCH();
     k_scan_blocks<<<C, 1024, 0, st>>>(w.hist, nblk, w.tot);
     ANN_CHECK_LAUNCH();
     k_offsets<<<1, 32, 0, st>>>(w.tot, C, offsets_out);
     ANN_CHECK_LAUNCH();
-    k_scatter<<<(unsigned)nblk, 32, C * sizeof(int32_t), st>>>(w.assign, N, r, C, nblk, w.hist,
+    k_scatter<<<(unsigned)nblk, 32, C * sizeof(int32_t), st>>>(assign, N, r, C, nblk, w.hist,
                                                                offsets_out, members_out);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
+}
+
+int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
+                  const float* init_centroids, const uint32_t* sample_idx, int64_t S, int iters,
+                  float* centroids_out, uint32_t* members_out, int64_t* offsets_out,
+                  const PartitionWs& w, cudaStream_t st) {
+    int rc = kmeans_stage(X, d, dtype, C, init_centroids, sample_idx, S, iters, centroids_out, w,
+                          st);
+    if (rc) return rc;
+    for (int64_t p0 = 0; p0 < N; p0 += w.chunk) {
+        int64_t np = N - p0 < w.chunk ? N - p0 : w.chunk;
+        rc = assign_chunk(X, dtype, d, nullptr, p0, np, C, r, w, w.assign + p0 * r, nullptr, st);
+        if (rc) return rc;
+    }
+    return shard_lists(w.assign, N, r, C, w, members_out, offsets_out, st);
+}
+
+
+// ---- blockwise-adaptive assignment with selective replication ------------------
+// (Sec. V-A, Sec. V-B, Algorithm 1.)  Vectors are taken once, in id order, in
+// blocks; per block: originals to their nearest candidate with room, then the
+// cluster statistics (squared radius, replica threshold theta), then replicas.
+// Candidates of vector v: cand[v*M + j], j < M, its M centroids of smallest
+// (d32, id) in that order, with d32 in cdd[v*M + j].
+//
+// The paper's tests d' < eps d and d' < eps tau R[c'] are taken on squared d32
+// values in FP64: dd' < (eps*eps)*dd and dd' < ((eps*tau)*(eps*tau))*rad2.  For
+// a float x and a double rhs, x < rhs holds exactly when x < the smallest float
+// >= rhs (no float lies strictly between rhs and that float), so each double
+// right-hand side is turned into one float threshold (rounded up) once, and the
+// per-candidate comparisons are FP32.
+__device__ __forceinline__ double sel_et2(double eps, double tau0, int64_t beta) {
+    const double tau = __dadd_rn(1.0, __ddiv_rn(__dsub_rn(tau0, 1.0), (double)beta));
+    const double et = __dmul_rn(eps, tau);
+    return __dmul_rn(et, et);
+}
+
+// No capacity limit: each original is the vector's nearest candidate.  Writes
+// slot 0 of assign and folds the block's squared radii into rad2b[b*C + c]
+// (float bits; non-negative floats order like their bit patterns).
+__global__ void k_sel_orig(const uint32_t* __restrict__ cand, const float* __restrict__ cdd,
+                           int64_t N, int M, int omega, int64_t block, int C,
+                           uint32_t* __restrict__ rad2b, uint32_t* __restrict__ assign) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = v < N;
+    const unsigned act = __ballot_sync(0xffffffffu, in);
+    if (!in) return;
+    const uint32_t c = cand[v * M];
+    const uint32_t bits = __float_as_uint(cdd[v * M]);
+    assign[v * omega] = c;
+    const uint64_t key = (uint64_t)(v / block) * (uint64_t)C + c;
+    const unsigned peers = __match_any_sync(act, key);
+    const uint32_t mx = __reduce_max_sync(peers, bits);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(rad2b + key, mx);
+}
+
+// Per cluster: running maximum of the squared radius over blocks, turned into
+// the radius-test threshold of each block (tau of block b = 1 + (tau0-1)/b).
+__global__ void k_sel_thresholds(const uint32_t* __restrict__ rad2b, int64_t nb, int C,
+                                 double eps, double tau0, float* __restrict__ rthr) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    uint32_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const uint32_t x = rad2b[b * C + c];
+        run = x > run ? x : run;
+        const double et2 = sel_et2(eps, tau0, b + 1);
+        rthr[b * C + c] = __double2float_ru(__dmul_rn(et2, (double)__uint_as_float(run)));
+    }
+}
+
+// No capacity limit: replicas of every vector in parallel (no size check).
+__global__ void k_sel_rep(const uint32_t* __restrict__ cand, const float* __restrict__ cdd,
+                          int64_t N, int M, int omega, int64_t block, int C, int test, double e2,
+                          const float* __restrict__ rthr, uint32_t* __restrict__ assign,
+                          unsigned long long* __restrict__ stats) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = v < N;
+    const unsigned act = __ballot_sync(0xffffffffu, in);
+    if (!in) return;
+    const uint32_t* cv = cand + v * M;
+    const float* dv = cdd + v * M;
+    const float* rt = rthr + (v / block) * C;
+    const float dthr = test ? __double2float_ru(__dmul_rn(e2, (double)dv[0])) : 0.0f;
+    int assigned = 1;
+    for (int j = 1; j < M && assigned < omega; ++j) {
+        const uint32_t c2 = cv[j];
+        if (test) {
+            const float x = dv[j];
+            if (!(x < dthr && x < rt[c2])) continue;
+        }
+        assign[v * omega + assigned++] = c2;
+    }
+    for (int q = assigned; q < omega; ++q) assign[v * omega + q] = ANN_PAD;
+    const unsigned nrep = __reduce_add_sync(act, (unsigned)(assigned - 1));
+    if ((threadIdx.x & 31) == __ffs(act) - 1 && nrep) atomicAdd(stats, (unsigned long long)nrep);
+}
+
+// With a capacity limit the blocks' vectors depend on one another in id order,
+// so one CTA walks them: all warps stage SEL_CH vectors' candidates into shared
+// memory, then warp 0 takes them 32 at a time (lane = vector, in id order).  A
+// group of 32 whose first choices all fit the rooms left is committed at once
+// (the serial order would accept exactly those); otherwise its lanes go one by
+// one.  Cluster counters live in shared memory.
+constexpr int SEL_CH = 512;
+
+__host__ __device__ constexpr size_t sel_seq_smem(int C, int M) {
+    return (size_t)C * (4 * 8 + 4 + 4 + 4) + (size_t)SEL_CH * M * 8;
+}
+
+__global__ void __launch_bounds__(1024, 1)
+k_sel_seq(const uint32_t* __restrict__ cand, const float* __restrict__ cdd, int64_t N, int M,
+          int omega, int64_t block, int C, unsigned long long cap, int test, double e2,
+          double eps, double tau0, uint32_t* __restrict__ assign, uint8_t* __restrict__ oj,
+          unsigned long long* __restrict__ stats) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long* tot = (unsigned long long*)sm;
+    unsigned long long* org = tot + C;
+    unsigned long long* rep = org + C;
+    unsigned long long* theta = rep + C;
+    uint32_t* rad2 = (uint32_t*)(theta + C);
+    float* rthr = (float*)(rad2 + C);
+    int32_t* demand = (int32_t*)(rthr + C);
+    uint32_t* sK = (uint32_t*)(demand + C);
+    float* sD = (float*)(sK + (size_t)SEL_CH * M);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = tid; c < C; c += blockDim.x) {
+        tot[c] = org[c] = rep[c] = theta[c] = 0;
+        rad2[c] = 0;
+        demand[c] = 0;
+    }
+    unsigned long long nrep = 0, novf = 0;
+    const unsigned lt = (1u << lane) - 1;
+    for (int64_t b0 = 0, beta = 1; b0 < N; b0 += block, ++beta) {
+        const int64_t b1 = N - b0 < block ? N : b0 + block;
+        for (int phase = 0; phase < 2; ++phase) {
+            if (phase == 1) {  // statistics after the block's originals
+                __syncthreads();
+                const double et2 = sel_et2(eps, tau0, beta);
+                for (int c = tid; c < C; c += blockDim.x) {
+                    const unsigned long long proj =
+                        (org[c] * (unsigned long long)N + (unsigned long long)b1 - 1) /
+                        (unsigned long long)b1;
+                    theta[c] = cap > proj ? cap - proj : 0;
+                    rthr[c] = __double2float_ru(__dmul_rn(et2, (double)__uint_as_float(rad2[c])));
+                }
+            }
+            for (int64_t q0 = b0; q0 < b1; q0 += SEL_CH) {
+                const int n = (int)(b1 - q0 < SEL_CH ? b1 - q0 : SEL_CH);
+                __syncthreads();
+                for (int e = tid; e < n * M; e += blockDim.x) {
+                    sK[e] = cand[q0 * M + e];
+                    sD[e] = cdd[q0 * M + e];
+                }
+                __syncthreads();
+                if (warp != 0) continue;
+                for (int i0 = 0; i0 < n; i0 += 32) {
+                    const int i = i0 + lane;
+                    const bool in = i < n;
+                    const int64_t v = q0 + i;
+                    const uint32_t* kv = sK + (size_t)i * M;
+                    const float* dv = sD + (size_t)i * M;
+                    if (phase == 0) {
+                        // ---- originals: nearest candidate with tot < cap
+                        const uint32_t c0 = in ? kv[0] : 0xFFFFFFFFu;
+                        const unsigned peers = __match_any_sync(0xffffffffu, c0);
+                        const unsigned rank = __popc(peers & lt);
+                        const bool ok = !in || tot[c0] + rank < cap;
+                        const bool all = __all_sync(0xffffffffu, ok);
+                        int jj = 0;
+                        if (all) {
+                            if (in) {
+                                if (rank == 0) {
+                                    tot[c0] += __popc(peers);
+                                    org[c0] += __popc(peers);
+                                }
+                                atomicMax(rad2 + c0, __float_as_uint(dv[0]));
+                            }
+                        } else {
+                            for (int l = 0; l < 32; ++l) {
+                                if (lane == l && in) {
+                                    jj = -1;
+                                    for (int j = 0; j < M; ++j)
+                                        if (tot[kv[j]] < cap) {
+                                            jj = j;
+                                            break;
+                                        }
+                                    if (jj < 0) {
+                                        jj = 0;
+                                        ++novf;
+                                    }
+                                    const uint32_t c = kv[jj];
+                                    tot[c] += 1;
+                                    org[c] += 1;
+                                    const uint32_t bits = __float_as_uint(dv[jj]);
+                                    if (bits > rad2[c]) rad2[c] = bits;
+                                }
+                                __syncwarp();
+                            }
+                        }
+                        if (in) {
+                            assign[v * omega] = kv[jj];
+                            oj[v] = (uint8_t)jj;
+                        }
+                        __syncwarp();
+                    } else {
+                        // ---- replicas (Algorithm 1)
+                        const int jo = in ? oj[v] : 0;
+                        const float dthr =
+                            (in && test) ? __double2float_ru(__dmul_rn(e2, (double)dv[jo])) : 0.0f;
+                        uint32_t elig = 0;
+                        if (in)
+                            for (int j = 0; j < M; ++j) {
+                                if (j == jo) continue;
+                                const float x = dv[j];
+                                if (!test || (x < dthr && x < rthr[kv[j]])) elig |= 1u << j;
+                            }
+                        // first omega-1 eligible candidates, ignoring the size check
+                        uint32_t prop = 0, m = elig;
+                        for (int q = 1; q < omega && m; ++q) {
+                            const uint32_t bit = m & (0u - m);
+                            prop |= bit;
+                            m ^= bit;
+                        }
+                        for (uint32_t t = prop; t; t &= t - 1) atomicAdd(demand + kv[__ffs(t) - 1], 1);
+                        __syncwarp();
+                        bool ok = true;
+                        for (uint32_t t = prop; t; t &= t - 1) {
+                            const uint32_t c2 = kv[__ffs(t) - 1];
+                            const unsigned long long dm = (unsigned long long)demand[c2];
+                            ok = ok && rep[c2] + dm <= theta[c2] && tot[c2] + dm <= cap;
+                        }
+                        const bool all = __all_sync(0xffffffffu, ok);
+                        for (uint32_t t = prop; t; t &= t - 1) demand[kv[__ffs(t) - 1]] = 0;
+                        __syncwarp();
+                        uint32_t took = 0;
+                        if (all) {
+                            took = prop;
+                            for (uint32_t t = prop; t; t &= t - 1) {
+                                const uint32_t c2 = kv[__ffs(t) - 1];
+                                atomicAdd(rep + c2, 1ull);
+                                atomicAdd(tot + c2, 1ull);
+                            }
+                        } else {
+                            for (int l = 0; l < 32; ++l) {
+                                if (lane == l && in) {
+                                    int assigned = 1;
+                                    for (uint32_t t = elig; t && assigned < omega; t &= t - 1) {
+                                        const uint32_t c2 = kv[__ffs(t) - 1];
+                                        if (rep[c2] < theta[c2] && tot[c2] < cap) {
+                                            rep[c2] += 1;
+                                            tot[c2] += 1;
+                                            took |= t & (0u - t);
+                                            ++assigned;
+                                        }
+                                    }
+                                }
+                                __syncwarp();
+                            }
+                        }
+                        if (in) {
+                            int q = 1;
+                            for (uint32_t t = took; t; t &= t - 1) assign[v * omega + q++] = kv[__ffs(t) - 1];
+                            nrep += (unsigned long long)(q - 1);
+                            for (; q < omega; ++q) assign[v * omega + q] = ANN_PAD;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+    if (warp == 0) {
+        for (int o = 16; o; o >>= 1) {
+            nrep += __shfl_down_sync(0xffffffffu, nrep, o);
+            novf += __shfl_down_sync(0xffffffffu, novf, o);
+        }
+        if (lane == 0) {
+            stats[0] = nrep;
+            stats[1] = novf;
+        }
+    }
+}
+
+size_t selective_ws(int64_t N, int d, int C, int64_t S, int M, int omega, int64_t block,
+                    SelectiveWs* out, void* base, size_t cap) {
+    Carver cv(base, cap);
+    SelectiveWs w;
+    const size_t pw = partition_ws(N, d, C, M, S, nullptr, nullptr, 0);
+    uint8_t* pbase = cv.take<uint8_t>(pw);
+    if (out) partition_ws(N, d, C, M, S, &w.p, pbase, pw);
+    const int64_t nb = N > 0 ? (N + block - 1) / block : 1;
+    w.cdd = cv.take<float>((size_t)(N > 0 ? N : 1) * M);
+    w.sel = cv.take<uint32_t>((size_t)(N > 0 ? N : 1) * omega);
+    w.oj = cv.take<uint8_t>((size_t)(N > 0 ? N : 1));
+    w.rad2b = cv.take<uint32_t>((size_t)nb * C);
+    w.rthr = cv.take<float>((size_t)nb * C);
+    w.stats = cv.take<unsigned long long>(2);
+    w.nb = nb;
+    if (out) *out = w;
+    return cv.used + 256;
+}
+
+int run_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
+                            const float* init_centroids, const uint32_t* sample_idx, int64_t S,
+                            int iters, const SelectiveArgs& a, float* centroids_out,
+                            uint32_t* assign_out, uint32_t* members_out, int64_t* offsets_out,
+                            int64_t* stats_out, const SelectiveWs& w, cudaStream_t st) {
+    const PartitionWs& pw = w.p;
+    int rc = kmeans_stage(X, d, dtype, C, init_centroids, sample_idx, S, iters, centroids_out, pw,
+                          st);
+    if (rc) return rc;
+    const int M = a.M, omega = a.omega;
+    uint32_t* cand = pw.assign;  // [N x M]
+    for (int64_t p0 = 0; p0 < N; p0 += pw.chunk) {
+        const int64_t np = N - p0 < pw.chunk ? N - p0 : pw.chunk;
+        rc = assign_chunk(X, dtype, d, nullptr, p0, np, C, M, pw, cand + p0 * M, nullptr, st,
+                          w.cdd + p0 * M);
+        if (rc) return rc;
+    }
+    uint32_t* sel = assign_out ? assign_out : w.sel;
+    const int test = isinf(a.eps) ? 0 : 1;
+    const double e2 = a.eps * a.eps;
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.stats, 0, 2 * sizeof(unsigned long long), st));
+    if (a.cap == 0) {
+        ANN_CHECK_CUDA(cudaMemsetAsync(w.rad2b, 0, sizeof(uint32_t) * (size_t)w.nb * C, st));
+        const unsigned g = (unsigned)((N + 255) / 256);
+        k_sel_orig<<<g, 256, 0, st>>>(cand, w.cdd, N, M, omega, a.block, C, w.rad2b, sel);
+        ANN_CHECK_LAUNCH();
+        k_sel_thresholds<<<(C + 127) / 128, 128, 0, st>>>(w.rad2b, w.nb, C,
+                                                          test ? a.eps : 0.0, a.tau0, w.rthr);
+        ANN_CHECK_LAUNCH();
+        k_sel_rep<<<g, 256, 0, st>>>(cand, w.cdd, N, M, omega, a.block, C, test, e2, w.rthr, sel,
+                                     w.stats);
+        ANN_CHECK_LAUNCH();
+    } else {
+        const size_t smem = sel_seq_smem(C, M);
+        ANN_CHECK_CUDA(cudaFuncSetAttribute(k_sel_seq, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        k_sel_seq<<<1, 1024, smem, st>>>(cand, w.cdd, N, M, omega, a.block, C,
+                                         (unsigned long long)a.cap, test, e2,
+                                         test ? a.eps : 0.0, a.tau0, sel, w.oj, w.stats);
+        ANN_CHECK_LAUNCH();
+    }
+    if (stats_out)
+        ANN_CHECK_CUDA(cudaMemcpyAsync(stats_out, w.stats, 2 * sizeof(int64_t),
+                                       cudaMemcpyDeviceToDevice, st));
+    return shard_lists(sel, N, omega, C, pw, members_out, offsets_out, st);
 }
 
 }  // namespace ann

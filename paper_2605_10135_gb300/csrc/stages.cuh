@@ -34,6 +34,33 @@ int run_partition(const void* X, int64_t N, int d, int dtype, int C, int r, cons
                   uint32_t* members_out, int64_t* offsets_out, const PartitionWs& w,
                   cudaStream_t st);
 
+// Blockwise-adaptive assignment with selective replication (Sec. V).
+struct SelectiveArgs {
+    double eps;    // +inf: no distance / radius test
+    double tau0;   // tau of the first block
+    int64_t block; // vectors per block
+    int64_t cap;   // members per shard, 0 = no limit
+    int omega;     // most shards per vector
+    int M;         // candidate centroids per vector
+};
+struct SelectiveWs {
+    PartitionWs p;      // k-means state; p.assign holds the [N x M] candidate lists
+    float* cdd;         // [N x M] d32 of the candidates
+    uint32_t* sel;      // [N x omega] assignment (when the caller passes none)
+    uint8_t* oj;        // [N] candidate index of each original
+    uint32_t* rad2b;    // [nb x C] squared radius per block (float bits)
+    float* rthr;        // [nb x C] radius-test thresholds
+    unsigned long long* stats;  // [2] replicas, overflowed originals
+    int64_t nb;
+};
+size_t selective_ws(int64_t N, int d, int C, int64_t S, int M, int omega, int64_t block,
+                    SelectiveWs* out, void* base, size_t cap);
+int run_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
+                            const float* init_centroids, const uint32_t* sample_idx, int64_t S,
+                            int iters, const SelectiveArgs& a, float* centroids_out,
+                            uint32_t* assign_out, uint32_t* members_out, int64_t* offsets_out,
+                            int64_t* stats_out, const SelectiveWs& w, cudaStream_t st);
+
 // ---- kNN tiles --------------------------------------------------------------------
 struct KnnProblem {
     int64_t a_row0;    // first row of the problem in the A buffer (padded index space)

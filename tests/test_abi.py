@@ -95,3 +95,34 @@ def test_host_side_failures_return_status_codes(L):
     rc = L.ann_shard_knn(dummy, 1000, 64, 3, dummy, ct.cast(buf, ct.c_void_p), 2, 2000, 16, 0, 0,
                          None, dummy, dummy, None, 0, None)
     assert rc == 5 and b"workspace" in L.ann_last_error().lower()
+
+
+def test_selective_partition_arguments_validate_on_host(L):
+    n = ct.c_size_t(0)
+    P = ann._SelectiveParams
+    ok = P(1.2, 2.0, 4096, 0, 2, 8)
+    assert L.ann_partition_selective_workspace(10000, 96, 16, 1000, ct.byref(ok), ct.byref(n)) == 0
+    small = n.value
+    assert small > 10000 * 8 * 8
+    capped = P(1.2, 2.0, 4096, 3000, 2, 8)
+    assert L.ann_partition_selective_workspace(10000, 96, 16, 1000, ct.byref(capped),
+                                               ct.byref(n)) == 0
+    inf = P(float("inf"), 1.0, 1, 0, 3, 16)
+    assert L.ann_partition_selective_workspace(10000, 96, 16, 1000, ct.byref(inf), ct.byref(n)) == 0
+    bad = [P(1.2, 2.0, 4096, 0, 9, 8),            # omega > cand
+           P(1.2, 2.0, 4096, 0, 2, 17),           # cand > C
+           P(1.2, 2.0, 0, 0, 2, 8),               # block
+           P(float("nan"), 2.0, 4096, 0, 2, 8),   # eps
+           P(-1.0, 2.0, 4096, 0, 2, 8),
+           P(1.2, float("inf"), 4096, 0, 2, 8),   # tau0
+           P(1.2, 2.0, 4096, -5, 2, 8)]           # capacity
+    for p in bad:
+        assert L.ann_partition_selective_workspace(10000, 96, 16, 1000, ct.byref(p),
+                                                   ct.byref(n)) == 1
+    assert L.ann_partition_selective_workspace(10000, 96, 16, 1000, None, ct.byref(n)) == 1
+    big = P(1.2, 2.0, 4096, 0, 2, 33)
+    assert L.ann_partition_selective_workspace(10000, 96, 64, 1000, ct.byref(big), ct.byref(n)) == 1
+    dummy = ct.c_void_p(16)
+    rc = L.ann_partition_selective(dummy, 10000, 96, 0, 16, dummy, dummy, 1000, 5, ct.byref(ok),
+                                   dummy, None, dummy, dummy, None, None, 0, None)
+    assert rc == 5 and b"workspace" in L.ann_last_error().lower()
