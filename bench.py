@@ -240,7 +240,9 @@ def main():
     ap.add_argument("--tau0", type=float, default=2.0)
     ap.add_argument("--sel-block", type=int, default=65536, help="vectors per assignment block")
     ap.add_argument("--capacity", type=int, default=0, help="members per shard, 0 = no limit")
-    ap.add_argument("--cand", type=int, default=16, help="candidate centroids per vector")
+    ap.add_argument("--cand", type=int, default=8, help="candidate centroids per vector")
+    ap.add_argument("--entries", type=int, default=1024,
+                    help="search also from the nearest of this many sampled entry vectors")
     ap.add_argument("--tile-counters", action="store_true",
                     help="after timing, run one step with the counting kernel variant and "
                          "report its per-role cycle counters")
@@ -390,6 +392,10 @@ def main():
     entry = int(ann.medoid(Xd).item())
     ids, cnt = ann.search(out["graph"], out["degree"], Xd, Q, entry, 64, 10)
     recall = float(ann.recall(ids, gt, 10).item())
+    ent = torch.from_numpy(np.sort(np.random.default_rng(w.seed + 22).choice(
+        w.N, min(args.entries, w.N), replace=False)).astype(np.int32)).to(dev)
+    ids_e, cnt_e = ann.search_entries(out["graph"], out["degree"], Xd, Q, ent, 64, 10)
+    recall_e = float(ann.recall(ids_e, gt, 10).item())
     status = ann.device_status()
 
     # one more step with events between the stages (not timed above)
@@ -514,6 +520,8 @@ def main():
                 "member_rows": int(out["offsets"][-1].item())}),
             "search_recall_at_10": recall, "search_Ls": 64, "queries": args.nq,
             "mean_dist_count": float(cnt.float().mean().item()),
+            "search_recall_at_10_from_entries": recall_e, "search_entries": int(ent.numel()),
+            "mean_dist_count_from_entries": float(cnt_e.float().mean().item()),
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
             "distance_tflops": achieved,
             "stages_ms": stages_ms,

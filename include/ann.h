@@ -329,6 +329,17 @@ int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
 int ann_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
                int d, int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
                uint32_t* out_id, uint32_t* out_count, void* stream);
+/* ann_search_entries: ann_search, except that each query starts from the vector
+ *   of smallest (d32(q, x), id) among the ne ids in entries (device uint32[ne];
+ *   ids >= N are skipped; a query with no valid entry returns ANN_PAD ids and
+ *   sets the bad-input bit of the device status).  out_count includes the
+ *   distances to the valid entries.  Not in the paper, which searches from the medoid: an exact
+ *   kNN graph of well-separated clusters has no edges between them, so one
+ *   entry reaches only its own cluster.  Limits: 1 <= ne <= 2^20. */
+int ann_search_entries(const uint32_t* graph, const uint32_t* degree, int R, const void* X,
+                       int64_t N, int d, int dtype, const void* Q, int64_t nq,
+                       const uint32_t* entries, int ne, int Ls, int topk, uint32_t* out_id,
+                       uint32_t* out_count, void* stream);
 int ann_recall(const uint32_t* found, int found_stride, const uint32_t* truth, int truth_stride,
                int64_t nq, int kk, float* recall_out, void* stream);
 

@@ -72,6 +72,8 @@ def lib():
             "ann_search": (I32, [P, P, I32, P, I64, I32, I32, P, I64, ct.c_uint32, I32, I32, P, P,
                                  P]),
             "ann_recall": (I32, [P, I32, P, I32, I64, I32, P, P]),
+            "ann_search_entries": (I32, [P, P, I32, P, I64, I32, I32, P, I64, P, I32, I32, I32, P,
+                                         P, P]),
             "ann_search_eval": (I32, [P, P, I32, P, I64, I32, I32, P, I64, P, ct.c_uint32, I32, P,
                                       P, P, P]),
             "ann_learned_train_workspace": (I32, [I64, I32, I32, I64, I32, I32, PSZ]),
@@ -408,6 +410,24 @@ def search(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q: torch.
     cnt = torch.empty(nq, dtype=torch.int32, device=X.device)
     _check(lib().ann_search(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype], _ptr(Q), nq,
                             int(entry), Ls, topk, _ptr(out), _ptr(cnt), _stream()))
+    return out, cnt
+
+
+def search_entries(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q: torch.Tensor,
+                   entries: torch.Tensor, Ls: int, topk: int = 10):
+    """Beam search of each query from its nearest listed entry (smallest (d32, id)):
+    (ids [nq, topk], distance counts [nq], entry distances included)."""
+    graph, degree = _cuda(graph, "graph"), _cuda(degree, "degree")
+    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    entries = _cuda(entries.to(torch.int32), "entries")
+    N, d = X.shape
+    R = graph.shape[1]
+    nq = Q.shape[0]
+    out = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
+    cnt = torch.empty(nq, dtype=torch.int32, device=X.device)
+    _check(lib().ann_search_entries(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype],
+                                    _ptr(Q), nq, _ptr(entries), entries.numel(), Ls, topk,
+                                    _ptr(out), _ptr(cnt), _stream()))
     return out, cnt
 
 

@@ -671,8 +671,21 @@ int ann_search(const uint32_t* graph, const uint32_t* degree, int R, const void*
     int rc = search_args(R, N, d, dtype, nq, entry, Ls, topk);
     if (rc) return rc;
     ANN_REQUIRE(nq == 0 || (graph && degree && X && Q && out_id && out_count), "NULL pointer");
-    return run_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, Ls, topk, out_id, out_count,
-                      (cudaStream_t)stream);
+    return run_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, nullptr, 0, Ls, topk,
+                      out_id, out_count, (cudaStream_t)stream);
+}
+
+int ann_search_entries(const uint32_t* graph, const uint32_t* degree, int R, const void* X,
+                       int64_t N, int d, int dtype, const void* Q, int64_t nq,
+                       const uint32_t* entries, int ne, int Ls, int topk, uint32_t* out_id,
+                       uint32_t* out_count, void* stream) {
+    int rc = search_args(R, N, d, dtype, nq, 0, Ls, topk);
+    if (rc) return rc;
+    ANN_REQUIRE(ne >= 1 && ne <= (1 << 20), "ne must be in [1, 2^20]");
+    ANN_REQUIRE(nq == 0 || (graph && degree && X && Q && entries && out_id && out_count),
+                "NULL pointer");
+    return run_search(graph, degree, R, X, N, d, dtype, Q, nq, 0, entries, ne, Ls, topk, out_id,
+                      out_count, (cudaStream_t)stream);
 }
 
 int ann_recall(const uint32_t* found, int found_stride, const uint32_t* truth, int truth_stride,

@@ -46,9 +46,9 @@ constexpr int LSMAX = 256;
 
 __global__ void k_search(const uint32_t* __restrict__ graph, const uint32_t* __restrict__ degree,
                          int R, const void* X, int64_t N, int d, int dtype, const void* Q, int64_t nq,
-                         uint32_t entry, int Ls, int topk, int vis_mask,
-                         uint32_t* __restrict__ out_id, uint32_t* __restrict__ out_count,
-                         int* status) {
+                         uint32_t entry, const uint32_t* __restrict__ entries, int ne, int Ls,
+                         int topk, int vis_mask, uint32_t* __restrict__ out_id,
+                         uint32_t* __restrict__ out_count, int* status) {
     extern __shared__ __align__(16) uint8_t sm[];
     float* qv = (float*)sm;                       // [d]
     uint32_t* lid = (uint32_t*)(qv + ((d + 3) & ~3));  // [LSMAX]
@@ -61,8 +61,36 @@ __global__ void k_search(const uint32_t* __restrict__ graph, const uint32_t* __r
     for (int t = lane; t < d; t += 32) qv[t] = load_elem(Q, dtype, q * d + t);
     for (int h = lane; h <= vis_mask; h += 32) vis[h] = ANN_PAD;
     __syncwarp();
-    int n = 1;
     uint32_t count = 1, nvis = 1;
+    if (entries) {
+        // start from the listed entry of smallest (d32, id): lane-parallel, then a
+        // warp argmin on the packed (distance bits, id) key
+        unsigned long long best = ~0ull;
+        uint32_t nvalid = 0;
+        for (int e = lane; e < ne; e += 32) {
+            uint32_t v = entries[e];
+            if (v >= (uint32_t)N) continue;
+            ++nvalid;
+            const float dv = d32_vec(qv, X, dtype, v, d);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(dv) << 32) | (unsigned long long)v;
+            best = key < best ? key : best;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, o);
+            best = x < best ? x : best;
+            nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
+        }
+        if (best == ~0ull) {  // no valid entry
+            if (lane == 0) atomicOr(status, DEV_BAD_INPUT);
+            for (int e = lane; e < topk; e += 32) out_id[q * topk + e] = ANN_PAD;
+            if (lane == 0) out_count[q] = 0;
+            return;
+        }
+        entry = (uint32_t)(best & 0xFFFFFFFFull);
+        count += nvalid;
+    }
+    int n = 1;
     if (lane == 0) {
         lid[0] = entry;
         ld[0] = d32_vec(qv, X, dtype, entry, d);
@@ -211,15 +239,16 @@ int search_vis_mask(int Ls, int R) {
 }
 
 int run_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N, int d,
-               int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
-               uint32_t* out_id, uint32_t* out_count, cudaStream_t st) {
+               int dtype, const void* Q, int64_t nq, uint32_t entry, const uint32_t* entries,
+               int ne, int Ls, int topk, uint32_t* out_id, uint32_t* out_count, cudaStream_t st) {
     if (nq == 0) return ANN_OK;
     const int vis_mask = search_vis_mask(Ls, R);
     const size_t smem = (size_t)((d + 3) & ~3) * 4 + (size_t)LSMAX * 12 + (size_t)(vis_mask + 1) * 4;
     ANN_CHECK_CUDA(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
-    k_search<<<(unsigned)nq, 32, smem, st>>>(graph, degree, R, X, N, d, dtype, Q, nq, entry, Ls, topk,
-                                             vis_mask, out_id, out_count, device_status_ptr());
+    k_search<<<(unsigned)nq, 32, smem, st>>>(graph, degree, R, X, N, d, dtype, Q, nq, entry,
+                                             entries, ne, Ls, topk, vis_mask, out_id, out_count,
+                                             device_status_ptr());
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }

@@ -175,8 +175,9 @@ int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
 // ---- query side ------------------------------------------------------------------
 int search_vis_mask(int Ls, int R);
 int run_search(const uint32_t* graph, const uint32_t* degree, int R, const void* X, int64_t N,
-               int d, int dtype, const void* Q, int64_t nq, uint32_t entry, int Ls, int topk,
-               uint32_t* out_id, uint32_t* out_count, cudaStream_t st);
+               int d, int dtype, const void* Q, int64_t nq, uint32_t entry,
+               const uint32_t* entries, int ne, int Ls, int topk, uint32_t* out_id,
+               uint32_t* out_count, cudaStream_t st);
 int run_recall(const uint32_t* found, int fs, const uint32_t* truth, int ts, int64_t nq, int kk,
                float* recall_out, unsigned long long* hits, cudaStream_t st);
 

@@ -270,6 +270,36 @@ def test_search_bit_exact(kind):
     assert abs(float(rec.item()) - oracle.recall_at(rids, gt)) < 1e-6
 
 
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_search_from_nearest_entry_bit_exact(kind):
+    """Each query starts at its nearest listed entry by (d32, id), picked by brute
+    force on the host with the oracle's d32; ids >= N in the list are skipped."""
+    if kind == "u8":
+        X = datagen.clustered_u8(3000, 64, 16, seed=171)
+        Q = datagen.clustered_u8(60, 64, 16, seed=172)
+    else:
+        X = datagen.gaussian_mixture_f32(3000, 32, seed=173)
+        Q = datagen.gaussian_mixture_f32(60, 32, seed=174)
+    mem, off = _oracle_shards(X, 4, 2, seed=175)
+    oid, od = oracle.shard_knn(X, mem, off, 24)
+    qid, qd = oracle.prune(oid, od, mem, off, 12)
+    og, ogd, odeg = oracle.merge(qid, qd, mem, off, X.shape[0])
+    rng = np.random.default_rng(176)
+    entries = np.concatenate([rng.choice(len(X), 40, replace=False),
+                              [len(X) + 5]]).astype(np.uint32)
+    if kind == "u8":  # a listed id twice: computed twice, counted twice
+        entries[3] = entries[7]
+    Ls = 32
+    gids, gcnt = ann.search_entries(T(og), T(odeg), T(X), T(Q), T(entries), Ls, 10)
+    gids, gcnt = as_u32(gids), gcnt.cpu().numpy().astype(np.int64)
+    valid = [int(e) for e in entries if e < len(X)]
+    for qi in range(len(Q)):
+        e = min(valid, key=lambda v: (oracle.d32(Q[qi], X[v]), v))
+        rids, rcnt = oracle.search(og, odeg, X, Q[qi:qi + 1], e, Ls, 10)
+        assert np.array_equal(gids[qi], rids[0])
+        assert gcnt[qi] == rcnt[0] + len(valid)
+
+
 # ------------------------------------------------------------------- end to end
 
 def test_end_to_end_u8_bit_exact():
