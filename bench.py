@@ -3,7 +3,9 @@
 A step is one pass of the whole build on the 1M-vector Sift-like workload
 (N=1e6, d=128 uint8, 16 shards, r=2, k=64, R=32): k-means partition with
 replication -> exact per-shard kNN (tcgen05 distance tiles + fused top-k) ->
-rank-detour prune -> dedup-then-reprune merge, inputs resident in HBM.
+rank-detour prune -> dedup-then-reprune merge, inputs resident in HBM.  The
+build is captured once as a CUDA graph and every step replays it (all kernels
+run again); --eager launches every kernel from the host instead.
 
 Prints one JSON line (rank 0).  value = vectors indexed per second over all
 ranks; e2e = the same with the vectors copied from pinned host memory and the
@@ -183,7 +185,9 @@ def union_recall_at_10(ann, Xd, out, N, nq, seed):
     import torch
     rng = np.random.default_rng(seed)
     vs = np.sort(rng.choice(N, min(nq, N), replace=False))
-    q = Xd[torch.from_numpy(vs).to(Xd.device)]
+    dev = out["graph"].device
+    q = (Xd[torch.from_numpy(vs).to(Xd.device)] if Xd.is_cuda
+         else Xd[torch.from_numpy(vs)]).to(dev)
     gt_id, _ = ann.knn_query(Xd, q, 11)
     gt = gt_id.cpu().numpy().view(np.uint32)
     members = out["members"].cpu().numpy().view(np.uint32)
@@ -225,7 +229,10 @@ def main():
                          "(32-d MLP embedding screened, re-ranked exactly)")
     ap.add_argument("--rerank-k", type=int, default=0, help="screened list width (0: default)")
     ap.add_argument("--graph", action="store_true",
-                    help="capture one whole build as a CUDA graph and time its replays")
+                    help="capture one whole build as a CUDA graph and time its replays (the "
+                         "default where the build is capturable)")
+    ap.add_argument("--eager", action="store_true",
+                    help="time eager builds (every kernel launched from the host each step)")
     ap.add_argument("--autotune", action="store_true",
                     help="time the candidate tile plans during the first warm-up step")
     ap.add_argument("--learn-steps", type=int, default=300)
@@ -241,6 +248,9 @@ def main():
     ap.add_argument("--sel-block", type=int, default=65536, help="vectors per assignment block")
     ap.add_argument("--capacity", type=int, default=0, help="members per shard, 0 = no limit")
     ap.add_argument("--cand", type=int, default=8, help="candidate centroids per vector")
+    ap.add_argument("--host-x", action="store_true",
+                    help="leave the vectors in pinned host memory: the kernels read them over "
+                         "the host link (NVLink-C2C) instead of from a device copy")
     ap.add_argument("--entries", type=int, default=1024,
                     help="search also from the nearest of this many sampled entry vectors")
     ap.add_argument("--tile-counters", action="store_true",
@@ -279,7 +289,7 @@ def main():
     sample, init_rows = w.kmeans_inputs()
     init = X[init_rows].astype(np.float32)
     Xh = torch.from_numpy(X).pin_memory()
-    Xd = Xh.to(dev)
+    Xd = Xh if args.host_x else Xh.to(dev)
     init_d = torch.from_numpy(init).to(dev)
     samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
     prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "f16": ann.F16_RERANK,
@@ -317,7 +327,10 @@ def main():
         out = step(Xd)
     torch.cuda.synchronize()
     ann.autotune(0)
-    if args.graph:
+    use_graph = args.graph or not args.eager
+    if use_graph and (prec == ann.LEARNED or sel is not None):
+        use_graph = False  # host decisions between stages: not capturable
+    if use_graph:
         captured = ann.CapturedBuild(Xd, cfg, init_d, samp_d)
         for _ in range(2):
             out = step(Xd)
@@ -369,7 +382,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        xd = Xh.to(dev, non_blocking=True)
+        xd = Xh if args.host_x else Xh.to(dev, non_blocking=True)
         o = step(xd)
         graph_h.copy_(o["graph"], non_blocking=True)
         gdist_h.copy_(o["gdist"], non_blocking=True)
@@ -526,7 +539,9 @@ def main():
             "distance_tflops": achieved,
             "stages_ms": stages_ms,
             "tile_plan_autotuned": tuned,
-            "cuda_graph": bool(args.graph),
+            "cuda_graph": bool(use_graph),
+            "vectors_in": ("pinned host memory, read by the kernels over NVLink-C2C"
+                           if args.host_x else "device memory"),
             "device_status": status,
         },
         "roofline": {

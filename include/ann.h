@@ -12,6 +12,16 @@
  *  - Every pointer argument is a DEVICE pointer (cudaMalloc / PyTorch CUDA
  *    tensor) owned by the caller, unless the argument says "host".  The
  *    library never frees or retains caller memory.
+ *  - The vectors X of ann_partition, ann_partition_selective, ann_shard_knn,
+ *    ann_medoid, ann_knn_query, ann_search and ann_search_entries, and their
+ *    queries Q, may instead be page-locked
+ *    host memory mapped into the device's address space at the same address
+ *    (cudaHostAlloc / cudaHostRegister with unified addressing, a pinned
+ *    PyTorch CPU tensor): the kernels then read the vectors over the host link
+ *    (NVLink-C2C on Grace-Blackwell), so X need not fit in device memory.
+ *    Pageable host memory or another device's memory is refused with
+ *    ANN_ERR_INVALID_ARG before any launch (the check runs once the workspace
+ *    checks have passed).
  *  - Scratch memory comes from a caller-supplied workspace of at least the
  *    size the matching *_workspace() call reports; it may be reused after the
  *    call's work on the stream has completed.

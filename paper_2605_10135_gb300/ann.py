@@ -112,6 +112,19 @@ def _cuda(t: torch.Tensor, name: str) -> torch.Tensor:
     return t.contiguous()
 
 
+def _vectors(t: torch.Tensor, name: str):
+    """A vector array the kernels may read: a CUDA tensor, or a pinned (page-locked)
+    CPU tensor, which the kernels read over the host link.  Returns (tensor, the
+    CUDA device that outputs go to)."""
+    if t.is_cuda:
+        return t.contiguous(), t.device
+    if not t.is_pinned():
+        raise ValueError(f"{name} must be a CUDA tensor or a pinned CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a pinned CPU tensor must be contiguous")
+    return t, torch.device("cuda", torch.cuda.current_device())
+
+
 def _ws(nbytes: int, device) -> torch.Tensor | None:
     if nbytes <= 256:
         return None
@@ -194,12 +207,11 @@ def device_status() -> int:
 def partition(X: torch.Tensor, C: int, r: int, init_centroids: torch.Tensor,
               sample_idx: torch.Tensor, iters: int):
     """k-means shards + replication into the r nearest: (centroids, members, offsets)."""
-    X = _cuda(X, "X")
+    X, dev = _vectors(X, "X")
     N, d = X.shape
     init = _cuda(init_centroids.to(torch.float32), "init_centroids")
     sample = _cuda(sample_idx.to(torch.int32), "sample_idx")
     S = sample.numel()
-    dev = X.device
     cent = torch.empty((C, d), dtype=torch.float32, device=dev)
     members = torch.empty(N * r, dtype=torch.int32, device=dev)
     offsets = torch.empty(C + 1, dtype=torch.int64, device=dev)
@@ -232,12 +244,11 @@ def partition_selective(X: torch.Tensor, C: int, omega: int, init_centroids: tor
     """k-means shards + selective replication: (centroids, members [rows], offsets,
     stats [2] = (replicas, overflowed originals), assign [N, omega] or None).
     Reads offsets[C] back to the host (the number of member rows)."""
-    X = _cuda(X, "X")
+    X, dev = _vectors(X, "X")
     N, d = X.shape
     init = _cuda(init_centroids.to(torch.float32), "init_centroids")
     sample = _cuda(sample_idx.to(torch.int32), "sample_idx")
     S = sample.numel()
-    dev = X.device
     p = _SelectiveParams(float(sel.epsilon), float(sel.tau0), int(sel.block), int(sel.capacity),
                          int(omega), int(min(sel.cand, C)))
     cent = torch.empty((C, d), dtype=torch.float32, device=dev)
@@ -259,13 +270,12 @@ def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: 
               precision: int = EXACT, rerank_k: int = 0, model: torch.Tensor | None = None):
     """kNN inside every shard: (knn_id [rows, k] int32, knn_d [rows, k] float32).
     model: the MLP parameters (float32, on the device) for precision=LEARNED."""
-    X = _cuda(X, "X")
+    X, dev = _vectors(X, "X")
     N, d = X.shape
     members = _cuda(members, "members")
     offsets = _cuda(offsets, "offsets")
     C = offsets.numel() - 1
     rows = members.numel()
-    dev = X.device
     knn_id = torch.empty((rows, k), dtype=torch.int32, device=dev)
     knn_d = torch.empty((rows, k), dtype=torch.float32, device=dev)
     L = lib()
@@ -360,12 +370,12 @@ def merge(pr_id: torch.Tensor, pr_d: torch.Tensor, members: torch.Tensor, offset
 
 def medoid(X: torch.Tensor) -> torch.Tensor:
     """Device int32[1]: the vector nearest to the mean (the search entry point)."""
-    X = _cuda(X, "X")
+    X, dev = _vectors(X, "X")
     N, d = X.shape
-    out = torch.empty(1, dtype=torch.int32, device=X.device)
+    out = torch.empty(1, dtype=torch.int32, device=dev)
     L = lib()
     nb = _wsize(L.ann_medoid_workspace, N, d)
-    ws = _ws(nb, X.device)
+    ws = _ws(nb, dev)
     _check(L.ann_medoid(_ptr(X), N, d, _DT[X.dtype], _ptr(out), _ptr(ws), nb, _stream()))
     return out
 
@@ -385,14 +395,14 @@ def medoid_noalloc(X: torch.Tensor, out: torch.Tensor | None = None) -> torch.Te
 
 def knn_query(X: torch.Tensor, Q: torch.Tensor, k: int):
     """Exact top-k of each query over all vectors: (ids [nq, k], dists [nq, k])."""
-    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    (X, dev), (Q, _) = _vectors(X, "X"), _vectors(Q, "Q")
     N, d = X.shape
     nq = Q.shape[0]
-    out_id = torch.empty((nq, k), dtype=torch.int32, device=X.device)
-    out_d = torch.empty((nq, k), dtype=torch.float32, device=X.device)
+    out_id = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    out_d = torch.empty((nq, k), dtype=torch.float32, device=dev)
     L = lib()
     nb = _wsize(L.ann_knn_query_workspace, N, nq, d, _DT[X.dtype], k)
-    ws = _ws(nb, X.device)
+    ws = _ws(nb, dev)
     _check(L.ann_knn_query(_ptr(X), N, _ptr(Q), nq, d, _DT[X.dtype], k, _ptr(out_id), _ptr(out_d),
                            _ptr(ws), nb, _stream()))
     return out_id, out_d
@@ -402,12 +412,12 @@ def search(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q: torch.
            entry: int, Ls: int, topk: int = 10):
     """Best-first beam search of each query: (ids [nq, topk], distance counts [nq])."""
     graph, degree = _cuda(graph, "graph"), _cuda(degree, "degree")
-    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    (X, dev), (Q, _) = _vectors(X, "X"), _vectors(Q, "Q")
     N, d = X.shape
     R = graph.shape[1]
     nq = Q.shape[0]
-    out = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
-    cnt = torch.empty(nq, dtype=torch.int32, device=X.device)
+    out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    cnt = torch.empty(nq, dtype=torch.int32, device=dev)
     _check(lib().ann_search(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype], _ptr(Q), nq,
                             int(entry), Ls, topk, _ptr(out), _ptr(cnt), _stream()))
     return out, cnt
@@ -418,13 +428,13 @@ def search_entries(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q
     """Beam search of each query from its nearest listed entry (smallest (d32, id)):
     (ids [nq, topk], distance counts [nq], entry distances included)."""
     graph, degree = _cuda(graph, "graph"), _cuda(degree, "degree")
-    X, Q = _cuda(X, "X"), _cuda(Q, "Q")
+    (X, dev), (Q, _) = _vectors(X, "X"), _vectors(Q, "Q")
     entries = _cuda(entries.to(torch.int32), "entries")
     N, d = X.shape
     R = graph.shape[1]
     nq = Q.shape[0]
-    out = torch.empty((nq, topk), dtype=torch.int32, device=X.device)
-    cnt = torch.empty(nq, dtype=torch.int32, device=X.device)
+    out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    cnt = torch.empty(nq, dtype=torch.int32, device=dev)
     _check(lib().ann_search_entries(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype],
                                     _ptr(Q), nq, _ptr(entries), entries.numel(), Ls, topk,
                                     _ptr(out), _ptr(cnt), _stream()))
@@ -516,11 +526,12 @@ class CapturedBuild:
                              "back to the host)")
         self.X, self.cfg = X, cfg
         self.init, self.sample = init_centroids, sample_idx
-        side = torch.cuda.Stream(device=X.device)
-        side.wait_stream(torch.cuda.current_stream(X.device))
+        dev = _vectors(X, "X")[1]
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):  # first run: one-time driver and attribute setup
             build_index(X, cfg, init_centroids, sample_idx)
-        torch.cuda.current_stream(X.device).wait_stream(side)
+        torch.cuda.current_stream(dev).wait_stream(side)
         self.graph = torch.cuda.CUDAGraph()
         l0 = launch_count()
         with torch.cuda.graph(self.graph):

@@ -82,6 +82,30 @@ int* device_status_ptr() {
 
 static bool valid_dtype(int dt) { return dt >= ANN_F32 && dt <= ANN_U8; }
 
+// Vector arrays (X, queries) may be device memory of the current device, managed
+// memory, or page-locked host memory mapped into the device's address space at
+// the same address (unified addressing): on a Grace-Blackwell node the kernels
+// then read the vectors from host memory over NVLink-C2C, so X need not fit in
+// HBM.  Anything else (pageable host memory, another device's memory) is refused
+// here instead of being handed to a kernel.
+static int check_readable(const void* p, const char* name) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ANN_ERR_INVALID_ARG, "%s: not a CUDA-visible pointer (%s)", name,
+                    cudaGetErrorString(e));
+    }
+    int cur = -1;
+    ANN_CHECK_CUDA(cudaGetDevice(&cur));
+    if (a.type == cudaMemoryTypeDevice && a.device == cur) return ANN_OK;
+    if (a.type == cudaMemoryTypeManaged) return ANN_OK;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer == p) return ANN_OK;
+    return fail(ANN_ERR_INVALID_ARG,
+                "%s must be memory of the current device or page-locked host memory mapped "
+                "at the same address", name);
+}
+
 static int check_ws(void* ws, size_t have, size_t need) {
     if (need > 256 && (!ws || have < need))
         return fail(ANN_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, have);
@@ -218,6 +242,7 @@ int ann_partition(const void* X, int64_t N, int d, int dtype, int C, int r,
     ANN_REQUIRE(N == 0 || (X && members_out), "NULL pointer");
     ANN_REQUIRE(S == 0 || iters == 0 || sample_idx, "sample_idx is NULL");
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if (N > 0 && (rc = check_readable(X, "X"))) return rc;
     PartitionWs w;
     partition_ws(N, d, C, r, S, &w, ws, ws_bytes);
     if (N == 0) {
@@ -268,6 +293,7 @@ int ann_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
     ANN_REQUIRE(N == 0 || (X && members_out), "NULL pointer");
     ANN_REQUIRE(S == 0 || iters == 0 || sample_idx, "sample_idx is NULL");
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if (N > 0 && (rc = check_readable(X, "X"))) return rc;
     SelectiveWs w;
     selective_ws(N, d, C, S, p->cand, p->omega, p->block, &w, ws, ws_bytes);
     cudaStream_t st = (cudaStream_t)stream;
@@ -430,6 +456,7 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         if ((rc = learned_plan(k, rerank_k, &pl))) return rc;
         if ((rc = check_ws(ws, ws_bytes, learned_knn_bytes(N, d, C, rows, pl)))) return rc;
         if (rows == 0) return ANN_OK;
+        if ((rc = check_readable(X, "X"))) return rc;
         Carver cv(ws, ws_bytes);
         const size_t kb = knn_ws(C, rows, pl, nullptr, nullptr, 0);
         uint8_t* kbase = cv.take<uint8_t>(kb);
@@ -450,6 +477,7 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     size_t need = knn_ws(C, rows, pl, nullptr, nullptr, 0);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
     if (rows == 0) return ANN_OK;
+    if ((rc = check_readable(X, "X"))) return rc;
     KnnWs w;
     knn_ws(C, rows, pl, &w, ws, ws_bytes);
     cudaStream_t st = (cudaStream_t)stream;
@@ -612,6 +640,7 @@ int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, 
     ANN_REQUIRE(valid_dtype(dtype), "bad dtype");
     ANN_REQUIRE(X && entry_out, "NULL pointer");
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if ((rc = check_readable(X, "X"))) return rc;
     double* part;
     float* mean;
     unsigned long long* best;
@@ -646,6 +675,7 @@ int ann_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     ANN_REQUIRE(nq == 0 || (X && Q && out_id && out_d), "NULL pointer");
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
     if (nq == 0) return ANN_OK;
+    if ((rc = check_readable(X, "X")) || (rc = check_readable(Q, "Q"))) return rc;
     KnnPlan pl;
     knn_plan(d, dtype, k, ANN_EXACT, 0, &pl);
     QueryWs w;
@@ -671,6 +701,7 @@ int ann_search(const uint32_t* graph, const uint32_t* degree, int R, const void*
     int rc = search_args(R, N, d, dtype, nq, entry, Ls, topk);
     if (rc) return rc;
     ANN_REQUIRE(nq == 0 || (graph && degree && X && Q && out_id && out_count), "NULL pointer");
+    if (nq > 0 && ((rc = check_readable(X, "X")) || (rc = check_readable(Q, "Q")))) return rc;
     return run_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, nullptr, 0, Ls, topk,
                       out_id, out_count, (cudaStream_t)stream);
 }
@@ -684,6 +715,7 @@ int ann_search_entries(const uint32_t* graph, const uint32_t* degree, int R, con
     ANN_REQUIRE(ne >= 1 && ne <= (1 << 20), "ne must be in [1, 2^20]");
     ANN_REQUIRE(nq == 0 || (graph && degree && X && Q && entries && out_id && out_count),
                 "NULL pointer");
+    if (nq > 0 && ((rc = check_readable(X, "X")) || (rc = check_readable(Q, "Q")))) return rc;
     return run_search(graph, degree, R, X, N, d, dtype, Q, nq, 0, entries, ne, Ls, topk, out_id,
                       out_count, (cudaStream_t)stream);
 }
