@@ -509,6 +509,45 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
                 precision=precision, recall_estimate=est, model=model, selective_stats=sel_stats)
 
 
+def build_index_streamed(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
+                         sample_idx: torch.Tensor) -> dict:
+    """build_index one shard at a time, for inputs whose kNN lists do not fit in
+    device memory at once: after the partition, each shard's kNN lists are built
+    and pruned before the next shard starts, so only the pruned lists of all
+    shards (rows x R) stay resident.  X may be a pinned host tensor (the kernels
+    read it over the host link).  Every output equals build_index's; knn_id /
+    knn_d are not returned.  Reads the shard offsets back to the host."""
+    if cfg.precision == LEARNED:
+        raise ValueError("the learned form is not streamed")
+    N = X.shape[0]
+    sel_stats = None
+    if cfg.selective is None:
+        cent, members, offsets = partition(X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters)
+    else:
+        cent, members, offsets, sel_stats, _ = partition_selective(
+            X, cfg.C, cfg.r, init_centroids, sample_idx, cfg.iters, cfg.selective)
+    off = offsets.cpu().tolist()
+    dev = members.device
+    rows = off[-1]
+    pr_id = torch.empty((rows, cfg.R), dtype=torch.int32, device=dev)
+    pr_d = torch.empty((rows, cfg.R), dtype=torch.float32, device=dev)
+    for s in range(cfg.C):
+        a, b = off[s], off[s + 1]
+        if a == b:
+            continue
+        m_s = members[a:b]
+        o_s = torch.tensor([0, b - a], dtype=torch.int64, device=dev)
+        kid, kd = shard_knn(X, m_s, o_s, cfg.k, cfg.precision, cfg.rerank_k)
+        pid, pd = prune(kid, kd, m_s, o_s, cfg.R, cfg.rule, N=N)
+        pr_id[a:b].copy_(pid)
+        pr_d[a:b].copy_(pd)
+        del kid, kd, pid, pd
+    graph, gdist, degree = merge(pr_id, pr_d, members, offsets, N)
+    return dict(centroids=cent, members=members, offsets=offsets, pr_id=pr_id, pr_d=pr_d,
+                graph=graph, gdist=gdist, degree=degree, precision=cfg.precision,
+                selective_stats=sel_stats)
+
+
 class CapturedBuild:
     """build_index captured once as a CUDA graph and replayed (all precisions but
     LEARNED, whose fallback decision reads its recall estimate on the host).
