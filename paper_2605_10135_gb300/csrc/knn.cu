@@ -731,16 +731,21 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) l0 = clock64();
                     tmem_wait_ld32(vb);
                     if (PROF) s.c_ldw += clock64() - l0;
-                    if (c + 2 < HALF / 32) tmem_ld32(tb + (c + 2) * 32, va);
+                    if (c + 2 < HALF / 32) {
+                        tmem_ld32(tb + (c + 2) * 32, va);
+                    } else {
+                        // the tile's last chunk is in registers: hand the accumulator
+                        // back to the MMA warp before working on it
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acce_bar + 8 * a);
+                    }
                     if (jt + (c + 1) * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
                                         edge, gidrow);
                     __syncwarp();
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce_bar + 8 * a);
         }
         // each warp empties its own buffer (under the lock: the partner may still
         // be sweeping)
