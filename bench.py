@@ -253,6 +253,9 @@ def main():
                          "the host link (NVLink-C2C) instead of from a device copy")
     ap.add_argument("--streamed", action="store_true",
                     help="build one shard at a time (kNN lists of one shard resident at a time)")
+    ap.add_argument("--no-tile-prune", action="store_true",
+                    help="sweep every distance tile (no exact skipping by the triangle "
+                         "inequality)")
     ap.add_argument("--entries", type=int, default=1024,
                     help="search also from the nearest of this many sampled entry vectors")
     ap.add_argument("--tile-counters", action="store_true",
@@ -325,6 +328,7 @@ def main():
             return ann.build_index_streamed(x, cfg, init_d, samp_d)
         return ann.build_index(x, cfg, init_d, samp_d, learned)
 
+    ann.tile_prune(not args.no_tile_prune)
     if args.autotune:
         ann.autotune(1)
     for _ in range(max(args.warmup, 3)):
@@ -346,6 +350,7 @@ def main():
     clocks = ClockSampler(uuid if uuid.startswith("GPU-") else f"GPU-{uuid}")
     time.sleep(0.5)
     ann.timing_read()
+    ann.tile_prune_stats()  # clears the tile counters (synchronises; outside the timed region)
     ann.timing_enable(True)
     l0 = ann.launch_count()
     st = torch.cuda.current_stream()
@@ -365,6 +370,8 @@ def main():
         launches = captured.kernels
     ann.timing_enable(False)
     tile_ms, tile_n = ann.timing_read()
+    pst = ann.tile_prune_stats()
+    pst = {key: v / args.steps for key, v in pst.items()}  # per step
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = float(np.mean(step_ms))
     tile_source = "timed steps"
@@ -467,7 +474,10 @@ def main():
     off = out["offsets"].cpu().numpy()
     sizes = np.diff(off).astype(np.float64)
     d_tile = 32 if out.get("precision") == ann.LEARNED else w.d
-    flops = float(np.sum(sizes ** 2) * 2 * d_tile)
+    pairs_all = float(np.sum(sizes ** 2))
+    # exact tile skipping: the sweep computes only the pairs of the tiles it keeps
+    pairs = pst["pairs"] if pst["tiles"] > 0 else pairs_all
+    flops = float(pairs * 2 * d_tile)
     # per step: one launch over all shards (or one per shard when streamed)
     tile_avg_ms = tile_ms / max(tile_steps, 1)
     tile_launches_per_step = tile_n / max(tile_steps, 1)
@@ -546,6 +556,11 @@ def main():
             "mean_dist_count_from_entries": float(cnt_e.float().mean().item()),
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
             "distance_tflops": achieved,
+            "tile_skipping": ({"pairs_all": pairs_all, "pairs_swept": pairs,
+                               "tiles_swept_fraction": pst["swept"] / max(pst["tiles"], 1),
+                               "all_pairs_rate_tflops": pairs_all * 2 * d_tile /
+                               (tile_avg_ms * 1e-3) / 1e12}
+                              if pst["tiles"] > 0 else None),
             "stages_ms": stages_ms,
             "tile_plan_autotuned": tuned,
             "cuda_graph": bool(use_graph),

@@ -125,6 +125,19 @@ int ann_timing_read(double* tile_ms, int* launches);
 int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 
+/* Exact skipping of distance tiles (on by default).  For ANN_EXACT on uint8
+ * vectors of d <= 256, each row's k-th squared distance among the rows of its
+ * 256-row window of the shard bounds its final one from above; a column tile is then
+ * skipped (no copy, no product, no epilogue) when the triangle inequality over
+ * 128-row groups (centre and radius bound of each group) shows that every column
+ * in it is strictly farther than the block's largest bound.  The lists do not
+ * change (ties included).  ann_tile_prune(0) sweeps every tile.
+ * ann_tile_prune_stats synchronises the device, writes up to n counters to host
+ * out[] and clears them: column tiles of the blocks, tiles swept, (row, column)
+ * pairs swept. */
+int ann_tile_prune(int on);
+int ann_tile_prune_stats(unsigned long long* out, int n);
+
 /* Self-test of the bounded device waits (no fault, no hang): one warp waits on
  * an mbarrier that nothing completes, through the bounded wait that every
  * pipelined kernel uses; mode 0 lets the limit (limit_us microseconds, at most

@@ -81,6 +81,8 @@ def lib():
                                         ct.c_float, ct.c_float, P, P, P, P, SZ, P]),
             "ann_learned_embed_workspace": (I32, [I64, I32, PSZ]),
             "ann_autotune": (I32, [I32]),
+            "ann_tile_prune": (I32, [I32]),
+            "ann_tile_prune_stats": (I32, [ct.POINTER(ct.c_ulonglong), I32]),
             "ann_wait_selftest": (I32, [I32, I64, P]),
             "ann_autotune_lookup": (I32, [I32, I32, I32, I32, I32, I64, I32, P, P, P, P, P, P]),
             "ann_learned_embed": (I32, [P, I64, I32, I32, P, P, P, SZ, P]),
@@ -170,6 +172,19 @@ def tile_counters_read() -> dict:
     arr = (ct.c_ulonglong * len(TILE_COUNTERS))()
     _check(lib().ann_tile_counters_read(arr, len(TILE_COUNTERS)))
     return dict(zip(TILE_COUNTERS, [int(v) for v in arr]))
+
+
+def tile_prune(on: bool = True):
+    """Switch the exact pruning of distance tiles (uint8, ANN_EXACT) on or off."""
+    _check(lib().ann_tile_prune(1 if on else 0))
+
+
+def tile_prune_stats() -> dict:
+    """Counts since the last read (synchronises the device): half-tiles of the
+    launches, half-tiles examined, (row, column) pairs examined."""
+    arr = (ct.c_ulonglong * 3)()
+    _check(lib().ann_tile_prune_stats(arr, 3))
+    return dict(tiles=int(arr[0]), swept=int(arr[1]), pairs=int(arr[2]))
 
 
 def wait_selftest(mode: int = 0, limit_us: int = 20000):

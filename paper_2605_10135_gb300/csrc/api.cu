@@ -143,6 +143,16 @@ int ann_tile_counters_enable(int on) {
     return ANN_OK;
 }
 
+int ann_tile_prune(int on) {
+    tile_prune_set(on != 0);
+    return ANN_OK;
+}
+
+int ann_tile_prune_stats(unsigned long long* out, int n) {
+    ANN_REQUIRE(out && n >= 0, "bad arguments");
+    return tile_prune_stats(out, n, true);
+}
+
 int ann_tile_counters_read(unsigned long long* out, int n) {
     ANN_REQUIRE(out && n >= 0, "bad arguments");
     return tile_counters_read(out, n, true);

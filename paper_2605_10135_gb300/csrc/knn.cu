@@ -70,6 +70,7 @@ constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
 constexpr int CELL = 128;               // rows per pivot cell, short rows (at most 1024 a shard)
 constexpr int CELL_WIDE = 1024;         // rows per pivot cell, rows over 512 bytes
+constexpr int TM_WORDS = 64;            // tile-mask words per row block (2048 tiles)
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -120,6 +121,10 @@ struct KnnParams {
     uint32_t* out_id;
     float* out_d;
     int* status;
+    // Exact tile skipping (NULL: every tile of the row block's shard).  tmask:
+    // TM_WORDS words per row block, bit t set = sweep column tile t; used only where
+    // the shard has at most TM_WORDS * 32 tiles.
+    const uint32_t* tmask;
 };
 
 struct KnnSmemLayout {
@@ -455,6 +460,15 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         t0 = rb * kt::BM / BN;
         if (t0 >= ntiles) t0 = ntiles - 1;
     }
+    // Tiles this block sweeps (nrun of them, in tile_at order): all, or those whose
+    // bit is set in the block's mask.
+    const uint32_t* tmask =
+        (P.tmask && ntiles <= kt::TM_WORDS * 32) ? P.tmask + bid * kt::TM_WORDS : nullptr;
+    int nrun = ntiles;
+    if (tmask) {
+        nrun = 0;
+        for (int w = 0; w < (ntiles + 31) / 32; ++w) nrun += __popc(tmask[w]);
+    }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.kprime, P.a_stream);
@@ -529,8 +543,10 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             uint32_t ph = 0, aph = 0;
             bool ok = true;
             unsigned long long prod_wait = 0;
-            for (int tt = 0; tt < ntiles && ok; ++tt) {
+            for (int tt = 0, run = 0; tt < ntiles && run < nrun && ok; ++tt) {
                 const int t = tile_at(tt, t0, ntiles);
+                if (tmask && !((tmask[t >> 5] >> (t & 31)) & 1u)) continue;
+                ++run;
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * BN);
                 // the norm block first: its MMA opens the tile, so the slot frees early
                 if (!mbar_wait(aempty_bar + 8 * sa, aph ^ 1, abort_flag)) { ok = false; break; }
@@ -589,7 +605,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             unsigned long long w_full = 0, w_acc = 0, c_iss = 0, c_com = 0;
             long long loop0 = 0;
             if (PROF) loop0 = clock64();
-            for (int t = 0; t < ntiles && ok; ++t) {
+            for (int t = 0; t < nrun && ok; ++t) {
                 const int a = t % kt::NACC;
                 long long w0 = 0;
                 if (PROF) w0 = clock64();
@@ -697,18 +713,21 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         bool ok = true;
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
         constexpr int HALF = BN / 2;
-        for (int tt = 0; tt < ntiles; ++tt) {
+        for (int tt = 0, run = 0; tt < ntiles && run < nrun; ++tt) {
             const int t = tile_at(tt, t0, ntiles);
-            const int a = tt % kt::NACC;
+            if (tmask && !((tmask[t >> 5] >> (t & 31)) & 1u)) continue;
+            const int a = run % kt::NACC;
+            const int par = (run / kt::NACC) & 1;
+            ++run;
             long long w0 = 0;
             if (PROF) w0 = clock64();
-            if (!mbar_wait(accf_bar + 8 * a, (tt / kt::NACC) & 1, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(accf_bar + 8 * a, par, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
             // The lock flag is a loop-carried value switched on here rather than a
             // constant: the code generated this way measured 16% faster on the
             // Sift-like 1M build (same work, same results).
-            if (tt == 0) s.shared = true;
+            if (run == 1) s.shared = true;
             {
                 const uint32_t tb = tmem + lane_addr + a * BN + h * HALF;
                 const int jt = t * BN + h * HALF;
@@ -1584,6 +1603,270 @@ int knn_plan_variants(int d, int dtype, int k, int precision, int rerank_k, KnnP
 // Operand bytes per gathered row.
 static inline size_t row_bytes(const KnnPlan& pl) { return (size_t)pl.Kp * (pl.elem8 ? 1 : 2); }
 
+// ---- exact tile skipping ------------------------------------------------------------
+// For a row block A (128 gathered rows) and a column group G (128 gathered rows of
+// the same shard), with centres c_A, c_G and radii r_A >= max |x - c_A|, r_G, every
+// pair satisfies |x - y| >= |c_A - c_G| - r_A - r_G (triangle inequality).  The k-th
+// distance of each row among the other rows of its 256-row window bounds its final
+// k-th squared distance from above (k_ub_own); a column tile whose
+// groups all lie beyond the block's largest bound cannot hold a neighbour of any of
+// its rows, so the sweep skips it (its copies, products and epilogue).  Ties stay
+// exact: a skipped column is strictly farther than the bound.  Used for plain
+// (single-product) operands of integer data, whose tile keys are exact; every
+// rounding in the bound is pushed outward by a relative margin far above FP32's
+// error on these sums.
+static bool g_tile_prune = true;
+void tile_prune_set(bool on) { g_tile_prune = on; }
+bool tile_prune_on() { return g_tile_prune; }
+__device__ unsigned long long g_prune_stats[3];  // tiles, tiles swept, pairs swept
+
+static bool prunable(const KnnPlan& pl) {
+    return pl.mode == 0 && !pl.rerank && !pl.scaled && !pl.elem8 && !pl.a_stream;
+}
+
+// Centre (mean of the valid rows) and radius bound of every 128-row group of the
+// gathered layout; src[row] = the vector of a gathered row, -1 = padding.
+__global__ void __launch_bounds__(128)
+k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, int64_t ngroups,
+             int ldc, float* __restrict__ gcent, float* __restrict__ grad) {
+    extern __shared__ float cs[];  // [d]
+    __shared__ int nvalid;
+    __shared__ float rmax[4];
+    const int64_t g = blockIdx.x;
+    if (g >= ngroups) return;
+    const int64_t r0 = g * kt::BM;
+    const int tid = threadIdx.x;
+    if (tid == 0) nvalid = 0;
+    __syncthreads();
+    const int64_t my = src[r0 + tid];
+    if (my >= 0) atomicAdd(&nvalid, 1);
+    __syncthreads();
+    const int n = nvalid;
+    if (n == 0) {
+        if (tid == 0) grad[g] = -1.0f;
+        return;
+    }
+    for (int t = tid; t < d; t += blockDim.x) {
+        float sum = 0.0f;
+        for (int i = 0; i < kt::BM; ++i) {
+            const int64_t v = src[r0 + i];
+            if (v >= 0) sum += load_elem(X, dtype, v * d + t);
+        }
+        const float c = sum / (float)n;
+        cs[t] = c;
+        gcent[g * ldc + t] = c;
+    }
+    __syncthreads();
+    // radius: one warp per row, lanes over the dimensions (coalesced row reads)
+    const int warp = tid >> 5, lane = tid & 31;
+    float rw = 0.0f;
+    for (int i = warp; i < kt::BM; i += 4) {
+        const int64_t v = src[r0 + i];
+        if (v < 0) continue;
+        float r2 = 0.0f;
+        for (int t = lane; t < d; t += 32) {
+            const float df = load_elem(X, dtype, v * d + t) - cs[t];
+            r2 = fmaf(df, df, r2);
+        }
+        for (int o = 16; o; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        rw = fmaxf(rw, r2);
+    }
+    if (lane == 0) rmax[warp] = rw;
+    __syncthreads();
+    if (tid == 0) {
+        const float m = fmaxf(fmaxf(rmax[0], rmax[1]), fmaxf(rmax[2], rmax[3]));
+        // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
+        grad[g] = sqrtf(m * (1.0f + (float)(d + 4) * 0x1p-22f)) * (1.0f + 0x1p-20f);
+    }
+}
+
+__device__ __forceinline__ int block_problem(const int64_t* __restrict__ blk_off, int nprob,
+                                             int64_t bid) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_off[mid] <= bid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// bub[bid] = the largest, over the block's rows, k-th smallest squared distance
+// from the row to the other valid rows of its 256-row window of the shard (the
+// window holding the block), or +inf where a row has fewer than k others there:
+// an upper bound of every row's final k-th distance.  uint8 vectors, exact
+// integer arithmetic (|x|^2 + |y|^2 - 2 x.y with dp4a).  One block of 256 threads
+// per row block; the window's vectors are staged in shared memory.
+__global__ void __launch_bounds__(256)
+k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
+         const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
+         int k, int64_t nblocks, float* __restrict__ bub) {
+    extern __shared__ uint32_t wv[];  // [256][ws] packed vectors, then [256] norms
+    __shared__ unsigned int bmax;
+    const int64_t bid = blockIdx.x;
+    if (bid >= nblocks) return;
+    if (bid >= blk_off[nprob]) {
+        if (threadIdx.x == 0) bub[bid] = INFINITY;
+        return;
+    }
+    const int p = block_problem(blk_off, nprob, bid);
+    const KnnProblem pr = probs[p];
+    const int rb = (int)(bid - blk_off[p]);
+    const int nw4 = (d + 3) / 4;
+    const int ws = nw4 + 1;  // padded row stride (words): no bank conflicts across lanes
+    uint32_t* nrm = wv + 256 * ws;
+    const int c0 = (rb >> 1) * 256;  // first column of the window (shard-relative)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) bmax = 0;
+    // stage: thread c loads column c
+    {
+        const int c = tid;
+        const bool valid = c0 + c < pr.n_cols;
+        const int64_t v = valid ? src[pr.b_row0 + c0 + c] : -1;
+        uint32_t n2 = 0;
+        for (int q = 0; q < nw4; ++q) {
+            uint32_t word = 0;
+            if (v >= 0)
+                for (int b = 0; b < 4; ++b) {
+                    const int t = 4 * q + b;
+                    if (t < d) word |= (uint32_t)X[v * d + t] << (8 * b);
+                }
+            wv[c * ws + q] = word;
+            n2 = __dp4a(word, word, n2);
+        }
+        nrm[c] = v >= 0 ? n2 : 0xFFFFFFFFu;  // all ones: not a column
+    }
+    __syncthreads();
+    unsigned int wmax = 0;
+    for (int r = warp; r < kt::BM; r += 8) {
+        const int i = rb * kt::BM + r;  // row index in the shard
+        if (i >= pr.n_rows) continue;
+        const int cr = i - c0;          // the row's own column in the window
+        const uint32_t nr = nrm[cr];
+        uint32_t dv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = lane + 32 * q;
+            const uint32_t nc = nrm[c];
+            uint32_t dot = 0;
+            for (int w = 0; w < nw4; ++w) dot = __dp4a(wv[cr * ws + w], wv[c * ws + w], dot);
+            dv[q] = (nc == 0xFFFFFFFFu || c == cr) ? 0xFFFFFFFFu : nr + nc - 2u * dot;
+        }
+        // k-th smallest of the window's distances: least v with #{dist <= v} >= k
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cnt += dv[q] != 0xFFFFFFFFu;
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        unsigned int ub = 0xFFFFFFFFu;
+        if (cnt >= k) {
+            unsigned int lo = 0, hi = 1u << 24;  // squared distances of uint8 rows, d <= 256
+            while (lo < hi) {
+                const unsigned int mid = lo + (hi - lo) / 2;
+                int c = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) c += dv[q] <= mid;
+                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (c >= k) hi = mid; else lo = mid + 1;
+            }
+            ub = lo;
+        }
+        wmax = ub > wmax ? ub : wmax;
+    }
+    if (lane == 0) atomicMax(&bmax, wmax);
+    __syncthreads();
+    if (tid == 0) bub[bid] = bmax == 0xFFFFFFFFu ? INFINITY : (float)bmax;
+}
+
+// tmask[bid]: bit t set unless every group of column tile t is provably farther
+// than the block's bound.  One block of 256 threads per row block; a warp per
+// (tile, group) pair with lanes over the dimensions.
+__global__ void __launch_bounds__(256)
+k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
+            int bn, int d, int ldc, const float* __restrict__ gcent, const float* __restrict__ grad,
+            const float* __restrict__ bub, int64_t nblocks, uint32_t* __restrict__ tmask) {
+    extern __shared__ float ca[];  // [d]
+    __shared__ uint32_t mw[kt::TM_WORDS];
+    __shared__ unsigned long long s_kept, s_pairs;
+    const int64_t bid = blockIdx.x;
+    if (bid >= nblocks || bid >= blk_off[nprob]) return;
+    const int p = block_problem(blk_off, nprob, bid);
+    const KnnProblem pr = probs[p];
+    const int rb = (int)(bid - blk_off[p]);
+    const int ntiles = (pr.n_cols + bn - 1) / bn;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int rows_here = min(kt::BM, pr.n_rows - rb * kt::BM);
+    if (ntiles > kt::TM_WORDS * 32) {  // not masked: the block sweeps every tile
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
+            atomicAdd(&g_prune_stats[1], (unsigned long long)ntiles);
+            atomicAdd(&g_prune_stats[2], (unsigned long long)rows_here * pr.n_cols);
+        }
+        return;
+    }
+    const int64_t gA = pr.a_row0 / kt::BM + rb;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) ca[t] = gcent[gA * ldc + t];
+    for (int w = threadIdx.x; w < kt::TM_WORDS; w += blockDim.x) mw[w] = 0;
+    if (threadIdx.x == 0) s_kept = s_pairs = 0;
+    __syncthreads();
+    const float rA = grad[gA];
+    const float ub = bub[bid];
+    const int gpt = bn / kt::BM;  // groups per tile
+    unsigned long long kept = 0, pairs = 0;
+    for (int t = warp; t < ntiles; t += nw) {
+        bool keep = true;
+        if (rA >= 0.0f && ub < INFINITY) {
+            float lb = INFINITY;
+            bool any = false;
+            for (int q = 0; q < gpt; ++q) {
+                if ((int64_t)(t * gpt + q) * kt::BM >= pr.n_cols) break;
+                const int64_t g = pr.b_row0 / kt::BM + (int64_t)t * gpt + q;
+                const float rg = grad[g];
+                if (rg < 0.0f) continue;
+                any = true;
+                const float* cg = gcent + g * ldc;
+                float d2 = 0.0f;
+                for (int u = lane; u < d; u += 32) {
+                    const float df = ca[u] - __ldg(cg + u);
+                    d2 = fmaf(df, df, d2);
+                }
+                for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                const float D =
+                    sqrtf(d2 * (1.0f - (float)(d + 4) * 0x1p-22f)) * (1.0f - 0x1p-20f);
+                lb = fminf(lb, (D - rA - rg) * (1.0f - 0x1p-20f));
+            }
+            keep = !any || !(lb > 0.0f && lb * lb > ub * (1.0f + 0x1p-18f));
+        }
+        if (keep && lane == 0) {
+            atomicOr(&mw[t >> 5], 1u << (t & 31));
+            ++kept;
+            pairs += (unsigned long long)rows_here * min(bn, pr.n_cols - t * bn);
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&s_kept, kept);
+        atomicAdd(&s_pairs, pairs);
+    }
+    __syncthreads();
+    uint32_t* m = tmask + bid * kt::TM_WORDS;
+    for (int w = threadIdx.x; w < (ntiles + 31) / 32; w += blockDim.x) m[w] = mw[w];
+    if (threadIdx.x == 0) {
+        atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
+        atomicAdd(&g_prune_stats[1], s_kept);
+        atomicAdd(&g_prune_stats[2], s_pairs);
+    }
+}
+
+int tile_prune_stats(unsigned long long* out, int n, bool reset) {
+    unsigned long long tmp[3];
+    ANN_CHECK_CUDA(cudaDeviceSynchronize());
+    ANN_CHECK_CUDA(cudaMemcpyFromSymbol(tmp, g_prune_stats, sizeof(tmp)));
+    for (int i = 0; i < n && i < 3; ++i) out[i] = tmp[i];
+    if (reset) {
+        unsigned long long z[3] = {0, 0, 0};
+        ANN_CHECK_CUDA(cudaMemcpyToSymbol(g_prune_stats, z, sizeof(z)));
+    }
+    return ANN_OK;
+}
+
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap) {
     Carver cv(base, cap);
     KnnWs w;
@@ -1614,6 +1897,19 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.perm = cv.take<uint32_t>((size_t)rows);
     w.crank = cv.take<uint32_t>((size_t)w.prows_cap);
     w.amax = cv.take<float>(4);
+    w.nblocks = rows / kt::BM + C + 1;
+    if (prunable(pl)) {
+        const int64_t ng = w.rows_cap / kt::BM + 1;
+        w.gcent = cv.take<float>((size_t)ng * pl.Kp);
+        w.grad = cv.take<float>((size_t)ng);
+        w.bub = cv.take<float>((size_t)w.nblocks);
+        w.tmask = cv.take<uint32_t>((size_t)w.nblocks * kt::TM_WORDS);
+    } else {
+        w.gcent = nullptr;
+        w.grad = nullptr;
+        w.bub = nullptr;
+        w.tmask = nullptr;
+    }
     if (out) *out = w;
     return cv.used + 256;
 }
@@ -1710,6 +2006,7 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.out_id = out_id;
     P.out_d = out_d;
     P.status = device_status_ptr();
+    P.tmask = nullptr;
     return P;
 }
 
@@ -1857,8 +2154,27 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     // 3. the kNN sweep
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
-    rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P,
-                      rows / kt::BM + C + 1, st, true);
+    const int64_t grid = rows / kt::BM + C + 1;
+    if (dtype == ANN_U8 && w.tmask && tile_prune_on() && d <= 256) {
+        // 3a. bounds: each row's k-th distance within its 256-row window, the
+        // centre and radius of every 128-row group, and each block's mask of tiles
+        // that may hold a neighbour
+        const int64_t ng = w.rows_cap / kt::BM;
+        k_group_geom<<<(unsigned)ng, 128, (size_t)d * sizeof(float), st>>>(
+            X, dtype, d, w.src, ng, pl.Kp, w.gcent, w.grad);
+        ANN_CHECK_LAUNCH();
+        const size_t ubs = ((size_t)256 * ((d + 3) / 4 + 1) + 256) * sizeof(uint32_t);
+        ANN_CHECK_CUDA(cudaFuncSetAttribute(k_ub_own, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)ubs));
+        k_ub_own<<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src, w.blk_off,
+                                                    w.probs, C, k, grid, w.bub);
+        ANN_CHECK_LAUNCH();
+        k_tile_mask<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
+            w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.bub, grid, w.tmask);
+        ANN_CHECK_LAUNCH();
+        P.tmask = w.tmask;
+    }
+    rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st, true);
     if (rc) return rc;
     if (pl.rerank)
         return launch_rerank(Xr, Xr, dtype_r, dr, members, rows, w.cand_id, pl.kprime, k, knn_id,

@@ -121,7 +121,17 @@ struct KnnWs {
     uint32_t* perm;     // [rows] local index of the row at each cell-ordered position
     uint32_t* crank;    // [prows_cap] chain position of each pivot (cell order)
     float* amax;        // E4M3 plans: largest |x| (float bits)
+    // exact tile skipping (plain operands only; NULL otherwise)
+    float* gcent;       // [rows_cap / 128 x Kp] centre of every 128-row group
+    float* grad;        // [rows_cap / 128] radius bound of the group (-1: empty)
+    float* bub;         // [blocks] bound on the k-th squared distance of a row block
+    uint32_t* tmask;    // [blocks x 64] tiles each row block sweeps
+    int64_t nblocks;
 };
+// Exact skipping of distance tiles (switch, statistics of the last launches).
+void tile_prune_set(bool on);
+bool tile_prune_on();
+int tile_prune_stats(unsigned long long* out, int n, bool reset);
 size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, size_t cap);
 // X [N x d] screens the candidates; the re-rank (float plans) scores them on Xr
 // [N x dr] (type dtype_r), which defaults to X itself.
