@@ -1636,9 +1636,11 @@ k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, i
     if (g >= ngroups) return;
     const int64_t r0 = g * kt::BM;
     const int tid = threadIdx.x;
+    __shared__ int64_t rs[kt::BM];
     if (tid == 0) nvalid = 0;
     __syncthreads();
     const int64_t my = src[r0 + tid];
+    rs[tid] = my;
     if (my >= 0) atomicAdd(&nvalid, 1);
     __syncthreads();
     const int n = nvalid;
@@ -1648,8 +1650,9 @@ k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, i
     }
     for (int t = tid; t < d; t += blockDim.x) {
         float sum = 0.0f;
+#pragma unroll 8
         for (int i = 0; i < kt::BM; ++i) {
-            const int64_t v = src[r0 + i];
+            const int64_t v = rs[i];
             if (v >= 0) sum += load_elem(X, dtype, v * d + t);
         }
         const float c = sum / (float)n;
@@ -1661,7 +1664,7 @@ k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, i
     const int warp = tid >> 5, lane = tid & 31;
     float rw = 0.0f;
     for (int i = warp; i < kt::BM; i += 4) {
-        const int64_t v = src[r0 + i];
+        const int64_t v = rs[i];
         if (v < 0) continue;
         float r2 = 0.0f;
         for (int t = lane; t < d; t += 32) {
@@ -1693,9 +1696,11 @@ __device__ __forceinline__ int block_problem(const int64_t* __restrict__ blk_off
 // bub[bid] = the largest, over the block's rows, k-th smallest squared distance
 // from the row to the other valid rows of its 256-row window of the shard (the
 // window holding the block), or +inf where a row has fewer than k others there:
-// an upper bound of every row's final k-th distance.  uint8 vectors, exact
-// integer arithmetic (|x|^2 + |y|^2 - 2 x.y with dp4a).  One block of 256 threads
-// per row block; the window's vectors are staged in shared memory.
+// an upper bound of every row's final k-th distance.  uint8 vectors with d a
+// multiple of 4, NW4 = d / 4 words at most; exact integer arithmetic
+// (|x|^2 + |y|^2 - 2 x.y with dp4a).  One block of 256 threads per row block; the
+// window's vectors are staged in shared memory, each row's words held in registers.
+template <int NW4>
 __global__ void __launch_bounds__(256)
 k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
          const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
@@ -1711,29 +1716,24 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
     const int p = block_problem(blk_off, nprob, bid);
     const KnnProblem pr = probs[p];
     const int rb = (int)(bid - blk_off[p]);
-    const int nw4 = (d + 3) / 4;
+    const int nw4 = d / 4;
     const int ws = nw4 + 1;  // padded row stride (words): no bank conflicts across lanes
     uint32_t* nrm = wv + 256 * ws;
     const int c0 = (rb >> 1) * 256;  // first column of the window (shard-relative)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bmax = 0;
-    // stage: thread c loads column c
-    {
-        const int c = tid;
+    // stage: warp w loads columns w, w + 8, ...; lane q loads word q (coalesced)
+    for (int c = warp; c < 256; c += 8) {
         const bool valid = c0 + c < pr.n_cols;
         const int64_t v = valid ? src[pr.b_row0 + c0 + c] : -1;
         uint32_t n2 = 0;
-        for (int q = 0; q < nw4; ++q) {
-            uint32_t word = 0;
-            if (v >= 0)
-                for (int b = 0; b < 4; ++b) {
-                    const int t = 4 * q + b;
-                    if (t < d) word |= (uint32_t)X[v * d + t] << (8 * b);
-                }
+        for (int q = lane; q < nw4; q += 32) {
+            const uint32_t word = v >= 0 ? ((const uint32_t*)(X + v * d))[q] : 0u;
             wv[c * ws + q] = word;
             n2 = __dp4a(word, word, n2);
         }
-        nrm[c] = v >= 0 ? n2 : 0xFFFFFFFFu;  // all ones: not a column
+        for (int o = 16; o; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        if (lane == 0) nrm[c] = v >= 0 ? n2 : 0xFFFFFFFFu;  // all ones: not a column
     }
     __syncthreads();
     unsigned int wmax = 0;
@@ -1742,13 +1742,19 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
         if (i >= pr.n_rows) continue;
         const int cr = i - c0;          // the row's own column in the window
         const uint32_t nr = nrm[cr];
+        uint32_t rw[NW4];
+#pragma unroll
+        for (int w = 0; w < NW4; ++w) rw[w] = w < nw4 ? wv[cr * ws + w] : 0u;
         uint32_t dv[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int c = lane + 32 * q;
             const uint32_t nc = nrm[c];
+            const uint32_t* cw = wv + c * ws;
             uint32_t dot = 0;
-            for (int w = 0; w < nw4; ++w) dot = __dp4a(wv[cr * ws + w], wv[c * ws + w], dot);
+#pragma unroll
+            for (int w = 0; w < NW4; ++w)
+                if (w < nw4) dot = __dp4a(rw[w], cw[w], dot);
             dv[q] = (nc == 0xFFFFFFFFu || c == cr) ? 0xFFFFFFFFu : nr + nc - 2u * dot;
         }
         // k-th smallest of the window's distances: least v with #{dist <= v} >= k
@@ -2155,7 +2161,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
     const int64_t grid = rows / kt::BM + C + 1;
-    if (dtype == ANN_U8 && w.tmask && tile_prune_on() && d <= 256) {
+    if (dtype == ANN_U8 && w.tmask && tile_prune_on() && d <= 256 && d % 4 == 0 &&
+        ((uintptr_t)X & 3) == 0) {
         // 3a. bounds: each row's k-th distance within its 256-row window, the
         // centre and radius of every 128-row group, and each block's mask of tiles
         // that may hold a neighbour
@@ -2163,11 +2170,18 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         k_group_geom<<<(unsigned)ng, 128, (size_t)d * sizeof(float), st>>>(
             X, dtype, d, w.src, ng, pl.Kp, w.gcent, w.grad);
         ANN_CHECK_LAUNCH();
-        const size_t ubs = ((size_t)256 * ((d + 3) / 4 + 1) + 256) * sizeof(uint32_t);
-        ANN_CHECK_CUDA(cudaFuncSetAttribute(k_ub_own, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)ubs));
-        k_ub_own<<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src, w.blk_off,
-                                                    w.probs, C, k, grid, w.bub);
+        const size_t ubs = ((size_t)256 * (d / 4 + 1) + 256) * sizeof(uint32_t);
+        if (d <= 128) {
+            ANN_CHECK_CUDA(cudaFuncSetAttribute(
+                k_ub_own<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
+            k_ub_own<32><<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src,
+                                                            w.blk_off, w.probs, C, k, grid, w.bub);
+        } else {
+            ANN_CHECK_CUDA(cudaFuncSetAttribute(
+                k_ub_own<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
+            k_ub_own<64><<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src,
+                                                            w.blk_off, w.probs, C, k, grid, w.bub);
+        }
         ANN_CHECK_LAUNCH();
         k_tile_mask<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
             w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.bub, grid, w.tmask);
