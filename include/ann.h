@@ -126,8 +126,10 @@ int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 
 /* Exact skipping of distance tiles (on by default).  For ANN_EXACT on uint8
- * vectors of d <= 256, each row's k-th squared distance among the rows of its
- * 256-row window of the shard bounds its final one from above; a column tile is then
+ * vectors of d <= 256 (d a multiple of 4) and on float32 vectors of d <= 200, each
+ * row's k'-th squared distance among the rows of its 256-row window of the shard
+ * (k' = the screened list width) bounds its final one from above; for float32 the
+ * bound also carries a margin for the error of the tile keys.  A column tile is then
  * skipped (no copy, no product, no epilogue) when the triangle inequality over
  * 128-row groups (centre and radius bound of each group) shows that every column
  * in it is strictly farther than the block's largest bound.  The lists do not

@@ -1621,17 +1621,18 @@ bool tile_prune_on() { return g_tile_prune; }
 __device__ unsigned long long g_prune_stats[3];  // tiles, tiles swept, pairs swept
 
 static bool prunable(const KnnPlan& pl) {
-    return pl.mode == 0 && !pl.rerank && !pl.scaled && !pl.elem8 && !pl.a_stream;
+    return !pl.scaled && !pl.elem8 && !pl.a_stream;
 }
 
 // Centre (mean of the valid rows) and radius bound of every 128-row group of the
 // gathered layout; src[row] = the vector of a gathered row, -1 = padding.
 __global__ void __launch_bounds__(128)
 k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, int64_t ngroups,
-             int ldc, float* __restrict__ gcent, float* __restrict__ grad) {
+             int ldc, float* __restrict__ gcent, float* __restrict__ grad,
+             float* __restrict__ gmaxn) {
     extern __shared__ float cs[];  // [d]
     __shared__ int nvalid;
-    __shared__ float rmax[4];
+    __shared__ float rmax[4], nmax[4];
     const int64_t g = blockIdx.x;
     if (g >= ngroups) return;
     const int64_t r0 = g * kt::BM;
@@ -1645,7 +1646,10 @@ k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, i
     __syncthreads();
     const int n = nvalid;
     if (n == 0) {
-        if (tid == 0) grad[g] = -1.0f;
+        if (tid == 0) {
+            grad[g] = -1.0f;
+            gmaxn[g] = 0.0f;
+        }
         return;
     }
     for (int t = tid; t < d; t += blockDim.x) {
@@ -1662,21 +1666,31 @@ k_group_geom(const void* X, int dtype, int d, const int64_t* __restrict__ src, i
     __syncthreads();
     // radius: one warp per row, lanes over the dimensions (coalesced row reads)
     const int warp = tid >> 5, lane = tid & 31;
-    float rw = 0.0f;
+    float rw = 0.0f, nw = 0.0f;
     for (int i = warp; i < kt::BM; i += 4) {
         const int64_t v = rs[i];
         if (v < 0) continue;
-        float r2 = 0.0f;
+        float r2 = 0.0f, n2 = 0.0f;
         for (int t = lane; t < d; t += 32) {
-            const float df = load_elem(X, dtype, v * d + t) - cs[t];
+            const float x = load_elem(X, dtype, v * d + t);
+            const float df = x - cs[t];
             r2 = fmaf(df, df, r2);
+            n2 = fmaf(x, x, n2);
         }
-        for (int o = 16; o; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        for (int o = 16; o; o >>= 1) {
+            r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        }
         rw = fmaxf(rw, r2);
+        nw = fmaxf(nw, n2);
     }
-    if (lane == 0) rmax[warp] = rw;
+    if (lane == 0) {
+        rmax[warp] = rw;
+        nmax[warp] = nw;
+    }
     __syncthreads();
     if (tid == 0) {
+        gmaxn[g] = fmaxf(fmaxf(nmax[0], nmax[1]), fmaxf(nmax[2], nmax[3])) * (1.0f + 0x1p-16f);
         const float m = fmaxf(fmaxf(rmax[0], rmax[1]), fmaxf(rmax[2], rmax[3]));
         // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
         grad[g] = sqrtf(m * (1.0f + (float)(d + 4) * 0x1p-22f)) * (1.0f + 0x1p-20f);
@@ -1782,13 +1796,90 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
     if (tid == 0) bub[bid] = bmax == 0xFFFFFFFFu ? INFINITY : (float)bmax;
 }
 
+// As k_ub_own for float vectors (d <= 200): FP32 direct-form squared distances
+// (x - y)^2 summed in index order, the k-th smallest found by bisection on the bit
+// patterns of the non-negative floats.
+__global__ void __launch_bounds__(256)
+k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src,
+             const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
+             int k, int64_t nblocks, float* __restrict__ bub) {
+    extern __shared__ float wf[];  // [256][d + 1]
+    __shared__ unsigned int bmax;
+    const int64_t bid = blockIdx.x;
+    if (bid >= nblocks) return;
+    if (bid >= blk_off[nprob]) {
+        if (threadIdx.x == 0) bub[bid] = INFINITY;
+        return;
+    }
+    const int p = block_problem(blk_off, nprob, bid);
+    const KnnProblem pr = probs[p];
+    const int rb = (int)(bid - blk_off[p]);
+    const int ws = d + 1;
+    const int c0 = (rb >> 1) * 256;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ unsigned char cvalid[256];
+    if (tid == 0) bmax = 0;
+    for (int c = warp; c < 256; c += 8) {
+        const bool valid = c0 + c < pr.n_cols;
+        const int64_t v = valid ? src[pr.b_row0 + c0 + c] : -1;
+        for (int t = lane; t < d; t += 32) wf[c * ws + t] = v >= 0 ? X[v * d + t] : 0.0f;
+        if (lane == 0) cvalid[c] = v >= 0;
+    }
+    __syncthreads();
+    const uint32_t NONE = 0x7F800000u;  // +inf: not a column
+    unsigned int wmax = 0;
+    for (int r = warp; r < kt::BM; r += 8) {
+        const int i = rb * kt::BM + r;
+        if (i >= pr.n_rows) continue;
+        const int cr = i - c0;
+        uint32_t dv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = lane + 32 * q;
+            const float* xr = wf + cr * ws;
+            const float* xc = wf + c * ws;
+            float s2 = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                const float df = xr[t] - xc[t];
+                s2 = fmaf(df, df, s2);
+            }
+            dv[q] = (!cvalid[c] || c == cr) ? NONE : __float_as_uint(s2);
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cnt += dv[q] != NONE;
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        unsigned int ub = NONE;
+        if (cnt >= k) {
+            unsigned int lo = 0, hi = NONE;
+            while (lo < hi) {
+                const unsigned int mid = lo + (hi - lo) / 2;
+                int c = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) c += dv[q] <= mid;
+                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (c >= k) hi = mid; else lo = mid + 1;
+            }
+            ub = lo;
+        }
+        wmax = ub > wmax ? ub : wmax;
+    }
+    if (lane == 0) atomicMax(&bmax, wmax);
+    __syncthreads();
+    // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
+    if (tid == 0)
+        bub[bid] = bmax >= NONE ? INFINITY
+                                : __uint_as_float(bmax) * (1.0f + (float)(d + 4) * 0x1p-22f);
+}
+
 // tmask[bid]: bit t set unless every group of column tile t is provably farther
 // than the block's bound.  One block of 256 threads per row block; a warp per
 // (tile, group) pair with lanes over the dimensions.
 __global__ void __launch_bounds__(256)
 k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
             int bn, int d, int ldc, const float* __restrict__ gcent, const float* __restrict__ grad,
-            const float* __restrict__ bub, int64_t nblocks, uint32_t* __restrict__ tmask) {
+            const float* __restrict__ gmaxn, float kslack, const float* __restrict__ bub,
+            int64_t nblocks, uint32_t* __restrict__ tmask) {
     extern __shared__ float ca[];  // [d]
     __shared__ uint32_t mw[kt::TM_WORDS];
     __shared__ unsigned long long s_kept, s_pairs;
@@ -1815,6 +1906,7 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
     __syncthreads();
     const float rA = grad[gA];
     const float ub = bub[bid];
+    const float nA = gmaxn[gA];
     const int gpt = bn / kt::BM;  // groups per tile
     unsigned long long kept = 0, pairs = 0;
     for (int t = warp; t < ntiles; t += nw) {
@@ -1837,9 +1929,14 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
                 for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
                 const float D =
                     sqrtf(d2 * (1.0f - (float)(d + 4) * 0x1p-22f)) * (1.0f - 0x1p-20f);
-                lb = fminf(lb, (D - rA - rg) * (1.0f - 0x1p-20f));
+                // kslack (float data): twice the largest error of a tile key's squared
+                // distance, which scales with |x|^2 + |y|^2
+                const float lbg = (D - rA - rg) * (1.0f - 0x1p-20f);
+                const float need = ub * (1.0f + 0x1p-18f) + kslack * (nA + gmaxn[g]);
+                if (!(lbg > 0.0f && lbg * lbg > need)) lb = -1.0f;  // this group may hold one
+                else lb = fminf(lb, lbg);
             }
-            keep = !any || !(lb > 0.0f && lb * lb > ub * (1.0f + 0x1p-18f));
+            keep = !any || !(lb > 0.0f);
         }
         if (keep && lane == 0) {
             atomicOr(&mw[t >> 5], 1u << (t & 31));
@@ -1908,11 +2005,13 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
         const int64_t ng = w.rows_cap / kt::BM + 1;
         w.gcent = cv.take<float>((size_t)ng * pl.Kp);
         w.grad = cv.take<float>((size_t)ng);
+        w.gmaxn = cv.take<float>((size_t)ng);
         w.bub = cv.take<float>((size_t)w.nblocks);
         w.tmask = cv.take<uint32_t>((size_t)w.nblocks * kt::TM_WORDS);
     } else {
         w.gcent = nullptr;
         w.grad = nullptr;
+        w.gmaxn = nullptr;
         w.bub = nullptr;
         w.tmask = nullptr;
     }
@@ -2161,30 +2260,46 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
     const int64_t grid = rows / kt::BM + C + 1;
-    if (dtype == ANN_U8 && w.tmask && tile_prune_on() && d <= 256 && d % 4 == 0 &&
-        ((uintptr_t)X & 3) == 0) {
-        // 3a. bounds: each row's k-th distance within its 256-row window, the
-        // centre and radius of every 128-row group, and each block's mask of tiles
-        // that may hold a neighbour
+    const bool skip_u8 = dtype == ANN_U8 && pl.mode == 0 && !pl.rerank && d <= 256 &&
+                         d % 4 == 0 && ((uintptr_t)X & 3) == 0;
+    const bool skip_f32 = dtype == ANN_F32 && pl.mode == 1 && pl.rerank && d <= 200;
+    if (w.tmask && tile_prune_on() && (skip_u8 || skip_f32)) {
+        // 3a. bounds: each row's k'-th distance within its 256-row window (k' = the
+        // heap width), the centre and radius of every 128-row group, and each block's
+        // mask of tiles that may hold a neighbour
         const int64_t ng = w.rows_cap / kt::BM;
         k_group_geom<<<(unsigned)ng, 128, (size_t)d * sizeof(float), st>>>(
-            X, dtype, d, w.src, ng, pl.Kp, w.gcent, w.grad);
+            X, dtype, d, w.src, ng, pl.Kp, w.gcent, w.grad, w.gmaxn);
         ANN_CHECK_LAUNCH();
-        const size_t ubs = ((size_t)256 * (d / 4 + 1) + 256) * sizeof(uint32_t);
-        if (d <= 128) {
-            ANN_CHECK_CUDA(cudaFuncSetAttribute(
-                k_ub_own<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
-            k_ub_own<32><<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src,
-                                                            w.blk_off, w.probs, C, k, grid, w.bub);
+        float kslack = 0.0f;
+        if (skip_u8) {
+            const size_t ubs = ((size_t)256 * (d / 4 + 1) + 256) * sizeof(uint32_t);
+            if (d <= 128) {
+                ANN_CHECK_CUDA(cudaFuncSetAttribute(
+                    k_ub_own<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
+                k_ub_own<32><<<(unsigned)grid, 256, ubs, st>>>(
+                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
+            } else {
+                ANN_CHECK_CUDA(cudaFuncSetAttribute(
+                    k_ub_own<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
+                k_ub_own<64><<<(unsigned)grid, 256, ubs, st>>>(
+                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
+            }
         } else {
+            // Split BF16 keys (three products, FP32 accumulation): the error of a
+            // squared distance stays below (2^-16 + (d + 4) 2^-24)(|x|^2 + |y|^2);
+            // a skipped column must clear the bound by twice that, taken 4x larger.
+            kslack = 8.0f * (0x1p-16f + (float)(d + 4) * 0x1p-24f);
+            const size_t ubs = (size_t)256 * (d + 1) * sizeof(float);
             ANN_CHECK_CUDA(cudaFuncSetAttribute(
-                k_ub_own<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
-            k_ub_own<64><<<(unsigned)grid, 256, ubs, st>>>((const uint8_t*)X, d, w.src,
-                                                            w.blk_off, w.probs, C, k, grid, w.bub);
+                k_ub_own_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
+            k_ub_own_f32<<<(unsigned)grid, 256, ubs, st>>>(
+                (const float*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
         }
         ANN_CHECK_LAUNCH();
         k_tile_mask<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
-            w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.bub, grid, w.tmask);
+            w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.gmaxn, kslack, w.bub, grid,
+            w.tmask);
         ANN_CHECK_LAUNCH();
         P.tmask = w.tmask;
     }

@@ -124,6 +124,7 @@ struct KnnWs {
     // exact tile skipping (plain operands only; NULL otherwise)
     float* gcent;       // [rows_cap / 128 x Kp] centre of every 128-row group
     float* grad;        // [rows_cap / 128] radius bound of the group (-1: empty)
+    float* gmaxn;       // [rows_cap / 128] largest |y|^2 of the group
     float* bub;         // [blocks] bound on the k-th squared distance of a row block
     uint32_t* tmask;    // [blocks x 64] tiles each row block sweeps
     int64_t nblocks;

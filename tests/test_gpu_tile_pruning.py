@@ -83,3 +83,17 @@ def test_pruned_sweep_matches_the_oracle():
     oid, od = oracle.shard_knn(X, m, o, 32, rows=rows)
     assert np.array_equal(as_u32(ids)[rows], oid)
     assert np.array_equal(ds.cpu().numpy()[rows].astype(np.float64), od)
+
+
+@pytest.mark.parametrize("kind", ["deep", "gauss"])
+def test_float_pruned_sweep_equals_full_sweep(kind):
+    """FP32 data (split BF16 keys, screened list re-ranked in FP32): the skipping
+    keeps a margin for the key error, so the lists equal the full sweep's."""
+    if kind == "deep":
+        X = datagen.anisotropic_mixture(30000, 96, 16, 0.25, True, np.float32, seed=431)
+    else:
+        X = datagen.gaussian_mixture_f32(30000, 64, 12, 6.0, seed=432)
+    mem, off = _shards(X, 2, 433)
+    (ia, da), (ib, db), st = _both(X, mem, off, 32)
+    assert torch.equal(ia, ib) and torch.equal(da, db)
+    assert 0 < st["swept"] <= st["tiles"]
