@@ -421,6 +421,48 @@ int ann_learned_embed_workspace(int64_t N, int d, size_t* bytes);
 int ann_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Shard-task scheduling over GPU instances that may leave (Sec. IV "Cloud
+ * Instance Task Scheduler" and "Spot instance cost analysis").  Host code; no
+ * device memory involved (every pointer here is a host pointer).
+ *
+ * ann_sched_decide: one decision at time `now`.  Pending tasks (ids, estimated
+ *   durations in seconds, data transfers included) are taken longest first (ties:
+ *   smaller id).  Availability-based scheduling (always on): only the n_idle idle
+ *   instances (ids) can receive a task.  With ANN_SCHED_TIME in `policy`
+ *   (time-based scheduling), an instance whose end time is announced (idle_end
+ *   finite; +INFINITY when unknown) receives a task only if idle_end - now covers
+ *   the estimate, and a task goes to the fitting instance with the least
+ *   remaining time (ties: smaller id); otherwise to the idle instance of smallest
+ *   id.  A task that fits nowhere stays pending while smaller ones are tried.
+ *   task_of_idle[j] = the task given to idle instance j, or -1.
+ * ann_sched_simulate: discrete-event run of the scheduler.  Instance j is up in
+ *   [inst_start[j], inst_end[j]) (+INFINITY: never leaves); inst_notice[j] = 1
+ *   when its end is announced to the scheduler (NULL: never).  Decisions use est;
+ *   a task occupies its instance for actual[t] (NULL: est).  A task still
+ *   running when its instance leaves is lost and goes back to the pending list
+ *   (reallocation).  At one instant: completions, then departures, then
+ *   arrivals, then one decision.  Outputs per task: the instance that completed
+ *   it (-1 if none), first start, completion time, attempts.  summary[6] =
+ *   makespan, GPU active seconds (lost runs included), lost seconds,
+ *   reallocations, unfinished tasks, cost = makespan x cpu_price + GPU active
+ *   seconds x gpu_price.  Returns ANN_ERR_UNSUPPORTED if a task was left
+ *   unfinished (no instance could take it).
+ * ann_sched_estimate: build-time model fitted by least squares on timed samples,
+ *   t = a + b s (model 0: linear in the shard size, the paper's assumption) or
+ *   t = a + b s^2 (model 1: the exact kNN graph's n^2 d work); est_out[i] for
+ *   task_size[i].  Needs two distinct sample sizes. */
+enum ann_sched_policy { ANN_SCHED_AVAIL = 0, ANN_SCHED_TIME = 1 };
+int ann_sched_decide(double now, int n_pending, const int* pending_ids, const double* pending_est,
+                     int n_idle, const int* idle_ids, const double* idle_end, int policy,
+                     int* task_of_idle);
+int ann_sched_simulate(int n_tasks, const double* est, const double* actual, int n_inst,
+                       const double* inst_start, const double* inst_end, const int* inst_notice,
+                       int policy, double cpu_price, double gpu_price, int* task_inst,
+                       double* task_start, double* task_end, int* task_tries, double* summary);
+int ann_sched_estimate(int n_samples, const double* sample_size, const double* sample_time,
+                       int model, int n_tasks, const double* task_size, double* est_out);
+
 #ifdef __cplusplus
 }
 #endif

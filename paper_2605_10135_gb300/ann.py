@@ -595,3 +595,77 @@ class CapturedBuild:
     def replay(self) -> dict:
         self.graph.replay()
         return self.out
+
+
+# ---------------------------------------------------------------- shard-task scheduler
+SCHED_AVAIL, SCHED_TIME = 0, 1
+
+
+def _host_lib():
+    """The library's host-only entry points (no GPU needed)."""
+    L = lib()
+    D, I32 = ct.c_double, ct.c_int
+    P = ct.c_void_p
+    L.ann_sched_decide.restype = I32
+    L.ann_sched_decide.argtypes = [D, I32, P, P, I32, P, P, I32, P]
+    L.ann_sched_simulate.restype = I32
+    L.ann_sched_simulate.argtypes = [I32, P, P, I32, P, P, P, I32, D, D, P, P, P, P, P]
+    L.ann_sched_estimate.restype = I32
+    L.ann_sched_estimate.argtypes = [I32, P, P, I32, I32, P, P]
+    return L
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def sched_decide(now: float, pending_ids, pending_est, idle_ids, idle_end, policy: int = SCHED_TIME):
+    """One scheduling decision (Sec. IV): the task id given to each idle instance, or -1."""
+    import numpy as np
+    pid = np.ascontiguousarray(pending_ids, dtype=np.int32)
+    pes = np.ascontiguousarray(pending_est, dtype=np.float64)
+    iid = np.ascontiguousarray(idle_ids, dtype=np.int32)
+    ien = np.ascontiguousarray(idle_end, dtype=np.float64)
+    out = np.full(len(iid), -1, np.int32)
+    _check(_host_lib().ann_sched_decide(float(now), len(pid), _np_ptr(pid), _np_ptr(pes), len(iid),
+                                        _np_ptr(iid), _np_ptr(ien), int(policy), _np_ptr(out)))
+    return out
+
+
+def sched_simulate(est, inst_start, inst_end, inst_notice=None, actual=None,
+                   policy: int = SCHED_TIME, cpu_price: float = 0.0, gpu_price: float = 0.0):
+    """Discrete-event run of the scheduler: dict of per-task arrays and the summary
+    (makespan, gpu_active, lost, reallocations, unfinished, cost)."""
+    import numpy as np
+    est = np.ascontiguousarray(est, dtype=np.float64)
+    act = None if actual is None else np.ascontiguousarray(actual, dtype=np.float64)
+    st = np.ascontiguousarray(inst_start, dtype=np.float64)
+    en = np.ascontiguousarray(inst_end, dtype=np.float64)
+    no = None if inst_notice is None else np.ascontiguousarray(inst_notice, dtype=np.int32)
+    n, m = len(est), len(st)
+    ti = np.empty(n, np.int32)
+    ts = np.empty(n, np.float64)
+    te = np.empty(n, np.float64)
+    tr = np.empty(n, np.int32)
+    sm = np.empty(6, np.float64)
+    rc = _host_lib().ann_sched_simulate(n, _np_ptr(est), _np_ptr(act), m, _np_ptr(st), _np_ptr(en),
+                                        _np_ptr(no), int(policy), float(cpu_price),
+                                        float(gpu_price), _np_ptr(ti), _np_ptr(ts), _np_ptr(te),
+                                        _np_ptr(tr), _np_ptr(sm))
+    if rc not in (0, 2):
+        _check(rc)
+    keys = ("makespan", "gpu_active", "lost", "reallocations", "unfinished", "cost")
+    return dict(task_inst=ti, task_start=ts, task_end=te, tries=tr,
+                summary=dict(zip(keys, sm.tolist())))
+
+
+def sched_estimate(sample_size, sample_time, task_size, model: int = 0):
+    """Build-time estimates from timed samples: t = a + b s (0) or a + b s^2 (1)."""
+    import numpy as np
+    ss = np.ascontiguousarray(sample_size, dtype=np.float64)
+    stt = np.ascontiguousarray(sample_time, dtype=np.float64)
+    tz = np.ascontiguousarray(task_size, dtype=np.float64)
+    out = np.empty(len(tz), np.float64)
+    _check(_host_lib().ann_sched_estimate(len(ss), _np_ptr(ss), _np_ptr(stt), int(model), len(tz),
+                                          _np_ptr(tz), _np_ptr(out)))
+    return out
