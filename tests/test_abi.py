@@ -126,3 +126,22 @@ def test_selective_partition_arguments_validate_on_host(L):
     rc = L.ann_partition_selective(dummy, 10000, 96, 0, 16, dummy, dummy, 1000, 5, ct.byref(ok),
                                    dummy, None, dummy, dummy, None, None, 0, None)
     assert rc == 5 and b"workspace" in L.ann_last_error().lower()
+
+
+def test_pageable_vectors_are_refused_before_any_launch(L):
+    """Vectors must be device memory or page-locked host memory mapped for the
+    device; a plain host array is refused on the host (here, with no GPU at all,
+    the pointer query itself fails) after the workspace checks pass."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device path; tests/test_gpu_host_vectors.py covers GPUs")
+    X = np.zeros((100, 16), np.uint8)
+    n = ct.c_size_t(0)
+    assert L.ann_medoid_workspace(100, 16, ct.byref(n)) == 0
+    ws = (ct.c_char * max(n.value, 1))()
+    l0 = L.ann_launch_count()
+    rc = L.ann_medoid(X.ctypes.data_as(ct.c_void_p), 100, 16, 3, ct.c_void_p(16),
+                      ct.cast(ws, ct.c_void_p), n.value, None)
+    assert rc == 1
+    assert L.ann_launch_count() == l0
