@@ -619,25 +619,34 @@ k_sel_seq(const uint32_t* __restrict__ cand, const float* __restrict__ cdd, int6
                                 atomicMax(rad2 + c0, __float_as_uint(dv[0]));
                             }
                         } else {
-                            for (int l = 0; l < 32; ++l) {
-                                if (lane == l && in) {
-                                    jj = -1;
-                                    for (int j = 0; j < M; ++j)
-                                        if (tot[kv[j]] < cap) {
-                                            jj = j;
-                                            break;
-                                        }
-                                    if (jj < 0) {
-                                        jj = 0;
-                                        ++novf;
-                                    }
-                                    const uint32_t c = kv[jj];
-                                    tot[c] += 1;
-                                    org[c] += 1;
-                                    const uint32_t bits = __float_as_uint(dv[jj]);
-                                    if (bits > rad2[c]) rad2[c] = bits;
-                                }
-                                __syncwarp();
+                            // Deferred acceptance within the group (lanes in id order):
+                            // each lane proposes to its current candidate, a cluster
+                            // keeps its proposers of smallest lane up to the room it had
+                            // at the group's start, the others move on; a lane whose
+                            // candidates are all full goes to its nearest one (an
+                            // overflow, which takes no room from later lanes: that
+                            // cluster was full for them too).  With one priority order
+                            // for all clusters this is the result of taking the lanes
+                            // one at a time.
+                            int jp = 0;
+                            bool ovf = false;
+                            for (int round = 0; round <= 32 * M; ++round) {
+                                const bool act = in && !ovf;
+                                const uint32_t c = act ? kv[jp] : 0xFFFFFFFFu;
+                                const unsigned pe = __match_any_sync(0xffffffffu, c);
+                                const unsigned rk = __popc(pe & lt);
+                                const bool rej = act && !(tot[c] + rk < cap);
+                                if (!__any_sync(0xffffffffu, rej)) break;
+                                if (rej && ++jp == M) ovf = true;
+                            }
+                            __syncwarp();
+                            jj = ovf ? 0 : jp;
+                            if (in) {
+                                if (ovf) ++novf;
+                                const uint32_t c = kv[jj];
+                                atomicAdd(tot + c, 1ull);
+                                atomicAdd(org + c, 1ull);
+                                atomicMax(rad2 + c, __float_as_uint(dv[jj]));
                             }
                         }
                         if (in) {
@@ -680,6 +689,28 @@ k_sel_seq(const uint32_t* __restrict__ cand, const float* __restrict__ cdd, int6
                             took = prop;
                             for (uint32_t t = prop; t; t &= t - 1) {
                                 const uint32_t c2 = kv[__ffs(t) - 1];
+                                atomicAdd(rep + c2, 1ull);
+                                atomicAdd(tot + c2, 1ull);
+                            }
+                        } else if (omega == 2) {
+                            // one replica each: the same deferred acceptance over the
+                            // eligible candidates, room = min(theta - rep, cap - tot)
+                            // at the group's start
+                            uint32_t rem = in ? elig : 0u;
+                            for (int round = 0; round <= 32 * M; ++round) {
+                                const bool act = rem != 0;
+                                const uint32_t c = act ? kv[__ffs(rem) - 1] : 0xFFFFFFFFu;
+                                const unsigned pe = __match_any_sync(0xffffffffu, c);
+                                const unsigned rk = __popc(pe & lt);
+                                const bool rej =
+                                    act && !(rep[c] + rk < theta[c] && tot[c] + rk < cap);
+                                if (!__any_sync(0xffffffffu, rej)) break;
+                                if (rej) rem &= rem - 1;
+                            }
+                            __syncwarp();
+                            took = rem & (0u - rem);
+                            if (took) {
+                                const uint32_t c2 = kv[__ffs(took) - 1];
                                 atomicAdd(rep + c2, 1ull);
                                 atomicAdd(tot + c2, 1ull);
                             }
