@@ -68,3 +68,26 @@ def test_reference_arm_other_ranks_print_nothing(capsys):
 
     assert bench.run_reference(A(), configs.GAUSS_10K, 2, 1) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_has_the_contract_keys(capsys):
+    """--impl reference on rank 0: one JSON line with the metric, the oracle as the
+    CPU baseline and an e2e block without host-device bytes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_10135_gb300 import configs
+
+    class A:
+        warmup = 3
+        steps = 1
+
+    bench.run_reference(A(), configs.GAUSS_10K, 1, 0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC
+    assert j["unit"] == "vectors/s" and j["higher_is_better"] is True and j["value"] > 0
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
+    assert j["cpu_baseline"]["value"] == j["value"]
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
+    assert j["config"]["workload"] == configs.GAUSS_10K.name
