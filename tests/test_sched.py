@@ -132,3 +132,16 @@ def test_estimate_linear_and_quadratic():
                        osched.estimate(s.tolist(), (3 * s + 1).tolist(), 0, [7.0]))
     with pytest.raises(ann.AnnError):
         ann.sched_estimate([5.0, 5.0], [1.0, 2.0], [1.0])
+
+
+def test_restatement_pinned_by_hand():
+    """The plain restatement itself on the hand-worked scenarios above."""
+    ti, ts, te, tr, sm = osched.simulate([12, 8, 3, 6], None, [0, 0, 5], [INF, 10, INF],
+                                         [0, 1, 0], 1, 2.0, 3.0)
+    assert ti == [0, 1, 2, 2] and ts == [0.0, 0.0, 11.0, 5.0] and te == [12.0, 8.0, 14.0, 11.0]
+    assert sm[0] == 14.0 and sm[1] == 29.0 and sm[5] == 14.0 * 2.0 + 29.0 * 3.0
+    ti, ts, te, tr, sm = osched.simulate([10, 4], None, [0, 0], [5, INF], [0, 0], 1)
+    assert tr == [2, 1] and te == [15.0, 4.0] and sm[2] == 5.0 and sm[3] == 1.0
+    assert osched.decide(0.0, [(0, 15.0), (1, 8.0)], [(0, 10.0), (1, INF)], 1) == {0: 1, 1: 0}
+    assert osched.decide(0.0, [(0, 15.0), (1, 12.0)], [(0, 10.0), (1, INF)], 1) == {1: 0}
+    assert osched.estimate([1, 2, 3], [3, 5, 7], 0, [10]) == [21.0]
