@@ -195,7 +195,7 @@ def _selective_py(X, cent, omega, M, eps, tau0, block, cap):
     return a, [sum(replicas), n_ovf]
 
 
-@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("seed", range(18))
 def test_matches_plain_python_on_tiny_inputs(seed):
     rng = np.random.default_rng(100 + seed)
     N, d, C = int(rng.integers(20, 60)), int(rng.integers(2, 6)), int(rng.integers(3, 7))
