@@ -462,6 +462,121 @@ void or_merge(const uint32_t* pr_id, const double* pr_d, const uint32_t* members
     free(start); free(fill); free(rowlist);
 }
 
+/* ---- prune and merge variants (alternatives to the rank-detour prune and the
+ * plain edge union; not printed in the paper, which inherits its prune from the
+ * shard builder) ---------------------------------------------------------
+ * Occlusion prune (the robust prune of graph builders in the Vamana family): walk
+ * u's list in (distance, id) order and keep v unless some kept w satisfies
+ * alpha * |w - v| <= |u - v|, i.e. on squared distances
+ * (alpha * alpha) * d64(w, v) <= d64(u, v), where d64(u, v) is the distance the
+ * list carries; stop at R kept.  Kept entries stay in list order. */
+void or_prune_alpha(const void* X, int d, int dtype, const uint32_t* knn_id, const double* knn_d,
+                    const uint32_t* members, int64_t rows, int k, int R, double alpha,
+                    uint32_t* pr_id, double* pr_d) {
+    const double a2 = alpha * alpha;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < rows; p++) {
+        (void)members;
+        int kept = 0;
+        for (int j = 0; j < k && kept < R; j++) {
+            const uint32_t v = knn_id[p * k + j];
+            if (v == OR_PAD) continue;
+            const double duv = knn_d[p * k + j];
+            int occluded = 0;
+            for (int e = 0; e < kept && !occluded; e++) {
+                const uint32_t w = pr_id[p * R + e];
+                if (a2 * or_d64(X, dtype, w, X, dtype, v, d) <= duv) occluded = 1;
+            }
+            if (occluded) continue;
+            pr_id[p * R + kept] = v;
+            pr_d[p * R + kept] = duv;
+            kept++;
+        }
+        for (int e = kept; e < R; e++) {
+            pr_id[p * R + e] = OR_PAD;
+            pr_d[p * R + e] = INFINITY;
+        }
+    }
+}
+
+/* Merged graph with reverse edges: for every v, the first ceil(R/2) entries of its
+ * list, then the vectors u whose lists hold v (each with the distance of that
+ * edge) in (distance, id) order, then the rest of v's own list, skipping ids
+ * already taken, up to R; the result sorted by (distance, id). */
+void or_merge_reverse(const uint32_t* graph, const double* gdist, const uint32_t* degree,
+                      int64_t N, int R, uint32_t* out_g, double* out_d, uint32_t* out_deg) {
+    int64_t* cnt = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    for (int64_t u = 0; u < N; u++)
+        for (uint32_t j = 0; j < degree[u]; j++) cnt[graph[u * R + j] + 1]++;
+    for (int64_t v = 0; v < N; v++) cnt[v + 1] += cnt[v];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    memcpy(fill, cnt, sizeof(int64_t) * (size_t)N);
+    const int64_t ne = cnt[N];
+    uint32_t* rsrc = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(ne > 0 ? ne : 1));
+    double* rdist = (double*)malloc(sizeof(double) * (size_t)(ne > 0 ? ne : 1));
+    for (int64_t u = 0; u < N; u++)
+        for (uint32_t j = 0; j < degree[u]; j++) {
+            const uint32_t v = graph[u * R + j];
+            rsrc[fill[v]] = (uint32_t)u;
+            rdist[fill[v]] = gdist[u * R + j];
+            fill[v]++;
+        }
+    const int half = (R + 1) / 2;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t v = 0; v < N; v++) {
+        uint32_t* lid = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)R);
+        double* ld = (double*)malloc(sizeof(double) * (size_t)R);
+        int n = 0;
+        const int dv = (int)degree[v];
+        for (int j = 0; j < dv && j < half; j++) {
+            lid[n] = graph[v * R + j];
+            ld[n] = gdist[v * R + j];
+            n++;
+        }
+        /* reverse sources of v by (distance, id): repeated selection */
+        const int64_t r0 = cnt[v], r1 = cnt[v + 1];
+        char* used = (char*)calloc((size_t)(r1 - r0 + 1), 1);
+        while (n < R) {
+            int64_t best = -1;
+            for (int64_t e = r0; e < r1; e++) {
+                if (used[e - r0]) continue;
+                if (best < 0 || rdist[e] < rdist[best] ||
+                    (rdist[e] == rdist[best] && rsrc[e] < rsrc[best]))
+                    best = e;
+            }
+            if (best < 0) break;
+            used[best - r0] = 1;
+            int dup = 0;
+            for (int q = 0; q < n; q++) dup |= lid[q] == rsrc[best];
+            if (dup) continue;
+            lid[n] = rsrc[best];
+            ld[n] = rdist[best];
+            n++;
+        }
+        for (int j = half; j < dv && n < R; j++) {
+            int dup = 0;
+            for (int q = 0; q < n; q++) dup |= lid[q] == graph[v * R + j];
+            if (dup) continue;
+            lid[n] = graph[v * R + j];
+            ld[n] = gdist[v * R + j];
+            n++;
+        }
+        /* sorted by (distance, id) */
+        for (int a = 1; a < n; a++)
+            for (int b = a; b > 0 && (ld[b] < ld[b - 1] || (ld[b] == ld[b - 1] && lid[b] < lid[b - 1])); b--) {
+                const uint32_t ti = lid[b]; lid[b] = lid[b - 1]; lid[b - 1] = ti;
+                const double td = ld[b]; ld[b] = ld[b - 1]; ld[b - 1] = td;
+            }
+        for (int q = 0; q < R; q++) {
+            out_g[v * R + q] = q < n ? lid[q] : OR_PAD;
+            out_d[v * R + q] = q < n ? ld[q] : INFINITY;
+        }
+        out_deg[v] = (uint32_t)n;
+        free(lid); free(ld); free(used);
+    }
+    free(cnt); free(fill); free(rsrc); free(rdist);
+}
+
 /* ---- query evaluation (Sec. VI-B2: a CPU query following DiskANN's search
  * strategy; top-10 recall) ---------------------------------------------
  * Medoid: the vector nearest (d32) to the FP64 mean rounded to float, ties to

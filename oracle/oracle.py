@@ -34,6 +34,8 @@ def lib():
             "or_prune": (None, [P, P, P, P, I32, I32, I32, I32, P, P]),
             "or_merge": (None, [P, P, P, P, I32, I64, I32, P, I64, P, P, P]),
             "or_medoid": (I64, [P, I64, I32, I32]),
+            "or_prune_alpha": (None, [P, I32, I32, P, P, P, I64, I32, I32, D, P, P]),
+            "or_merge_reverse": (None, [P, P, P, I64, I32, P, P, P]),
             "or_search": (None, [P, P, I32, P, I64, I32, I32, P, I32, I64, I64, I32, I32, P, P]),
             "or_bruteforce": (None, [P, I64, I32, I32, P, I32, I64, I32, P, P]),
         }
@@ -182,6 +184,32 @@ def merge(pr_id, pr_d, members, offsets, N, gids=None):
     lib().or_merge(_p(pr_id), _p(pr_d), _p(members), _p(offsets), C, N, R, _p(gp), ng,
                    _p(graph), _p(gd), _p(deg))
     return graph, gd, deg
+
+
+def prune_alpha(X, knn_id, knn_d, R, alpha=1.2):
+    """Occlusion prune of every list from k to R (kept entries in list order)."""
+    X = _c(X)
+    knn_id = _c(knn_id, np.uint32)
+    knn_d = _c(knn_d, np.float64)
+    rows, k = knn_id.shape
+    pid = np.empty((rows, R), np.uint32)
+    pd = np.empty((rows, R), np.float64)
+    lib().or_prune_alpha(_p(X), X.shape[1], dtype_code(X), _p(knn_id), _p(knn_d), None, rows, k,
+                         R, float(alpha), _p(pid), _p(pd))
+    return pid, pd
+
+
+def merge_reverse(graph, gdist, degree):
+    """Merged graph with reverse edges: (graph, gdist, degree)."""
+    graph = _c(graph, np.uint32)
+    gdist = _c(gdist, np.float64)
+    degree = _c(degree, np.uint32)
+    N, R = graph.shape
+    og = np.empty((N, R), np.uint32)
+    od = np.empty((N, R), np.float64)
+    odeg = np.empty(N, np.uint32)
+    lib().or_merge_reverse(_p(graph), _p(gdist), _p(degree), N, R, _p(og), _p(od), _p(odeg))
+    return og, od, odeg
 
 
 def medoid(X) -> int:
