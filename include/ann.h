@@ -99,7 +99,9 @@ enum ann_prune_rule { ANN_PRUNE_RANK = 0, ANN_PRUNE_TRUNC = 1 };
 const char* ann_last_error(void);
 
 /* Library ABI version (major*100 + minor); 103 adds ANN_F16_RERANK, the learned
- * form, the autotuner and the wait self-test to 100. */
+ * form, the autotuner and the wait self-test to 100; 104 adds
+ * ann_partition_selective, ann_search_entries, host-resident vectors, the tile
+ * skipping switch and statistics, and the scheduler calls. */
 int ann_version(void);
 
 /* Number of kernels this library has launched in this process (host counter). */
@@ -126,7 +128,8 @@ int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 
 /* Exact skipping of distance tiles (on by default).  For ANN_EXACT on uint8
- * vectors of d <= 256 (d a multiple of 4) and on float32 vectors of d <= 200, each
+ * vectors of d <= 256 (d a multiple of 4, X 4-byte aligned) and on float32 vectors
+ * of d <= 200, each
  * row's k'-th squared distance among the rows of its 256-row window of the shard
  * (k' = the screened list width) bounds its final one from above; for float32 the
  * bound also carries a margin for the error of the tile keys.  A column tile is then

@@ -128,7 +128,7 @@ extern "C" {
 
 const char* ann_last_error(void) { return ann::g_err; }
 
-int ann_version(void) { return 103; }  // 1.03: learned form, autotuner, wait self-test
+int ann_version(void) { return 104; }  // 1.04: selective partition, tile skipping, scheduler
 
 unsigned long long ann_launch_count(void) { return g_launches.load(); }
 
