@@ -1,9 +1,10 @@
 """Benchmark of one divide-and-merge index build on GB300.
 
-A step is one pass of the whole build on the 1M-vector Sift-like workload
-(N=1e6, d=128 uint8, 16 shards, r=2, k=64, R=32): k-means partition with
-replication -> exact per-shard kNN (tcgen05 distance tiles + fused top-k) ->
-rank-detour prune -> dedup-then-reprune merge, inputs resident in HBM.  The
+A step is one pass of the whole build on the 10M-vector Deep-like workload
+(N=1e7, d=96 float32, unit norm, 64 shards, r=2, k=64, R=32; --workload picks
+another): k-means partition with replication -> exact per-shard kNN (tcgen05
+distance tiles + fused top-k, FP32 re-rank) -> rank-detour prune ->
+dedup-then-reprune merge, inputs resident in HBM.  The
 build is captured once as a CUDA graph and every step replays it (all kernels
 run again); --eager launches every kernel from the host instead.
 
@@ -125,38 +126,80 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_sample(w, X, budget_rows=1500):
-    """Time the plain oracle on a bounded sample of the workload and extrapolate
-    to the whole build; returns (vectors/s, threads, description, seconds)."""
-    import oracle
+class OracleLeg:
+    """The plain oracle timed on a bounded sample of the workload, extrapolated to
+    the whole build.
 
-    sample, init_rows = w.kmeans_inputs()
-    init = X[init_rows].astype(np.float32)
-    t0 = time.perf_counter()
-    cent, _ = oracle.kmeans(X, init, sample, 10)
-    t_kmeans = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    members, offsets = oracle.shards(oracle.assign(X, cent, w.r), w.C)
-    t_assign = time.perf_counter() - t0
-    rows_total = int(offsets[-1])
-    rows = np.linspace(0, max(rows_total - 1, 0), budget_rows).astype(np.int64)
-    t0 = time.perf_counter()
-    oracle.shard_knn(X, members, offsets, w.k, rows=rows)
-    t_knn = (time.perf_counter() - t0) / budget_rows * rows_total
-    # prune + merge: per-row cost on a small graph of the same degrees
-    Xs = X[:6000]
-    ms_, os_ = oracle.shards(oracle.assign(Xs, cent, w.r), w.C)
-    kid, kd = oracle.shard_knn(Xs, ms_, os_, w.k)
-    t0 = time.perf_counter()
-    pid, pd = oracle.prune(kid, kd, ms_, os_, w.R)
-    oracle.merge(pid, pd, ms_, os_, Xs.shape[0])
-    t_pm = (time.perf_counter() - t0) * (w.N / Xs.shape[0])
-    total = t_kmeans + t_assign + t_knn + t_pm
-    desc = (f"oracle: k-means (10 iterations) and the replicated assignment of all "
-            f"{w.N} vectors run in full; the exact kNN of {budget_rows} shard rows spread "
-            f"evenly over all {rows_total} rows, scaled by rows; prune+merge of a "
-            f"6000-vector graph, scaled by N")
-    return w.N / total, oracle.num_threads(), desc, total
+    Set-up (untimed): the oracle's own partition of all N vectors, which the kNN
+    of sampled shard rows needs.  One step (timed): k-means (10 iterations on the
+    whole k-means sample), the replicated assignment of `assign_rows` vectors
+    spread evenly over X (scaled by N), the exact kNN of `budget_rows` shard rows
+    spread evenly over all rows (scaled by rows), and prune + merge of a
+    6000-vector graph of the same degrees (scaled by N)."""
+
+    def __init__(self, w, X, assign_rows=200_000):
+        import oracle
+
+        self.o, self.w, self.X = oracle, w, X
+        sample, init_rows = w.kmeans_inputs()
+        self.sample = sample
+        self.init = X[init_rows].astype(np.float32)
+        self.arows = np.linspace(0, w.N - 1, min(assign_rows, w.N)).astype(np.int64)
+        Xs = X[:6000]
+        if w.uneven is None:
+            self.cent, _ = oracle.kmeans(X, self.init, sample, 10)
+            self.members, self.offsets = oracle.shards(oracle.assign(X, self.cent, w.r), w.C)
+            self.small = (Xs, *oracle.shards(oracle.assign(Xs, self.cent, w.r), w.C))
+        else:  # the partition is an input: no k-means, no assignment
+            self.members, self.offsets = w.shards()
+            from paper_2605_10135_gb300 import datagen
+            self.small = (Xs, *datagen.uneven_shards(len(Xs), w.C, w.r, 20, 160, seed=w.seed))
+        self.rows_total = int(self.offsets[-1])
+
+    def step(self, budget_rows=1500):
+        """Returns (vectors/s, threads, description, extrapolated seconds, wall seconds)."""
+        o, w, X = self.o, self.w, self.X
+        wall0 = time.perf_counter()
+        t_kmeans = t_assign = 0.0
+        if w.uneven is None:
+            t0 = time.perf_counter()
+            o.kmeans(X, self.init, self.sample, 10)
+            t_kmeans = time.perf_counter() - t0
+            Xa = X[self.arows]
+            t0 = time.perf_counter()
+            o.assign(Xa, self.cent, w.r)
+            t_assign = (time.perf_counter() - t0) * (w.N / len(self.arows))
+        rows = np.linspace(0, max(self.rows_total - 1, 0), budget_rows).astype(np.int64)
+        t0 = time.perf_counter()
+        o.shard_knn(X, self.members, self.offsets, w.k, rows=rows)
+        t_knn = (time.perf_counter() - t0) / budget_rows * self.rows_total
+        Xs, ms_, os_ = self.small
+        kid, kd = o.shard_knn(Xs, ms_, os_, w.k)
+        t0 = time.perf_counter()
+        pid, pd = o.prune(kid, kd, ms_, os_, w.R)
+        o.merge(pid, pd, ms_, os_, Xs.shape[0])
+        t_pm = (time.perf_counter() - t0) * (w.N / Xs.shape[0])
+        total = t_kmeans + t_assign + t_knn + t_pm
+        part = (f"k-means (10 iterations on the {len(self.sample)}-row sample) in full; the "
+                f"replicated assignment of {len(self.arows)} of the {w.N} vectors, scaled by N"
+                if w.uneven is None else "the partition is given (synthetic uneven shards)")
+        desc = (f"oracle: {part}; the exact kNN of {budget_rows} shard rows spread evenly over "
+                f"all {self.rows_total} rows, scaled by rows; prune+merge of a 6000-vector "
+                f"graph, scaled by N")
+        return w.N / total, o.num_threads(), desc, total, time.perf_counter() - wall0
+
+
+def workload_config(w, args):
+    """The workload a line measures, identical in both arms' JSON lines."""
+    return {"workload": w.name, "N": w.N, "d": w.d, "elem": w.dtype, "shards": w.C,
+            "replicas": w.r, "k": w.k, "R": w.R,
+            "partition": ("k-means, 10 iterations" if w.uneven is None else
+                          "synthetic uneven shards, sizes log-uniform on [%d, %d] rescaled to "
+                          "r N rows" % tuple(w.uneven)),
+            "tile_launch": "one per shard" if getattr(args, "per_shard", False) else
+                           "one grouped launch over all shards",
+            "precision": args.precision, "epsilon": args.epsilon,
+            "l2": "flushed (512 MB write) before every timed GPU step"}
 
 
 # ------------------------------------------------------------------ multi-rank helpers
@@ -218,7 +261,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sift1m_d128_u8")
+    ap.add_argument("--workload", default="deep10m_d96_f32")
     ap.add_argument("--nq", type=int, default=1000)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
@@ -258,6 +301,9 @@ def main():
                          "inequality)")
     ap.add_argument("--entries", type=int, default=1024,
                     help="search also from the nearest of this many sampled entry vectors")
+    ap.add_argument("--per-shard", action="store_true",
+                    help="one distance-tile launch per shard instead of one grouped launch "
+                         "over all shards (same lists)")
     ap.add_argument("--tile-counters", action="store_true",
                     help="after timing, run one step with the counting kernel variant and "
                          "report its per-role cycle counters")
@@ -297,6 +343,11 @@ def main():
     Xd = Xh if args.host_x else Xh.to(dev)
     init_d = torch.from_numpy(init).to(dev)
     samp_d = torch.from_numpy(sample.view(np.int32)).to(dev)
+    shards = None  # synthetic uneven partition: (members, offsets, per-shard host offsets)
+    if w.uneven is not None:
+        mem_np, off_np = w.shards()
+        shards = (torch.from_numpy(mem_np.view(np.int32)).to(dev), torch.from_numpy(off_np).to(dev),
+                  off_np.tolist() if args.per_shard else None)
     prec = {"exact": ann.EXACT, "bf16": ann.BF16_RERANK, "f16": ann.F16_RERANK,
             "fp8": ann.FP8_RERANK, "learned": ann.LEARNED}[args.precision]
     sel = None
@@ -324,6 +375,8 @@ def main():
             if x.data_ptr() != captured.X.data_ptr():
                 captured.X.copy_(x, non_blocking=True)
             return captured.replay()
+        if shards is not None:
+            return ann.build_from_shards(x, shards[0], shards[1], cfg, shards[2])
         if args.streamed:
             return ann.build_index_streamed(x, cfg, init_d, samp_d)
         return ann.build_index(x, cfg, init_d, samp_d, learned)
@@ -339,7 +392,7 @@ def main():
     if use_graph and (prec == ann.LEARNED or sel is not None or args.streamed):
         use_graph = False  # host decisions between stages: not capturable
     if use_graph:
-        captured = ann.CapturedBuild(Xd, cfg, init_d, samp_d)
+        captured = ann.CapturedBuild(Xd, cfg, init_d, samp_d, shards)
         for _ in range(2):
             out = step(Xd)
         torch.cuda.synchronize()
@@ -379,7 +432,9 @@ def main():
     if tile_n == 0:  # graph replays record no host-side kernel events: one eager step
         flush.zero_()
         ann.timing_enable(True)
-        ann.build_index(Xd, cfg, init_d, samp_d, learned)
+        captured_save, captured = captured, None
+        step(Xd)
+        captured = captured_save
         torch.cuda.synchronize()
         ann.timing_enable(False)
         tile_ms, tile_n = ann.timing_read()
@@ -391,7 +446,9 @@ def main():
     graph_h = torch.empty((w.N, w.R), dtype=torch.int32).pin_memory()
     gdist_h = torch.empty((w.N, w.R), dtype=torch.float32).pin_memory()
     deg_h = torch.empty(w.N, dtype=torch.int32).pin_memory()
-    for i in range(max(3, args.steps // 2)):
+    # half the timed steps (at least 3; 3 when a step takes over a second)
+    n_e2e = 3 if ms > 1000.0 else max(3, args.steps // 2)
+    for i in range(n_e2e):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -429,7 +486,9 @@ def main():
     torch.cuda.synchronize()
     sev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     sev[0].record(st)
-    if sel is None:
+    if shards is not None:
+        mem_s, off_s = shards[0], shards[1]
+    elif sel is None:
         cent_s, mem_s, off_s = ann.partition(Xd, cfg.C, cfg.r, init_d, samp_d, cfg.iters)
     else:
         cent_s, mem_s, off_s, _, _ = ann.partition_selective(Xd, cfg.C, cfg.r, init_d, samp_d,
@@ -443,7 +502,10 @@ def main():
         if float(est_s.item()) < learned.min_recall:
             prec_s, model_s = ann.EXACT, None
     sev[2].record(st)
-    kid_s, kd_s = ann.shard_knn(Xd, mem_s, off_s, cfg.k, prec_s, cfg.rerank_k, model_s)
+    if shards is not None and shards[2] is not None:
+        kid_s, kd_s = ann.shard_knn_per_shard(Xd, mem_s, shards[2], cfg.k, prec_s, cfg.rerank_k)
+    else:
+        kid_s, kd_s = ann.shard_knn(Xd, mem_s, off_s, cfg.k, prec_s, cfg.rerank_k, model_s)
     sev[3].record(st)
     pid_s, pd_s = ann.prune(kid_s, kd_s, mem_s, off_s, cfg.R, cfg.rule, N=w.N)
     sev[4].record(st)
@@ -465,7 +527,9 @@ def main():
     if args.tile_counters:
         ann.tile_counters_read()
         ann.tile_counters_enable(True)
+        captured_save, captured = captured, None  # eager: replays keep the captured kernel
         step(Xd)
+        captured = captured_save
         counters = ann.tile_counters_read()
         ann.tile_counters_enable(False)
 
@@ -522,21 +586,11 @@ def main():
         "vs_baseline": None,
         "dtype": dtype,
         "data": "synthetic",
-        "config": {
-            "workload": w.name, "N": w.N, "d": w.d, "elem": w.dtype, "shards": w.C,
-            "replicas": w.r, "k": w.k, "R": w.R, "kmeans_iters": 10,
-            "precision": args.precision,
-            "learned": (None if prec != ann.LEARNED else {
-                "steps": args.learn_steps, "batch": args.learn_batch,
-                "sample_rows": int(learned.sample.numel()),
-                "recall_estimate": out.get("recall_estimate"),
-                "fell_back_to_exact": out.get("precision") != ann.LEARNED,
-                "timed_step_includes_training": True}),
-            "tile_operands": operands, "tensor_products_per_pair": products,
-            "l2": "flushed (512 MB write) before every timed step",
+        "config": workload_config(w, args),
+        "quality": {
             "recall_at_10": graph_recall,
             "recall_definition": ("graph recall@10 vs the exact kNN graph (exact build: 1.0 by "
-                                  "construction, bit-exact vs the oracle in the parity tests)"
+                                  "construction, checked against the oracle in the parity tests)"
                                   if prec == ann.EXACT else
                                   "graph recall@10 of the shard kNN lists vs the exact form's "
                                   "lists on the same partition"),
@@ -544,16 +598,25 @@ def main():
             "union_recall_definition": ("for nq sampled vectors: the 10 nearest of the union of "
                                         "the vector's shard kNN lists vs its exact 10 nearest "
                                         "over all N (partition locality)"),
+            "search_recall_at_10": recall, "search_Ls": 64, "queries": args.nq,
+            "mean_dist_count": float(cnt.float().mean().item()),
+            "search_recall_at_10_from_entries": recall_e, "search_entries": int(ent.numel()),
+            "mean_dist_count_from_entries": float(cnt_e.float().mean().item()),
+        },
+        "detail": {
+            "learned": (None if prec != ann.LEARNED else {
+                "steps": args.learn_steps, "batch": args.learn_batch,
+                "sample_rows": int(learned.sample.numel()),
+                "recall_estimate": out.get("recall_estimate"),
+                "fell_back_to_exact": out.get("precision") != ann.LEARNED,
+                "timed_step_includes_training": True}),
+            "tile_operands": operands, "tensor_products_per_pair": products,
             "selective": (None if sel is None else {
                 "epsilon": sel.epsilon, "tau0": sel.tau0, "block": sel.block,
                 "capacity": sel.capacity, "cand": sel.cand,
                 "replicated_share": float(out["selective_stats"][0].item()) / w.N,
                 "overflowed_originals": int(out["selective_stats"][1].item()),
                 "member_rows": int(out["offsets"][-1].item())}),
-            "search_recall_at_10": recall, "search_Ls": 64, "queries": args.nq,
-            "mean_dist_count": float(cnt.float().mean().item()),
-            "search_recall_at_10_from_entries": recall_e, "search_entries": int(ent.numel()),
-            "mean_dist_count_from_entries": float(cnt_e.float().mean().item()),
             "shard_sizes_min_max": [int(sizes.min()), int(sizes.max())],
             "distance_tflops": achieved,
             "tile_skipping": ({"pairs_all": pairs_all, "pairs_swept": pairs,
@@ -592,7 +655,7 @@ def main():
     if counters is not None:
         line["tile_counters"] = counters
     if world == 1 and not args.no_baseline:
-        v, cores, desc, _ = oracle_sample(w, X)
+        v, cores, desc, _, _ = OracleLeg(w, X).step(budget_rows=1500)
         line["cpu_baseline"] = {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
                                 "sample": desc}
     print(json.dumps(line))
@@ -605,20 +668,26 @@ def run_reference(args, w, world, rank):
     if rank != 0:
         return
     X = w.vectors()
-    for _ in range(max(args.warmup, 3) and 1):
-        oracle_sample(w, X, budget_rows=64)
-    vals, tms = [], []
+    leg = OracleLeg(w, X)
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        leg.step(budget_rows=400)
+    vals, tms, walls = [], [], []
+    desc, cores = "", 0
     for _ in range(args.steps):
-        v, cores, desc, total = oracle_sample(w, X, budget_rows=800)
+        v, cores, desc, total, wall = leg.step(budget_rows=400)
         vals.append(v)
         tms.append(total * 1e3)
+        walls.append(wall * 1e3)
     v = float(np.mean(vals))
+    ms = float(np.mean(tms))
+    dtype = {"u8": "u8", "f32": "f64", "f16": "f64"}[w.dtype]
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": float(np.mean(tms)),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic", "config": {"workload": w.name, "N": w.N, "d": w.d, "shards": w.C,
-                                        "replicas": w.r, "k": w.k, "R": w.R},
+        "steps": args.steps, "warmup": warm, "ms_per_step": ms,
+        "extrapolated": True, "wall_ms_per_step": float(np.mean(walls)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": workload_config(w, args),
         "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -13,7 +13,8 @@
  *    tensor) owned by the caller, unless the argument says "host".  The
  *    library never frees or retains caller memory.
  *  - The vectors X of ann_partition, ann_partition_selective, ann_shard_knn,
- *    ann_medoid, ann_knn_query, ann_search and ann_search_entries, and their
+ *    ann_medoid, ann_medoid_noalloc, ann_knn_query, ann_search and
+ *    ann_search_entries, and their
  *    queries Q, may instead be page-locked
  *    host memory mapped into the device's address space at the same address
  *    (cudaHostAlloc / cudaHostRegister with unified addressing, a pinned
@@ -21,7 +22,7 @@
  *    (NVLink-C2C on Grace-Blackwell), so X need not fit in device memory.
  *    Pageable host memory or another device's memory is refused with
  *    ANN_ERR_INVALID_ARG before any launch (the check runs once the workspace
- *    checks have passed).
+ *    checks, or ann_medoid_noalloc's size checks, have passed).
  *  - Scratch memory comes from a caller-supplied workspace of at least the
  *    size the matching *_workspace() call reports; it may be reused after the
  *    call's work on the stream has completed.
@@ -291,7 +292,14 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
 
 /* ---------------------------------------------------------------------------
  * ann_prune - intermediate degree k (L) to final degree R per shard row, by
- * `rule` (enum ann_prune_rule).  Integer logic on the lists only: the output
+ * `rule` (enum ann_prune_rule).  The paper builds each shard graph with an
+ * intermediate degree L and a final index degree R (Sec. III "Motivation",
+ * the (R, L) = (32, 64) and (64, 128) settings; Sec. VI-B2, default R = 64,
+ * L = 128) and takes the reduction from its shard builder, CAGRA (Sec. II-A);
+ * it prints no rule.  ANN_PRUNE_RANK is the reading used here: for row u with
+ * list v_0 .. v_{k-1}, c_j counts the i < j whose own list ranks v_j before
+ * position j (a two-hop path with both hops ranked ahead of the direct edge),
+ * and the R entries of smallest (c_j, j) are kept.  Integer logic on the lists only: the output
  * depends on knn_id alone (knn_d is carried), so identical lists give
  * identical results.  pr_id / pr_d: [rows x R], kept entries in list order
  * then ANN_PAD / +inf.  N = number of vectors (ids < N).  The workspace holds
@@ -344,8 +352,10 @@ int ann_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry_out, 
  * library until the process exits.  Limits: d <= 4096 and
  * ceil(N / 4096) * d <= 524288 (e.g. N <= 2^21 at d = 1024); larger inputs are
  * rejected with ANN_ERR_INVALID_ARG (use ann_medoid with a workspace).  The
- * first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  All calls share
+ * first call in a CUDA context looks up the array's device address (with that
+ * context's device current) and caches it per context, so a context created
+ * again after a device reset gets a fresh lookup; make the first call in a
+ * context before any stream capture.  All calls share
  * the one array: calls whose work overlaps on the GPU (different streams, or
  * several host threads) race and must be serialised by the caller.  The paper
  * has no counterpart: this entry point exists only for such callers. */

@@ -282,17 +282,26 @@ def partition_selective(X: torch.Tensor, C: int, omega: int, init_centroids: tor
 
 
 def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: int,
-              precision: int = EXACT, rerank_k: int = 0, model: torch.Tensor | None = None):
+              precision: int = EXACT, rerank_k: int = 0, model: torch.Tensor | None = None,
+              out: tuple[torch.Tensor, torch.Tensor] | None = None):
     """kNN inside every shard: (knn_id [rows, k] int32, knn_d [rows, k] float32).
-    model: the MLP parameters (float32, on the device) for precision=LEARNED."""
+    model: the MLP parameters (float32, on the device) for precision=LEARNED.
+    out: contiguous (knn_id, knn_d) arrays to write into."""
     X, dev = _vectors(X, "X")
     N, d = X.shape
     members = _cuda(members, "members")
     offsets = _cuda(offsets, "offsets")
     C = offsets.numel() - 1
     rows = members.numel()
-    knn_id = torch.empty((rows, k), dtype=torch.int32, device=dev)
-    knn_d = torch.empty((rows, k), dtype=torch.float32, device=dev)
+    if out is None:
+        knn_id = torch.empty((rows, k), dtype=torch.int32, device=dev)
+        knn_d = torch.empty((rows, k), dtype=torch.float32, device=dev)
+    else:
+        knn_id, knn_d = out
+        if (knn_id.shape != (rows, k) or knn_d.shape != (rows, k) or not knn_id.is_contiguous()
+                or not knn_d.is_contiguous() or knn_id.dtype != torch.int32
+                or knn_d.dtype != torch.float32):
+            raise ValueError("out must be contiguous int32 / float32 arrays [rows, k]")
     L = lib()
     nb = _wsize(L.ann_shard_knn_workspace, N, d, _DT[X.dtype], C, rows, k, precision, rerank_k)
     ws = _ws(nb, dev)
@@ -456,6 +465,28 @@ def search_entries(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q
     return out, cnt
 
 
+def search_eval(graph: torch.Tensor, degree: torch.Tensor, X: torch.Tensor, Q: torch.Tensor,
+                gt: torch.Tensor, entry: int, Ls: int):
+    """ann_search_eval: beam search of each query from `entry` (top 10) and its
+    recall@10 against gt [nq, 10]: (ids [nq, 10], recall device float[1],
+    distance counts [nq])."""
+    graph, degree = _cuda(graph, "graph"), _cuda(degree, "degree")
+    (X, dev), (Q, _) = _vectors(X, "X"), _vectors(Q, "Q")
+    gt = _cuda(gt, "gt")
+    N, d = X.shape
+    R = graph.shape[1]
+    nq = Q.shape[0]
+    if gt.shape != (nq, 10):
+        raise ValueError("gt must be [nq, 10]")
+    out = torch.empty((nq, 10), dtype=torch.int32, device=dev)
+    rec = torch.empty(1, dtype=torch.float32, device=dev)
+    cnt = torch.empty(nq, dtype=torch.int32, device=dev)
+    _check(lib().ann_search_eval(_ptr(graph), _ptr(degree), R, _ptr(X), N, d, _DT[X.dtype],
+                                 _ptr(Q), nq, _ptr(gt), int(entry), Ls, _ptr(out), _ptr(rec),
+                                 _ptr(cnt), _stream()))
+    return out, rec, cnt
+
+
 def recall(found: torch.Tensor, truth: torch.Tensor, kk: int = 10) -> torch.Tensor:
     """Device float[1]: mean |first kk found  intersect  first kk truth| / kk."""
     found, truth = _cuda(found, "found"), _cuda(truth, "truth")
@@ -524,6 +555,51 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
                 precision=precision, recall_estimate=est, model=model, selective_stats=sel_stats)
 
 
+_SHARD_OFFS: dict = {}
+
+
+def shard_knn_per_shard(X: torch.Tensor, members: torch.Tensor, host_offsets: list[int], k: int,
+                        precision: int = EXACT, rerank_k: int = 0):
+    """shard_knn with one tile launch per shard (host_offsets: the offsets as a
+    host list); the same lists as the grouped call."""
+    dev = members.device
+    rows = members.numel()
+    knn_id = torch.empty((rows, k), dtype=torch.int32, device=dev)
+    knn_d = torch.empty((rows, k), dtype=torch.float32, device=dev)
+    off = list(host_offsets)
+    key = (str(dev), tuple(off))
+    if key not in _SHARD_OFFS:  # made once, outside any stream capture
+        _SHARD_OFFS[key] = torch.tensor([[0, off[s + 1] - off[s]] for s in range(len(off) - 1)],
+                                        dtype=torch.int64, device=dev)
+    o_all = _SHARD_OFFS[key]
+    for s in range(len(off) - 1):
+        a, b = off[s], off[s + 1]
+        if a < b:
+            shard_knn(X, members[a:b], o_all[s], k, precision, rerank_k,
+                      out=(knn_id[a:b], knn_d[a:b]))
+    return knn_id, knn_d
+
+
+def build_from_shards(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor,
+                      cfg: BuildConfig, per_shard_offsets: list[int] | None = None) -> dict:
+    """per-shard kNN -> prune -> merge over a given partition (members [rows] sorted
+    by id within each shard, offsets [C + 1]), e.g. shards of uneven sizes made
+    elsewhere.  All shards go to one grouped tile launch; with per_shard_offsets
+    (the offsets as a host list) every shard gets a launch of its own instead (the
+    same lists, for comparison)."""
+    N = X.shape[0]
+    if per_shard_offsets is None:
+        knn_id, knn_d = shard_knn(X, members, offsets, cfg.k, cfg.precision, cfg.rerank_k)
+    else:
+        knn_id, knn_d = shard_knn_per_shard(X, members, per_shard_offsets, cfg.k, cfg.precision,
+                                            cfg.rerank_k)
+    pr_id, pr_d = prune(knn_id, knn_d, members, offsets, cfg.R, cfg.rule, N=N)
+    graph, gdist, degree = merge(pr_id, pr_d, members, offsets, N)
+    return dict(centroids=None, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
+                pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree,
+                precision=cfg.precision, recall_estimate=None, model=None, selective_stats=None)
+
+
 def build_index_streamed(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
                          sample_idx: torch.Tensor) -> dict:
     """build_index one shard at a time, for inputs whose kNN lists do not fit in
@@ -571,8 +647,10 @@ class CapturedBuild:
     vectors into .X (same shape and type) before replay().  Every replay runs the
     whole build with no host work between kernels."""
 
-    def __init__(self, X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
-                 sample_idx: torch.Tensor):
+    def __init__(self, X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor | None,
+                 sample_idx: torch.Tensor | None, shards: tuple | None = None):
+        """shards = (members, offsets[, per-shard host offsets]): capture
+        build_from_shards over that partition instead of build_index."""
         if cfg.precision == LEARNED:
             raise ValueError("the learned form is not capturable")
         if cfg.selective is not None:
@@ -580,16 +658,22 @@ class CapturedBuild:
                              "back to the host)")
         self.X, self.cfg = X, cfg
         self.init, self.sample = init_centroids, sample_idx
+        if shards is None:
+            run = lambda: build_index(X, cfg, init_centroids, sample_idx)
+        else:
+            m, o = shards[0], shards[1]
+            per = shards[2] if len(shards) > 2 else None
+            run = lambda: build_from_shards(X, m, o, cfg, per)
         dev = _vectors(X, "X")[1]
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):  # first run: one-time driver and attribute setup
-            build_index(X, cfg, init_centroids, sample_idx)
+            run()
         torch.cuda.current_stream(dev).wait_stream(side)
         self.graph = torch.cuda.CUDAGraph()
         l0 = launch_count()
         with torch.cuda.graph(self.graph):
-            self.out = build_index(X, cfg, init_centroids, sample_idx)
+            self.out = run()
         self.kernels = launch_count() - l0  # library kernels in one replay
 
     def replay(self) -> dict:

@@ -24,6 +24,9 @@ class Workload:
     k: int
     R: int
     seed: int
+    # synthetic uneven shards (log-uniform sizes on [lo, hi], rescaled to r N rows)
+    # in place of the k-means partition; None: the k-means partition
+    uneven: tuple | None = None
 
     def vectors(self, n: int | None = None, seed_offset: int = 0) -> np.ndarray:
         n = self.N if n is None else n
@@ -54,6 +57,11 @@ class Workload:
     def kmeans_inputs(self, n: int | None = None):
         return datagen.kmeans_sample(self.N if n is None else n, self.C, seed=self.seed + 7)
 
+    def shards(self):
+        """(members, offsets) of the synthetic uneven partition."""
+        lo, hi = self.uneven
+        return datagen.uneven_shards(self.N, self.C, self.r, lo, hi, seed=self.seed + 9)
+
 
 # Small float mixture (oracle finishes in seconds): N=1e4, d=64, 4 shards.
 GAUSS_10K = Workload("gauss10k_d64_f32", 10_000, 64, "f32", 4, 2, 32, 16, 1001)
@@ -61,8 +69,10 @@ GAUSS_10K = Workload("gauss10k_d64_f32", 10_000, 64, "f32", 4, 2, 32, 16, 1001)
 SIFT_1M = Workload("sift1m_d128_u8", 1_000_000, 128, "u8", 16, 2, 64, 32, 1002)
 # Deep-like unit-norm floats: N=1e7, d=96, 64 shards.
 DEEP_10M = Workload("deep10m_d96_f32", 10_000_000, 96, "f32", 64, 2, 64, 32, 1003)
-# Laion-like power-law floats: N=2e6, d=768, 128 uneven shards.
-LAION_2M = Workload("laion2m_d768_f32", 2_000_000, 768, "f32", 128, 2, 32, 32, 1004)
+# Laion-like power-law floats: N=2e6, d=768, 128 uneven shards (log-uniform sizes
+# on [5e3, 4e5], rescaled to the 4e6 shard rows), no k-means.
+LAION_2M = Workload("laion2m_d768_f32", 2_000_000, 768, "f32", 128, 2, 32, 32, 1004,
+                    uneven=(5_000, 400_000))
 # High-dimensional FP16 embeddings: N=1e7, d=1024, 128 shards.
 EMBED_10M = Workload("embed10m_d1024_f16", 10_000_000, 1024, "f16", 128, 2, 64, 32, 1005)
 

@@ -663,6 +663,9 @@ int ann_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* ent
     ANN_REQUIRE(N >= 1 && N < (1ll << 32) && d >= 1, "N and d must be >= 1");
     ANN_REQUIRE(valid_dtype(dtype), "bad dtype");
     ANN_REQUIRE(X && entry_out, "NULL pointer");
+    int rc = medoid_noalloc_check(N, d);
+    if (rc) return rc;
+    if ((rc = check_readable(X, "X"))) return rc;
     return run_medoid_noalloc(X, N, d, dtype, entry_out, (cudaStream_t)stream);
 }
 
@@ -745,10 +748,12 @@ int ann_search_eval(const uint32_t* graph, const uint32_t* degree, int R, const 
                     int64_t N, int d, int dtype, const void* Q, int64_t nq, const uint32_t* gt,
                     uint32_t entry, int Ls, uint32_t* out_id, float* recall_out,
                     uint32_t* dist_count_out, void* stream) {
+    ANN_REQUIRE(Ls >= 10, "Ls must be >= 10 for recall@10");
+    ANN_REQUIRE(nq == 0 || gt, "gt is NULL");
+    ANN_REQUIRE(recall_out, "recall_out is NULL");
     int rc = ann_search(graph, degree, R, X, N, d, dtype, Q, nq, entry, Ls, 10, out_id,
                         dist_count_out, stream);
     if (rc) return rc;
-    ANN_REQUIRE(Ls >= 10, "Ls must be >= 10 for recall@10");
     return ann_recall(out_id, 10, gt, 10, nq, 10, recall_out, stream);
 }
 

@@ -64,7 +64,7 @@ constexpr int A_AUG_BYTES = BM * 32;
 constexpr int NAUG = 1;                 // norm-block slots (loaded first in each tile)
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
-constexpr int CAP = 8;                  // survivor buffer entries per row and epilogue warp
+constexpr int PH_MAX = 256;             // candidate pool entries per row half, at most
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
@@ -77,13 +77,13 @@ constexpr int TM_WORDS = 64;            // tile-mask words per row block (2048 t
 enum TileCounter {
     TC_EPI_CYCLES = 0,   // epilogue threads: cycles from first wait to the end of the sweep
     TC_EPI_WAIT,         // epilogue threads: cycles waiting for a finished accumulator
-    TC_EPI_FLUSH,        // epilogue threads: cycles inside heap flushes
+    TC_EPI_FLUSH,        // epilogue threads: cycles inside pool compactions
     TC_CHUNKS,           // warp-level: 32-column chunks examined
     TC_SLOW_CHUNKS,      // warp-level: chunks where some row had a candidate
-    TC_FLUSHES,          // warp-level: flush calls
-    TC_FLUSH_ITERS,      // warp-level: lockstep insert iterations
-    TC_INSERTS,          // thread-level: heap insertions
-    TC_APPENDS,          // thread-level: buffered survivors
+    TC_FLUSHES,          // warp-level: compaction calls
+    TC_FLUSH_ITERS,      // warp-level: rows compacted
+    TC_INSERTS,          // thread-level: pool entries left after compactions (unused: 0)
+    TC_APPENDS,          // thread-level: survivors appended to the pools
     TC_MMA_WAIT_FULL,    // MMA thread: cycles waiting for B stages
     TC_MMA_WAIT_ACC,     // MMA thread: cycles waiting for a free accumulator
     TC_PROD_WAIT,        // producer: cycles waiting for a free stage
@@ -117,6 +117,11 @@ struct KnnParams {
     int nst;       // main pipeline stages
     int kbe;       // elements per 128-byte K block (64 for 16-bit, 128 for 8-bit operands)
     int kind8;     // 1: E4M3 operands (tcgen05.mma kind::f8f6f4, K = 32 per MMA)
+    // K steps of 32 bytes (one MMA each) that hold data: steps at and beyond ksteps
+    // are zero padding of the last K block and are not issued.  Split operands with
+    // resident A (compact layout): steps [0, hs) are the hi section, [hs, 2 hs) the
+    // lo section, both of B and of A.
+    int ksteps, hs;
     uint32_t idesc_neg, idesc_aug;
     uint32_t* out_id;
     float* out_d;
@@ -125,10 +130,29 @@ struct KnnParams {
     // TM_WORDS words per row block, bit t set = sweep column tile t; used only where
     // the shard has at most TM_WORDS * 32 tiles.
     const uint32_t* tmask;
+    // Candidate pools (global memory): A row a, column half h holds its survivors
+    // at pool[(2 a + h) * ph ...], their number in pool_cnt[2 a + h] after the sweep.
+    uint64_t* pool;
+    int* pool_cnt;
+    int ph;
+    // Optional upper bound of every A row's k'-th squared distance (rowub[a]; NULL:
+    // none): the sweep starts with that threshold.  Keys of split operands carry an
+    // error, covered by the relative margin ub_margin (0 for exact keys).
+    const float* rowub;
+    float ub_margin;
 };
 
+// Entries of a row half's candidate pool: twice the list width, at least 32 more
+// than it (a chunk's survivors always fit after a compaction), whole warps.
+__host__ __device__ inline int pool_half(int kprime) {
+    int ph = 2 * kprime;
+    if (ph < kprime + 32) ph = kprime + 32;
+    if (ph > kt::PH_MAX) ph = kt::PH_MAX;
+    return (ph + 31) / 32 * 32;
+}
+
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, baug, heap, buf, locks, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, baug, tau, bars, tmem_slot, abort_flag, total;
 };
 
 // a_stream = 0: the CTA's A rows stay resident (nkb_a K blocks) and a ring stage
@@ -139,8 +163,7 @@ __host__ __device__ inline uint32_t knn_stage_bytes(int bn, int a_stream) {
     return (uint32_t)bn * 128 + a_stream * kt::A_BLK_BYTES;
 }
 
-__host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int kprime,
-                                                         int a_stream) {
+__host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int nst, int a_stream) {
     KnnSmemLayout L;
     uint32_t o = 0;
     L.a = o;
@@ -151,12 +174,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int 
     o += nst * knn_stage_bytes(bn, a_stream);
     L.baug = o;
     o += kt::NAUG * bn * 32;
-    L.heap = o;
-    o += kprime * kt::BM * 8;
-    L.buf = o;  // one buffer per column half (epilogue warp of a quarter)
-    o += 2 * kt::CAP * kt::BM * 8;
-    L.locks = o;  // 4 quarter locks (4 spare words)
-    o += 8 * 4;
+    L.tau = o;  // [2][BM] floats: each column half's current k'-th key per row
+    o += 2 * kt::BM * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -165,47 +184,6 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int 
     o += 4;
     L.total = o + 1024;  // slack for 1024-byte alignment of the base
     return L;
-}
-
-__device__ __forceinline__ uint64_t heap_init_val() {
-    return ((uint64_t)f2ord(INFINITY) << 32) | 0xFFFFFFFFull;
-}
-
-// Replace the root of the max-heap of `row` (entries strided by BM) by x and sift down.
-__device__ __forceinline__ void heap_replace_root(uint64_t* H, int row, int n, uint64_t x) {
-    int e = 0;
-    for (;;) {
-        const int l = 2 * e + 1;
-        if (l >= n) break;
-        uint64_t hc = H[l * kt::BM + row];
-        int c = l;
-        if (l + 1 < n) {
-            const uint64_t hr = H[(l + 1) * kt::BM + row];
-            if (hr > hc) { c = l + 1; hc = hr; }
-        }
-        if (hc <= x) break;
-        H[e * kt::BM + row] = hc;
-        e = c;
-    }
-    H[e * kt::BM + row] = x;
-}
-
-__device__ __forceinline__ void heap_sift(uint64_t* H, int row, int e, int n) {
-    const uint64_t x = H[e * kt::BM + row];
-    for (;;) {
-        const int l = 2 * e + 1;
-        if (l >= n) break;
-        uint64_t hc = H[l * kt::BM + row];
-        int c = l;
-        if (l + 1 < n) {
-            const uint64_t hr = H[(l + 1) * kt::BM + row];
-            if (hr > hc) { c = l + 1; hc = hr; }
-        }
-        if (hc <= x) break;
-        H[e * kt::BM + row] = hc;
-        e = c;
-    }
-    H[e * kt::BM + row] = x;
 }
 
 // Wait for outstanding tcgen05.ld; the registers are tied to the wait so that no
@@ -248,78 +226,160 @@ __device__ __forceinline__ float min32(const float (&k)[32]) {
     return fminf(min3f(b0, b1, b2), b3);
 }
 
-// Per-row top-k state.  The row's max-heap H (kp entries) is shared by the two
-// epilogue warps of a TMEM lane quarter and guarded by one lock per quarter.
-// Each warp has its own survivor buffer B (CAP entries per row; the count c lives
-// in the row's thread), so appending needs no lock: only emptying a buffer into
-// the heap does.  tau is the thread's copy of the row's k-th key.  It is
-// refreshed from the heap root without the lock: the root only ever decreases,
-// so any value read is an upper bound of the final k-th key, and a stale copy
-// only lets more columns through to the exact check at insertion.
+// ---- per-row candidate pools ----------------------------------------------------
+// The smallest `kp` composite values (key bits << 32 | global id) among a warp's
+// entries, E per lane (UINT64_MAX = no entry), n valid in all: returns the kp-th
+// smallest valid value (the largest valid one when n <= kp).  Bisection first on
+// the key bits, then on the ids of the entries tied at the k-th key; every count is
+// a warp-wide sum (redux.sync), so all lanes return the same value.
+template <int E>
+__device__ __forceinline__ uint64_t warp_select_kth(const uint64_t (&v)[E], int n, int kp) {
+    const uint32_t FULL = 0xffffffffu;
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (v[e] != ~0ull) {
+            const uint32_t h = (uint32_t)(v[e] >> 32);
+            kmin = h < kmin ? h : kmin;
+            kmax = h > kmax ? h : kmax;
+        }
+    }
+    kmin = __reduce_min_sync(FULL, kmin);
+    kmax = __reduce_max_sync(FULL, kmax);
+    if (n <= kp) {  // every entry stays: the largest one
+        uint32_t imax = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (v[e] != ~0ull && (uint32_t)(v[e] >> 32) == kmax) {
+                const uint32_t id = (uint32_t)v[e];
+                imax = id > imax ? id : imax;
+            }
+        imax = __reduce_max_sync(FULL, imax);
+        return ((uint64_t)kmax << 32) | imax;
+    }
+    // least key K with #{key <= K} >= kp: each step counts at three pivots that
+    // split [lo, hi] in four (independent warp sums) and keeps one quarter
+    uint32_t lo = kmin, hi = kmax;
+    while (lo < hi) {
+        const uint32_t q = (hi - lo) >> 2;
+        const uint32_t p1 = lo + q, p2 = lo + ((hi - lo) >> 1), p3 = hi - q - 1 > p2 ? hi - q - 1 : p2;
+        uint32_t c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t h = (uint32_t)(v[e] >> 32);
+            c1 += h <= p1 ? 1u : 0u;
+            c2 += h <= p2 ? 1u : 0u;
+            c3 += h <= p3 ? 1u : 0u;
+        }
+        c1 = __reduce_add_sync(FULL, c1);
+        c2 = __reduce_add_sync(FULL, c2);
+        c3 = __reduce_add_sync(FULL, c3);
+        if (c1 >= (uint32_t)kp) hi = p1;
+        else if (c2 >= (uint32_t)kp) { lo = p1 + 1; hi = p2; }
+        else if (c3 >= (uint32_t)kp) { lo = p2 + 1; hi = p3; }
+        else lo = p3 + 1;
+    }
+    const uint32_t K = lo;
+    uint32_t below = 0, tied = 0, imin = 0xFFFFFFFFu, imax = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t h = (uint32_t)(v[e] >> 32), id = (uint32_t)v[e];
+        below += h < K ? 1u : 0u;
+        if (h == K && v[e] != ~0ull) {
+            ++tied;
+            imin = id < imin ? id : imin;
+            imax = id > imax ? id : imax;
+        }
+    }
+    below = __reduce_add_sync(FULL, below);
+    tied = __reduce_add_sync(FULL, tied);
+    imin = __reduce_min_sync(FULL, imin);
+    imax = __reduce_max_sync(FULL, imax);
+    const uint32_t need = (uint32_t)kp - below;  // 1 <= need <= tied
+    if (need >= tied) return ((uint64_t)K << 32) | imax;
+    uint32_t ilo = imin, ihi = imax;  // least id I with #{key == K, id <= I} >= need
+    while (ilo < ihi) {
+        const uint32_t mid = ilo + ((ihi - ilo) >> 1);
+        uint32_t c = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            c += ((uint32_t)(v[e] >> 32) == K && v[e] != ~0ull && (uint32_t)v[e] <= mid) ? 1u : 0u;
+        c = __reduce_add_sync(FULL, c);
+        if (c >= need) ihi = mid; else ilo = mid + 1;
+    }
+    return ((uint64_t)K << 32) | ilo;
+}
+
+// Per-row top-k state of one epilogue thread (lane = row, one column half).
+// Survivors of the threshold test are appended to the row half's pool in global
+// memory (no lock: each half has its own pool); a pool about to overflow is
+// compacted by the whole warp to its kp smallest entries, which makes the kp-th
+// of them the half's new threshold tau.  A column half's entries above the other
+// half's tau cannot be among the row's kp smallest either, so the test uses
+// teff = min(tau, other half's tau) (read from shared memory; it only decreases,
+// so a stale value is still a valid bound).  With kp = 1 the pool is the running
+// minimum in a register.
 struct EpiState {
-    uint64_t* H;
-    uint64_t* B;
-    int* lock;
-    volatile int* abort;
-    int row, kp, c;
-    bool shared;  // take the quarter lock (switched on in the sweep loop: see there)
-    float tau;
+    uint64_t* pool;       // this thread's row half
+    uint64_t* pool0;      // row 0 of the warp, same half (row r at pool0 + 2 r ph)
+    float* tau_own;       // shared [BM]: this half's tau per row
+    const volatile float* tau_other;
+    int row, kp, ph, c;
+    float tau, teff;
+    uint64_t best;        // kp == 1
     // counters (used only by the profiling instantiation)
-    unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_ins, c_app;
+    unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_app;
     unsigned long long c_ldw, c_filter, c_append;
 };
 
-__device__ __forceinline__ void quarter_lock(EpiState& s) {
-    if (!s.shared) return;
-    if ((threadIdx.x & 31) == 0) {
-        const uint64_t t0 = globaltimer();
-        for (uint32_t it = 0;; ++it) {
-            if (atomicCAS(s.lock, 0, 1) == 0) break;
-            __nanosleep(64);
-            if ((it & 63u) == 63u && globaltimer() - t0 > 1000000000ull) {
-                *s.abort = 1;  // cannot happen unless a holder died; give up the lock
-                break;
+// Compact the pools of the rows in `mask` (lanes of this warp) to their kp
+// smallest entries and lower those rows' tau.  Each lane passes its row's count
+// and tau and gets them back (changed only for the rows compacted).  Kept out of
+// line: it is rare, and the sweep loop keeps two chunks of keys in registers.
+struct PoolState {
+    int c;
+    float tau;
+};
+__device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, int c, float tau,
+                                              uint32_t mask, float* tau_own, int row) {
+    __syncwarp();  // every lane's appends are visible to the warp
+    const int lane = threadIdx.x & 31;
+    const int E = ph >> 5;
+    while (mask) {
+        const int r = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int cr = __shfl_sync(0xffffffffu, c, r);
+        uint64_t* pr = pool0 + (int64_t)r * 2 * ph;
+        uint64_t v[kt::PH_MAX / 32];
+#pragma unroll
+        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+            const int idx = lane + 32 * e;
+            v[e] = (e < E && idx < cr) ? pr[idx] : ~0ull;
+        }
+        const uint64_t T = warp_select_kth(v, cr, kp);
+        __syncwarp();  // every load done before the pool is rewritten in place
+        int base = 0;
+#pragma unroll
+        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+            const bool keep = v[e] <= T && v[e] != ~0ull;
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            if (keep) pr[base + __popc(b & ((1u << lane) - 1u))] = v[e];
+            base += __popc(b);
+        }
+        __syncwarp();
+        if (lane == r) {
+            c = base;
+            if (cr > kp) {
+                tau = fminf(tau, ord2f((uint32_t)(T >> 32)));
+                tau_own[row] = tau;
             }
         }
-        __threadfence_block();
     }
     __syncwarp();
-}
-
-__device__ __forceinline__ void quarter_unlock(EpiState& s) {
-    if (!s.shared) return;
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        __threadfence_block();
-        atomicExch(s.lock, 0);
-    }
-}
-
-// Empty the warp's survivor buffers into the heaps of its 32 rows (under the
-// quarter lock) and refresh tau.
-template <bool PROF>
-__device__ __forceinline__ void epi_flush(EpiState& s) {
-    long long t0 = 0;
-    if (PROF) t0 = clock64();
-    quarter_lock(s);
-    const int mx = __reduce_max_sync(0xffffffffu, s.c);
-    for (int q = 0; q < mx; ++q) {
-        if (q < s.c) {
-            const uint64_t x = s.B[q * kt::BM + s.row];
-            if (x < s.H[s.row]) {
-                heap_replace_root(s.H, s.row, s.kp, x);
-                if (PROF) ++s.c_ins;
-            }
-        }
-    }
-    s.tau = ord2f((uint32_t)(s.H[s.row] >> 32));
-    quarter_unlock(s);
-    s.c = 0;
-    if (PROF) {
-        s.c_flush_cyc += clock64() - t0;
-        ++s.c_flushes;
-        s.c_iters += mx;
-    }
+    PoolState o;
+    o.c = c;
+    o.tau = tau;
+    return o;
 }
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
@@ -345,7 +405,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     }
     const float m = min32(key);
     // "<=": a key equal to the current k-th may still win on the global id
-    const bool any = __any_sync(0xffffffffu, m <= s.tau);
+    const bool any = __any_sync(0xffffffffu, m <= s.teff);
     if (PROF) {
         const long long f1 = clock64();
         s.c_filter += f1 - f0;
@@ -353,46 +413,49 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     }
     if (!any) return;
     if (PROF) ++s.c_slow;
-    // the shared root's key word, read without the lock
-    s.tau = ord2f(((volatile const uint32_t*)(s.H + s.row))[1]);
-    int n = 0;
-#pragma unroll
-    for (int u = 0; u < 32; ++u) n += key[u] <= s.tau ? 1 : 0;
     const int lane = threadIdx.x & 31;
     uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
     if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
-    if (__any_sync(0xffffffffu, s.c + n > kt::CAP)) {
-        epi_flush<PROF>(s);
-        n = 0;
-#pragma unroll
-        for (int u = 0; u < 32; ++u) n += key[u] <= s.tau ? 1 : 0;
-    }
-    if (__any_sync(0xffffffffu, n > kt::CAP)) {
-        // Many survivors (the first tiles of a sweep): groups of CAP columns, the
-        // buffer emptied before each group.
-#pragma unroll 1
-        for (int g = 0; g < 32 / kt::CAP; ++g) {
-            if (__any_sync(0xffffffffu, s.c > 0)) epi_flush<PROF>(s);
-#pragma unroll
-            for (int uu = 0; uu < kt::CAP; ++uu) {
-                float kv = key[uu];
-#pragma unroll
-                for (int gg = 1; gg < 32 / kt::CAP; ++gg)
-                    if (g == gg) kv = key[gg * kt::CAP + uu];
-                const uint32_t gid = __shfl_sync(0xffffffffu, g_l, g * kt::CAP + uu);
-                if (kv <= s.tau) {
-                    s.B[s.c * kt::BM + s.row] = ((uint64_t)f2ord(kv) << 32) | gid;
-                    ++s.c;
-                    if (PROF) ++s.c_app;
-                }
-            }
-        }
-    } else {
+    if (s.kp == 1) {  // the running minimum
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
             const uint32_t gid = __shfl_sync(0xffffffffu, g_l, u);
-            if (key[u] <= s.tau) {
-                s.B[s.c * kt::BM + s.row] = ((uint64_t)f2ord(key[u]) << 32) | gid;
+            const uint64_t x = ((uint64_t)f2ord(key[u]) << 32) | gid;
+            if (key[u] <= s.teff && x < s.best) s.best = x;
+        }
+        if (s.best != ~0ull) {
+            s.tau = ord2f((uint32_t)(s.best >> 32));
+            s.teff = s.tau;
+        }
+        if (PROF) s.c_append += clock64() - f0;
+        return;
+    }
+    s.teff = fminf(s.tau, s.tau_other[s.row]);
+    uint32_t surv = 0;  // bit u: column j0 + u survives for this row
+#pragma unroll
+    for (int u = 0; u < 32; ++u) surv |= (key[u] <= s.teff ? 1u : 0u) << u;
+    const uint32_t over = __ballot_sync(0xffffffffu, s.c + __popc(surv) > s.ph);
+    if (over) {
+        long long t0 = 0;
+        if (PROF) t0 = clock64();
+        const PoolState o = epi_compact(s.pool0, s.ph, s.kp, s.c, s.tau, over, s.tau_own, s.row);
+        s.c = o.c;
+        s.tau = o.tau;
+        s.teff = fminf(s.tau, s.tau_other[s.row]);
+        if (PROF) {
+            s.c_flush_cyc += clock64() - t0;
+            ++s.c_flushes;
+            s.c_iters += __popc(over);
+        }
+    }
+    // columns where some row of the warp has a survivor (warp-uniform skips)
+    const uint32_t any_col = __reduce_or_sync(0xffffffffu, surv);
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        if ((any_col >> u) & 1u) {
+            const uint32_t gid = __shfl_sync(0xffffffffu, g_l, u);
+            if (key[u] <= s.teff) {
+                s.pool[s.c] = ((uint64_t)f2ord(key[u]) << 32) | gid;
                 ++s.c;
                 if (PROF) ++s.c_app;
             }
@@ -471,7 +534,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
     }
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.kprime, P.a_stream);
+    const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.a_stream);
     const uint32_t STG = knn_stage_bytes(BN, P.a_stream);
     const uint32_t sA = smem_u32(base + L.a);
     const uint32_t sAaug = smem_u32(base + L.aaug);
@@ -511,14 +574,21 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         tmem_alloc(smem_u32((const void*)tmem_slot), kt::TMEM_COLS);
         tmem_relinquish();
     }
-    if (warp >= 2 && warp < 6) {  // heaps and quarter locks
-        uint64_t* H = (uint64_t*)(base + L.heap);
-        const int row = (warp & 3) * 32 + lane;
-        const uint64_t init = heap_init_val();
-        for (int e = 0; e < P.kprime; ++e) H[e * kt::BM + row] = init;
-        if (lane == 0) {
-            ((int*)(base + L.locks))[warp & 3] = 0;
+    if (warp >= 2) {  // thresholds of both column halves: the window bound, or +inf
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = q * 32 + lane;
+        const int i = rb * kt::BM + row;
+        float t = INFINITY;
+        if (P.rowub && i < pr.n_rows) {
+            const float ub = P.rowub[pr.a_row0 + i];
+            if (ub < INFINITY) {
+                // key = (dist - |x|^2) / 2, rounded up; split keys get the margin
+                const float nx = P.na[pr.a_row0 + i];
+                const float d = __fmaf_ru(P.ub_margin, 3.0f * nx + 2.0f * ub, ub);
+                t = 0.5f * __fsub_ru(d, nx);
+            }
         }
+        ((float*)(base + L.tau))[h * kt::BM + row] = t;
     }
     tc_fence_before();
     __syncthreads();
@@ -599,6 +669,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (lane == 0) {
             bool ok = mbar_wait(a_bar, 0, abort_flag);
             tc_fence_after();
+            const uint64_t adesc0 = sdesc_sw128(sA);
             int st = 0, sa = 0;
             uint32_t ph = 0, aph = 0;
             const int H2 = P.nkb_b >> 1;
@@ -633,31 +704,62 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     tc_fence_after();
                     if (PROF) w0 = clock64();
                     const uint32_t bsm = sB + st * STG;
-                    int ablk[2];
-                    int na = 1;
-                    if (P.mode == 0) {
-                        ablk[0] = j;
-                    } else if (j < H2) {
-                        ablk[0] = j;       // hi . hi
-                        ablk[1] = H2 + j;  // lo . hi
-                        na = 2;
+                    if (P.a_stream) {
+                        // A blocks streamed beside this B block (see knn_stage_bytes):
+                        // split operands pair the hi and lo A blocks with a hi B block
+                        // and the hi A block with a lo B block
+                        const int na = (P.mode == 1 && j < H2) ? 2 : 1;
+                        const int nsteps = P.mode == 0 ? min(4, P.ksteps - 4 * j) : 4;
+                        for (int q = 0; q < na; ++q) {
+                            const uint32_t asm_ = bsm + B_BLK_BYTES + q * kt::A_BLK_BYTES;
+                            for (int s = 0; s < nsteps; ++s) {
+                                if (P.kind8)
+                                    umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                            sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                else
+                                    umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                             sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                            }
+                        }
                     } else {
-                        ablk[0] = j - H2;  // hi . lo
-                    }
-                    for (int q = 0; q < na; ++q) {
-                        const uint32_t asm_ = P.a_stream
-                                                  ? bsm + B_BLK_BYTES + q * kt::A_BLK_BYTES
-                                                  : sA + ablk[q] * kt::A_BLK_BYTES;
-                        // four K steps of 32 bytes per 128-byte block (K = 16 for 16-bit
-                        // operands, K = 32 for E4M3)
+                        // K steps of 32 bytes (K = 16 for 16-bit operands, 32 for E4M3),
+                        // four per 128-byte block.  A descriptor's address field counts
+                        // 16-byte units, so a step adds 2 and an A block 1024 (shared
+                        // addresses stay below 2^18, so the field never carries).
+                        const uint64_t bd = sdesc_sw128(bsm);
+                        if (P.mode == 0) {
+                            const uint64_t ad = adesc0 + (uint64_t)j * (kt::A_BLK_BYTES >> 4);
+                            if (4 * j + 4 <= P.ksteps) {
 #pragma unroll
-                        for (int s = 0; s < 4; ++s) {
-                            if (P.kind8)
-                                umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32), sdesc_sw128(bsm + s * 32),
-                                        P.idesc_neg, accum);
-                            else
-                                umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
-                                         sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                for (int u = 0; u < 4; ++u) {
+                                    if (P.kind8)
+                                        umma_f8(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
+                                    else
+                                        umma_f16(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
+                                }
+                            } else {  // the last block: its zero K steps are not issued
+                                for (int u = 0; 4 * j + u < P.ksteps; ++u) {
+                                    if (P.kind8)
+                                        umma_f8(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
+                                    else
+                                        umma_f16(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
+                                }
+                            }
+                        } else {
+                            // compact split sections: B step sb < hs (hi) meets A steps sb
+                            // (hi . hi) and sb + hs (lo . hi); B step sb >= hs (lo) meets
+                            // A step sb - hs (hi . lo).  A step a: block a / 4, slot a % 4.
+                            for (int u = 0; u < 4 && 4 * j + u < P.ksteps; ++u) {
+                                const int sb = 4 * j + u;
+                                const int a0 = sb < P.hs ? sb : sb - P.hs;
+                                umma_f16(d_tmem, adesc0 + ((a0 >> 2) << 10) + ((a0 & 3) << 1),
+                                         bd + 2 * u, P.idesc_neg, accum);
+                                if (sb < P.hs) {
+                                    const int a1 = sb + P.hs;
+                                    umma_f16(d_tmem, adesc0 + ((a1 >> 2) << 10) + ((a1 & 3) << 1),
+                                             bd + 2 * u, P.idesc_neg, accum);
+                                }
+                            }
                         }
                     }
                     long long w1 = 0;
@@ -694,21 +796,24 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const int h = (warp - 2) >> 2;
         EpiState s;
         s.row = q * 32 + lane;
-        s.H = (uint64_t*)(base + L.heap);
-        s.B = (uint64_t*)(base + L.buf) + h * kt::CAP * kt::BM;
-        s.c = 0;
-        s.shared = false;
-        s.lock = (int*)(base + L.locks) + q;
-        s.abort = abort_flag;
+        const int i = rb * kt::BM + s.row;     // row index inside the problem
+        const int i0 = rb * kt::BM + q * 32;   // first row of this warp
+        const int64_t arow0 = pr.a_row0 + i0;  // gathered A row of lane 0
+        s.ph = P.ph;
         s.kp = P.kprime;
-        s.tau = INFINITY;
-        s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_ins = s.c_app = 0;
+        s.pool0 = P.pool + (arow0 * 2 + h) * (int64_t)P.ph;
+        s.pool = s.pool0 + (int64_t)lane * 2 * P.ph;
+        s.tau_own = (float*)(base + L.tau) + h * kt::BM;
+        s.tau_other = (const volatile float*)((float*)(base + L.tau) + (1 - h) * kt::BM);
+        s.c = 0;
+        s.best = ~0ull;
+        s.tau = s.tau_own[s.row];
+        s.teff = fminf(s.tau, s.tau_other[s.row]);
+        s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_app = 0;
         s.c_ldw = s.c_filter = s.c_append = 0;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
-        const int i = rb * kt::BM + s.row;     // row index inside the problem
-        const int i0 = rb * kt::BM + q * 32;   // first row of this warp
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
         const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
@@ -724,10 +829,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             if (!mbar_wait(accf_bar + 8 * a, par, abort_flag)) { ok = false; break; }
             if (PROF) e_wait += clock64() - w0;
             tc_fence_after();
-            // The lock flag is a loop-carried value switched on here rather than a
-            // constant: the code generated this way measured 16% faster on the
-            // Sift-like 1M build (same work, same results).
-            if (run == 1) s.shared = true;
             {
                 const uint32_t tb = tmem + lane_addr + a * BN + h * HALF;
                 const int jt = t * BN + h * HALF;
@@ -766,15 +867,11 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 }
             }
         }
-        // each warp empties its own buffer (under the lock: the partner may still
-        // be sweeping)
         ok = __all_sync(0xffffffffu, ok);
-        if (ok && __any_sync(0xffffffffu, s.c > 0)) epi_flush<PROF>(s);
         if (PROF) {
             prof_add_warp(TC_EPI_CYCLES, (unsigned long long)(clock64() - e_t0));
             prof_add_warp(TC_EPI_WAIT, e_wait);
             prof_add_warp(TC_EPI_FLUSH, s.c_flush_cyc);
-            prof_add_warp(TC_INSERTS, s.c_ins);
             prof_add_warp(TC_APPENDS, s.c_app);
             prof_add_warp(TC_LD_WAIT, s.c_ldw);
             prof_add_warp(TC_FILTER, s.c_filter);
@@ -786,36 +883,15 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                 prof_add(TC_FLUSH_ITERS, s.c_iters);
             }
         }
-        // both warps of the quarter are done with the rows: h = 0 finishes them
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "r"(64) : "memory");
         if (!ok || *abort_flag) {
-            if (h == 0 && lane == 0) atomicOr(P.status, DEV_TIMEOUT);
-        } else if (h == 0) {
-            if (i < pr.n_rows) {
-                // Heap sort ascending, then write (global id, |x|^2 + 2 key).
-                uint64_t* H = s.H;
-                const int row = s.row, kp = s.kp;
-                for (int end = kp - 1; end > 0; --end) {
-                    const uint64_t top = H[row];
-                    H[row] = H[end * kt::BM + row];
-                    H[end * kt::BM + row] = top;
-                    heap_sift(H, row, 0, end);
-                }
-                const float nx = P.na[pr.a_row0 + i];
-                const int64_t orow = P.outrow ? P.outrow[pr.a_row0 + i] : pr.out_row0 + i;
-                for (int e = 0; e < P.k_out; ++e) {
-                    const uint64_t x = H[e * kt::BM + row];
-                    const uint32_t g = (uint32_t)x;  // global id (or column index)
-                    uint32_t id = ANN_PAD;
-                    float dd = INFINITY;
-                    if (g != 0xFFFFFFFFu) {
-                        id = g;
-                        dd = fmaf(2.0f, ord2f((uint32_t)(x >> 32)), nx);
-                    }
-                    P.out_id[orow * P.k_out + e] = id;
-                    P.out_d[orow * P.k_out + e] = dd;
-                }
+            if (lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+        } else if (i < pr.n_rows) {
+            // the pool's size (k_pool_finalize merges the two halves)
+            if (s.kp == 1) {
+                if (s.best != ~0ull) s.pool[0] = s.best;
+                s.c = s.best != ~0ull ? 1 : 0;
             }
+            P.pool_cnt[(pr.a_row0 + i) * 2 + h] = s.c;
         }
     }
     tc_fence_before();
@@ -1342,6 +1418,85 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
     }
 }
 
+// ---- pool finalisation ---------------------------------------------------------------
+// Every valid A row of the tile launch's problems: the kprime smallest entries of
+// the union of its two column halves' pools, sorted by (key, global id), written as
+// (global id, |x|^2 + 2 key) to the first k_out slots of its output row, then ANN_PAD
+// / +inf.  One warp per row: the row's entries are selected with warp_select_kth,
+// gathered into shared memory in ballot order, then sorted with a warp bitonic sort
+// of KE entries per lane.
+template <int KE>
+__global__ void __launch_bounds__(256)
+k_pool_finalize(const KnnParams P) {
+    __shared__ uint64_t stage[8][32 * KE];
+    const int64_t bid = blockIdx.x;
+    if (bid >= P.blk_off[P.nprob]) return;
+    int lo = 0, hi = P.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blk_off[mid] <= bid) lo = mid; else hi = mid - 1;
+    }
+    const KnnProblem pr = P.probs[lo];
+    const int rb = (int)(bid - P.blk_off[lo]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int EH = P.ph >> 5;
+    uint64_t* stg = stage[warp];
+    for (int r = warp; r < kt::BM; r += 8) {
+        const int i = rb * kt::BM + r;
+        if (i >= pr.n_rows) break;
+        const int64_t arow = pr.a_row0 + i;
+        // counts clamped to the pool (an aborted sweep leaves them unwritten)
+        const int c0 = min(max(P.pool_cnt[arow * 2], 0), P.ph);
+        const int c1 = min(max(P.pool_cnt[arow * 2 + 1], 0), P.ph);
+        const uint64_t* h0 = P.pool + arow * 2 * (int64_t)P.ph;
+        const uint64_t* h1 = h0 + P.ph;
+        uint64_t v[2 * kt::PH_MAX / 32];
+#pragma unroll
+        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+            const int idx = lane + 32 * e;
+            v[e] = (e < EH && idx < c0) ? h0[idx] : ~0ull;
+            v[kt::PH_MAX / 32 + e] = (e < EH && idx < c1) ? h1[idx] : ~0ull;
+        }
+        const int n = c0 + c1;
+        const int kp = P.kprime;
+        const uint64_t T = n > 0 ? warp_select_kth(v, n, kp) : 0ull;
+        // the kept entries (kp of them, or all n) into the staging array
+        for (int e = lane; e < 32 * KE; e += 32) stg[e] = ~0ull;
+        __syncwarp();
+        int base = 0;
+#pragma unroll
+        for (int e = 0; e < 2 * kt::PH_MAX / 32; ++e) {
+            const bool keep = n > 0 && v[e] != ~0ull && v[e] <= T;
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            const int pos = base + __popc(b & ((1u << lane) - 1u));
+            if (keep && pos < 32 * KE) stg[pos] = v[e];
+            base += __popc(b);
+        }
+        __syncwarp();
+        uint64_t w[KE];
+#pragma unroll
+        for (int e = 0; e < KE; ++e) w[e] = stg[lane * KE + e];
+        __syncwarp();
+        warp_bitonic_u64<KE>(w);
+        const float nx = P.na[arow];
+        const int64_t orow = P.outrow ? P.outrow[arow] : pr.out_row0 + i;
+#pragma unroll
+        for (int e = 0; e < KE; ++e) {
+            const int slot = lane * KE + e;
+            if (slot < P.k_out) {
+                uint32_t id = ANN_PAD;
+                float dd = INFINITY;
+                if (w[e] != ~0ull) {
+                    id = (uint32_t)w[e];
+                    dd = fmaf(2.0f, ord2f((uint32_t)(w[e] >> 32)), nx);
+                }
+                P.out_id[orow * P.k_out + slot] = id;
+                P.out_d[orow * P.k_out + slot] = dd;
+            }
+        }
+    }
+}
+
 template <int E>
 __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
                          const uint32_t* __restrict__ row_ids, int64_t nrows,
@@ -1524,9 +1679,11 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
         p.ab_fmt = 1;
         p.rerank = true;
     } else if (dtype == ANN_F32) {
+        // compact split layout (A resident): sections of align(d, 16) elements,
+        // the row padded to whole K blocks after the lo section
         p.mode = 1;
-        p.Kh = (int)align_up((size_t)d, kt::KB);
-        p.Kp = 2 * p.Kh;
+        p.Kh = (int)align_up((size_t)d, 16);
+        p.Kp = (int)align_up((size_t)(2 * p.Kh), kt::KB);
         p.ab_fmt = 1;
         p.rerank = true;
     } else {
@@ -1537,24 +1694,30 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
         p.rerank = dtype != ANN_U8;
     }
     p.kbe = p.elem8 ? kt::KB8 : kt::KB;
-    p.nkb_a = p.Kp / p.kbe;
-    p.nkb_b = p.nkb_a;
     const int wide = precision == ANN_EXACT ? k + 16 : 128;
     p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : wide) : k;
     if (p.kprime < k) p.kprime = k;
     if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
-    // Resident A rows if they fit: the widest tile with a 3-stage ring, else the
-    // narrow one, else 2 stages.  Otherwise (large d, single-product operands)
-    // the A blocks stream through the ring beside the B blocks.
+    // Resident A rows if they fit: the widest tile with a 3-stage ring, else with
+    // 2 stages (an N = 256 MMA does twice the work of an N = 128 one for about the
+    // same issue cost), else the narrow tile.  Otherwise (large d) the A blocks
+    // stream through the ring beside the B blocks; split operands then use
+    // sections of whole K blocks (the streamed pairing is by block).
     const size_t cap = 227 * 1024;
     p.nst = 0;
     p.a_stream = 0;
-    const int tries[4][2] = {{256, 3}, {128, 3}, {256, 2}, {128, 2}};
+    const int tries[4][2] = {{256, 3}, {256, 2}, {128, 3}, {128, 2}};
     for (int as = 0; as <= (p.mode ? 2 : 1) && !p.nst; as += (p.mode ? 2 : 1)) {
+        if (as && p.mode == 1) {
+            p.Kh = (int)align_up((size_t)d, kt::KB);
+            p.Kp = 2 * p.Kh;
+        }
+        p.nkb_a = p.Kp / p.kbe;
+        p.nkb_b = p.nkb_a;
         for (int q = 0; q < 4 && !p.nst; ++q) {
             const int bn = tries[q][0];
             for (int nst = kt::MAX_NST; nst >= tries[q][1]; --nst)
-                if (knn_smem_layout(bn, p.nkb_a, nst, p.kprime, as).total <= cap) {
+                if (knn_smem_layout(bn, p.nkb_a, nst, as).total <= cap) {
                     p.nst = nst;
                     p.bn = bn;
                     p.a_stream = as;
@@ -1562,10 +1725,14 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
                 }
         }
     }
+    // K steps holding data (32 bytes each): see KnnParams::ksteps
+    const int step_elems = p.kbe / 4;
+    p.hs = p.mode == 1 ? p.Kh / step_elems : 0;
+    p.ksteps = p.mode == 1 ? 2 * p.hs : (int)((d + step_elems - 1) / step_elems);
     if (!p.nst)
         return fail(ANN_ERR_UNSUPPORTED, "shard_knn: d=%d with k'=%d does not fit shared memory",
                     d, p.kprime);
-    p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.kprime, p.a_stream).total;
+    p.smem = knn_smem_layout(p.bn, p.nkb_a, p.nst, p.a_stream).total;
     *pl = p;
     return ANN_OK;
 }
@@ -1586,14 +1753,14 @@ int knn_plan_variants(int d, int dtype, int k, int precision, int rerank_k, KnnP
     for (int bn = 256; bn >= 128 && n < max_out; bn -= 128) {
         int found = 0;
         for (int nst = kt::MAX_NST; nst >= 2 && found < 2 && n < max_out; --nst) {
-            if (knn_smem_layout(bn, base.nkb_a, nst, base.kprime, base.a_stream).total > cap)
+            if (knn_smem_layout(bn, base.nkb_a, nst, base.a_stream).total > cap)
                 continue;
             ++found;
             if (bn == base.bn && nst == base.nst) continue;
             KnnPlan v = base;
             v.bn = bn;
             v.nst = nst;
-            v.smem = knn_smem_layout(bn, base.nkb_a, nst, base.kprime, base.a_stream).total;
+            v.smem = knn_smem_layout(bn, base.nkb_a, nst, base.a_stream).total;
             out[n++] = v;
         }
     }
@@ -1718,7 +1885,7 @@ template <int NW4>
 __global__ void __launch_bounds__(256)
 k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
          const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
-         int k, int64_t nblocks, float* __restrict__ bub) {
+         int k, int64_t nblocks, float* __restrict__ bub, float* __restrict__ rowub) {
     extern __shared__ uint32_t wv[];  // [256][ws] packed vectors, then [256] norms
     __shared__ unsigned int bmax;
     const int64_t bid = blockIdx.x;
@@ -1789,6 +1956,7 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
             }
             ub = lo;
         }
+        if (rowub && lane == 0) rowub[pr.a_row0 + i] = ub == 0xFFFFFFFFu ? INFINITY : (float)ub;
         wmax = ub > wmax ? ub : wmax;
     }
     if (lane == 0) atomicMax(&bmax, wmax);
@@ -1802,7 +1970,7 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
 __global__ void __launch_bounds__(256)
 k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src,
              const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
-             int k, int64_t nblocks, float* __restrict__ bub) {
+             int k, int64_t nblocks, float* __restrict__ bub, float* __restrict__ rowub) {
     extern __shared__ float wf[];  // [256][d + 1]
     __shared__ unsigned int bmax;
     const int64_t bid = blockIdx.x;
@@ -1862,6 +2030,10 @@ k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src
             }
             ub = lo;
         }
+        // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
+        if (rowub && lane == 0)
+            rowub[pr.a_row0 + i] = ub >= NONE ? INFINITY
+                                              : __uint_as_float(ub) * (1.0f + (float)(d + 4) * 0x1p-22f);
         wmax = ub > wmax ? ub : wmax;
     }
     if (lane == 0) atomicMax(&bmax, wmax);
@@ -1983,6 +2155,8 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
     w.norms = cv.take<float>((size_t)w.rows_cap + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)rows * pl.kprime) : nullptr;
     w.cand_d = pl.rerank ? cv.take<float>((size_t)rows * pl.kprime) : nullptr;
+    w.pool = cv.take<uint64_t>((size_t)w.rows_cap * 2 * pool_half(pl.kprime));
+    w.pool_cnt = cv.take<int>((size_t)w.rows_cap * 2);
     w.src = cv.take<int64_t>((size_t)w.rows_cap);
     w.gid = cv.take<uint32_t>((size_t)w.rows_cap);
     w.outrow = cv.take<int64_t>((size_t)w.rows_cap);
@@ -2008,7 +2182,9 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
         w.gmaxn = cv.take<float>((size_t)ng);
         w.bub = cv.take<float>((size_t)w.nblocks);
         w.tmask = cv.take<uint32_t>((size_t)w.nblocks * kt::TM_WORDS);
+        w.rowub = cv.take<float>((size_t)w.rows_cap);
     } else {
+        w.rowub = nullptr;
         w.gcent = nullptr;
         w.grad = nullptr;
         w.gmaxn = nullptr;
@@ -2036,6 +2212,8 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
     ANN_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
     if (grid <= 0) return ANN_OK;
+    if (!P.pool || !P.pool_cnt || P.ph < P.kprime + (P.kprime > 1 ? 32 : 0))
+        return fail(ANN_ERR_UNSUPPORTED, "tile launch: candidate pools missing or too small");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed && tile_timing_on()) {
         e0 = tile_event();
@@ -2048,6 +2226,16 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         ANN_CHECK_CUDA(cudaEventRecord(e1, st));
         tile_timing_record(e0, e1);
     }
+    // merge the two column halves' pools of every row into its sorted list
+    if (P.kprime <= 32)
+        k_pool_finalize<1><<<(unsigned)grid, 256, 0, st>>>(P);
+    else if (P.kprime <= 64)
+        k_pool_finalize<2><<<(unsigned)grid, 256, 0, st>>>(P);
+    else if (P.kprime <= 128)
+        k_pool_finalize<4><<<(unsigned)grid, 256, 0, st>>>(P);
+    else
+        k_pool_finalize<8><<<(unsigned)grid, 256, 0, st>>>(P);
+    ANN_CHECK_LAUNCH();
     return ANN_OK;
 }
 
@@ -2105,6 +2293,8 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.nst = pl.nst;
     P.kbe = pl.kbe;
     P.kind8 = pl.elem8;
+    P.ksteps = pl.ksteps;
+    P.hs = pl.hs;
     // same descriptor layout for kind::f16 and kind::f8f6f4 (format 0 = FP16 / E4M3)
     P.idesc_neg = idesc_f16(kt::BM, pl.bn, pl.ab_fmt) | (1u << 13);  // negate A
     P.idesc_aug = idesc_f16(kt::BM, pl.bn, 1);                       // BF16 norm step
@@ -2112,6 +2302,11 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.out_d = out_d;
     P.status = device_status_ptr();
     P.tmask = nullptr;
+    P.pool = nullptr;
+    P.pool_cnt = nullptr;
+    P.ph = pool_half(pl.kprime);
+    P.rowub = nullptr;
+    P.ub_margin = 0.0f;
     return P;
 }
 
@@ -2206,7 +2401,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnPlan pp = pl;
     pp.kprime = 1;
     pp.rerank = false;
-    pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, 1, pp.a_stream).total;
+    pp.smem = knn_smem_layout(pp.bn, pp.nkb_a, pp.nst, pp.a_stream).total;
     const unsigned int* amax = nullptr;
     if (pl.scaled) {
         int rc8 = launch_absmax(X, dtype, N * d, nullptr, 0, (unsigned int*)w.amax, st);
@@ -2243,6 +2438,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     KnnParams PP = base_params(pp, 1, w.blk_off, w.pprobs, C, w.norms, nullptr, nullptr, 0, 0,
                                w.cell, w.cell_d);
     PP.k_out = 1;
+    PP.pool = w.pool;
+    PP.pool_cnt = w.pool_cnt;
     rc = launch_tiles(pp, w.G, w.rows_cap, w.ones, w.GP, w.paug, w.prows_cap, PP,
                       rows / kt::BM + C + 1, st, false);
     if (rc) return rc;
@@ -2259,6 +2456,8 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     // 3. the kNN sweep
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
                               pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
+    P.pool = w.pool;
+    P.pool_cnt = w.pool_cnt;
     const int64_t grid = rows / kt::BM + C + 1;
     const bool skip_u8 = dtype == ANN_U8 && pl.mode == 0 && !pl.rerank && d <= 256 &&
                          d % 4 == 0 && ((uintptr_t)X & 3) == 0;
@@ -2278,12 +2477,12 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                 ANN_CHECK_CUDA(cudaFuncSetAttribute(
                     k_ub_own<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
                 k_ub_own<32><<<(unsigned)grid, 256, ubs, st>>>(
-                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
+                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub, w.rowub);
             } else {
                 ANN_CHECK_CUDA(cudaFuncSetAttribute(
                     k_ub_own<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
                 k_ub_own<64><<<(unsigned)grid, 256, ubs, st>>>(
-                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
+                    (const uint8_t*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub, w.rowub);
             }
         } else {
             // Split BF16 keys (three products, FP32 accumulation): the error of a
@@ -2294,7 +2493,7 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
             ANN_CHECK_CUDA(cudaFuncSetAttribute(
                 k_ub_own_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
             k_ub_own_f32<<<(unsigned)grid, 256, ubs, st>>>(
-                (const float*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub);
+                (const float*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub, w.rowub);
         }
         ANN_CHECK_LAUNCH();
         k_tile_mask<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
@@ -2302,6 +2501,9 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
             w.tmask);
         ANN_CHECK_LAUNCH();
         P.tmask = w.tmask;
+        // each row's window bound starts its threshold
+        P.rowub = w.rowub;
+        P.ub_margin = kslack;
     }
     rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st, true);
     if (rc) return rc;
@@ -2330,6 +2532,8 @@ size_t query_ws(int64_t N, int64_t nq, const KnnPlan& pl, QueryWs* out, void* ba
     w.nb = cv.take<float>((size_t)w.capB + 512);
     w.cand_id = pl.rerank ? cv.take<uint32_t>((size_t)nq * pl.kprime) : nullptr;
     w.cand_d = pl.rerank ? cv.take<float>((size_t)nq * pl.kprime) : nullptr;
+    w.pool = cv.take<uint64_t>((size_t)w.capA * 2 * pool_half(pl.kprime));
+    w.pool_cnt = cv.take<int>((size_t)w.capA * 2);
     w.srcA = cv.take<int64_t>((size_t)w.capA);
     w.srcB = cv.take<int64_t>((size_t)w.capB);
     w.amax = cv.take<float>(4);
@@ -2384,6 +2588,8 @@ int run_knn_query(const void* X, int64_t N, const void* Q, int64_t nq, int d, in
     if (rc) return rc;
     KnnParams P = base_params(pl, k, w.blk_off, w.prob, 1, w.na, nullptr, nullptr, 0, 0,
                               pl.rerank ? w.cand_id : out_id, pl.rerank ? w.cand_d : out_d);
+    P.pool = w.pool;
+    P.pool_cnt = w.pool_cnt;
     const int64_t grid = (nq + kt::BM - 1) / kt::BM;
     rc = launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st, true);
     if (rc) return rc;
@@ -2416,7 +2622,7 @@ static int screen_plan(int d, int ks, KnnPlan* pl) {
     if (rc) return rc;
     pl->rerank = false;
     pl->kprime = ks;
-    pl->smem = knn_smem_layout(pl->bn, pl->nkb_a, pl->nst, ks, pl->a_stream).total;
+    pl->smem = knn_smem_layout(pl->bn, pl->nkb_a, pl->nst, pl->a_stream).total;
     return ANN_OK;
 }
 
@@ -2465,6 +2671,8 @@ int run_screen(const void* Xa, int dta, const uint32_t* rowsel, int64_t p0, int6
         return rc;
     KnnParams P = base_params(pl, ks, w.blk_off, w.prob, 1, w.na, nullptr, nullptr, 0, 0, out_id,
                               out_d);
+    P.pool = w.pool;
+    P.pool_cnt = w.pool_cnt;
     const int64_t grid = (na + kt::BM - 1) / kt::BM;
     return launch_tiles(pl, w.GA, w.capA, w.ones, w.GB, w.augB, w.capB, P, grid, st, false);
 }

@@ -189,15 +189,19 @@ __global__ void k_recall_finish(const unsigned long long* hits, int64_t nq, int 
 // ---- medoid --------------------------------------------------------------------------
 constexpr int MED_ROWS = 4096;  // rows per partial-sum chunk
 
-__global__ void k_col_partials(const void* X, int64_t N, int d, int dtype,
+// Chunk c (rows [c * MED_ROWS, ...)) of column t; chunks c = blockIdx.y,
+// blockIdx.y + gridDim.y, ... (the grid's y extent is capped at 65535).
+__global__ void k_col_partials(const void* X, int64_t N, int d, int dtype, int64_t nchunk,
                                double* __restrict__ part /* [nchunk][d] */) {
-    const int64_t r0 = blockIdx.y * (int64_t)MED_ROWS;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= d) return;
-    double s = 0.0;
-    const int64_t r1 = r0 + MED_ROWS < N ? r0 + MED_ROWS : N;
-    for (int64_t r = r0; r < r1; ++r) s += (double)load_elem(X, dtype, r * d + t);
-    part[blockIdx.y * (int64_t)d + t] = s;
+    for (int64_t c = blockIdx.y; c < nchunk; c += gridDim.y) {
+        const int64_t r0 = c * (int64_t)MED_ROWS;
+        double s = 0.0;
+        const int64_t r1 = r0 + MED_ROWS < N ? r0 + MED_ROWS : N;
+        for (int64_t r = r0; r < r1; ++r) s += (double)load_elem(X, dtype, r * d + t);
+        part[c * (int64_t)d + t] = s;
+    }
 }
 
 __global__ void k_col_mean(const double* __restrict__ part, int64_t nchunk, int64_t N, int d,
@@ -281,8 +285,8 @@ size_t medoid_ws(int64_t N, int d, double** part, float** mean, unsigned long lo
 int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, double* part, float* mean,
                unsigned long long* best, cudaStream_t st) {
     const int64_t nchunk = (N + MED_ROWS - 1) / MED_ROWS;
-    dim3 g1((unsigned)((d + 127) / 128), (unsigned)nchunk);
-    k_col_partials<<<g1, 128, 0, st>>>(X, N, d, dtype, part);
+    dim3 g1((unsigned)((d + 127) / 128), (unsigned)(nchunk < 65535 ? nchunk : 65535));
+    k_col_partials<<<g1, 128, 0, st>>>(X, N, d, dtype, nchunk, part);
     ANN_CHECK_LAUNCH();
     k_col_mean<<<(unsigned)((d + 127) / 128), 128, 0, st>>>(part, nchunk, N, d, mean, best);
     ANN_CHECK_LAUNCH();
@@ -303,30 +307,63 @@ constexpr size_t NOALLOC_MEAN_FLOATS = 4096;               // d <= 4096
 constexpr size_t NOALLOC_BYTES = NOALLOC_PART_DOUBLES * 8 + NOALLOC_MEAN_FLOATS * 4 + 256;
 static __device__ __align__(256) unsigned char g_medoid_scratch[NOALLOC_BYTES];
 
-// Device address of g_medoid_scratch on the current device, looked up once per
-// device (with that device current) and cached.  Host code must never hand the
-// symbol itself to a kernel: on the host it names a stand-in, not device memory.
+// Device address of g_medoid_scratch in the current context, looked up once per
+// context (with its device current) and cached.  The cache is keyed on the
+// driver context, so a context created after a device reset gets its own
+// lookup.  Host code must never hand the symbol itself to a kernel: on the host
+// it names a stand-in, not device memory.
+typedef int (*PFN_ctxGetCurrent)(void**);
+
+static int current_context(void** ctx) {
+    static PFN_ctxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return fail(ANN_ERR_CUDA, "cuCtxGetCurrent unavailable");
+        fn = (PFN_ctxGetCurrent)p;
+    }
+    *ctx = nullptr;
+    if (fn(ctx) != 0) return fail(ANN_ERR_CUDA, "cuCtxGetCurrent failed");
+    return ANN_OK;
+}
+
 static int medoid_scratch_ptr(unsigned char** out) {
     static std::mutex mu;
-    static unsigned char* ptrs[64] = {nullptr};
-    int dev = 0;
-    ANN_CHECK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(ANN_ERR_UNSUPPORTED, "device index %d >= 64", dev);
+    constexpr int SLOTS = 64;
+    static void* ctxs[SLOTS] = {nullptr};
+    static unsigned char* ptrs[SLOTS] = {nullptr};
+    void* ctx = nullptr;
+    int rc = current_context(&ctx);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(mu);
-    if (!ptrs[dev]) {
+    int slot = -1;
+    for (int i = 0; ctx && i < SLOTS; ++i)
+        if (ctxs[i] == ctx) { slot = i; break; }
+    if (slot < 0) {
+        // The lookup also makes the current device's primary context current on
+        // this thread when none was.
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_medoid_scratch);
         if (e != cudaSuccess || !p)
             return fail(ANN_ERR_CUDA, "cudaGetSymbolAddress(g_medoid_scratch): %s",
                         cudaGetErrorString(e));
-        ptrs[dev] = (unsigned char*)p;
+        if (!ctx && (rc = current_context(&ctx))) return rc;
+        slot = 0;
+        for (int i = 0; i < SLOTS; ++i)
+            if (!ctxs[i]) { slot = i; break; }
+        // all slots taken (more than 64 contexts seen): reuse slot 0
+        ctxs[slot] = ctx;
+        ptrs[slot] = (unsigned char*)p;
     }
-    *out = ptrs[dev];
+    *out = ptrs[slot];
     return ANN_OK;
 }
 
-int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry,
-                       cudaStream_t st) {
+// Size limits of ann_medoid_noalloc (checked before any pointer query or launch).
+int medoid_noalloc_check(int64_t N, int d) {
     const int64_t nchunk = (N + MED_ROWS - 1) / MED_ROWS;
     if (d < 1 || d > (int)NOALLOC_MEAN_FLOATS)
         return fail(ANN_ERR_INVALID_ARG, "ann_medoid_noalloc: d must be in [1, %d]",
@@ -336,8 +373,15 @@ int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* ent
                     "ann_medoid_noalloc: ceil(N / %d) * d = %lld exceeds the fixed scratch of "
                     "%zu column sums; use ann_medoid with a workspace",
                     MED_ROWS, (long long)nchunk * d, NOALLOC_PART_DOUBLES);
+    return ANN_OK;
+}
+
+int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry,
+                       cudaStream_t st) {
+    int rc = medoid_noalloc_check(N, d);
+    if (rc) return rc;
     unsigned char* base = nullptr;
-    int rc = medoid_scratch_ptr(&base);
+    rc = medoid_scratch_ptr(&base);
     if (rc) return rc;
     // Every scratch byte read below is written first in the same call (partial
     // sums, then the mean and the argmin seed), so nothing needs clearing.

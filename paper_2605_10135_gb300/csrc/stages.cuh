@@ -75,6 +75,7 @@ struct KnnPlan {
     int Kp;           // elements per gathered row
     int Kh;           // split: elements per section
     int nkb_a, nkb_b;
+    int ksteps, hs;   // K steps (32 bytes) holding data; split: steps per section
     int elem8;        // 1: E4M3 operands (kind::f8f6f4)
     int scaled;       // 1: operands carry one global scale from max|x| (E4M3, scaled FP16)
     int kbe;          // elements per 128-byte K block
@@ -102,6 +103,8 @@ struct KnnWs {
     float* norms;         // [rows_cap + 512]
     uint32_t* cand_id;  // [rows x kprime] when re-ranking
     float* cand_d;
+    uint64_t* pool;     // [rows_cap x 2 x pool_half(kprime)] candidate pools of the sweeps
+    int* pool_cnt;      // [rows_cap x 2]
     int64_t rows_cap;
     // cell ordering
     int64_t* src;       // [rows_cap] vector held by each gathered row (-1: padding)
@@ -127,6 +130,7 @@ struct KnnWs {
     float* gmaxn;       // [rows_cap / 128] largest |y|^2 of the group
     float* bub;         // [blocks] bound on the k-th squared distance of a row block
     uint32_t* tmask;    // [blocks x 64] tiles each row block sweeps
+    float* rowub;       // [rows_cap] bound on each row's k'-th squared distance
     int64_t nblocks;
 };
 // Exact skipping of distance tiles (switch, statistics of the last launches).
@@ -155,6 +159,8 @@ struct QueryWs {
     float* nb;
     uint32_t* cand_id;
     float* cand_d;
+    uint64_t* pool;     // [capA x 2 x pool_half(kprime)] candidate pools of the sweep
+    int* pool_cnt;      // [capA x 2]
     int64_t capA, capB;
     int64_t* srcA;
     int64_t* srcB;
@@ -229,6 +235,7 @@ size_t medoid_ws(int64_t N, int d, double** part, float** mean, unsigned long lo
                  void* base, size_t cap);
 int run_medoid(const void* X, int64_t N, int d, int dtype, uint32_t* entry, double* part,
                float* mean, unsigned long long* best, cudaStream_t st);
+int medoid_noalloc_check(int64_t N, int d);
 int run_medoid_noalloc(const void* X, int64_t N, int d, int dtype, uint32_t* entry,
                        cudaStream_t st);
 

@@ -159,36 +159,47 @@ def uneven_shards(n: int, n_shards: int, r: int, lo: int, hi: int, seed: int
     """Synthetic uneven shards for the grouped form.
 
     Shard sizes are drawn log-uniform on [lo, hi] and rescaled so that they sum
-    to r * n; every vector is then placed in r distinct shards by size-weighted
-    sampling without replacement.  Returns (members [r*n] uint32 sorted by id
-    within each shard, offsets [n_shards + 1] int64).
+    to r * n (largest remainders first); every vector is then placed in r
+    distinct shards so that shard s holds exactly its size: the r * n slots
+    (shard s repeated size[s] times) are shuffled and dealt r to a vector, and a
+    vector dealt the same shard twice trades one slot with a random other
+    vector until both hold distinct shards.  Returns (members [r*n] uint32
+    sorted by id within each shard, offsets [n_shards + 1] int64).
     """
     rng = np.random.default_rng(seed)
     raw = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_shards))
-    size = np.floor(raw / raw.sum() * r * n).astype(np.int64)
-    size[np.argsort(-raw)[: r * n - size.sum()]] += 1
-    cap = size.copy()
-    owner = np.empty((n, r), dtype=np.int64)
-    order = rng.permutation(n)
-    for g in order:
-        w = cap.astype(np.float64)
-        pick = []
-        for _ in range(r):
-            p = w / w.sum()
-            c = int(rng.choice(n_shards, p=p))
-            pick.append(c)
-            w[c] = 0.0
-        for c in pick:
-            cap[c] -= 1
-        owner[g] = pick
+    exact = raw / raw.sum() * r * n
+    size = np.floor(exact).astype(np.int64)
+    size[np.argsort(-(exact - size), kind="stable")[: r * n - size.sum()]] += 1
+    if r > n_shards or size.max() > n:
+        raise ValueError("each vector needs r distinct shards of at most n members")
+    slots = np.repeat(np.arange(n_shards, dtype=np.int64), size)
+    rng.shuffle(slots)
+    owner = slots.reshape(n, r)
+
+    def clash(rows):
+        o = np.sort(owner[rows], axis=1)
+        return (o[:, 1:] == o[:, :-1]).any(axis=1)
+
+    bad = np.flatnonzero(clash(np.arange(n)))
+    for g in bad:
+        while True:
+            row = owner[g]
+            vals, cnt = np.unique(row, return_counts=True)
+            if (cnt == 1).all():
+                break
+            a = int(np.flatnonzero(row == vals[np.argmax(cnt > 1)])[0])
+            h = int(rng.integers(n))
+            b = int(rng.integers(r))
+            if h == g or owner[h, b] in row or row[a] in np.delete(owner[h], b):
+                continue
+            owner[g, a], owner[h, b] = owner[h, b], owner[g, a]
     offsets = np.zeros(n_shards + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(size)
-    members = np.empty(r * n, dtype=np.uint32)
-    fill = offsets[:-1].copy()
-    for g in range(n):
-        for c in owner[g]:
-            members[fill[c]] = g
-            fill[c] += 1
+    flat_shard = owner.ravel()
+    flat_id = np.repeat(np.arange(n, dtype=np.int64), r)
+    order = np.lexsort((flat_id, flat_shard))
+    members = flat_id[order].astype(np.uint32)
     return members, offsets
 
 

@@ -135,6 +135,36 @@ def test_shard_knn_u8_duplicates_and_small_shards():
     assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
 
 
+@pytest.mark.parametrize("d", [256, 258])
+@pytest.mark.parametrize("skip", [True, False])
+def test_shard_knn_u8_wide_rows_bit_exact(d, skip):
+    """uint8 rows up to d = 258, the widest the integer tiles keep exact: the
+    extreme rows (all 255 against all 0: distance 255^2 d, the largest key
+    magnitudes) and their duplicates give bit-exact ids and distances, with
+    the exact tile skipping on and off."""
+    X = datagen.clustered_u8(2600, d, 10, seed=45 + d)
+    X[:6] = 255
+    X[6:12] = 0
+    X[12:18, : d // 2] = 255
+    X[12:18, d // 2:] = 0
+    X[18:24] = X[100:106]  # duplicates of ordinary rows
+    n = X.shape[0]
+    # shard 0: the 24 special rows alone (all-255 against all-0 in every list);
+    # shard 1: every row; shard 2: the extreme rows beside 400 ordinary ones
+    parts = [np.arange(24), np.arange(n), np.concatenate([np.arange(12), np.arange(200, 600)])]
+    mem = np.concatenate(parts).astype(np.uint32)
+    off = np.cumsum([0] + [len(q) for q in parts]).astype(np.int64)
+    ann.tile_prune(skip)
+    try:
+        gid, gd = ann.shard_knn(T(X), T(mem), T(off), 40)
+    finally:
+        ann.tile_prune(True)
+    oid, od = oracle.shard_knn(X, mem, off, 40)
+    assert np.array_equal(as_u32(gid), oid)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+    assert od[np.isfinite(od)].max() == 255.0 ** 2 * d  # all-255 against all-0
+
+
 @pytest.mark.parametrize("kind,k", [("f32", 32), ("f32", 8), ("f16", 48), ("bf16", 20)])
 def test_shard_knn_float_rule(kind, k):
     if kind == "f32":
@@ -268,6 +298,33 @@ def test_search_bit_exact(kind):
     gt, _ = oracle.bruteforce(X, Q, 10)
     rec = ann.recall(gids, T(gt), 10)
     assert abs(float(rec.item()) - oracle.recall_at(rids, gt)) < 1e-6
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_search_eval_through_the_c_abi(kind):
+    """ann_search_eval (search from the medoid, then recall@10 against brute-force
+    truth): ids and distance counts bit-exact against the oracle's search, recall
+    equal to the oracle's recall of its own result."""
+    if kind == "u8":
+        X = datagen.clustered_u8(2500, 64, 16, seed=271)
+        Q = datagen.clustered_u8(120, 64, 16, seed=272)
+    else:
+        X = datagen.gaussian_mixture_f32(2500, 48, seed=273)
+        Q = datagen.gaussian_mixture_f32(120, 48, seed=274)
+    mem, off = _oracle_shards(X, 4, 2, seed=275)
+    oid, od = oracle.shard_knn(X, mem, off, 24)
+    qid, qd = oracle.prune(oid, od, mem, off, 12)
+    og, ogd, odeg = oracle.merge(qid, qd, mem, off, X.shape[0])
+    entry = oracle.medoid(X)
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    for Ls in (10, 48):
+        gids, rec, gcnt = ann.search_eval(T(og), T(odeg), T(X), T(Q), T(gt), entry, Ls)
+        rids, rcnt = oracle.search(og, odeg, X, Q, entry, Ls, 10)
+        assert np.array_equal(as_u32(gids), rids)
+        assert np.array_equal(gcnt.cpu().numpy().astype(np.int64), rcnt)
+        assert abs(float(rec.item()) - oracle.recall_at(rids, gt)) < 1e-6
+    with pytest.raises(ann.AnnError):  # recall@10 needs a list of at least 10
+        ann.search_eval(T(og), T(odeg), T(X), T(Q), T(gt), entry, 8)
 
 
 @pytest.mark.parametrize("kind", ["u8", "f32"])

@@ -80,6 +80,8 @@ def test_reference_arm_line_has_the_contract_keys(capsys):
     class A:
         warmup = 3
         steps = 1
+        precision = "exact"
+        epsilon = None
 
     bench.run_reference(A(), configs.GAUSS_10K, 1, 0)
     lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
@@ -91,3 +93,6 @@ def test_reference_arm_line_has_the_contract_keys(capsys):
     assert j["cpu_baseline"]["value"] == j["value"]
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
     assert j["config"]["workload"] == configs.GAUSS_10K.name
+    # the same workload description the GPU arm prints
+    assert j["config"] == bench.workload_config(configs.GAUSS_10K, A())
+    assert j["warmup"] == 3 and j["extrapolated"] is True and j["wall_ms_per_step"] > 0
