@@ -73,9 +73,9 @@ __device__ __forceinline__ int shard_of(const int64_t* __restrict__ offsets, int
 }
 
 // Shared memory of one prune warp: table keys, list, overflow list, counts,
-// overflow count, table positions, overflow positions.
+// overflow count, table positions, overflow positions, slot occupancy bits.
 __host__ __device__ constexpr size_t prune_warp_smem(int KM) {
-    return (size_t)1024 * 4 + (size_t)KM * 12 + 16 + 1024 + (size_t)KM;
+    return (size_t)1024 * 4 + (size_t)KM * 12 + 16 + 1024 + (size_t)KM + 128;
 }
 
 // ---- prune ------------------------------------------------------------------------
@@ -128,11 +128,13 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
     int* novf_p = cnt + KM;                      // [1] (+pad)
     uint8_t* tpos = (uint8_t*)(novf_p + 4);      // [TS]
     uint8_t* ovf_pos = tpos + TS;                // [KM]
+    uint32_t* occ_bits = (uint32_t*)(ovf_pos + KM);  // [TS / 32]: slot h used = bit h
     const uint32_t lt = (1u << lane) - 1;
     const bool vec = (k & 3) == 0;
     // the table starts empty once; after each row only the slots its ids used are
     // emptied again
     for (int h = lane; h < TS; h += 32) tkey[h] = ANN_PAD;
+    occ_bits[lane] = 0;
     __syncwarp();
 
     for (int64_t p = blockIdx.x * (int64_t)nwb + wib; p < rows; p += (int64_t)gridDim.x * nwb) {
@@ -161,6 +163,7 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 const uint32_t h = tslot(id);
                 if (atomicCAS(&tkey[h], ANN_PAD, id) == ANN_PAD) {
                     tpos[h] = (uint8_t)j;
+                    atomicOr(&occ_bits[h >> 5], 1u << (h & 31));
                 } else {
                     const int o = atomicAdd(novf_p, 1);
                     ovf[o] = id;
@@ -169,6 +172,10 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
             }
             __syncwarp();
             const int novf = *novf_p;
+            // Each lane holds 32 of the table's occupancy bits: an id whose slot is
+            // empty (most of a neighbour's list) is rejected with one shuffle,
+            // without a shared-memory probe.
+            const uint32_t occ = occ_bits[lane];
             // Lane-parallel over the neighbours v_i: each lane reads whole lists
             // (16-byte loads), so all of a row's list reads are in flight at once.
             // The neighbours' rows are looked up first, all lanes' loads together.
@@ -178,34 +185,46 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 const int i = lane + 32 * e;
                 wrow[e] = i < m ? row_in_range(start, rowlist, list[i], m0, m1) : -1;
             }
+            // every lane runs the same loops (the occupancy shuffles need the whole
+            // warp); a lane without a neighbour row reads nothing
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int i = lane + 32 * e;
                 const int64_t w = wrow[e];
-                if (w < 0) continue;
-                const uint32_t* Lw = knn_id + w * k;
+                const bool has = w >= 0;
+                const uint32_t* Lw = knn_id + (has ? w : 0) * k;
                 if (vec) {
                     for (int t0 = 0; t0 < k; t0 += 16) {
                         uint4 q4[4];
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
-                            q4[r] = t0 + 4 * r < k ? __ldg((const uint4*)(Lw + t0) + r)
-                                                   : make_uint4(ANN_PAD, ANN_PAD, ANN_PAD, ANN_PAD);
+                            q4[r] = (has && t0 + 4 * r < k)
+                                        ? __ldg((const uint4*)(Lw + t0) + r)
+                                        : make_uint4(ANN_PAD, ANN_PAD, ANN_PAD, ANN_PAD);
 #pragma unroll
                         for (int r = 0; r < 4; ++r) {
                             const uint32_t xs[4] = {q4[r].x, q4[r].y, q4[r].z, q4[r].w};
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const int t = t0 + 4 * r + c;
-                                const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, xs[c]);
-                                if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                                const uint32_t h = tslot(xs[c]);
+                                const uint32_t ow = __shfl_sync(0xffffffffu, occ, (int)(h >> 5));
+                                if (has && ((ow >> (h & 31)) & 1u)) {
+                                    const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, xs[c]);
+                                    if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                                }
                             }
                         }
                     }
                 } else {
                     for (int t = 0; t < k; ++t) {
-                        const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, __ldg(Lw + t));
-                        if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                        const uint32_t x = has ? __ldg(Lw + t) : ANN_PAD;
+                        const uint32_t h = tslot(x);
+                        const uint32_t ow = __shfl_sync(0xffffffffu, occ, (int)(h >> 5));
+                        if (has && ((ow >> (h & 31)) & 1u)) {
+                            const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, x);
+                            if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                        }
                     }
                 }
             }
@@ -216,6 +235,7 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
                 sel[e] = j < m ? (((uint32_t)cnt[j] << 16) | (uint32_t)j) : 0xFFFFFFFFu;
             }
             for (int j = lane; j < m; j += 32) tkey[tslot(list[j])] = ANN_PAD;
+            occ_bits[lane] = 0;
             warp_sort<E, uint32_t>(sel);
         }
         // sel[] (element index lane*E+e) now ranks positions; keep the first min(R, m).

@@ -65,6 +65,7 @@ constexpr int NAUG = 1;                 // norm-block slots (loaded first in eac
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
 constexpr int PH_MAX = 256;             // candidate pool entries per row half, at most
+constexpr int SC = 16;                  // survivors a thread stashes before a tile's release
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
@@ -152,7 +153,7 @@ __host__ __device__ inline int pool_half(int kprime) {
 }
 
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, baug, tau, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, baug, tau, stash, bars, tmem_slot, abort_flag, total;
 };
 
 // a_stream = 0: the CTA's A rows stay resident (nkb_a K blocks) and a ring stage
@@ -176,6 +177,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int 
     o += kt::NAUG * bn * 32;
     L.tau = o;  // [2][BM] floats: each column half's current k'-th key per row
     o += 2 * kt::BM * 4;
+    L.stash = o;  // [EPI_WARPS][SC][32] survivors (key bits << 32 | column), lane-minor
+    o += kt::EPI_WARPS * kt::SC * 32 * 8;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -310,6 +313,79 @@ __device__ __forceinline__ uint64_t warp_select_kth(const uint64_t (&v)[E], int 
     return ((uint64_t)K << 32) | ilo;
 }
 
+// A bound T with kp <= #{entries <= T} <= maxkeep (n > maxkeep valid entries, E per
+// lane): the same search on the key bits as warp_select_kth, stopped as soon as the
+// keys at or below the upper end of the range number at most maxkeep; only when
+// more than maxkeep entries share the kp-th key are the ids of those entries
+// searched (then exactly kp stay).  Every entry at or below T is kept by the
+// caller, so the bound tightens by whole keys without an exact selection.
+template <int E>
+__device__ __forceinline__ uint64_t warp_select_bound(const uint64_t (&v)[E], int n, int kp,
+                                                      int maxkeep) {
+    const uint32_t FULL = 0xffffffffu;
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (v[e] != ~0ull) {
+            const uint32_t h = (uint32_t)(v[e] >> 32);
+            kmin = h < kmin ? h : kmin;
+            kmax = h > kmax ? h : kmax;
+        }
+    }
+    kmin = __reduce_min_sync(FULL, kmin);
+    kmax = __reduce_max_sync(FULL, kmax);
+    // invariant: #{key <= hi} = chi >= kp, #{key < lo} < kp
+    uint32_t lo = kmin, hi = kmax, chi = (uint32_t)n;
+    while (chi > (uint32_t)maxkeep && lo < hi) {
+        const uint32_t q = (hi - lo) >> 2;
+        const uint32_t p1 = lo + q, p2 = lo + ((hi - lo) >> 1), p3 = hi - q - 1 > p2 ? hi - q - 1 : p2;
+        uint32_t c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t h = (uint32_t)(v[e] >> 32);
+            c1 += h <= p1 ? 1u : 0u;
+            c2 += h <= p2 ? 1u : 0u;
+            c3 += h <= p3 ? 1u : 0u;
+        }
+        c1 = __reduce_add_sync(FULL, c1);
+        c2 = __reduce_add_sync(FULL, c2);
+        c3 = __reduce_add_sync(FULL, c3);
+        if (c1 >= (uint32_t)kp) { hi = p1; chi = c1; }
+        else if (c2 >= (uint32_t)kp) { lo = p1 + 1; hi = p2; chi = c2; }
+        else if (c3 >= (uint32_t)kp) { lo = p2 + 1; hi = p3; chi = c3; }
+        else lo = p3 + 1;
+    }
+    if (chi <= (uint32_t)maxkeep) return ((uint64_t)hi << 32) | 0xFFFFFFFFull;
+    // more than maxkeep entries at or below the kp-th key K = hi: the ties at K are
+    // split by id so that exactly kp entries stay
+    const uint32_t K = hi;
+    uint32_t below = 0, imin = 0xFFFFFFFFu, imax = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t h = (uint32_t)(v[e] >> 32), id = (uint32_t)v[e];
+        below += h < K ? 1u : 0u;
+        if (h == K && v[e] != ~0ull) {
+            imin = id < imin ? id : imin;
+            imax = id > imax ? id : imax;
+        }
+    }
+    below = __reduce_add_sync(FULL, below);
+    imin = __reduce_min_sync(FULL, imin);
+    imax = __reduce_max_sync(FULL, imax);
+    const uint32_t need = (uint32_t)kp - below;
+    uint32_t ilo = imin, ihi = imax;
+    while (ilo < ihi) {
+        const uint32_t mid = ilo + ((ihi - ilo) >> 1);
+        uint32_t c = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            c += ((uint32_t)(v[e] >> 32) == K && v[e] != ~0ull && (uint32_t)v[e] <= mid) ? 1u : 0u;
+        c = __reduce_add_sync(FULL, c);
+        if (c >= need) ihi = mid; else ilo = mid + 1;
+    }
+    return ((uint64_t)K << 32) | ilo;
+}
+
 // Per-row top-k state of one epilogue thread (lane = row, one column half).
 // Survivors of the threshold test are appended to the row half's pool in global
 // memory (no lock: each half has its own pool); a pool about to overflow is
@@ -324,7 +400,9 @@ struct EpiState {
     uint64_t* pool0;      // row 0 of the warp, same half (row r at pool0 + 2 r ph)
     float* tau_own;       // shared [BM]: this half's tau per row
     const volatile float* tau_other;
-    int row, kp, ph, c;
+    uint64_t* stash;      // shared: this warp's stash, entry e of lane l at [e * 32 + l]
+    const uint32_t* gidrow;  // global id of each column of the shard (NULL: the column)
+    int row, kp, ph, c, sn;
     float tau, teff;
     uint64_t best;        // kp == 1
     // counters (used only by the profiling instantiation)
@@ -356,7 +434,12 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
             const int idx = lane + 32 * e;
             v[e] = (e < E && idx < cr) ? pr[idx] : ~0ull;
         }
-        const uint64_t T = warp_select_kth(v, cr, kp);
+        // keep between kp and maxkeep entries: a quarter of the slack may stay
+        // above the kp-th, which lets the bound stop early
+        int maxkeep = kp + ((ph - kp) >> 2);
+        if (maxkeep > ph - 32) maxkeep = ph - 32;
+        if (maxkeep < kp) maxkeep = kp;
+        const uint64_t T = cr > maxkeep ? warp_select_bound(v, cr, kp, maxkeep) : ~0ull - 1;
         __syncwarp();  // every load done before the pool is rewritten in place
         int base = 0;
 #pragma unroll
@@ -369,7 +452,7 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
         __syncwarp();
         if (lane == r) {
             c = base;
-            if (cr > kp) {
+            if (cr > maxkeep) {
                 tau = fminf(tau, ord2f((uint32_t)(T >> 32)));
                 tau_own[row] = tau;
             }
@@ -382,12 +465,68 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
     return o;
 }
 
+// Compact the pools of the rows whose count would pass ph with `add` more entries.
+template <bool PROF>
+__device__ __forceinline__ void epi_make_room(EpiState& s, int add) {
+    const uint32_t over = __ballot_sync(0xffffffffu, s.c + add > s.ph);
+    if (over) {
+        long long t0 = 0;
+        if (PROF) t0 = clock64();
+        const PoolState o = epi_compact(s.pool0, s.ph, s.kp, s.c, s.tau, over, s.tau_own, s.row);
+        s.c = o.c;
+        s.tau = o.tau;
+        s.teff = fminf(s.tau, s.tau_other[s.row]);
+        if (PROF) {
+            s.c_flush_cyc += clock64() - t0;
+            ++s.c_flushes;
+            s.c_iters += __popc(over);
+        }
+    }
+}
+
+// Move every thread's stashed survivors (key bits << 32 | shard column) into its
+// pool as (key bits << 32 | global id), after a tile's accumulator is released.
+template <bool PROF>
+__device__ __forceinline__ void epi_flush_stash(EpiState& s) {
+    if (!__any_sync(0xffffffffu, s.sn > 0)) return;
+    long long f0 = 0;
+    if (PROF) f0 = clock64();
+    epi_make_room<PROF>(s, s.sn);
+    const int lane = threadIdx.x & 31;
+    const int mx = __reduce_max_sync(0xffffffffu, (uint32_t)s.sn);
+    for (int e0 = 0; e0 < mx; e0 += 4) {
+        uint64_t v[4];
+        uint32_t g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = e0 + q < s.sn ? s.stash[(e0 + q) * 32 + lane] : ~0ull;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t col = (uint32_t)v[q];
+            g[q] = (v[q] != ~0ull && s.gidrow) ? __ldg(s.gidrow + col) : col;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (v[q] != ~0ull && ord2f((uint32_t)(v[q] >> 32)) <= s.teff) {
+                s.pool[s.c] = (v[q] & 0xFFFFFFFF00000000ull) | g[q];
+                ++s.c;
+                if (PROF) ++s.c_app;
+            }
+        }
+    }
+    s.sn = 0;
+    __syncwarp();
+    if (PROF) s.c_append += clock64() - f0;
+}
+
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
-// (every comparison with NaN is false, and the minimum skips NaN).
+// (every comparison with NaN is false, and the minimum skips NaN).  A chunk with
+// survivors stashes them (shared memory, no global id yet) so the accumulator can
+// go back to the MMA warp soon; a thread whose stash cannot take them has the
+// stashes emptied first, and a chunk with more survivors than a stash holds (the
+// first tiles of a sweep) goes straight to the pools.
 template <bool PROF>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], int j0, int i,
-                                          int n_cols, int self_exclude, bool edge,
-                                          const uint32_t* __restrict__ gidrow) {
+                                          int n_cols, int self_exclude, bool edge) {
     long long f0 = 0;
     if (PROF) {
         ++s.c_chunks;
@@ -414,9 +553,9 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     if (!any) return;
     if (PROF) ++s.c_slow;
     const int lane = threadIdx.x & 31;
-    uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
-    if (gidrow && j0 + lane < n_cols) g_l = __ldg(gidrow + j0 + lane);
     if (s.kp == 1) {  // the running minimum
+        uint32_t g_l = (uint32_t)(j0 + lane);  // global id of column j0 + lane
+        if (s.gidrow && j0 + lane < n_cols) g_l = __ldg(s.gidrow + j0 + lane);
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
             const uint32_t gid = __shfl_sync(0xffffffffu, g_l, u);
@@ -434,31 +573,37 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     uint32_t surv = 0;  // bit u: column j0 + u survives for this row
 #pragma unroll
     for (int u = 0; u < 32; ++u) surv |= (key[u] <= s.teff ? 1u : 0u) << u;
-    const uint32_t over = __ballot_sync(0xffffffffu, s.c + __popc(surv) > s.ph);
-    if (over) {
-        long long t0 = 0;
-        if (PROF) t0 = clock64();
-        const PoolState o = epi_compact(s.pool0, s.ph, s.kp, s.c, s.tau, over, s.tau_own, s.row);
-        s.c = o.c;
-        s.tau = o.tau;
-        s.teff = fminf(s.tau, s.tau_other[s.row]);
-        if (PROF) {
-            s.c_flush_cyc += clock64() - t0;
-            ++s.c_flushes;
-            s.c_iters += __popc(over);
+    if (__any_sync(0xffffffffu, s.sn + __popc(surv) > kt::SC)) {
+        epi_flush_stash<PROF>(s);
+        surv = 0;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) surv |= (key[u] <= s.teff ? 1u : 0u) << u;
+        if (__any_sync(0xffffffffu, __popc(surv) > kt::SC)) {
+            // straight to the pools, global ids shuffled from the lanes that hold them
+            uint32_t g_l = (uint32_t)(j0 + lane);
+            if (s.gidrow && j0 + lane < n_cols) g_l = __ldg(s.gidrow + j0 + lane);
+            epi_make_room<PROF>(s, __popc(surv));
+            const uint32_t any_col = __reduce_or_sync(0xffffffffu, surv);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                if ((any_col >> u) & 1u) {
+                    const uint32_t gid = __shfl_sync(0xffffffffu, g_l, u);
+                    if (key[u] <= s.teff) {
+                        s.pool[s.c] = ((uint64_t)f2ord(key[u]) << 32) | gid;
+                        ++s.c;
+                        if (PROF) ++s.c_app;
+                    }
+                }
+            }
+            if (PROF) s.c_append += clock64() - f0;
+            return;
         }
     }
-    // columns where some row of the warp has a survivor (warp-uniform skips)
-    const uint32_t any_col = __reduce_or_sync(0xffffffffu, surv);
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
-        if ((any_col >> u) & 1u) {
-            const uint32_t gid = __shfl_sync(0xffffffffu, g_l, u);
-            if (key[u] <= s.teff) {
-                s.pool[s.c] = ((uint64_t)f2ord(key[u]) << 32) | gid;
-                ++s.c;
-                if (PROF) ++s.c_app;
-            }
+        if ((surv >> u) & 1u) {
+            s.stash[s.sn * 32 + lane] = ((uint64_t)f2ord(key[u]) << 32) | (uint32_t)(j0 + u);
+            ++s.sn;
         }
     }
     if (PROF) s.c_append += clock64() - f0;
@@ -669,7 +814,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (lane == 0) {
             bool ok = mbar_wait(a_bar, 0, abort_flag);
             tc_fence_after();
-            const uint64_t adesc0 = sdesc_sw128(sA);
             int st = 0, sa = 0;
             uint32_t ph = 0, aph = 0;
             const int H2 = P.nkb_b >> 1;
@@ -704,60 +848,64 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     tc_fence_after();
                     if (PROF) w0 = clock64();
                     const uint32_t bsm = sB + st * STG;
-                    if (P.a_stream) {
-                        // A blocks streamed beside this B block (see knn_stage_bytes):
-                        // split operands pair the hi and lo A blocks with a hi B block
-                        // and the hi A block with a lo B block
-                        const int na = (P.mode == 1 && j < H2) ? 2 : 1;
-                        const int nsteps = P.mode == 0 ? min(4, P.ksteps - 4 * j) : 4;
-                        for (int q = 0; q < na; ++q) {
-                            const uint32_t asm_ = bsm + B_BLK_BYTES + q * kt::A_BLK_BYTES;
-                            for (int s = 0; s < nsteps; ++s) {
-                                if (P.kind8)
-                                    umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32),
-                                            sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
-                                else
-                                    umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
-                                             sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                    if (P.mode == 1 && !P.a_stream) {
+                        // compact split sections (A resident): B step sb < hs (hi)
+                        // meets A steps sb (hi . hi) and sb + hs (lo . hi); B step
+                        // sb >= hs (lo) meets A step sb - hs (hi . lo).  A step a sits
+                        // in block a / 4 at byte 32 (a % 4).
+                        for (int u = 0; u < 4 && 4 * j + u < P.ksteps; ++u) {
+                            const int sb = 4 * j + u;
+                            const int a0 = sb < P.hs ? sb : sb - P.hs;
+                            umma_f16(d_tmem,
+                                     sdesc_sw128(sA + (a0 >> 2) * kt::A_BLK_BYTES + (a0 & 3) * 32),
+                                     sdesc_sw128(bsm + u * 32), P.idesc_neg, accum);
+                            if (sb < P.hs) {
+                                const int a1 = sb + P.hs;
+                                umma_f16(d_tmem,
+                                         sdesc_sw128(sA + (a1 >> 2) * kt::A_BLK_BYTES +
+                                                     (a1 & 3) * 32),
+                                         sdesc_sw128(bsm + u * 32), P.idesc_neg, accum);
                             }
                         }
                     } else {
-                        // K steps of 32 bytes (K = 16 for 16-bit operands, 32 for E4M3),
-                        // four per 128-byte block.  A descriptor's address field counts
-                        // 16-byte units, so a step adds 2 and an A block 1024 (shared
-                        // addresses stay below 2^18, so the field never carries).
-                        const uint64_t bd = sdesc_sw128(bsm);
+                        int ablk[2];
+                        int na = 1;
                         if (P.mode == 0) {
-                            const uint64_t ad = adesc0 + (uint64_t)j * (kt::A_BLK_BYTES >> 4);
-                            if (4 * j + 4 <= P.ksteps) {
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    if (P.kind8)
-                                        umma_f8(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
-                                    else
-                                        umma_f16(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
-                                }
-                            } else {  // the last block: its zero K steps are not issued
-                                for (int u = 0; 4 * j + u < P.ksteps; ++u) {
-                                    if (P.kind8)
-                                        umma_f8(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
-                                    else
-                                        umma_f16(d_tmem, ad + 2 * u, bd + 2 * u, P.idesc_neg, accum);
-                                }
-                            }
+                            ablk[0] = j;
+                        } else if (j < H2) {
+                            ablk[0] = j;       // hi . hi
+                            ablk[1] = H2 + j;  // lo . hi
+                            na = 2;
                         } else {
-                            // compact split sections: B step sb < hs (hi) meets A steps sb
-                            // (hi . hi) and sb + hs (lo . hi); B step sb >= hs (lo) meets
-                            // A step sb - hs (hi . lo).  A step a: block a / 4, slot a % 4.
-                            for (int u = 0; u < 4 && 4 * j + u < P.ksteps; ++u) {
-                                const int sb = 4 * j + u;
-                                const int a0 = sb < P.hs ? sb : sb - P.hs;
-                                umma_f16(d_tmem, adesc0 + ((a0 >> 2) << 10) + ((a0 & 3) << 1),
-                                         bd + 2 * u, P.idesc_neg, accum);
-                                if (sb < P.hs) {
-                                    const int a1 = sb + P.hs;
-                                    umma_f16(d_tmem, adesc0 + ((a1 >> 2) << 10) + ((a1 & 3) << 1),
-                                             bd + 2 * u, P.idesc_neg, accum);
+                            ablk[0] = j - H2;  // hi . lo
+                        }
+                        // K steps of the block that hold data: the last block of plain
+                        // operands may end in zero steps, which are not issued
+                        const bool full = P.mode == 1 || 4 * j + 4 <= P.ksteps;
+                        for (int q = 0; q < na; ++q) {
+                            const uint32_t asm_ = P.a_stream
+                                                      ? bsm + B_BLK_BYTES + q * kt::A_BLK_BYTES
+                                                      : sA + ablk[q] * kt::A_BLK_BYTES;
+                            // four K steps of 32 bytes per 128-byte block (K = 16 for
+                            // 16-bit operands, K = 32 for E4M3)
+                            if (full) {
+#pragma unroll
+                                for (int s = 0; s < 4; ++s) {
+                                    if (P.kind8)
+                                        umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                                sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                    else
+                                        umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                                 sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                }
+                            } else {
+                                for (int s = 0; 4 * j + s < P.ksteps; ++s) {
+                                    if (P.kind8)
+                                        umma_f8(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                                sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
+                                    else
+                                        umma_f16(d_tmem, sdesc_sw128(asm_ + s * 32),
+                                                 sdesc_sw128(bsm + s * 32), P.idesc_neg, accum);
                                 }
                             }
                         }
@@ -806,6 +954,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.tau_own = (float*)(base + L.tau) + h * kt::BM;
         s.tau_other = (const volatile float*)((float*)(base + L.tau) + (1 - h) * kt::BM);
         s.c = 0;
+        s.sn = 0;
+        s.stash = (uint64_t*)(base + L.stash) + (warp - 2) * kt::SC * 32;
+        s.gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
         s.best = ~0ull;
         s.tau = s.tau_own[s.row];
         s.teff = fminf(s.tau, s.tau_other[s.row]);
@@ -816,7 +967,6 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         if (PROF) e_t0 = clock64();
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
-        const uint32_t* gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
         constexpr int HALF = BN / 2;
         for (int tt = 0, run = 0; tt < ntiles && run < nrun; ++tt) {
             const int t = tile_at(tt, t0, ntiles);
@@ -845,8 +995,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) s.c_ldw += clock64() - l0;
                     tmem_ld32(tb + (c + 1) * 32, vb);
                     if (jt + c * 32 < pr.n_cols)
-                        epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge,
-                                        gidrow);
+                        epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge);
                     __syncwarp();
                     if (PROF) l0 = clock64();
                     tmem_wait_ld32(vb);
@@ -862,9 +1011,12 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     }
                     if (jt + (c + 1) * 32 < pr.n_cols)
                         epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
-                                        edge, gidrow);
+                                        edge);
                     __syncwarp();
                 }
+                // the accumulator is back with the MMA warp: the tile's stashed
+                // survivors join the pools while the next tile is computed
+                epi_flush_stash<PROF>(s);
             }
         }
         ok = __all_sync(0xffffffffu, ok);
