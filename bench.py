@@ -196,8 +196,9 @@ def workload_config(w, args):
             "partition": ("k-means, 10 iterations" if w.uneven is None else
                           "synthetic uneven shards, sizes log-uniform on [%d, %d] rescaled to "
                           "r N rows" % tuple(w.uneven)),
-            "tile_launch": "one per shard" if getattr(args, "per_shard", False) else
-                           "one grouped launch over all shards",
+            "tile_launch": ("one per shard" if getattr(args, "per_shard", False) else
+                            "one grouped launch over all shards (a CTA per row block, "
+                            "largest shard first)"),
             "precision": args.precision, "epsilon": args.epsilon,
             "l2": "flushed (512 MB write) before every timed GPU step"}
 
@@ -220,6 +221,24 @@ def whole_job_rate(units_per_rank, world, ms):
     """Units processed by all ranks per second, timed by the slowest rank (weak scaling:
     every rank builds its own replica of the workload)."""
     return world * units_per_rank / (ms * 1e-3)
+
+
+def screening_error(X, row_vecs, ids, dist):
+    """(max, mean) of |dist - d| / d over the listed (row, id) pairs with d > 0, d the
+    squared distance in float64 (a measurement of the screening keys' error)."""
+    rel = []
+    for r in range(ids.shape[0]):
+        ok = ids[r] != 0xFFFFFFFF
+        if not ok.any():
+            continue
+        c = ids[r][ok].astype(np.int64)
+        d = ((X[c].astype(np.float64) - X[int(row_vecs[r])].astype(np.float64)) ** 2).sum(1)
+        pos = d > 0
+        rel.append(np.abs(dist[r][ok][pos] - d[pos]) / d[pos])
+    if not rel:
+        return 0.0, 0.0
+    a = np.concatenate(rel)
+    return float(a.max()), float(a.mean())
 
 
 def union_recall_at_10(ann, Xd, out, N, nq, seed):
@@ -480,6 +499,37 @@ def main():
         w.N, min(args.entries, w.N), replace=False)).astype(np.int32)).to(dev)
     ids_e, cnt_e = ann.search_entries(out["graph"], out["degree"], Xd, Q, ent, 64, 10)
     recall_e = float(ann.recall(ids_e, gt, 10).item())
+    # the merged graph with reverse edges (an alternative merge, not timed in the
+    # step): its own time, and search recall from the medoid and from the entries
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rg, _, rdeg = ann.merge_reverse(out["graph"], out["gdist"], out["degree"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ids_r, cnt_r = ann.search(rg, rdeg, Xd, Q, entry, 64, 10)
+    ids_re, _ = ann.search_entries(rg, rdeg, Xd, Q, ent, 64, 10)
+    reverse = {"merge_ms": ev0.elapsed_time(ev1),
+               "search_recall_at_10": float(ann.recall(ids_r, gt, 10).item()),
+               "mean_dist_count": float(cnt_r.float().mean().item()),
+               "search_recall_at_10_from_entries": float(ann.recall(ids_re, gt, 10).item()),
+               "mean_degree": float(rdeg.float().mean().item())}
+    del rg, rdeg, ids_r, ids_re
+    # screening error of float forms (the screened lists before the exact re-rank)
+    # against the FP64 distances, on 2000 sampled rows
+    screening = None
+    if w.dtype != "u8" and prec != ann.LEARNED and shards is None:
+        cid, cd = ann.shard_knn_screen(Xd, out["members"], out["offsets"], w.k, prec,
+                                       args.rerank_k)
+        rows_s = torch.from_numpy(np.linspace(0, cid.shape[0] - 1, 2000).astype(np.int64)).to(dev)
+        sid = cid.index_select(0, rows_s).cpu().numpy().view(np.uint32)
+        sdd = cd.index_select(0, rows_s).cpu().numpy().astype(np.float64)
+        mem_h = out["members"].index_select(0, rows_s).cpu().numpy().view(np.uint32)
+        mx, mean = screening_error(X, mem_h, sid, sdd)
+        screening = {"rows_sampled": 2000, "list_width": int(cid.shape[1]),
+                     "max_rel_error": mx, "mean_rel_error": mean,
+                     "definition": "|screening distance - d64| / d64 over every listed "
+                                   "(row, id) with d64 > 0, before the FP32 re-rank"}
+        del cid, cd
     status = ann.device_status()
 
     # one more step with events between the stages (not timed above)
@@ -602,6 +652,10 @@ def main():
             "mean_dist_count": float(cnt.float().mean().item()),
             "search_recall_at_10_from_entries": recall_e, "search_entries": int(ent.numel()),
             "mean_dist_count_from_entries": float(cnt_e.float().mean().item()),
+            "reverse_edges": reverse,
+            "reverse_edges_definition": ("the merged graph with reverse edges (ann_merge_reverse, "
+                                         "an alternative merge timed on its own) searched the "
+                                         "same way"),
         },
         "detail": {
             "learned": (None if prec != ann.LEARNED else {
@@ -611,6 +665,7 @@ def main():
                 "fell_back_to_exact": out.get("precision") != ann.LEARNED,
                 "timed_step_includes_training": True}),
             "tile_operands": operands, "tensor_products_per_pair": products,
+            "screening_error": screening,
             "selective": (None if sel is None else {
                 "epsilon": sel.epsilon, "tau0": sel.tau0, "block": sel.block,
                 "capacity": sel.capacity, "cand": sel.cand,

@@ -144,6 +144,7 @@ int ann_tile_counters_read(unsigned long long* out, int n);
 int ann_tile_prune(int on);
 int ann_tile_prune_stats(unsigned long long* out, int n);
 
+
 /* Self-test of the bounded device waits (no fault, no hang): one warp waits on
  * an mbarrier that nothing completes, through the bounded wait that every
  * pipelined kernel uses; mode 0 lets the limit (limit_us microseconds, at most
@@ -279,7 +280,8 @@ int ann_partition_selective(const void* X, int64_t N, int d, int dtype, int C,
  *                    ann_learned_train); NULL makes ANN_LEARNED the exact form
  *                    (ANN_EXACT).  Other precisions: NULL.
  * Limits: d <= 4096 (uint8: d <= 258, which keeps the integer tiles exact),
- * 1 <= k <= 96, 1 <= C <= 1024, every shard smaller than 2^24 members.  When
+ * 1 <= k <= 240, rerank_k <= 256, 1 <= C <= 1024, every shard smaller than 2^24
+ * members.  When
  * the 128 rows of a block do not fit shared memory (large d) their K blocks
  * stream through the ring beside the B blocks instead of staying resident.
  * ------------------------------------------------------------------------- */
@@ -289,6 +291,19 @@ int ann_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                   const int64_t* offsets, int C, int64_t rows, int k, int precision, int rerank_k,
                   const void* model, uint32_t* knn_id, float* knn_d, void* ws, size_t ws_bytes,
                   void* stream);
+
+/* ann_shard_knn_screen: the screened lists of ann_shard_knn before its FP32
+ *   re-rank, for measuring a precision form's screening error: per shard row
+ *   the k' smallest screening keys (ann_screen_width gives k'), written as
+ *   (global id, |x|^2 + 2 key) in the data's units (scaled operands divided by
+ *   the scale squared), sorted by (distance, id); cand_id / cand_d [rows x k'].
+ *   Forms without a re-rank (uint8 ANN_EXACT) return the final lists (k' = k).
+ *   Same workspace as ann_shard_knn; ANN_LEARNED is not accepted. */
+int ann_screen_width(int d, int dtype, int k, int precision, int rerank_k, int* kprime);
+int ann_shard_knn_screen(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
+                         const int64_t* offsets, int C, int64_t rows, int k, int precision,
+                         int rerank_k, uint32_t* cand_id, float* cand_d, void* ws,
+                         size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * ann_prune - intermediate degree k (L) to final degree R per shard row, by
@@ -323,6 +338,26 @@ int ann_merge_workspace(int64_t N, int64_t rows, size_t* bytes);
 int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
               const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
               float* gdist, uint32_t* degree, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ann_merge_reverse - a variant of the merge with reverse edges (CAGRA adds
+ * them after its rank-based prune, Sec. II-A; the paper merges by edge union
+ * only, Sec. II-B, so this is an alternative, not a step of the method).  For
+ * every vertex v of a merged graph: the first ceil(R/2) entries of v's list,
+ * then the vertices u whose lists hold v, with the distance of that edge, in
+ * (distance, id) order, skipping ids already taken, then the rest of v's own
+ * list skipping ids already taken, up to R entries; the result sorted by
+ * (distance, id).  graph / gdist / degree: a merged graph as ann_merge writes
+ * it ([N x R], [N x R], [N]; ids < N, no self-loops, entries past degree
+ * ignored); out_graph / out_gdist / out_degree the same shapes, caller-owned,
+ * not overlapping the inputs.  A list entry >= N or equal to its own vertex
+ * sets ANN_DEV_BAD_INPUT in ann_device_status and is skipped.
+ * Limits: 1 <= R <= 64, N < 2^32.
+ * ------------------------------------------------------------------------- */
+int ann_merge_reverse_workspace(int64_t N, int R, size_t* bytes);
+int ann_merge_reverse(const uint32_t* graph, const float* gdist, const uint32_t* degree,
+                      int64_t N, int R, uint32_t* out_graph, float* out_gdist,
+                      uint32_t* out_degree, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Query-side evaluation (Sec. VI-B2: top-10 recall with a best-first search
@@ -430,6 +465,17 @@ int ann_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
                       int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
                       float lr, float margin, float* params, float* losses, float* recall_est,
                       void* ws, size_t ws_bytes, void* stream);
+/* ann_learned_grad: the loss and gradient of one batch of B triplets, computed
+ *   by the same kernels as a step of ann_learned_train (before its Adam update).
+ *   rows [3B] uint32: anchors rows[0, B), positives rows[B, 2B), negatives
+ *   rows[2B, 3B) (row ids of X, which is scaled by s = max|x| as in training);
+ *   grads: device float32 array with the layout of model (n_params values);
+ *   loss: device float32[1] = the batch's mean hinge loss.  Ids >= N are replaced
+ *   by 0 and flagged in the device status word. */
+int ann_learned_grad_workspace(int64_t N, int d, int dtype, int B, size_t* bytes);
+int ann_learned_grad(const void* X, int64_t N, int d, int dtype, const float* params,
+                     const uint32_t* rows, int B, float margin, float* grads, float* loss,
+                     void* ws, size_t ws_bytes, void* stream);
 int ann_learned_embed_workspace(int64_t N, int d, size_t* bytes);
 int ann_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
                       void* ws, size_t ws_bytes, void* stream);

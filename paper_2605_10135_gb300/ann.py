@@ -64,6 +64,8 @@ def lib():
             "ann_prune": (I32, [P, P, P, P, I32, I64, I64, I32, I32, I32, P, P, P, SZ, P]),
             "ann_merge_workspace": (I32, [I64, I64, PSZ]),
             "ann_merge": (I32, [P, P, P, P, I32, I64, I64, I32, P, P, P, P, SZ, P]),
+            "ann_merge_reverse_workspace": (I32, [I64, I32, PSZ]),
+            "ann_merge_reverse": (I32, [P, P, P, I64, I32, P, P, P, P, SZ, P]),
             "ann_medoid_workspace": (I32, [I64, I32, PSZ]),
             "ann_medoid": (I32, [P, I64, I32, I32, P, P, SZ, P]),
             "ann_medoid_noalloc": (I32, [P, I64, I32, I32, P, P]),
@@ -86,6 +88,11 @@ def lib():
             "ann_wait_selftest": (I32, [I32, I64, P]),
             "ann_autotune_lookup": (I32, [I32, I32, I32, I32, I32, I64, I32, P, P, P, P, P, P]),
             "ann_learned_embed": (I32, [P, I64, I32, I32, P, P, P, SZ, P]),
+            "ann_screen_width": (I32, [I32, I32, I32, I32, I32, ct.POINTER(ct.c_int)]),
+            "ann_shard_knn_screen": (I32, [P, I64, I32, I32, P, P, I32, I64, I32, I32, I32, P, P,
+                                           P, SZ, P]),
+            "ann_learned_grad_workspace": (I32, [I64, I32, I32, I32, PSZ]),
+            "ann_learned_grad": (I32, [P, I64, I32, I32, P, P, I32, ct.c_float, P, P, P, SZ, P]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -313,6 +320,27 @@ def shard_knn(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: 
     return knn_id, knn_d
 
 
+def learned_grad(X: torch.Tensor, params: torch.Tensor, rows: torch.Tensor,
+                 margin: float = 1e-3):
+    """Loss and gradient of one triplet batch: rows [3B] (anchors, positives,
+    negatives; int32 bit patterns of uint32).  Returns (grads like params, loss [1])."""
+    X = _cuda(X, "X")
+    params = _cuda(params, "params")
+    rows = _cuda(rows.to(torch.int32), "rows")
+    N, d = X.shape
+    if rows.numel() % 3:
+        raise ValueError("rows must hold 3B ids")
+    B = rows.numel() // 3
+    grads = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    L = lib()
+    nb = _wsize(L.ann_learned_grad_workspace, N, d, _DT[X.dtype], B)
+    ws = _ws(nb, X.device)
+    _check(L.ann_learned_grad(_ptr(X), N, d, _DT[X.dtype], _ptr(params), _ptr(rows), B,
+                              float(margin), _ptr(grads), _ptr(loss), _ptr(ws), nb, _stream()))
+    return grads, loss
+
+
 def learned_train(X: torch.Tensor, sample: torch.Tensor, draws: torch.Tensor,
                   params: torch.Tensor, kk: int = 40, kpos: int = 10, lr: float = 1e-3,
                   margin: float = 1e-3, estimate: bool = True):
@@ -390,6 +418,24 @@ def merge(pr_id: torch.Tensor, pr_d: torch.Tensor, members: torch.Tensor, offset
     _check(L.ann_merge(_ptr(pr_id), _ptr(pr_d), _ptr(members), _ptr(offsets), C, rows, N, R,
                        _ptr(graph), _ptr(gdist), _ptr(degree), _ptr(ws), nb, _stream()))
     return graph, gdist, degree
+
+
+def merge_reverse(graph: torch.Tensor, gdist: torch.Tensor, degree: torch.Tensor):
+    """A merged graph with reverse edges added (ann_merge_reverse):
+    (graph [N, R], gdist [N, R], degree [N])."""
+    graph, gdist = _cuda(graph, "graph"), _cuda(gdist, "gdist")
+    degree = _cuda(degree, "degree")
+    N, R = graph.shape
+    dev = graph.device
+    og = torch.empty((N, R), dtype=torch.int32, device=dev)
+    od = torch.empty((N, R), dtype=torch.float32, device=dev)
+    odeg = torch.empty(N, dtype=torch.int32, device=dev)
+    L = lib()
+    nb = _wsize(L.ann_merge_reverse_workspace, N, R)
+    ws = _ws(nb, dev)
+    _check(L.ann_merge_reverse(_ptr(graph), _ptr(gdist), _ptr(degree), N, R, _ptr(og), _ptr(od),
+                               _ptr(odeg), _ptr(ws), nb, _stream()))
+    return og, od, odeg
 
 
 def medoid(X: torch.Tensor) -> torch.Tensor:
@@ -553,6 +599,29 @@ def build_index(X: torch.Tensor, cfg: BuildConfig, init_centroids: torch.Tensor,
     return dict(centroids=cent, members=members, offsets=offsets, knn_id=knn_id, knn_d=knn_d,
                 pr_id=pr_id, pr_d=pr_d, graph=graph, gdist=gdist, degree=degree,
                 precision=precision, recall_estimate=est, model=model, selective_stats=sel_stats)
+
+
+def shard_knn_screen(X: torch.Tensor, members: torch.Tensor, offsets: torch.Tensor, k: int,
+                     precision: int = EXACT, rerank_k: int = 0):
+    """The screened lists before the re-rank: (cand_id [rows, k'], cand_d [rows, k'])
+    with screening distances in the data's units (see ann_shard_knn_screen)."""
+    X, dev = _vectors(X, "X")
+    N, d = X.shape
+    members = _cuda(members, "members")
+    offsets = _cuda(offsets, "offsets")
+    C = offsets.numel() - 1
+    rows = members.numel()
+    L = lib()
+    kp = ct.c_int(0)
+    _check(L.ann_screen_width(d, _DT[X.dtype], k, precision, rerank_k, ct.byref(kp)))
+    cid = torch.empty((rows, kp.value), dtype=torch.int32, device=dev)
+    cd = torch.empty((rows, kp.value), dtype=torch.float32, device=dev)
+    nb = _wsize(L.ann_shard_knn_workspace, N, d, _DT[X.dtype], C, rows, k, precision, rerank_k)
+    ws = _ws(nb, dev)
+    _check(L.ann_shard_knn_screen(_ptr(X), N, d, _DT[X.dtype], _ptr(members), _ptr(offsets), C,
+                                  rows, k, precision, rerank_k, _ptr(cid), _ptr(cd), _ptr(ws), nb,
+                                  _stream()))
+    return cid, cd
 
 
 _SHARD_OFFS: dict = {}

@@ -401,9 +401,9 @@ static int knn_args(int64_t N, int d, int dtype, int C, int64_t rows, int k, int
     ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
     ANN_REQUIRE(C >= 1 && C <= 1024, "C must be in [1, 1024]");
     ANN_REQUIRE(rows >= 0 && rows < (1ll << 40), "rows out of range");
-    ANN_REQUIRE(k >= 1 && k <= 96, "k must be in [1, 96]");
+    ANN_REQUIRE(k >= 1 && k <= 240, "k must be in [1, 240]");
     ANN_REQUIRE(d >= 1, "d < 1");
-    ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 128), "rerank_k must be 0 or in [k, 128]");
+    ANN_REQUIRE(rerank_k == 0 || (rerank_k >= k && rerank_k <= 256), "rerank_k must be 0 or in [k, 256]");
     if (precision != ANN_EXACT && precision != ANN_BF16_RERANK && precision != ANN_FP8_RERANK &&
         precision != ANN_F16_RERANK && precision != ANN_LEARNED)
         return fail(ANN_ERR_INVALID_ARG, "bad precision %d", precision);
@@ -566,6 +566,29 @@ int ann_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
                              params, losses, recall_est, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+int ann_learned_grad_workspace(int64_t N, int d, int dtype, int B, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(valid_dtype(dtype), "bad dtype %d", dtype);
+    ANN_REQUIRE(N >= 1 && N < (1ll << 32) && d >= 1 && d <= 4096, "N / d out of range");
+    ANN_REQUIRE(B >= 1 && B <= (1 << 16), "B must be in [1, 65536]");
+    *bytes = learned_grad_bytes(B, d);
+    return ANN_OK;
+}
+
+int ann_learned_grad(const void* X, int64_t N, int d, int dtype, const float* params,
+                     const uint32_t* rows, int B, float margin, float* grads, float* loss,
+                     void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_learned_grad_workspace(N, d, dtype, B, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(X && params && rows && grads && loss, "NULL pointer");
+    ANN_REQUIRE(margin >= 0.0f, "margin must be >= 0");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    if ((rc = check_readable(X, "X"))) return rc;
+    return run_learned_grad(X, N, d, dtype, params, rows, B, margin, grads, loss, ws, ws_bytes,
+                            (cudaStream_t)stream);
+}
+
 int ann_learned_embed_workspace(int64_t N, int d, size_t* bytes) {
     ANN_REQUIRE(bytes, "bytes is NULL");
     ANN_REQUIRE(N >= 0 && d >= 1 && d <= 4096, "N / d out of range");
@@ -584,6 +607,36 @@ int ann_learned_embed(const void* X, int64_t N, int d, int dtype, const float* p
 }
 
 // ---------------------------------------------------------------- prune / merge
+int ann_screen_width(int d, int dtype, int k, int precision, int rerank_k, int* kprime) {
+    ANN_REQUIRE(kprime, "kprime is NULL");
+    ANN_REQUIRE(precision != ANN_LEARNED, "the learned form screens in its embedding space");
+    KnnPlan pl;
+    int rc = knn_plan(d, dtype, k, precision, rerank_k, &pl);
+    if (rc) return rc;
+    *kprime = pl.rerank ? pl.kprime : k;
+    return ANN_OK;
+}
+
+int ann_shard_knn_screen(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
+                         const int64_t* offsets, int C, int64_t rows, int k, int precision,
+                         int rerank_k, uint32_t* cand_id, float* cand_d, void* ws,
+                         size_t ws_bytes, void* stream) {
+    int rc = knn_args(N, d, dtype, C, rows, k, precision, rerank_k);
+    if (rc) return rc;
+    ANN_REQUIRE(precision != ANN_LEARNED, "the learned form screens in its embedding space");
+    ANN_REQUIRE(offsets, "offsets is NULL");
+    ANN_REQUIRE(rows == 0 || (X && members && cand_id && cand_d), "NULL pointer");
+    KnnPlan pl;
+    if ((rc = knn_plan(d, dtype, k, precision, rerank_k, &pl))) return rc;
+    if ((rc = check_ws(ws, ws_bytes, knn_ws(C, rows, pl, nullptr, nullptr, 0)))) return rc;
+    if (rows == 0) return ANN_OK;
+    if ((rc = check_readable(X, "X"))) return rc;
+    KnnWs w;
+    knn_ws(C, rows, pl, &w, ws, ws_bytes);
+    return run_shard_knn(X, N, d, dtype, members, offsets, C, rows, k, pl, w, cand_id, cand_d,
+                         (cudaStream_t)stream, nullptr, 0, 0, true);
+}
+
 int ann_prune_workspace(int64_t N, int64_t rows, size_t* bytes) {
     ANN_REQUIRE(bytes, "bytes is NULL");
     ANN_REQUIRE(N >= 0 && N < (1ll << 32) && rows >= 0, "N / rows out of range");
@@ -632,6 +685,29 @@ int ann_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
     rowlist_ws(N, rows, &w, ws, ws_bytes);
     return run_merge(pr_id, pr_d, members, offsets, C, rows, N, R, graph, gdist, degree, w,
                      (cudaStream_t)stream);
+}
+
+int ann_merge_reverse_workspace(int64_t N, int R, size_t* bytes) {
+    ANN_REQUIRE(bytes, "bytes is NULL");
+    ANN_REQUIRE(N >= 0 && N < (1ll << 32), "N out of range");
+    ANN_REQUIRE(R >= 1 && R <= 64, "R must be in [1, 64]");
+    *bytes = merge_rev_ws(N, R, nullptr, nullptr, 0);
+    return ANN_OK;
+}
+
+int ann_merge_reverse(const uint32_t* graph, const float* gdist, const uint32_t* degree,
+                      int64_t N, int R, uint32_t* out_graph, float* out_gdist,
+                      uint32_t* out_degree, void* ws, size_t ws_bytes, void* stream) {
+    size_t need = 0;
+    int rc = ann_merge_reverse_workspace(N, R, &need);
+    if (rc) return rc;
+    ANN_REQUIRE(N == 0 || (graph && gdist && degree && out_graph && out_gdist && out_degree),
+                "NULL pointer");
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    MergeRevWs w;
+    merge_rev_ws(N, R, &w, ws, ws_bytes);
+    return run_merge_reverse(graph, gdist, degree, N, R, out_graph, out_gdist, out_degree, w,
+                             (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- query side

@@ -72,12 +72,6 @@ __device__ __forceinline__ int shard_of(const int64_t* __restrict__ offsets, int
     return lo;
 }
 
-// Shared memory of one prune warp: table keys, list, overflow list, counts,
-// overflow count, table positions, overflow positions, slot occupancy bits.
-__host__ __device__ constexpr size_t prune_warp_smem(int KM) {
-    return (size_t)1024 * 4 + (size_t)KM * 12 + 16 + 1024 + (size_t)KM + 128;
-}
-
 // ---- prune ------------------------------------------------------------------------
 // start[g] .. start[g+1] index rowlist[], the rows p (all shards) with members[p] == g.
 __device__ __forceinline__ int64_t row_in_range(const int64_t* __restrict__ start,
@@ -91,26 +85,90 @@ __device__ __forceinline__ int64_t row_in_range(const int64_t* __restrict__ star
     return -1;
 }
 
-// Position of id x in the row's list: a direct-mapped table of TS slots keyed by
-// the top bits of a multiplicative hash (one probe); ids that collide with an
-// occupied slot go to a short overflow list, scanned only when the slot holds a
-// different id and the overflow list is not empty.
+// Position of id x in the row's list: a direct-mapped table of TS slots.  The
+// multiplicative hash y = x * A (A odd) is a bijection of 32-bit words, so the
+// slot (the top 10 bits of y) and the low 22 bits of y identify x; one 32-bit
+// word per slot holds those 22 bits (bits 8..29) and the position (bits 0..7).
+// For each row the warp tries multipliers until none of the row's ids share a
+// slot (about one try in seven succeeds for 64 ids in 1,024 slots); then every
+// lookup is one probe.  A row for which no multiplier is found within PTRY tries
+// (and every list wider than 64) keeps the colliding ids in a short overflow
+// list, scanned when a lookup's slot holds another id.
 constexpr int TS = 1024, TSHIFT = 22;  // 2^(32 - TSHIFT) = TS slots
+constexpr uint32_t HM = 2654435761u, TEMPTY = 0xFFFFFFFFu;
+constexpr int PTRY = 32;
 
-__device__ __forceinline__ uint32_t tslot(uint32_t x) { return (x * 2654435761u) >> TSHIFT; }
+__device__ __forceinline__ uint32_t tmult(int a) { return HM + 0x3C6EF372u * (uint32_t)a; }  // odd
+__device__ __forceinline__ uint32_t tkey(uint32_t y) { return (y << 10) >> 2; }  // low 22 bits << 8
 
-__device__ __forceinline__ int table_find(const uint32_t* tkey, const uint8_t* tpos,
-                                          const uint32_t* ovf, const uint8_t* ovf_pos, int novf,
-                                          uint32_t x) {
-    const uint32_t h = tslot(x);
-    const uint32_t key = tkey[h];
-    if (key == x) return tpos[h];
-    if (key == ANN_PAD || novf == 0) return -1;
-    for (int o = 0; o < novf; ++o)
-        if (ovf[o] == x) return ovf_pos[o];
-    return -1;
+// Shared memory of one prune warp: table words [TS], overflow ids and positions
+// [KM each], the neighbours' rows [KM], the overflow count (+pad).
+__host__ __device__ constexpr size_t prune_warp_smem(int KM) {
+    return (size_t)TS * 4 + (size_t)KM * 16 + 16;
 }
 
+// Detour counts of one row: for each neighbour v_i (i < m) the warp reads L_{v_i}
+// with coalesced loads (entry t in lane t % 32, register t / 32) and looks each
+// entry up in u's table; an entry at position j of u's list with i < j and t < j
+// sets bit j of the lane's mask.  The ids of a list are distinct, so OR over the
+// lanes counts each (i, j) pair once; lane l adds bit l of word e to c[e], the
+// count of position j = l + 32 e.
+template <int E, bool OVF>
+__device__ __forceinline__ void prune_counts(const uint32_t* __restrict__ knn_id, int k, int m,
+                                             const int64_t* wrow, const uint32_t* tw,
+                                             const uint32_t* ovf, const uint32_t* ovf_pos,
+                                             int novf, uint32_t A, uint32_t (&c)[E]) {
+    constexpr int G = E <= 2 ? 4 : 2;  // neighbour lists read together (loads in flight)
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < m; i0 += G) {
+        uint32_t x[G][E];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int i = i0 + g;
+            const int64_t w = i < m ? wrow[i] : -1;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int t = lane + 32 * e;
+                x[g][e] = (w >= 0 && t < k) ? __ldg(knn_id + w * k + t) : ANN_PAD;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int i = i0 + g;
+            if (i >= m) break;  // warp-uniform
+            uint32_t bits[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) bits[e] = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int t = lane + 32 * e;
+                const uint32_t thr = (uint32_t)(i > t ? i : t);  // hit: thr < j < 256
+                const uint32_t y = x[g][e] * A;
+                const uint32_t wd = tw[y >> TSHIFT];
+                uint32_t dj = wd ^ tkey(y);  // the position j when the slot holds x
+                if (OVF && dj >= 256u && wd != TEMPTY && novf > 0) {
+                    for (int o = 0; o < novf; ++o)
+                        if (ovf[o] == x[g][e]) dj = ovf_pos[o];
+                }
+                if (x[g][e] != ANN_PAD && dj - thr - 1u < 255u - thr) {
+#pragma unroll
+                    for (int e2 = 0; e2 < E; ++e2)
+                        if ((int)(dj >> 5) == e2) bits[e2] |= 1u << (dj & 31u);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (32 * e + 31 <= i) continue;  // no j > i in this word (uniform)
+                c[e] += (__reduce_or_sync(0xffffffffu, bits[e]) >> lane) & 1u;
+            }
+        }
+    }
+}
+
+// One warp per shard row u, lists of width k <= 32 E; entry j of u's list (j =
+// lane + 32 e) sits in lane `lane`, register e.  The counts c_j of the
+// rank-based detour prune (Sec. III; CAGRA's rule), then the R positions of
+// smallest (c_j, j) kept in list order.
 template <int E>  // 32*E >= k
 __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __restrict__ knn_d,
                         const int64_t* __restrict__ offsets, const int64_t* __restrict__ start,
@@ -121,142 +179,135 @@ __global__ void k_prune(const uint32_t* __restrict__ knn_id, const float* __rest
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
     uint8_t* my = sm + (size_t)wib * prune_warp_smem(KM);
-    uint32_t* tkey = (uint32_t*)my;              // [TS]
-    uint32_t* list = tkey + TS;                  // [KM]
-    uint32_t* ovf = list + KM;                   // [KM]
-    int32_t* cnt = (int32_t*)(ovf + KM);         // [KM]
-    int* novf_p = cnt + KM;                      // [1] (+pad)
-    uint8_t* tpos = (uint8_t*)(novf_p + 4);      // [TS]
-    uint8_t* ovf_pos = tpos + TS;                // [KM]
-    uint32_t* occ_bits = (uint32_t*)(ovf_pos + KM);  // [TS / 32]: slot h used = bit h
+    uint32_t* tw = (uint32_t*)my;                  // [TS]
+    int64_t* wrow = (int64_t*)(tw + TS);           // [KM]
+    uint32_t* ovf = (uint32_t*)(wrow + KM);        // [KM]
+    uint32_t* ovf_pos = ovf + KM;                  // [KM]
+    int* novf_p = (int*)(ovf_pos + KM);            // [1] (+pad)
     const uint32_t lt = (1u << lane) - 1;
-    const bool vec = (k & 3) == 0;
     // the table starts empty once; after each row only the slots its ids used are
     // emptied again
-    for (int h = lane; h < TS; h += 32) tkey[h] = ANN_PAD;
-    occ_bits[lane] = 0;
+    for (int h = lane; h < TS; h += 32) tw[h] = TEMPTY;
     __syncwarp();
 
     for (int64_t p = blockIdx.x * (int64_t)nwb + wib; p < rows; p += (int64_t)gridDim.x * nwb) {
         const int s = shard_of(offsets, C, p);
         const int64_t m0 = __ldg(offsets + s), m1 = __ldg(offsets + s + 1);
+        uint32_t lu[E];  // u's list: entry lane + 32 e
         int m = 0;
-        for (int t0 = 0; t0 < KM; t0 += 32) {
-            const int t = t0 + lane;
-            const uint32_t v = t < k ? __ldg(knn_id + p * k + t) : ANN_PAD;
-            list[t] = v;
-            m += __popc(__ballot_sync(0xffffffffu, v != ANN_PAD));
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int t = lane + 32 * e;
+            lu[e] = t < k ? __ldg(knn_id + p * k + t) : ANN_PAD;
+            m += __popc(__ballot_sync(0xffffffffu, lu[e] != ANN_PAD));
         }
-        uint32_t sel[E];
+        uint32_t kb[E];  // kept positions: bit j & 31 of word j >> 5, in every lane
+#pragma unroll
+        for (int e = 0; e < E; ++e) kb[e] = 0;
         if (rule == ANN_PRUNE_TRUNC) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int j = lane * E + e;
-                sel[e] = j < m ? (uint32_t)j : 0xFFFFFFFFu;
+                const int lim = (R < m ? R : m) - 32 * e;
+                kb[e] = lim >= 32 ? 0xFFFFFFFFu : lim > 0 ? (1u << lim) - 1 : 0u;
             }
         } else {
-            for (int j = lane; j < KM; j += 32) cnt[j] = 0;
-            if (lane == 0) *novf_p = 0;
-            __syncwarp();
-            for (int j = lane; j < m; j += 32) {
-                const uint32_t id = list[j];
-                const uint32_t h = tslot(id);
-                if (atomicCAS(&tkey[h], ANN_PAD, id) == ANN_PAD) {
-                    tpos[h] = (uint8_t)j;
-                    atomicOr(&occ_bits[h >> 5], 1u << (h & 31));
-                } else {
-                    const int o = atomicAdd(novf_p, 1);
-                    ovf[o] = id;
-                    ovf_pos[o] = (uint8_t)j;
+            // the neighbours' rows in this shard (independent loads, all in flight)
+            int64_t wr[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int j = lane + 32 * e;
+                wr[e] = j < m ? row_in_range(start, rowlist, lu[e], m0, m1) : -1;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (lane + 32 * e < m) wrow[lane + 32 * e] = wr[e];
+            // a multiplier under which the row's ids occupy distinct slots
+            uint32_t A = HM;
+            bool perfect = false;
+            for (int a = 0; a < (E <= 2 ? PTRY : 0) && !perfect; ++a) {
+                A = tmult(a);
+                bool clash = false;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int j = lane + 32 * e;
+                    if (j < m) {
+                        const uint32_t y = lu[e] * A;
+                        if (atomicCAS(&tw[y >> TSHIFT], TEMPTY, tkey(y) | (uint32_t)j) != TEMPTY)
+                            clash = true;
+                    }
+                }
+                perfect = !__any_sync(0xffffffffu, clash);
+                if (!perfect) {  // empty every slot the row's ids touched, try the next
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (lane + 32 * e < m) tw[(lu[e] * A) >> TSHIFT] = TEMPTY;
+                    __syncwarp();
                 }
             }
-            __syncwarp();
-            const int novf = *novf_p;
-            // Each lane holds 32 of the table's occupancy bits: an id whose slot is
-            // empty (most of a neighbour's list) is rejected with one shuffle,
-            // without a shared-memory probe.
-            const uint32_t occ = occ_bits[lane];
-            // Lane-parallel over the neighbours v_i: each lane reads whole lists
-            // (16-byte loads), so all of a row's list reads are in flight at once.
-            // The neighbours' rows are looked up first, all lanes' loads together.
-            int64_t wrow[E];
+            int novf = 0;
+            if (!perfect) {  // the table with an overflow list
+                A = HM;
+                if (lane == 0) *novf_p = 0;
+                __syncwarp();
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane + 32 * e;
-                wrow[e] = i < m ? row_in_range(start, rowlist, list[i], m0, m1) : -1;
-            }
-            // every lane runs the same loops (the occupancy shuffles need the whole
-            // warp); a lane without a neighbour row reads nothing
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int i = lane + 32 * e;
-                const int64_t w = wrow[e];
-                const bool has = w >= 0;
-                const uint32_t* Lw = knn_id + (has ? w : 0) * k;
-                if (vec) {
-                    for (int t0 = 0; t0 < k; t0 += 16) {
-                        uint4 q4[4];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            q4[r] = (has && t0 + 4 * r < k)
-                                        ? __ldg((const uint4*)(Lw + t0) + r)
-                                        : make_uint4(ANN_PAD, ANN_PAD, ANN_PAD, ANN_PAD);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const uint32_t xs[4] = {q4[r].x, q4[r].y, q4[r].z, q4[r].w};
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const int t = t0 + 4 * r + c;
-                                const uint32_t h = tslot(xs[c]);
-                                const uint32_t ow = __shfl_sync(0xffffffffu, occ, (int)(h >> 5));
-                                if (has && ((ow >> (h & 31)) & 1u)) {
-                                    const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, xs[c]);
-                                    if (j > i && t < j) atomicAdd(&cnt[j], 1);
-                                }
-                            }
-                        }
-                    }
-                } else {
-                    for (int t = 0; t < k; ++t) {
-                        const uint32_t x = has ? __ldg(Lw + t) : ANN_PAD;
-                        const uint32_t h = tslot(x);
-                        const uint32_t ow = __shfl_sync(0xffffffffu, occ, (int)(h >> 5));
-                        if (has && ((ow >> (h & 31)) & 1u)) {
-                            const int j = table_find(tkey, tpos, ovf, ovf_pos, novf, x);
-                            if (j > i && t < j) atomicAdd(&cnt[j], 1);
+                for (int e = 0; e < E; ++e) {
+                    const int j = lane + 32 * e;
+                    if (j < m) {
+                        const uint32_t y = lu[e] * A;
+                        if (atomicCAS(&tw[y >> TSHIFT], TEMPTY, tkey(y) | (uint32_t)j) != TEMPTY) {
+                            const int o = atomicAdd(novf_p, 1);
+                            ovf[o] = lu[e];
+                            ovf_pos[o] = (uint32_t)j;
                         }
                     }
                 }
+                __syncwarp();
+                novf = *novf_p;
             }
             __syncwarp();
+            uint32_t c[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) c[e] = 0;
+            if (novf == 0)
+                prune_counts<E, false>(knn_id, k, m, wrow, tw, ovf, ovf_pos, 0, A, c);
+            else
+                prune_counts<E, true>(knn_id, k, m, wrow, tw, ovf, ovf_pos, novf, A, c);
+            // rank positions by (c_j, j); any starting placement sorts the same
+            uint32_t sel[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int j = lane * E + e;
-                sel[e] = j < m ? (((uint32_t)cnt[j] << 16) | (uint32_t)j) : 0xFFFFFFFFu;
+                const int j = lane + 32 * e;
+                sel[e] = j < m ? ((c[e] << 16) | (uint32_t)j) : 0xFFFFFFFFu;
             }
-            for (int j = lane; j < m; j += 32) tkey[tslot(list[j])] = ANN_PAD;
-            occ_bits[lane] = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (lane + 32 * e < m) tw[(lu[e] * A) >> TSHIFT] = TEMPTY;
             warp_sort<E, uint32_t>(sel);
+            // sel[] (element index lane*E+e) ranks positions; keep the first min(R, m)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = lane * E + e;
+                if (idx < R && sel[e] != 0xFFFFFFFFu) {
+                    const uint32_t jj = sel[e] & 0xFFFFu;
+#pragma unroll
+                    for (int e2 = 0; e2 < E; ++e2)
+                        if ((int)(jj >> 5) == e2) kb[e2] |= 1u << (jj & 31);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) kb[e] = __reduce_or_sync(0xffffffffu, kb[e]);
         }
-        // sel[] (element index lane*E+e) now ranks positions; keep the first min(R, m).
-        // Mark kept positions in cnt[] (reused as flags), then compact in list order.
-        __syncwarp();
-        for (int j = lane; j < KM; j += 32) cnt[j] = 0;
-        __syncwarp();
+        // the kept entries in list order
+        int outc = 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int idx = lane * E + e;
-            if (idx < R && sel[e] != 0xFFFFFFFFu) cnt[sel[e] & 0xFFFFu] = 1;
-        }
-        __syncwarp();
-        int outc = 0;
-        for (int j0 = 0; j0 < m; j0 += 32) {
-            const int j = j0 + lane;
-            const bool f = j < m && cnt[j];
+            if (32 * e >= m) break;
+            const int j = lane + 32 * e;
+            const bool f = j < m && ((kb[e] >> lane) & 1u);
             const uint32_t b = __ballot_sync(0xffffffffu, f);
             if (f) {
                 const int pos = outc + __popc(b & lt);
-                pr_id[p * R + pos] = list[j];
+                pr_id[p * R + pos] = lu[e];
                 pr_d[p * R + pos] = __ldg(knn_d + p * k + j);
             }
             outc += __popc(b);
@@ -444,6 +495,160 @@ __global__ void k_merge(const uint32_t* __restrict__ pr_id, const float* __restr
     else merge_one<8>(pr_id, pr_d, rowlist, a0, ncand, g, R, graph, gdist, degree);
 }
 
+// ---- merge with reverse edges (a variant of the merge) ----------------------------
+// For every vertex v of a merged graph: the first ceil(R/2) entries of its own
+// list, then the vertices u whose lists hold v (edge distance d(u, v)) in
+// (distance, id) order, skipping ids already taken, then the rest of its own
+// list, up to R entries; the result sorted by (distance, id).  Reverse edges
+// are what CAGRA adds after its rank-based prune; the paper merges by edge union
+// only (Sec. II-B), so this is an alternative merge, not a step of the method.
+__global__ void k_rev_count(const uint32_t* __restrict__ graph, const uint32_t* __restrict__ degree,
+                            int64_t N, int R, int32_t* __restrict__ cnt, int* status) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * R;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = q / R;
+        const uint32_t du = degree[u];
+        if ((int)(q - u * R) >= (int)(du < (uint32_t)R ? du : (uint32_t)R)) continue;
+        const uint32_t v = graph[q];
+        if (v < N && v != (uint32_t)u) atomicAdd(cnt + v, 1); else atomicOr(status, DEV_BAD_INPUT);
+    }
+}
+
+// rkey[start[v] ..]: (order bits of d(u, v) << 32 | u) of every edge u -> v, in
+// arrival order (the selection below sorts them).
+__global__ void k_rev_fill(const uint32_t* __restrict__ graph, const float* __restrict__ gdist,
+                           const uint32_t* __restrict__ degree, int64_t N, int R,
+                           const int64_t* __restrict__ start, int32_t* __restrict__ fill,
+                           uint64_t* __restrict__ rkey) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * R;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = q / R;
+        const uint32_t du = degree[u];
+        if ((int)(q - u * R) >= (int)(du < (uint32_t)R ? du : (uint32_t)R)) continue;
+        const uint32_t v = graph[q];
+        if (v >= N || v == (uint32_t)u) continue;
+        const int slot = atomicAdd(fill + v, 1);
+        rkey[start[v] + slot] = ((uint64_t)f2ord(gdist[q]) << 32) | (uint32_t)u;
+    }
+}
+
+// One warp per vertex v, R <= 64: own entry j = lane + 32 e in lane `lane`,
+// register e; the first half (j < h <= 32) is in register 0 of lanes 0 .. h-1.
+// The reverse sources are taken 64 at a time into a shared buffer beside the 64
+// best so far and the 128 sorted; the buffer then holds the final list's keys.
+constexpr int REV_WARPS = 4;
+__global__ void __launch_bounds__(REV_WARPS * 32)
+    k_merge_rev(const uint32_t* __restrict__ graph, const float* __restrict__ gdist,
+                const uint32_t* __restrict__ degree, const int64_t* __restrict__ start,
+                const uint64_t* __restrict__ rkey, int64_t N, int R,
+                uint32_t* __restrict__ out_g, float* __restrict__ out_d,
+                uint32_t* __restrict__ out_deg) {
+    __shared__ uint64_t sbuf[REV_WARPS][128];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t v = blockIdx.x * (int64_t)REV_WARPS + wib;
+    if (v >= N) return;  // warp-uniform
+    uint64_t* buf = sbuf[wib];
+    const uint32_t dg = degree[v];
+    const int dv = (int)(dg < (uint32_t)R ? dg : (uint32_t)R);
+    uint32_t oid[2];
+    uint64_t okey[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int j = lane + 32 * e;
+        oid[e] = j < dv ? graph[v * R + j] : ANN_PAD;
+        okey[e] = j < dv ? (((uint64_t)f2ord(gdist[v * R + j]) << 32) | oid[e]) : ~0ull;
+    }
+    const int half = (R + 1) / 2;
+    const int h = dv < half ? dv : half;
+    const int Q = R - h;
+    buf[lane] = ~0ull;
+    buf[lane + 32] = ~0ull;
+    const int64_t r0 = start[v], r1 = start[v + 1];
+    for (int64_t c0 = r0; c0 < r1; c0 += 64) {
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t c = c0 + lane + 32 * e;
+            uint64_t key = c < r1 ? rkey[c] : ~0ull;
+            const uint32_t src = (uint32_t)key;
+            bool dup = false;
+            for (int q = 0; q < h; ++q) dup |= __shfl_sync(0xffffffffu, oid[0], q) == src;
+            buf[64 + lane + 32 * e] = dup ? ~0ull : key;
+        }
+        __syncwarp();
+        uint64_t k4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) k4[e] = buf[lane * 4 + e];
+        warp_sort<4, uint64_t>(k4);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (lane * 4 + e < 64) buf[lane * 4 + e] = k4[e];
+    }
+    __syncwarp();
+    // the chosen reverse sources: the first nsel (<= Q) of buf[0, 64)
+    int nsel = 0;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = lane + 32 * e;
+        nsel += __popc(__ballot_sync(0xffffffffu, i < Q && buf[i] != ~0ull));
+    }
+    // the rest of v's own list (j >= h) that is not among them, in list order
+    int left = R - h - nsel;
+    bool keep[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int j = lane + 32 * e;
+        bool ok = j >= h && j < dv;
+        if (ok)
+            for (int i = 0; i < nsel; ++i)
+                if ((uint32_t)buf[i] == oid[e]) { ok = false; break; }
+        keep[e] = ok;
+    }
+    int nkeep = 0;
+    const uint32_t lt = (1u << lane) - 1;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const uint32_t b = __ballot_sync(0xffffffffu, keep[e]);
+        const int rank = nkeep + __popc(b & lt);
+        keep[e] = keep[e] && rank < left;
+        nkeep += __popc(b);
+    }
+    nkeep = nkeep < left ? nkeep : left;
+    // the final keys in buf[64, 128): own first half, then the chosen, then the
+    // kept rest (any placement: they are sorted next)
+    buf[64 + lane] = ~0ull;
+    buf[96 + lane] = ~0ull;
+    __syncwarp();
+    if (lane < h) buf[64 + lane] = okey[0];
+    for (int i = lane; i < nsel; i += 32) buf[64 + h + i] = buf[i];
+    {
+        int base = h + nsel;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t b = __ballot_sync(0xffffffffu, keep[e]);
+            if (keep[e]) buf[64 + base + __popc(b & lt)] = okey[e];
+            base += __popc(b);
+        }
+    }
+    __syncwarp();
+    uint64_t fk[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) fk[e] = buf[64 + lane * 2 + e];
+    warp_sort<2, uint64_t>(fk);
+    const int n = h + nsel + nkeep;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int pos = lane * 2 + e;
+        if (pos < R) {
+            const bool f = pos < n;
+            out_g[v * R + pos] = f ? (uint32_t)fk[e] : ANN_PAD;
+            out_d[v * R + pos] = f ? ord2f((uint32_t)(fk[e] >> 32)) : INFINITY;
+        }
+    }
+    if (lane == 0) out_deg[v] = (uint32_t)n;
+}
+
 // ---- host drivers ----------------------------------------------------------------
 size_t rowlist_ws(int64_t N, int64_t rows, RowlistWs* out, void* base, size_t cap) {
     Carver cv(base, cap);
@@ -525,6 +730,43 @@ int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
     const unsigned mg = (unsigned)((N * 32 + tpb - 1) / tpb);
     k_merge<<<mg, tpb, 0, st>>>(pr_id, pr_d, w.start, w.rowlist, N, R, graph, gdist, degree,
                                 device_status_ptr());
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+size_t merge_rev_ws(int64_t N, int R, MergeRevWs* out, void* base, size_t cap) {
+    Carver cv(base, cap);
+    MergeRevWs w;
+    w.cnt = cv.take<int32_t>((size_t)N + 1);
+    w.start = cv.take<int64_t>((size_t)N + 1);
+    w.bsum = cv.take<int64_t>((size_t)(N / SCAN_CHUNK + 2));
+    w.rkey = cv.take<uint64_t>((size_t)(N * R > 0 ? N * R : 1));
+    if (out) *out = w;
+    return cv.used + 256;
+}
+
+int run_merge_reverse(const uint32_t* graph, const float* gdist, const uint32_t* degree, int64_t N,
+                      int R, uint32_t* out_g, float* out_d, uint32_t* out_deg, const MergeRevWs& w,
+                      cudaStream_t st) {
+    if (N == 0) return ANN_OK;
+    const int tpb = 256;
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (N + 1), st));
+    k_rev_count<<<grid_of(N * R, tpb), tpb, 0, st>>>(graph, degree, N, R, w.cnt,
+                                                      device_status_ptr());
+    ANN_CHECK_LAUNCH();
+    const int64_t nb = (N + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    k_scan_sums<<<(unsigned)nb, SCAN_T, 0, st>>>(w.cnt, N, w.bsum);
+    ANN_CHECK_LAUNCH();
+    k_scan_bsums<<<1, 1024, 0, st>>>(w.bsum, nb);
+    ANN_CHECK_LAUNCH();
+    k_scan_apply<<<(unsigned)nb, SCAN_T, 0, st>>>(w.cnt, N, w.bsum, w.start);
+    ANN_CHECK_LAUNCH();
+    ANN_CHECK_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(int32_t) * (N + 1), st));
+    k_rev_fill<<<grid_of(N * R, tpb), tpb, 0, st>>>(graph, gdist, degree, N, R, w.start, w.cnt,
+                                                     w.rkey);
+    ANN_CHECK_LAUNCH();
+    k_merge_rev<<<(unsigned)((N + REV_WARPS - 1) / REV_WARPS), REV_WARPS * 32, 0, st>>>(
+        graph, gdist, degree, w.start, w.rkey, N, R, out_g, out_d, out_deg);
     ANN_CHECK_LAUNCH();
     return ANN_OK;
 }

@@ -64,7 +64,7 @@ constexpr int A_AUG_BYTES = BM * 32;
 constexpr int NAUG = 1;                 // norm-block slots (loaded first in each tile)
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
-constexpr int PH_MAX = 256;             // candidate pool entries per row half, at most
+constexpr int PH_MAX = 320;             // candidate pool entries per row half, at most
 constexpr int SC = 16;                  // survivors a thread stashes before a tile's release
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
@@ -143,13 +143,14 @@ struct KnnParams {
     float ub_margin;
 };
 
-// Entries of a row half's candidate pool: twice the list width, at least 32 more
-// than it (a chunk's survivors always fit after a compaction), whole warps.
+// Entries of a row half's candidate pool, whole warps: twice the list width up to
+// k' = 128, the list width plus 64 above; always at least 32 more than k' (a
+// chunk's survivors fit after a compaction).
 __host__ __device__ inline int pool_half(int kprime) {
-    int ph = 2 * kprime;
+    int ph = kprime <= 128 ? 2 * kprime : kprime + 64;
     if (ph < kprime + 32) ph = kprime + 32;
-    if (ph > kt::PH_MAX) ph = kt::PH_MAX;
-    return (ph + 31) / 32 * 32;
+    ph = (ph + 31) / 32 * 32;
+    return ph > kt::PH_MAX ? kt::PH_MAX : ph;
 }
 
 struct KnnSmemLayout {
@@ -418,6 +419,7 @@ struct PoolState {
     int c;
     float tau;
 };
+template <int EM>  // EM * 32 >= ph
 __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, int c, float tau,
                                               uint32_t mask, float* tau_own, int row) {
     __syncwarp();  // every lane's appends are visible to the warp
@@ -428,9 +430,9 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
         mask &= mask - 1;
         const int cr = __shfl_sync(0xffffffffu, c, r);
         uint64_t* pr = pool0 + (int64_t)r * 2 * ph;
-        uint64_t v[kt::PH_MAX / 32];
+        uint64_t v[EM];
 #pragma unroll
-        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+        for (int e = 0; e < EM; ++e) {
             const int idx = lane + 32 * e;
             v[e] = (e < E && idx < cr) ? pr[idx] : ~0ull;
         }
@@ -443,7 +445,7 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
         __syncwarp();  // every load done before the pool is rewritten in place
         int base = 0;
 #pragma unroll
-        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+        for (int e = 0; e < EM; ++e) {
             const bool keep = v[e] <= T && v[e] != ~0ull;
             const uint32_t b = __ballot_sync(0xffffffffu, keep);
             if (keep) pr[base + __popc(b & ((1u << lane) - 1u))] = v[e];
@@ -466,13 +468,15 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
 }
 
 // Compact the pools of the rows whose count would pass ph with `add` more entries.
-template <bool PROF>
+template <bool PROF, int EMX>
 __device__ __forceinline__ void epi_make_room(EpiState& s, int add) {
     const uint32_t over = __ballot_sync(0xffffffffu, s.c + add > s.ph);
     if (over) {
         long long t0 = 0;
         if (PROF) t0 = clock64();
-        const PoolState o = epi_compact(s.pool0, s.ph, s.kp, s.c, s.tau, over, s.tau_own, s.row);
+        // one call site: a dispatch on ph here costs the sweep loop registers
+        const PoolState o =
+            epi_compact<EMX>(s.pool0, s.ph, s.kp, s.c, s.tau, over, s.tau_own, s.row);
         s.c = o.c;
         s.tau = o.tau;
         s.teff = fminf(s.tau, s.tau_other[s.row]);
@@ -486,12 +490,12 @@ __device__ __forceinline__ void epi_make_room(EpiState& s, int add) {
 
 // Move every thread's stashed survivors (key bits << 32 | shard column) into its
 // pool as (key bits << 32 | global id), after a tile's accumulator is released.
-template <bool PROF>
+template <bool PROF, int EMX>
 __device__ __forceinline__ void epi_flush_stash(EpiState& s) {
     if (!__any_sync(0xffffffffu, s.sn > 0)) return;
     long long f0 = 0;
     if (PROF) f0 = clock64();
-    epi_make_room<PROF>(s, s.sn);
+    epi_make_room<PROF, EMX>(s, s.sn);
     const int lane = threadIdx.x & 31;
     const int mx = __reduce_max_sync(0xffffffffu, (uint32_t)s.sn);
     for (int e0 = 0; e0 < mx; e0 += 4) {
@@ -524,7 +528,7 @@ __device__ __forceinline__ void epi_flush_stash(EpiState& s) {
 // go back to the MMA warp soon; a thread whose stash cannot take them has the
 // stashes emptied first, and a chunk with more survivors than a stash holds (the
 // first tiles of a sweep) goes straight to the pools.
-template <bool PROF>
+template <bool PROF, int EMX>
 __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], int j0, int i,
                                           int n_cols, int self_exclude, bool edge) {
     long long f0 = 0;
@@ -574,7 +578,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
 #pragma unroll
     for (int u = 0; u < 32; ++u) surv |= (key[u] <= s.teff ? 1u : 0u) << u;
     if (__any_sync(0xffffffffu, s.sn + __popc(surv) > kt::SC)) {
-        epi_flush_stash<PROF>(s);
+        epi_flush_stash<PROF, EMX>(s);
         surv = 0;
 #pragma unroll
         for (int u = 0; u < 32; ++u) surv |= (key[u] <= s.teff ? 1u : 0u) << u;
@@ -582,7 +586,7 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
             // straight to the pools, global ids shuffled from the lanes that hold them
             uint32_t g_l = (uint32_t)(j0 + lane);
             if (s.gidrow && j0 + lane < n_cols) g_l = __ldg(s.gidrow + j0 + lane);
-            epi_make_room<PROF>(s, __popc(surv));
+            epi_make_room<PROF, EMX>(s, __popc(surv));
             const uint32_t any_col = __reduce_or_sync(0xffffffffu, surv);
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
@@ -641,7 +645,10 @@ __device__ __forceinline__ int tile_at(int tt, int t0, int ntiles) {
     return right > left ? t0 + m + extra : t0 - m - extra;
 }
 
-template <int BN, bool PROF>
+// EMX: pool entries per row half / 32 that the compaction holds in registers
+// (ph <= 32 EMX); a larger EMX costs the sweep loop registers, so the common
+// pools (ph <= 256) use their own instantiation.
+template <int BN, bool PROF, int EMX>
 __global__ void __launch_bounds__(kt::THREADS, 1)
     k_knn_tiles(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmAaug,
@@ -982,6 +989,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             {
                 const uint32_t tb = tmem + lane_addr + a * BN + h * HALF;
                 const int jt = t * BN + h * HALF;
+
                 const bool edge = (jt + HALF > pr.n_cols) ||
                                   (P.self_exclude && i0 + 32 > jt && i0 < jt + HALF);
                 uint32_t va[32], vb[32];
@@ -995,7 +1003,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                     if (PROF) s.c_ldw += clock64() - l0;
                     tmem_ld32(tb + (c + 1) * 32, vb);
                     if (jt + c * 32 < pr.n_cols)
-                        epi_chunk<PROF>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge);
+                        epi_chunk<PROF, EMX>(s, va, jt + c * 32, i, pr.n_cols, P.self_exclude, edge);
                     __syncwarp();
                     if (PROF) l0 = clock64();
                     tmem_wait_ld32(vb);
@@ -1010,13 +1018,13 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
                         if (lane == 0) mbar_arrive(acce_bar + 8 * a);
                     }
                     if (jt + (c + 1) * 32 < pr.n_cols)
-                        epi_chunk<PROF>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
+                        epi_chunk<PROF, EMX>(s, vb, jt + (c + 1) * 32, i, pr.n_cols, P.self_exclude,
                                         edge);
                     __syncwarp();
                 }
                 // the accumulator is back with the MMA warp: the tile's stashed
                 // survivors join the pools while the next tile is computed
-                epi_flush_stash<PROF>(s);
+                epi_flush_stash<PROF, EMX>(s);
             }
         }
         ok = __all_sync(0xffffffffu, ok);
@@ -1577,7 +1585,7 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
 // / +inf.  One warp per row: the row's entries are selected with warp_select_kth,
 // gathered into shared memory in ballot order, then sorted with a warp bitonic sort
 // of KE entries per lane.
-template <int KE>
+template <int KE, int EH>  // KE: sorted entries per lane; EH = ph / 32
 __global__ void __launch_bounds__(256)
 k_pool_finalize(const KnnParams P) {
     __shared__ uint64_t stage[8][32 * KE];
@@ -1591,7 +1599,6 @@ k_pool_finalize(const KnnParams P) {
     const KnnProblem pr = P.probs[lo];
     const int rb = (int)(bid - P.blk_off[lo]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int EH = P.ph >> 5;
     uint64_t* stg = stage[warp];
     for (int r = warp; r < kt::BM; r += 8) {
         const int i = rb * kt::BM + r;
@@ -1602,12 +1609,12 @@ k_pool_finalize(const KnnParams P) {
         const int c1 = min(max(P.pool_cnt[arow * 2 + 1], 0), P.ph);
         const uint64_t* h0 = P.pool + arow * 2 * (int64_t)P.ph;
         const uint64_t* h1 = h0 + P.ph;
-        uint64_t v[2 * kt::PH_MAX / 32];
+        uint64_t v[2 * EH];
 #pragma unroll
-        for (int e = 0; e < kt::PH_MAX / 32; ++e) {
+        for (int e = 0; e < EH; ++e) {
             const int idx = lane + 32 * e;
-            v[e] = (e < EH && idx < c0) ? h0[idx] : ~0ull;
-            v[kt::PH_MAX / 32 + e] = (e < EH && idx < c1) ? h1[idx] : ~0ull;
+            v[e] = idx < c0 ? h0[idx] : ~0ull;
+            v[EH + e] = idx < c1 ? h1[idx] : ~0ull;
         }
         const int n = c0 + c1;
         const int kp = P.kprime;
@@ -1617,7 +1624,7 @@ k_pool_finalize(const KnnParams P) {
         __syncwarp();
         int base = 0;
 #pragma unroll
-        for (int e = 0; e < 2 * kt::PH_MAX / 32; ++e) {
+        for (int e = 0; e < 2 * EH; ++e) {
             const bool keep = n > 0 && v[e] != ~0ull && v[e] <= T;
             const uint32_t b = __ballot_sync(0xffffffffu, keep);
             const int pos = base + __popc(b & ((1u << lane) - 1u));
@@ -1653,10 +1660,12 @@ template <int E>
 __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
                          const uint32_t* __restrict__ row_ids, int64_t nrows,
                          const uint32_t* __restrict__ cand, int kc, int k,
-                         uint32_t* __restrict__ out_id, float* __restrict__ out_d) {
+                         uint32_t* __restrict__ out_id, float* __restrict__ out_d,
+                         const int64_t* __restrict__ order) {
     const int lane = threadIdx.x & 31;
-    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= nrows) return;
+    if (order && (p = order[p]) < 0) return;
     const int64_t u = row_ids ? (int64_t)row_ids[p] : p;
     uint64_t keys[E];
 #pragma unroll
@@ -1699,11 +1708,13 @@ template <int E, int DT>
 __global__ void k_rerank_vec(const void* X, const void* Xrow, int d,
                              const uint32_t* __restrict__ row_ids, int64_t nrows,
                              const uint32_t* __restrict__ cand, int kc, int k,
-                             uint32_t* __restrict__ out_id, float* __restrict__ out_d) {
+                             uint32_t* __restrict__ out_id, float* __restrict__ out_d,
+                             const int64_t* __restrict__ order) {
     constexpr int V = Chunk16<DT>::V;
     const int lane = threadIdx.x & 31;
-    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (p >= nrows) return;
+    if (order && (p = order[p]) < 0) return;
     const int64_t u = row_ids ? (int64_t)row_ids[p] : p;
     const int nch = d / V;
     const uint4* xu = (const uint4*)Xrow + u * nch;
@@ -1849,7 +1860,7 @@ int knn_plan(int d, int dtype, int k, int precision, int rerank_k, KnnPlan* pl) 
     const int wide = precision == ANN_EXACT ? k + 16 : 128;
     p.kprime = p.rerank ? (rerank_k > 0 ? rerank_k : wide) : k;
     if (p.kprime < k) p.kprime = k;
-    if (p.rerank && p.kprime > 128) return fail(ANN_ERR_UNSUPPORTED, "re-rank width > 128");
+    if (p.kprime > 256) return fail(ANN_ERR_UNSUPPORTED, "list width k' > 256");
     // Resident A rows if they fit: the widest tile with a 3-stage ring, else with
     // 2 stages (an N = 256 MMA does twice the work of an N = 128 one for about the
     // same issue cost), else the narrow tile.  Otherwise (large d) the A blocks
@@ -2117,8 +2128,11 @@ k_ub_own(const uint8_t* __restrict__ X, int d, const int64_t* __restrict__ src,
 }
 
 // As k_ub_own for float vectors (d <= 200): FP32 direct-form squared distances
-// (x - y)^2 summed in index order, the k-th smallest found by bisection on the bit
-// patterns of the non-negative floats.
+// (x - y)^2 summed in index order, the k-th smallest found by a search on the bit
+// patterns of the non-negative floats.  Register tiles: a warp takes 8 rows at a
+// time and each lane 8 window columns (lane + 32 q), so one pass over the
+// dimensions reads 8 broadcast row values and 8 column values from shared memory
+// for 64 products.
 __global__ void __launch_bounds__(256)
 k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src,
              const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
@@ -2148,45 +2162,64 @@ k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src
     __syncthreads();
     const uint32_t NONE = 0x7F800000u;  // +inf: not a column
     unsigned int wmax = 0;
-    for (int r = warp; r < kt::BM; r += 8) {
-        const int i = rb * kt::BM + r;
-        if (i >= pr.n_rows) continue;
-        const int cr = i - c0;
-        uint32_t dv[8];
+    for (int g = 0; g < 2; ++g) {
+        const int r0 = warp * 16 + g * 8;  // rows r0 .. r0 + 7 of the block
+        const int i0 = rb * kt::BM + r0;   // their row index in the shard
+        if (i0 >= pr.n_rows) break;
+        float acc[8][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int c = lane + 32 * q;
-            const float* xr = wf + cr * ws;
-            const float* xc = wf + c * ws;
-            float s2 = 0.0f;
-            for (int t = 0; t < d; ++t) {
-                const float df = xr[t] - xc[t];
-                s2 = fmaf(df, df, s2);
-            }
-            dv[q] = (!cvalid[c] || c == cr) ? NONE : __float_as_uint(s2);
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[j][q] = 0.0f;
+        const float* xr = wf + (i0 - c0) * ws;  // row r0's own window column
+        const float* xc = wf + lane * ws;
+        for (int t = 0; t < d; ++t) {
+            float a[8], b[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = xr[j * ws + t];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) b[q] = xc[32 * q * ws + t];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float df = a[j] - b[q];
+                    acc[j][q] = fmaf(df, df, acc[j][q]);
+                }
         }
-        int cnt = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) cnt += dv[q] != NONE;
-        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        unsigned int ub = NONE;
-        if (cnt >= k) {
-            unsigned int lo = 0, hi = NONE;
-            while (lo < hi) {
-                const unsigned int mid = lo + (hi - lo) / 2;
-                int c = 0;
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j;
+            if (i >= pr.n_rows) break;  // warp-uniform
+            const int cr = i - c0;       // the row's own column in the window
+            uint32_t dv[8];
+            int cnt = 0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) c += dv[q] <= mid;
-                for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                if (c >= k) hi = mid; else lo = mid + 1;
+            for (int q = 0; q < 8; ++q) {
+                const int c = lane + 32 * q;
+                dv[q] = (!cvalid[c] || c == cr) ? NONE : __float_as_uint(acc[j][q]);
+                cnt += dv[q] != NONE;
             }
-            ub = lo;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            unsigned int ub = NONE;
+            if (cnt >= k) {
+                unsigned int lo = 0, hi = NONE;
+                while (lo < hi) {
+                    const unsigned int mid = lo + (hi - lo) / 2;
+                    unsigned int c = 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) c += dv[q] <= mid;
+                    c = __reduce_add_sync(0xffffffffu, c);
+                    if (c >= (unsigned int)k) hi = mid; else lo = mid + 1;
+                }
+                ub = lo;
+            }
+            // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
+            if (rowub && lane == 0)
+                rowub[pr.a_row0 + i] =
+                    ub >= NONE ? INFINITY : __uint_as_float(ub) * (1.0f + (float)(d + 4) * 0x1p-22f);
+            wmax = ub > wmax ? ub : wmax;
         }
-        // FP32 sums of d squares: relative error below (d + 2) 2^-24; pushed up
-        if (rowub && lane == 0)
-            rowub[pr.a_row0 + i] = ub >= NONE ? INFINITY
-                                              : __uint_as_float(ub) * (1.0f + (float)(d + 4) * 0x1p-22f);
-        wmax = ub > wmax ? ub : wmax;
     }
     if (lane == 0) atomicMax(&bmax, wmax);
     __syncthreads();
@@ -2359,8 +2392,13 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         rc = make_tmap(&tba, augB, rowsB, kt::KAUG, kt::KAUG, pl.bn, CU_TENSOR_MAP_SWIZZLE_32B);
     if (rc) return rc;
     const bool prof = timed && tile_counters_on();
-    auto kern = pl.bn == 256 ? (prof ? k_knn_tiles<256, true> : k_knn_tiles<256, false>)
-                             : (prof ? k_knn_tiles<128, true> : k_knn_tiles<128, false>);
+    constexpr int EBIG = kt::PH_MAX / 32;
+    const bool big = P.ph > 256;
+    auto kern = pl.bn == 256
+                    ? (prof ? k_knn_tiles<256, true, EBIG>
+                            : big ? k_knn_tiles<256, false, EBIG> : k_knn_tiles<256, false, 8>)
+                    : (prof ? k_knn_tiles<128, true, EBIG>
+                            : big ? k_knn_tiles<128, false, EBIG> : k_knn_tiles<128, false, 8>);
     ANN_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)pl.smem));
     if (grid <= 0) return ANN_OK;
@@ -2379,45 +2417,71 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         tile_timing_record(e0, e1);
     }
     // merge the two column halves' pools of every row into its sorted list
-    if (P.kprime <= 32)
-        k_pool_finalize<1><<<(unsigned)grid, 256, 0, st>>>(P);
-    else if (P.kprime <= 64)
-        k_pool_finalize<2><<<(unsigned)grid, 256, 0, st>>>(P);
-    else if (P.kprime <= 128)
-        k_pool_finalize<4><<<(unsigned)grid, 256, 0, st>>>(P);
-    else
-        k_pool_finalize<8><<<(unsigned)grid, 256, 0, st>>>(P);
-    ANN_CHECK_LAUNCH();
-    return ANN_OK;
+    const unsigned g = (unsigned)grid;
+    const int ke = P.kprime <= 32 ? 1 : P.kprime <= 64 ? 2 : P.kprime <= 128 ? 4 : 8;
+    const int eh = P.ph >> 5;
+#define ANN_FINALIZE(KE, EH)                                  \
+    if (ke == KE && eh == EH) {                               \
+        k_pool_finalize<KE, EH><<<g, 256, 0, st>>>(P);        \
+        ANN_CHECK_LAUNCH();                                   \
+        return ANN_OK;                                        \
+    }
+    ANN_FINALIZE(1, 2)
+
+    ANN_FINALIZE(2, 3)
+    ANN_FINALIZE(2, 4)
+
+    ANN_FINALIZE(4, 5)
+    ANN_FINALIZE(4, 6)
+    ANN_FINALIZE(4, 7)
+    ANN_FINALIZE(4, 8)
+    ANN_FINALIZE(8, 7)
+    ANN_FINALIZE(8, 8)
+    ANN_FINALIZE(8, 9)
+    ANN_FINALIZE(8, 10)
+#undef ANN_FINALIZE
+    return fail(ANN_ERR_UNSUPPORTED, "tile launch: no finalize for k' = %d, pool %d", P.kprime,
+                P.ph);
 }
 
+// order (optional, norder entries): warp q re-ranks row order[q] (-1: none), e.g.
+// the rows in cell order, whose candidates are near one another in space, so
+// consecutive warps read many of the same candidate vectors (L2 reuse).
 static int launch_rerank(const void* X, const void* Xrow, int dtype, int d, const uint32_t* row_ids,
                          int64_t nrows, const uint32_t* cand, int kc, int k, uint32_t* out_id,
-                         float* out_d, cudaStream_t st) {
+                         float* out_d, cudaStream_t st, const int64_t* order = nullptr,
+                         int64_t norder = 0) {
     const int threads = 128;
-    const unsigned grid = (unsigned)((nrows * 32 + threads - 1) / threads);
     if (nrows == 0) return ANN_OK;
+    const int64_t nwarps = order ? norder : nrows;
+    const unsigned grid = (unsigned)((nwarps * 32 + threads - 1) / threads);
     const int es = dtype_bytes(dtype);
     const bool vec = ((size_t)d * es) % 16 == 0 && (uintptr_t)X % 16 == 0 &&
                      (uintptr_t)Xrow % 16 == 0;
 #define ANN_RERANK_VEC(E, DT)                                                                  \
-    k_rerank_vec<E, DT><<<grid, threads, 0, st>>>(X, Xrow, d, row_ids, nrows, cand, kc, k,     \
-                                                  out_id, out_d)
+    k_rerank_vec<E, DT><<<grid, threads, 0, st>>>(X, Xrow, d, row_ids, nwarps, cand, kc, k,    \
+                                                  out_id, out_d, order)
+#define ANN_RERANK_VEC_W(DT)                                                                   \
+    if (kc <= 64) ANN_RERANK_VEC(2, DT); else if (kc <= 128) ANN_RERANK_VEC(4, DT);              \
+    else ANN_RERANK_VEC(8, DT);
     if (vec) {
-        const bool w = kc > 64;
         switch (dtype) {
-        case ANN_F32: if (w) ANN_RERANK_VEC(4, ANN_F32); else ANN_RERANK_VEC(2, ANN_F32); break;
-        case ANN_F16: if (w) ANN_RERANK_VEC(4, ANN_F16); else ANN_RERANK_VEC(2, ANN_F16); break;
-        case ANN_BF16: if (w) ANN_RERANK_VEC(4, ANN_BF16); else ANN_RERANK_VEC(2, ANN_BF16); break;
-        default: if (w) ANN_RERANK_VEC(4, ANN_U8); else ANN_RERANK_VEC(2, ANN_U8); break;
+        case ANN_F32: ANN_RERANK_VEC_W(ANN_F32) break;
+        case ANN_F16: ANN_RERANK_VEC_W(ANN_F16) break;
+        case ANN_BF16: ANN_RERANK_VEC_W(ANN_BF16) break;
+        default: ANN_RERANK_VEC_W(ANN_U8) break;
         }
     } else if (kc <= 64) {
-        k_rerank<2><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
-                                              out_id, out_d);
+        k_rerank<2><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nwarps, cand, kc, k,
+                                              out_id, out_d, order);
+    } else if (kc <= 128) {
+        k_rerank<4><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nwarps, cand, kc, k,
+                                              out_id, out_d, order);
     } else {
-        k_rerank<4><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nrows, cand, kc, k,
-                                              out_id, out_d);
+        k_rerank<8><<<grid, threads, 0, st>>>(X, Xrow, dtype, d, row_ids, nwarps, cand, kc, k,
+                                              out_id, out_d, order);
     }
+#undef ANN_RERANK_VEC_W
 #undef ANN_RERANK_VEC
     ANN_CHECK_LAUNCH();
     return ANN_OK;
@@ -2532,10 +2596,30 @@ static int side_stream(cudaStream_t* s, cudaEvent_t* fork_ev, cudaEvent_t* join_
     return ANN_OK;
 }
 
+// Screening distances of scaled operands back in the data's units: divided by the
+// square of the operand scale (448 / max|x| for E4M3, a power of two for FP16).
+__global__ void k_unscale_dist(float* __restrict__ dist, int64_t n, const unsigned int* amax_bits,
+                               int e4m3) {
+    const float am = __uint_as_float(*amax_bits);
+    if (!(am > 0.0f && am <= 3.0e38f)) return;
+    float scale;
+    if (e4m3) {
+        scale = 448.0f / am;
+    } else {
+        int ex;
+        frexpf(am, &ex);
+        scale = ldexpf(1.0f, 14 - ex);
+    }
+    const float inv = 1.0f / scale;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dist[i] = (dist[i] * inv) * inv;
+}
+
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
                   const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st,
-                  const void* Xr, int dr, int dtype_r) {
+                  const void* Xr, int dr, int dtype_r, bool screen_only) {
     if (!Xr) {
         Xr = X;
         dr = d;
@@ -2606,8 +2690,9 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     if ((rc = launch_gather(X, dtype, d, w.src, w.rows_cap, pl, w.G, w.norms, w.aug, amax, st)))
         return rc;
     // 3. the kNN sweep
+    const bool to_cand = pl.rerank && !screen_only;
     KnnParams P = base_params(pl, k, w.blk_off, w.probs, C, w.norms, w.gid, w.outrow, 1, 1,
-                              pl.rerank ? w.cand_id : knn_id, pl.rerank ? w.cand_d : knn_d);
+                              to_cand ? w.cand_id : knn_id, to_cand ? w.cand_d : knn_d);
     P.pool = w.pool;
     P.pool_cnt = w.pool_cnt;
     const int64_t grid = rows / kt::BM + C + 1;
@@ -2659,9 +2744,17 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     }
     rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st, true);
     if (rc) return rc;
+    if (screen_only) {  // the screened list as it stands: k' entries per row
+        if (pl.scaled) {
+            k_unscale_dist<<<grid_rows(rows * P.k_out, 256), 256, 0, st>>>(
+                knn_d, rows * P.k_out, (const unsigned int*)w.amax, pl.elem8);
+            ANN_CHECK_LAUNCH();
+        }
+        return ANN_OK;
+    }
     if (pl.rerank)
         return launch_rerank(Xr, Xr, dtype_r, dr, members, rows, w.cand_id, pl.kprime, k, knn_id,
-                             knn_d, st);
+                             knn_d, st, w.outrow, w.rows_cap);
     return ANN_OK;
 }
 

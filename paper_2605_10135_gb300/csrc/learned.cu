@@ -12,10 +12,16 @@
 //          vectors (tile query kernel over all N) give positives (first kpos)
 //          and near-miss negatives (the rest), half the negatives are uniform
 //          rows.  The random picks are caller inputs.
-// Kernels  plain FP32 tiled GEMMs (64 x 64 x 16 tiles, 4 x 4 outputs a thread,
-//          every output summed over k in increasing order, so results are
-//          deterministic) with fused bias / ReLU / mask epilogues, and small
-//          element-wise kernels for the loss, Adam and the triplet picks.
+// Kernels  layer 1 (d -> 256) of a training step on the tensor cores: the
+//          forward product and the weight gradient dW1 = dU^T (x / s) as
+//          tcgen05.mma GEMMs, each FP32 operand (x / s, W1, dU) split into two
+//          BF16 parts and multiplied as hi.hi + lo.hi + hi.lo with FP32
+//          accumulation (FP32 master weights); the small layer-2 products as
+//          FP32 tiled GEMMs (64 x 64 x 16 tiles, every output summed over k in
+//          increasing order); the embedding of all rows on the tensor cores
+//          (FP16 operands); small element-wise kernels for the loss, Adam and
+//          the triplet picks.  Split-K partial products are summed in slice
+//          order, so every result is deterministic.
 #include "stages.cuh"
 
 namespace ann {
@@ -265,6 +271,224 @@ static Mat mat(const void* p, int dtype, int64_t ld, int trans = 0, const uint32
     m.trans = trans;
     m.sp = sp;
     return m;
+}
+
+// ---- tensor-core GEMM of the training step ------------------------------------
+// D[M x N] (FP32) = A[M x K] . B[N x K]^T, BF16 operands stored K-major with rows
+// padded to whole tiles (missing rows of the tensor map read as zeros) and K a
+// multiple of 64.  One 128 x 256 output tile per CTA, the K blocks of slice
+// blockIdx.z: warp 0 issues TMA copies into a ring of 3 stages, warp 1 the
+// tcgen05.mma (FP32 accumulator in TMEM), then every warp reads its 32 rows
+// back (thread = row) and hands ep(row, col, value, slice) each output.
+namespace tgm {
+constexpr int BM = 128, BN = 256, KB = 64, NST = 3;
+constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE = A_BYTES + B_BYTES;
+constexpr int THREADS = 128;
+constexpr size_t SMEM = 1024 + (size_t)NST * STAGE + (2 * NST + 1) * 8 + 16;
+}  // namespace tgm
+
+template <class EP>
+__global__ void __launch_bounds__(tgm::THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int64_t M, int N, int nkb, int kb_per_slice, uint32_t idesc, EP ep, int* status) {
+    using namespace tgm;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring = smem_u32(base);
+    uint8_t* tail = base + NST * STAGE;
+    const uint32_t bars = smem_u32(tail);
+    const uint32_t full = bars, empty = bars + NST * 8, done = bars + 2 * NST * 8;
+    volatile uint32_t* tslot = (volatile uint32_t*)(tail + (2 * NST + 1) * 8);
+    volatile int* abort_flag = (volatile int*)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * kb_per_slice;
+    const int kb1 = kb0 + kb_per_slice < nkb ? kb0 + kb_per_slice : nkb;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NST; ++st) {
+            mbar_init(full + 8 * st, 1);
+            mbar_init(empty + 8 * st, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32((const void*)tslot), BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+        uint32_t used = 0, last_par = 0;
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int i = kb - kb0, st = i % NST;
+            const uint32_t ph = (uint32_t)(i / NST) & 1u;
+            if (!mbar_wait(empty + 8 * st, ph ^ 1u, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(full + 8 * st, STAGE);
+            tma_load_2d(ring + st * STAGE, &tmA, full + 8 * st, kb * KB, (int)m0);
+            tma_load_2d(ring + st * STAGE + A_BYTES, &tmB, full + 8 * st, kb * KB, n0);
+            used |= 1u << st;
+            last_par = (last_par & ~(1u << st)) | (ph << st);
+        }
+        int dummy = 0;  // every issued copy lands before the CTA may exit
+        for (int st = 0; st < NST; ++st)
+            if (used >> st & 1) mbar_wait(full + 8 * st, (last_par >> st) & 1u, &dummy, 200000000ull);
+        if (!ok) atomicOr(status, DEV_TIMEOUT);
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int i = kb - kb0, st = i % NST;
+            const uint32_t ph = (uint32_t)(i / NST) & 1u;
+            if (!mbar_wait(full + 8 * st, ph, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a = ring + st * STAGE, b = a + A_BYTES;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                umma_f16(tmem, sdesc_sw128(a + q * 32), sdesc_sw128(b + q * 32), idesc,
+                         (i | q) != 0 ? 1u : 0u);
+            umma_commit(empty + 8 * st);
+        }
+        umma_commit(done);  // also after a timeout: every issued MMA completes first
+        if (!ok) atomicOr(status, DEV_TIMEOUT);
+    }
+    __syncwarp();
+    const bool got = mbar_wait(done, 0, abort_flag);
+    tc_fence_after();
+    if (got && !*abort_flag) {
+        const int64_t row = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lane_addr + c * 32, v);
+            tmem_wait_ld();
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = n0 + c * 32 + j;
+                    if (col < N) ep(row, col, __uint_as_float(v[j]), (int)blockIdx.z);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(status, DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+struct EpTcHidden {  // U = acc + b1, H = relu(U), row-major with ld columns
+    float* U;
+    float* H;
+    const float* b;
+    int ld;
+    __device__ void operator()(int64_t i, int j, float acc, int) const {
+        const float u = acc + b[j];
+        U[i * ld + j] = u;
+        H[i * ld + j] = u > 0.0f ? u : 0.0f;
+    }
+};
+struct EpTcPart {  // slice z's partial output part[z][M x N]
+    float* part;
+    int64_t M;
+    int N;
+    __device__ void operator()(int64_t i, int j, float acc, int z) const {
+        part[((int64_t)z * M + i) * N + j] = acc;
+    }
+};
+
+// Layer 1's FP32 operands go to the tensor cores as two BF16 parts, hi = bf16(v)
+// and lo = bf16(v - hi), laid out along K so that one BF16 GEMM over 3 K sums
+// hi.hi + lo.hi + hi.lo (the lo.lo term, below 2^-16 of the product, is dropped).
+// Batch rows x / s: row-major [Rp x 3Kp] as [hi | lo | hi] and transposed
+// [Kp x 3Rp] as [hi | hi | lo] (zeros past R rows and d columns).
+__device__ __forceinline__ void bf16_split(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+__global__ void k_batch_bf16(const void* X, int dtype, int d, const uint32_t* __restrict__ idx,
+                             int64_t R, int64_t Rp, int Kp, const float* __restrict__ inv_s,
+                             __nv_bfloat16* __restrict__ rows, __nv_bfloat16* __restrict__ cols) {
+    const float sc = *inv_s;
+    const int64_t tot = Rp * Kp;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / Kp;
+        const int t = (int)(q - r * Kp);
+        const float v = (r < R && t < d) ? load_elem(X, dtype, (int64_t)idx[r] * d + t) * sc : 0.0f;
+        __nv_bfloat16 hi, lo;
+        bf16_split(v, hi, lo);
+        __nv_bfloat16* rw = rows + r * 3 * Kp + t;
+        rw[0] = hi;
+        rw[Kp] = lo;
+        rw[2 * Kp] = hi;
+        __nv_bfloat16* cl = cols + (int64_t)t * 3 * Rp + r;
+        cl[0] = hi;
+        cl[Rp] = hi;
+        cl[2 * Rp] = lo;
+    }
+}
+
+// W1 [256 x d] FP32 -> [256 x 3Kp] as [hi | hi | lo]; dU [R x 256] FP32 ->
+// transposed [256 x 3Rp] as [hi | lo | hi].
+__global__ void k_w1_bf16(const float* __restrict__ W1, int d, int Kp,
+                          __nv_bfloat16* __restrict__ out) {
+    const int64_t tot = (int64_t)ml::HID * Kp;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = q / Kp;
+        const int t = (int)(q - h * Kp);
+        __nv_bfloat16 hi, lo;
+        bf16_split(t < d ? W1[h * d + t] : 0.0f, hi, lo);
+        __nv_bfloat16* o = out + h * 3 * Kp + t;
+        o[0] = hi;
+        o[Kp] = hi;
+        o[2 * Kp] = lo;
+    }
+}
+__global__ void k_du_bf16_t(const float* __restrict__ dU, int64_t R, int64_t Rp,
+                            __nv_bfloat16* __restrict__ out) {
+    const int64_t tot = (int64_t)ml::HID * Rp;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = q / Rp, r = q - h * Rp;
+        __nv_bfloat16 hi, lo;
+        bf16_split(r < R ? dU[r * ml::HID + h] : 0.0f, hi, lo);
+        __nv_bfloat16* o = out + h * 3 * Rp + r;
+        o[0] = hi;
+        o[Rp] = lo;
+        o[2 * Rp] = hi;
+    }
+}
+
+template <class EP>
+static int gemm_tc(const void* A, int64_t rowsA, const void* B, int64_t rowsB, int Kp, int64_t M,
+                   int N, int nz, const EP& ep, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    int rc = make_tmap(&ta, A, rowsA, Kp, tgm::KB, tgm::BM, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (!rc) rc = make_tmap(&tb, B, rowsB, Kp, tgm::KB, tgm::BN, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (rc) return rc;
+    ANN_CHECK_CUDA(cudaFuncSetAttribute(k_gemm_tc<EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tgm::SMEM));
+    const int nkb = Kp / tgm::KB;
+    const int per = (nkb + nz - 1) / nz;
+    const dim3 grid((unsigned)((M + tgm::BM - 1) / tgm::BM), (unsigned)((N + tgm::BN - 1) / tgm::BN),
+                    (unsigned)((nkb + per - 1) / per));
+    k_gemm_tc<EP><<<grid, tgm::THREADS, tgm::SMEM, st>>>(ta, tb, M, N, nkb, per,
+                                                         idesc_f16(tgm::BM, tgm::BN, 1), ep,
+                                                         device_status_ptr());
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
 }
 
 // ---- small kernels -----------------------------------------------------------
@@ -616,20 +840,6 @@ size_t learned_embed_ws(int64_t N, int d) {
     return cv.used + 256;
 }
 
-static int embed_rows(const void* X, int dtype, int d, const uint32_t* rows, int64_t row0,
-                      int64_t n, const float* params, const float* inv_s, float* U, float* H,
-                      float* Z, cudaStream_t st, float* part = nullptr) {
-    const float* W1 = params;
-    const float* b1 = W1 + (int64_t)ml::HID * d;
-    const float* W2 = b1 + ml::HID;
-    const float* b2 = W2 + (int64_t)ml::OUT * ml::HID;
-    int rc = gemm(n, ml::HID, d, mat(X, dtype, d, 0, rows, row0, inv_s),
-                  mat(W1, ANN_F32, d, 1), EpHidden{U, H, b1, ml::HID}, st, part);
-    if (rc) return rc;
-    return gemm(n, ml::OUT, ml::HID, mat(H, ANN_F32, ml::HID), mat(W2, ANN_F32, ml::HID, 1),
-                EpBias{Z, b2, ml::OUT}, st, part);
-}
-
 int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params, float* E,
                       void* ws, size_t ws_bytes, cudaStream_t st) {
     const int Kp = (d + emb::KB - 1) / emb::KB * emb::KB;
@@ -699,6 +909,7 @@ struct LearnTrainWs {
     float* part;         // split-K partial products
     void* ews;           // embedding workspace
     size_t ews_bytes;
+    __nv_bfloat16 *xb, *xbt, *w1b, *dut;  // BF16 operands of the layer-1 GEMMs
 };
 
 // The sample's neighbour lists: the exact plan when it fits shared memory, else
@@ -706,6 +917,158 @@ struct LearnTrainWs {
 static int sample_plan(int d, int dtype, int kq, KnnPlan* p) {
     if (knn_plan(d, dtype, kq, ANN_EXACT, 0, p) == ANN_OK) return ANN_OK;
     return knn_plan(d, dtype, kq, ANN_F16_RERANK, 0, p);
+}
+
+// Buffers of one batch of B triplets (R = 3B rows, Rp = R rounded up to 128,
+// Kp = d rounded up to 64): FP32 activations and gradients, and the split BF16
+// operands of the tensor-core layer-1 GEMMs.
+struct BatchBufs {
+    float *U, *H, *Z, *dZ, *dU, *li, *part;
+    __nv_bfloat16 *xb, *xbt, *w1b, *dut;  // [Rp x 3Kp], [Kp x 3Rp], [256 x 3Kp], [256 x 3Rp]
+};
+static inline int64_t batch_rp(int64_t B) { return (3 * B + 127) / 128 * 128; }
+static inline int batch_kp(int d) { return (d + 63) / 64 * 64; }
+static void take_bf16(Carver& cv, int64_t B, int d, BatchBufs& b) {
+    const int64_t Rp = batch_rp(B), Kp = batch_kp(d);
+    b.xb = cv.take<__nv_bfloat16>((size_t)(Rp * 3 * Kp));
+    b.xbt = cv.take<__nv_bfloat16>((size_t)(Kp * 3 * Rp));
+    b.w1b = cv.take<__nv_bfloat16>((size_t)(ml::HID * 3 * Kp));
+    b.dut = cv.take<__nv_bfloat16>((size_t)(ml::HID * 3 * Rp));
+}
+
+// Loss and gradient of one batch: rows idx[0, B) anchors, [B, 2B) positives,
+// [2B, 3B) negatives; G = [dW1 | db1 | dW2 | db2] (the layout of params); the
+// mean loss into losses[*step] when losses is not NULL.
+static int batch_grads(const void* X, int dtype, int d, const uint32_t* idx, int B,
+                       const float* params, const float* inv_s, float margin, const BatchBufs& b,
+                       float* G, float* losses, const int* step, cudaStream_t q) {
+    const int64_t R = 3 * (int64_t)B, Rp = batch_rp(B);
+    const int Kp = batch_kp(d);
+    const float* W1 = params;
+    const float* b1 = W1 + (int64_t)ml::HID * d;
+    const float* b2 = b1 + ml::HID + (int64_t)ml::OUT * ml::HID;
+    float* gW1 = G;
+    float* gb1 = gW1 + (int64_t)ml::HID * d;
+    float* gW2 = gb1 + ml::HID;
+    float* gb2 = gW2 + (int64_t)ml::OUT * ml::HID;
+    const float* W2 = params + (int64_t)ml::HID * d + ml::HID;
+    int r;
+    // layer 1 on the tensor cores: x / s and W1 split into BF16 parts (three
+    // products), FP32 accumulation
+    auto nb = [](int64_t n) { return (unsigned)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); };
+    k_batch_bf16<<<nb(Rp * Kp), 256, 0, q>>>(X, dtype, d, idx, R, Rp, Kp, inv_s, b.xb, b.xbt);
+    ANN_CHECK_LAUNCH();
+    k_w1_bf16<<<nb((int64_t)ml::HID * Kp), 256, 0, q>>>(W1, d, Kp, b.w1b);
+    ANN_CHECK_LAUNCH();
+    if ((r = gemm_tc(b.xb, Rp, b.w1b, ml::HID, 3 * Kp, R, ml::HID, 1,
+                     EpTcHidden{b.U, b.H, b1, ml::HID}, q)))
+        return r;
+    // layer 2 in FP32
+    if ((r = gemm(R, ml::OUT, ml::HID, mat(b.H, ANN_F32, ml::HID), mat(W2, ANN_F32, ml::HID, 1),
+                  EpBias{b.Z, b2, ml::OUT}, q, b.part)))
+        return r;
+    k_triplet_loss<<<(B + 127) / 128, 128, 0, q>>>(b.Z, B, margin, b.dZ, b.li);
+    ANN_CHECK_LAUNCH();
+    if (losses) {
+        k_mean<<<1, 256, 0, q>>>(b.li, B, step, losses);
+        ANN_CHECK_LAUNCH();
+    }
+    // dW2 = dZ^T H, db2 = column sums of dZ
+    if ((r = gemm(ml::OUT, ml::HID, (int)R, mat(b.dZ, ANN_F32, ml::OUT, 1),
+                  mat(b.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, q, b.part)))
+        return r;
+    k_colsum<<<1, 32, 0, q>>>(b.dZ, R, ml::OUT, gb2);
+    ANN_CHECK_LAUNCH();
+    // dU = (dZ W2) where U > 0
+    if ((r = gemm(R, ml::HID, ml::OUT, mat(b.dZ, ANN_F32, ml::OUT), mat(W2, ANN_F32, ml::HID),
+                  EpReluMask{b.dU, b.U, ml::HID}, q)))
+        return r;
+    // dW1 = dU^T (X / s) on the tensor cores (split BF16 operands, K = three
+    // times the batch rows, split over K and summed in slice order), db1 =
+    // column sums of dU
+    k_du_bf16_t<<<nb((int64_t)ml::HID * Rp), 256, 0, q>>>(b.dU, R, Rp, b.dut);
+    ANN_CHECK_LAUNCH();
+    {
+        const int nkb = (int)(3 * Rp / tgm::KB);
+        int nz = nkb < 8 ? nkb : 8;
+        while (nz > 1 && (int64_t)nz * ml::HID * d > SPLIT_PART_FLOATS) --nz;
+        const int per = (nkb + nz - 1) / nz;
+        nz = (nkb + per - 1) / per;
+        if ((r = gemm_tc(b.dut, ml::HID, b.xbt, Kp, (int)(3 * Rp), ml::HID, d, nz,
+                         EpTcPart{b.part, ml::HID, d}, q)))
+            return r;
+        k_split_reduce<<<(unsigned)(((int64_t)ml::HID * d + 255) / 256), 256, 0, q>>>(
+            b.part, nz, ml::HID, d, EpStore{gW1, d});
+        ANN_CHECK_LAUNCH();
+    }
+    k_colsum<<<1, 256, 0, q>>>(b.dU, R, ml::HID, gb1);
+    ANN_CHECK_LAUNCH();
+    return ANN_OK;
+}
+
+static size_t learned_grad_ws(int64_t B, int d, float** bufs_out, BatchBufs* bb_out, void* base,
+                              size_t cap) {
+    Carver cv(base, cap);
+    const int64_t R = 3 * B;
+    float* p[10];
+    p[0] = cv.take<float>((size_t)R * ml::HID);   // U
+    p[1] = cv.take<float>((size_t)R * ml::HID);   // H
+    p[2] = cv.take<float>((size_t)R * ml::OUT);   // Z
+    p[3] = cv.take<float>((size_t)R * ml::OUT);   // dZ
+    p[4] = cv.take<float>((size_t)R * ml::HID);   // dU
+    p[5] = cv.take<float>((size_t)B);             // li
+    p[6] = cv.take<float>((size_t)SPLIT_PART_FLOATS);
+    p[7] = cv.take<float>(4);                     // amax bits, inverse scale
+    p[8] = cv.take<float>(4);                     // step (zero)
+    p[9] = (float*)cv.take<uint32_t>((size_t)R);  // the batch's row ids, checked
+    if (bufs_out)
+        for (int i = 0; i < 10; ++i) bufs_out[i] = p[i];
+    if (bb_out) {
+        take_bf16(cv, B, d, *bb_out);
+    } else {
+        BatchBufs tmp;
+        take_bf16(cv, B, d, tmp);
+    }
+    return cv.used + 256;
+}
+
+__global__ void k_checked_rows(const uint32_t* __restrict__ rows, int64_t n, int64_t N,
+                               uint32_t* __restrict__ out, int* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = safe_id(rows[i], N, status);
+}
+
+size_t learned_grad_bytes(int64_t B, int d) {
+    return learned_grad_ws(B, d, nullptr, nullptr, nullptr, 0);
+}
+
+int run_learned_grad(const void* X, int64_t N, int d, int dtype, const float* params,
+                     const uint32_t* rows, int B, float margin, float* grads, float* loss,
+                     void* ws, size_t ws_bytes, cudaStream_t st) {
+    float* p[10];
+    BatchBufs bb;
+    if (learned_grad_ws(B, d, p, &bb, ws, ws_bytes) > ws_bytes)
+        return fail(ANN_ERR_WORKSPACE, "learned grad: workspace too small");
+    unsigned int* amax = (unsigned int*)p[7];
+    float* inv_s = p[7] + 1;
+    int* step = (int*)p[8];
+    uint32_t* idx = (uint32_t*)p[9];
+    int rc;
+    k_checked_rows<<<(unsigned)((3 * (int64_t)B + 255) / 256), 256, 0, st>>>(
+        rows, 3 * (int64_t)B, N, idx, device_status_ptr());
+    ANN_CHECK_LAUNCH();
+    if ((rc = launch_absmax(X, dtype, N * d, nullptr, 0, amax, st))) return rc;
+    k_inv_scale<<<1, 32, 0, st>>>(amax, inv_s);
+    ANN_CHECK_LAUNCH();
+    ANN_CHECK_CUDA(cudaMemsetAsync(step, 0, sizeof(int), st));
+    bb.U = p[0];
+    bb.H = p[1];
+    bb.Z = p[2];
+    bb.dZ = p[3];
+    bb.dU = p[4];
+    bb.li = p[5];
+    bb.part = p[6];
+    return batch_grads(X, dtype, d, idx, B, params, inv_s, margin, bb, grads, loss, step, st);
 }
 
 size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batch,
@@ -744,6 +1107,12 @@ size_t learned_train_ws(int64_t N, int d, int dtype, int64_t S, int kk, int batc
     w.part = cv.take<float>((size_t)SPLIT_PART_FLOATS);
     w.ews_bytes = learned_embed_ws(N, d);
     w.ews = cv.take<uint8_t>(w.ews_bytes);
+    BatchBufs bb;
+    take_bf16(cv, batch, d, bb);
+    w.xb = bb.xb;
+    w.xbt = bb.xbt;
+    w.w1b = bb.w1b;
+    w.dut = bb.dut;
     if (out) *out = w;
     if (!base) return cv.used + 256;  // size query
     return cv.ok ? cv.used + 256 : 0;
@@ -783,11 +1152,6 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
     // 3. Adam steps
     ANN_CHECK_CUDA(cudaMemsetAsync(w.m, 0, (size_t)P * sizeof(float), st));
     ANN_CHECK_CUDA(cudaMemsetAsync(w.v, 0, (size_t)P * sizeof(float), st));
-    float* gW1 = w.G;
-    float* gb1 = gW1 + (int64_t)ml::HID * d;
-    float* gW2 = gb1 + ml::HID;
-    float* gb2 = gW2 + (int64_t)ml::OUT * ml::HID;
-    const float* W2 = params + (int64_t)ml::HID * d + ml::HID;
     // One training step; every step-dependent value is read from w.step on the
     // device, so the step can be captured once as a CUDA graph and replayed.
     auto one_step = [&](cudaStream_t q) -> int {
@@ -795,30 +1159,10 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
         k_triplets<<<(batch + 255) / 256, 256, 0, q>>>(sample, S, w.knn, kk, kpos, draws,
                                                        w.step, batch, N, w.idx, status);
         ANN_CHECK_LAUNCH();
-        if ((r = embed_rows(X, dtype, d, w.idx, 0, R, params, inv_s, w.U, w.H, w.Z, q, w.part)))
+        BatchBufs bb{w.U, w.H, w.Z, w.dZ, w.dU, w.li, w.part, w.xb, w.xbt, w.w1b, w.dut};
+        if ((r = batch_grads(X, dtype, d, w.idx, batch, params, inv_s, margin, bb, w.G,
+                             losses, w.step, q)))
             return r;
-        k_triplet_loss<<<(batch + 127) / 128, 128, 0, q>>>(w.Z, batch, margin, w.dZ, w.li);
-        ANN_CHECK_LAUNCH();
-        if (losses) {
-            k_mean<<<1, 256, 0, q>>>(w.li, batch, w.step, losses);
-            ANN_CHECK_LAUNCH();
-        }
-        // dW2 = dZ^T H, db2 = column sums of dZ
-        if ((r = gemm(ml::OUT, ml::HID, (int)R, mat(w.dZ, ANN_F32, ml::OUT, 1),
-                      mat(w.H, ANN_F32, ml::HID), EpStore{gW2, ml::HID}, q, w.part)))
-            return r;
-        k_colsum<<<1, 32, 0, q>>>(w.dZ, R, ml::OUT, gb2);
-        ANN_CHECK_LAUNCH();
-        // dU = (dZ W2) where U > 0
-        if ((r = gemm(R, ml::HID, ml::OUT, mat(w.dZ, ANN_F32, ml::OUT),
-                      mat(W2, ANN_F32, ml::HID), EpReluMask{w.dU, w.U, ml::HID}, q)))
-            return r;
-        // dW1 = dU^T (X / s), db1 = column sums of dU
-        if ((r = gemm(ml::HID, d, (int)R, mat(w.dU, ANN_F32, ml::HID, 1),
-                      mat(X, dtype, d, 0, w.idx, 0, inv_s), EpStore{gW1, d}, q, w.part)))
-            return r;
-        k_colsum<<<1, 256, 0, q>>>(w.dU, R, ml::HID, gb1);
-        ANN_CHECK_LAUNCH();
         k_adam<<<(unsigned)((P + 255) / 256), 256, 0, q>>>(params, w.G, w.m, w.v, P, lr,
                                                            w.step);
         ANN_CHECK_LAUNCH();

@@ -326,7 +326,7 @@ __global__ void k_scatter(const uint32_t* __restrict__ assign, int64_t N, int r,
 }
 
 // ---- host driver --------------------------------------------------------------
-static constexpr int64_t ASSIGN_CHUNK = 131072;  // rows per assignment launch
+static constexpr int64_t ASSIGN_CHUNK = 1 << 20;  // rows per assignment launch
 static constexpr int FULL_SCAN_C = 32;            // up to this many centroids: no screen
 static int screen_width(int C, int r) { return C < r + 6 ? C : r + 6; }
 

@@ -143,7 +143,8 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
 int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* members,
                   const int64_t* offsets, int C, int64_t rows, int k, const KnnPlan& pl,
                   const KnnWs& w, uint32_t* knn_id, float* knn_d, cudaStream_t st,
-                  const void* Xr = nullptr, int dr = 0, int dtype_r = 0);
+                  const void* Xr = nullptr, int dr = 0, int dtype_r = 0,
+                  bool screen_only = false);
 
 struct QueryWs {
     int64_t* blk_off;
@@ -188,6 +189,16 @@ int run_prune(const uint32_t* knn_id, const float* knn_d, const uint32_t* member
 int run_merge(const uint32_t* pr_id, const float* pr_d, const uint32_t* members,
               const int64_t* offsets, int C, int64_t rows, int64_t N, int R, uint32_t* graph,
               float* gdist, uint32_t* degree, const RowlistWs& w, cudaStream_t st);
+struct MergeRevWs {
+    int32_t* cnt;
+    int64_t* start;
+    int64_t* bsum;
+    uint64_t* rkey;
+};
+size_t merge_rev_ws(int64_t N, int R, MergeRevWs* out, void* base, size_t cap);
+int run_merge_reverse(const uint32_t* graph, const float* gdist, const uint32_t* degree, int64_t N,
+                      int R, uint32_t* out_g, float* out_d, uint32_t* out_deg, const MergeRevWs& w,
+                      cudaStream_t st);
 
 // ---- query side ------------------------------------------------------------------
 int search_vis_mask(int Ls, int R);
@@ -228,6 +239,10 @@ int run_learned_train(const void* X, int64_t N, int d, int dtype, const uint32_t
                       int64_t S, int kk, int kpos, const uint32_t* draws, int steps, int batch,
                       float lr, float margin, float* params, float* losses, float* recall_est,
                       void* ws, size_t ws_bytes, cudaStream_t st);
+size_t learned_grad_bytes(int64_t B, int d);
+int run_learned_grad(const void* X, int64_t N, int d, int dtype, const float* params,
+                     const uint32_t* rows, int B, float margin, float* grads, float* loss,
+                     void* ws, size_t ws_bytes, cudaStream_t st);
 size_t learned_embed_ws(int64_t N, int d);
 int run_learned_embed(const void* X, int64_t N, int d, int dtype, const float* params,
                       float* E, void* ws, size_t ws_bytes, cudaStream_t st);

@@ -1,8 +1,11 @@
 """Learned candidate form on the GPU (through the C-ABI) against the FP64 oracle.
 
-The MLP runs in FP32 on the GPU and in FP64 in the oracle, so embeddings and
-training trajectories are compared within tolerances derived from FP32
-rounding; the learned kNN lists are compared through what is unique: exact
+The MLP's layer 1 runs on the tensor cores (FP16 operands for the embedding,
+split BF16 operands for the training step, FP32 accumulation), the rest in
+FP32; the oracle is FP64.  Embeddings, gradients and training trajectories are
+compared within tolerances derived from those roundings, the embedding against
+the oracle on the same rounded operands; the learned kNN lists are compared
+through what is unique: exact
 distances of every returned id, the list order, and - with a model that makes
 the embedding the identity - bit-exact equality with the exact shard kNN.
 """
@@ -65,6 +68,71 @@ def test_embedding_matches_oracle(kind, d):
     assert np.abs(E - OL.embed(X, p)).max() <= 1e-2 * np.abs(ref).max()
 
 
+# Layer 1 of the training step runs on the tensor cores with each FP32 operand
+# (x / s, W1, dU) split into two BF16 parts, hi + lo, and three products (hi.hi +
+# lo.hi + hi.lo): each product is within about 2^-16 of its FP32 value.  The
+# triplet gradients cancel (anchor, positive and negative terms of opposite sign),
+# which can raise a tensor's relative error by an order of magnitude; 1e-2 of each
+# tensor's norm leaves a wide margin, and the loss agrees to 1e-4.
+GRAD_RTOL = 1e-2
+
+
+@pytest.mark.parametrize("kind,d,B", [("f32", 48, 256), ("u8", 128, 100), ("f16", 300, 64)])
+def test_batch_gradient_matches_the_oracle(kind, d, B):
+    """ann_learned_grad (the training step's loss and gradient kernels) against the
+    FP64 loss_and_grads of the oracle on the same triplets, per parameter tensor:
+    |g - g64| / |g64| for W1, b1, W2, b2."""
+    rng = np.random.default_rng(71)
+    n = 3000
+    if kind == "f32":
+        X = datagen.gaussian_mixture_f32(n, d, 8, 3.0, seed=72)
+    elif kind == "u8":
+        X = datagen.clustered_u8(n, d, 8, seed=73)
+    else:
+        X = datagen.anisotropic_mixture(n, d, 8, 0.25, False, np.float16, seed=74)
+    p = datagen.mlp_init(d, seed=75)
+    rows = rng.integers(0, n, size=3 * B).astype(np.uint32)
+    margin = 0.05
+    g, loss = ann.learned_grad(T(X), T(p), T(rows), margin)
+    g = g.cpu().numpy().astype(np.float64)
+    Xs = X.astype(np.float64) / OL.input_scale(X)
+    a, pp, ng = rows[:B], rows[B:2 * B], rows[2 * B:]
+    l64, g64, hinge = OL.loss_and_grads(p, Xs[a], Xs[pp], Xs[ng], margin, d)
+    assert (hinge > 0).sum() > B // 4  # a batch with active and inactive triplets
+    assert abs(float(loss.item()) - l64) <= 1e-4 * abs(l64)
+    o = 0
+    for name, size in (("W1", OL.HIDDEN * d), ("b1", OL.HIDDEN), ("W2", OL.OUT * OL.HIDDEN),
+                       ("b2", OL.OUT)):
+        got, ref = g[o:o + size], g64[o:o + size]
+        o += size
+        if name == "b2":
+            # each triplet adds c (zn - zp) + c (zp - za) + c (za - zn) = 0: the exact
+            # b2 gradient vanishes, so only rounding remains, small against the rest
+            assert np.linalg.norm(ref) <= 1e-12 * np.linalg.norm(g64)
+            assert np.linalg.norm(got) <= GRAD_RTOL * np.linalg.norm(g64), name
+            continue
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= GRAD_RTOL, (name, err)
+
+
+def test_batch_gradient_is_zero_when_every_margin_holds():
+    """Negatives far beyond their positives and a zero margin: no hinge is active,
+    so the loss and every gradient entry are exactly zero."""
+    X = np.zeros((40, 16), np.float32)
+    X[20:] = 50.0
+    p = datagen.mlp_init(16, seed=76)
+    B = 10
+    rows = np.concatenate([np.arange(10), np.arange(10), np.arange(20, 30)]).astype(np.uint32)
+    g, loss = ann.learned_grad(T(X), T(p), T(rows), 0.0)
+    if float(loss.item()) == 0.0:
+        assert not torch.any(g != 0)
+    else:  # the random model may not separate the groups; the oracle decides
+        Xs = X.astype(np.float64) / OL.input_scale(X)
+        l64, _, hinge = OL.loss_and_grads(p, Xs[rows[:B]], Xs[rows[B:2 * B]], Xs[rows[2 * B:]],
+                                          0.0, 16)
+        assert l64 > 0
+
+
 def _train_case(steps, batch, seed):
     X = datagen.gaussian_mixture_f32(4000, 32, 8, 3.0, seed=seed)
     sample = datagen.row_sample(4000, 0.02, 64, seed=seed + 1)
@@ -74,10 +142,12 @@ def _train_case(steps, batch, seed):
 
 
 def test_training_steps_match_oracle():
-    """Three Adam steps: the per-step losses agree to FP32 rounding, and the
-    parameters agree except where a gradient component is so close to zero that
-    its FP32 and FP64 signs differ (Adam's first steps move every parameter by
-    about lr, whatever the gradient's size)."""
+    """Three Adam steps: the per-step losses agree to the rounding of layer 1's
+    split BF16 products (well under 1e-3), and the parameters agree except where a
+    gradient component is so close to zero that its rounded and FP64 signs differ
+    (Adam's first steps move every parameter by about lr, whatever the gradient's
+    size).  The gradients themselves are compared in
+    test_batch_gradient_matches_the_oracle."""
     X, sample, draws, p0 = _train_case(3, 256, 71)
     lr, margin, kk, kpos = 1e-3, 1e-3, 40, 10
     p = T(p0.copy())
@@ -86,10 +156,10 @@ def test_training_steps_match_oracle():
     knn = OL.sample_knn(X, sample, kk)
     ref_p, ref_l = OL.train(X, sample, knn, draws, lr, margin, p0, kpos)
     got_l = losses.cpu().numpy().astype(np.float64)
-    assert np.allclose(got_l, ref_l, rtol=1e-4, atol=1e-7)
+    assert np.allclose(got_l, ref_l, rtol=1e-3, atol=1e-7)
     dp = np.abs(p.cpu().numpy().astype(np.float64) - ref_p)
     assert dp.max() <= 2 * 3 * lr + 1e-6
-    assert (dp > 1e-5).mean() < 0.01
+    assert (dp > 1e-5).mean() < 0.05
 
 
 def test_training_lowers_loss_and_estimates_recall():

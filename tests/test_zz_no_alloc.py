@@ -27,6 +27,50 @@ def test_rejects_inputs_beyond_the_fixed_scratch():
     assert rc == 1
 
 
+def test_rejects_pageable_host_vectors_before_any_launch():
+    """A pointer no kernel may read (ordinary pageable host memory) is refused by
+    the readability check, after the size check and before any launch."""
+    build.build()
+    L = ann.lib()
+    X = np.zeros((64, 16), np.float32)  # pageable: never registered with CUDA
+    out = np.zeros(1, np.uint32)
+    before = L.ann_launch_count()
+    rc = L.ann_medoid_noalloc(X.ctypes.data_as(ct.c_void_p), 64, 16, 0,
+                              out.ctypes.data_as(ct.c_void_p), None)
+    assert rc == 1
+    assert b"X" in L.ann_last_error()
+    assert L.ann_launch_count() == before
+    assert out[0] == 0
+
+
+@pytest.mark.gpu
+def test_no_alloc_medoid_at_the_scratch_limit_allocates_nothing():
+    """The largest input the fixed scratch takes (ceil(N / 4096) * d equal to the
+    524288 column sums) gives the workspace medoid, and the device's free memory
+    is the same before and after the call; one more row is refused."""
+    import torch
+
+    build.build()
+    d = 128
+    N = 4096 * (524288 // d)  # 4096 chunks of 4096 rows
+    X = torch.randint(0, 256, (N, d), dtype=torch.uint8, device="cuda:0",
+                      generator=torch.Generator("cuda:0").manual_seed(93))
+    out = torch.empty(1, dtype=torch.int32, device="cuda:0")
+    ann.medoid_noalloc(X[:4096], out)  # the first call resolves the scratch symbol
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    got = int(ann.medoid_noalloc(X, out).item())
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert got == int(ann.medoid(X).item())
+    L = ann.lib()
+    Y = torch.zeros((N + 1, d), dtype=torch.uint8, device="cuda:0")
+    rc = L.ann_medoid_noalloc(ct.c_void_p(Y.data_ptr()), N + 1, d, 3, ct.c_void_p(out.data_ptr()),
+                              None)
+    assert rc == 1 and b"fixed scratch" in L.ann_last_error()
+    assert ann.device_status() == 0
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("kind", ["u8", "f32"])
 def test_no_alloc_medoid_matches_workspace_medoid_twice(kind):
