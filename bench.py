@@ -284,6 +284,9 @@ def main():
     ap.add_argument("--nq", type=int, default=1000)
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (smaller case for profiling)")
+    ap.add_argument("--shards", type=int, default=0,
+                    help="override the shard count C (with --n: a small case whose shards are "
+                         "as large as the full workload's)")
     ap.add_argument("--precision", default="exact",
                     choices=["exact", "bf16", "f16", "fp8", "learned"],
                     help="distance-tile form: exact (uint8 / FP32 split), BF16 / scaled FP16 / "
@@ -331,9 +334,10 @@ def main():
     from paper_2605_10135_gb300 import configs
 
     w = configs.BY_NAME[args.workload]
-    if args.n:
+    if args.n or args.shards:
         import dataclasses
-        w = dataclasses.replace(w, N=args.n, name=f"{w.name}@N={args.n}")
+        n, c = args.n or w.N, args.shards or w.C
+        w = dataclasses.replace(w, N=n, C=c, name=f"{w.name}@N={n},C={c}")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -2,16 +2,18 @@
 // use L = 2R) and merge of the replicated shard graphs by edge union (Sec. II-B,
 // Sec. IV Workflow (3)).
 //
-// Prune, one warp per shard row u: the row's list is staged in shared memory
-// with an id -> position hash; the lists of u's neighbours are read with
-// coalesced 128-byte warp loads; each entry that is also in L_u at a later
-// position j with a shorter detour rank increments c_j (shared atomics).  The
-// R entries of smallest (c_j, j) are chosen by a warp bitonic sort and written
-// in list order with a ballot/popc compaction.  Integer logic only.
+// Prune, one warp per shard row u: u's list goes into an id -> position table
+// in shared memory (one probe per lookup, a multiplier chosen per row so that
+// no two of its ids share a slot); the lists of u's neighbours are read with
+// coalesced warp loads, every entry looked up, and the counts c_j kept in
+// registers (a warp OR-reduction per neighbour).  The R entries of smallest
+// (c_j, j) are chosen by a warp bitonic sort and written in list order with a
+// ballot/popc compaction.  Integer logic only.
 //
 // Merge, one warp per vector g: its pruned lists (one per shard holding g) are
 // gathered, sorted by (id, distance) to drop duplicate ids (the smaller
 // distance survives), re-sorted by (distance, id), and the first R written.
+// A variant merge adds reverse edges to a merged graph (k_merge_rev).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 

@@ -26,15 +26,22 @@
 //              one column half per warp).  32-column chunks are read with
 //              tcgen05.ld (the next chunk's load overlaps the current chunk's
 //              work) and reduced with 3-input minima; a chunk is skipped unless
-//              some row of the warp has a key at or below its current k-th key.
-//              Survivors go to the warp's own per-row buffer without locking;
-//              a full buffer is emptied into the row's max-heap in shared memory
-//              under the quarter lock, all 32 rows of the warp in lockstep
-//              (composite (key, global id) order, so ties go to the smaller id).
+//              some row of the warp has a key at or below its threshold (the
+//              smaller of the bounds its two column halves have reached).
+//              Survivors (key, column) are stashed in shared memory and, once
+//              the tile's accumulator is back with the MMA warp, appended with
+//              their global ids to the row's candidate pool for that half (in
+//              global memory, no lock: each half has one writer).  A pool that
+//              would overflow is compacted by its warp: a cooperative selection
+//              finds a bound keeping between k' and k' plus a quarter of the
+//              slack entries, the rest are dropped and the threshold lowered.
+//              After the sweep k_pool_finalize selects each row's k' smallest
+//              (key, global id) from its two pools, so ties go to the smaller
+//              id whatever the order the candidates came in.
 // Rows are ordered by cell, cells along a chain of nearby pivots (see
 // run_shard_knn), and each sweep starts at the block's own tile and moves
-// outward, so the k-th key is tight after the first few tiles and later chunks
-// are almost always skipped.
+// outward, so the thresholds are tight after the first few tiles and later
+// chunks are almost always skipped.
 // Every wait is bounded; on a timeout the CTA records DEV_TIMEOUT, drains its
 // copies, frees TMEM and returns.
 //
@@ -71,7 +78,7 @@ constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
 constexpr int CELL = 128;               // rows per pivot cell, short rows (at most 1024 a shard)
 constexpr int CELL_WIDE = 1024;         // rows per pivot cell, rows over 512 bytes
-constexpr int TM_WORDS = 64;            // tile-mask words per row block (2048 tiles)
+constexpr int TL_MAX = 2048;            // tile-list entries per row block (shards of <= 2048 tiles)
 }  // namespace kt
 
 // Optional per-role cycle and event counters of k_knn_tiles (ann_tile_counters_*).
@@ -127,10 +134,12 @@ struct KnnParams {
     uint32_t* out_id;
     float* out_d;
     int* status;
-    // Exact tile skipping (NULL: every tile of the row block's shard).  tmask:
-    // TM_WORDS words per row block, bit t set = sweep column tile t; used only where
-    // the shard has at most TM_WORDS * 32 tiles.
-    const uint32_t* tmask;
+    // Exact tile skipping (NULL: every tile of the row block's shard).  tlist:
+    // TL_MAX entries per row block, the column tiles it sweeps in sweep order;
+    // tcount: their number (-1: sweep every tile).  Used only where the shard has
+    // at most TL_MAX tiles.
+    const uint16_t* tlist;
+    const int* tcount;
     // Candidate pools (global memory): A row a, column half h holds its survivors
     // at pool[(2 a + h) * ph ...], their number in pool_cnt[2 a + h] after the sweep.
     uint64_t* pool;
@@ -675,15 +684,12 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         t0 = rb * kt::BM / BN;
         if (t0 >= ntiles) t0 = ntiles - 1;
     }
-    // Tiles this block sweeps (nrun of them, in tile_at order): all, or those whose
-    // bit is set in the block's mask.
-    const uint32_t* tmask =
-        (P.tmask && ntiles <= kt::TM_WORDS * 32) ? P.tmask + bid * kt::TM_WORDS : nullptr;
-    int nrun = ntiles;
-    if (tmask) {
-        nrun = 0;
-        for (int w = 0; w < (ntiles + 31) / 32; ++w) nrun += __popc(tmask[w]);
-    }
+    // Tiles this block sweeps (nrun of them): with exact skipping, those of its tile
+    // list in list order (nearest first); else all, in tile_at order.
+    const uint16_t* tlist =
+        (P.tlist && ntiles <= kt::TL_MAX && P.tcount[bid] >= 0) ? P.tlist + bid * kt::TL_MAX
+                                                               : nullptr;
+    const int nrun = tlist ? P.tcount[bid] : ntiles;
 
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const KnnSmemLayout L = knn_smem_layout(BN, P.nkb_a, P.nst, P.a_stream);
@@ -765,9 +771,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             uint32_t ph = 0, aph = 0;
             bool ok = true;
             unsigned long long prod_wait = 0;
-            for (int tt = 0, run = 0; tt < ntiles && run < nrun && ok; ++tt) {
-                const int t = tile_at(tt, t0, ntiles);
-                if (tmask && !((tmask[t >> 5] >> (t & 31)) & 1u)) continue;
+            for (int run = 0; run < nrun && ok;) {
+                const int t = tlist ? (int)tlist[run] : tile_at(run, t0, ntiles);
                 ++run;
                 const int b_y = (int)(pr.b_row0 + (int64_t)t * BN);
                 // the norm block first: its MMA opens the tile, so the slot frees early
@@ -975,9 +980,8 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         bool ok = true;
         constexpr int HALF = BN / 2;
-        for (int tt = 0, run = 0; tt < ntiles && run < nrun; ++tt) {
-            const int t = tile_at(tt, t0, ntiles);
-            if (tmask && !((tmask[t >> 5] >> (t & 31)) & 1u)) continue;
+        for (int run = 0; run < nrun;) {
+            const int t = tlist ? (int)tlist[run] : tile_at(run, t0, ntiles);
             const int a = run % kt::NACC;
             const int par = (run / kt::NACC) & 1;
             ++run;
@@ -1656,6 +1660,39 @@ k_pool_finalize(const KnnParams P) {
     }
 }
 
+// k' = 1 (the pivot assignment): a thread per row takes the smaller of the two
+// halves' entries.
+__global__ void __launch_bounds__(kt::BM) k_pool_finalize1(const KnnParams P) {
+    const int64_t bid = blockIdx.x;
+    if (bid >= P.blk_off[P.nprob]) return;
+    int lo = 0, hi = P.nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blk_off[mid] <= bid) lo = mid; else hi = mid - 1;
+    }
+    const KnnProblem pr = P.probs[lo];
+    const int i = (int)(bid - P.blk_off[lo]) * kt::BM + (int)threadIdx.x;
+    if (i >= pr.n_rows) return;
+    const int64_t arow = pr.a_row0 + i;
+    const uint64_t* h0 = P.pool + arow * 2 * (int64_t)P.ph;
+    const uint64_t a = P.pool_cnt[arow * 2] > 0 ? h0[0] : ~0ull;
+    const uint64_t b = P.pool_cnt[arow * 2 + 1] > 0 ? h0[P.ph] : ~0ull;
+    const uint64_t w = a < b ? a : b;
+    const int64_t orow = P.outrow ? P.outrow[arow] : pr.out_row0 + i;
+    uint32_t id = ANN_PAD;
+    float dd = INFINITY;
+    if (w != ~0ull) {
+        id = (uint32_t)w;
+        dd = fmaf(2.0f, ord2f((uint32_t)(w >> 32)), P.na[arow]);
+    }
+    P.out_id[orow * P.k_out] = id;
+    P.out_d[orow * P.k_out] = dd;
+    for (int slot = 1; slot < P.k_out; ++slot) {
+        P.out_id[orow * P.k_out + slot] = ANN_PAD;
+        P.out_d[orow * P.k_out + slot] = INFINITY;
+    }
+}
+
 template <int E>
 __global__ void k_rerank(const void* X, const void* Xrow, int dtype, int d,
                          const uint32_t* __restrict__ row_ids, int64_t nrows,
@@ -2229,17 +2266,23 @@ k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src
                                 : __uint_as_float(bmax) * (1.0f + (float)(d + 4) * 0x1p-22f);
 }
 
-// tmask[bid]: bit t set unless every group of column tile t is provably farther
-// than the block's bound.  One block of 256 threads per row block; a warp per
-// (tile, group) pair with lanes over the dimensions.
+// tlist[bid]: the column tiles a row block sweeps, nearest first.  A tile is left
+// out when every one of its groups is provably farther than the block's bound;
+// the kept ones are ordered by the smallest distance from the block's centre to
+// a group ball of the tile, (|c_A - c_G| - r_G), so the thresholds tighten on the
+// first tiles of the sweep and fewer candidates pass them later.  tcount[bid]:
+// the number kept (-1 where the shard has more than TL_MAX tiles: the block then
+// sweeps every tile).  One block of 256 threads per row block; a warp per tile
+// with lanes over the dimensions, then a bitonic sort in shared memory.
 __global__ void __launch_bounds__(256)
-k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
+k_tile_list(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
             int bn, int d, int ldc, const float* __restrict__ gcent, const float* __restrict__ grad,
             const float* __restrict__ gmaxn, float kslack, const float* __restrict__ bub,
-            int64_t nblocks, uint32_t* __restrict__ tmask) {
+            int64_t nblocks, uint16_t* __restrict__ tlist, int* __restrict__ tcount) {
     extern __shared__ float ca[];  // [d]
-    __shared__ uint32_t mw[kt::TM_WORDS];
-    __shared__ unsigned long long s_kept, s_pairs;
+    __shared__ uint64_t sk[kt::TL_MAX];  // (order bits of the distance << 32 | tile)
+    __shared__ int s_n;
+    __shared__ unsigned long long s_pairs;
     const int64_t bid = blockIdx.x;
     if (bid >= nblocks || bid >= blk_off[nprob]) return;
     const int p = block_problem(blk_off, nprob, bid);
@@ -2248,8 +2291,9 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
     const int ntiles = (pr.n_cols + bn - 1) / bn;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int rows_here = min(kt::BM, pr.n_rows - rb * kt::BM);
-    if (ntiles > kt::TM_WORDS * 32) {  // not masked: the block sweeps every tile
+    if (ntiles > kt::TL_MAX) {  // no list: the block sweeps every tile
         if (threadIdx.x == 0) {
+            tcount[bid] = -1;
             atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
             atomicAdd(&g_prune_stats[1], (unsigned long long)ntiles);
             atomicAdd(&g_prune_stats[2], (unsigned long long)rows_here * pr.n_cols);
@@ -2258,19 +2302,22 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
     }
     const int64_t gA = pr.a_row0 / kt::BM + rb;
     for (int t = threadIdx.x; t < d; t += blockDim.x) ca[t] = gcent[gA * ldc + t];
-    for (int w = threadIdx.x; w < kt::TM_WORDS; w += blockDim.x) mw[w] = 0;
-    if (threadIdx.x == 0) s_kept = s_pairs = 0;
+    if (threadIdx.x == 0) {
+        s_n = 0;
+        s_pairs = 0;
+    }
     __syncthreads();
     const float rA = grad[gA];
     const float ub = bub[bid];
     const float nA = gmaxn[gA];
+    const bool bounded = rA >= 0.0f && ub < INFINITY;
     const int gpt = bn / kt::BM;  // groups per tile
-    unsigned long long kept = 0, pairs = 0;
+    unsigned long long pairs = 0;
     for (int t = warp; t < ntiles; t += nw) {
-        bool keep = true;
-        if (rA >= 0.0f && ub < INFINITY) {
-            float lb = INFINITY;
-            bool any = false;
+        float lb = INFINITY;  // smallest bound over the tile's groups (-1: may hold one)
+        float near = INFINITY;  // ordering key
+        bool any = false;
+        if (rA >= 0.0f) {
             for (int q = 0; q < gpt; ++q) {
                 if ((int64_t)(t * gpt + q) * kt::BM >= pr.n_cols) break;
                 const int64_t g = pr.b_row0 / kt::BM + (int64_t)t * gpt + q;
@@ -2284,6 +2331,8 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
                     d2 = fmaf(df, df, d2);
                 }
                 for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                near = fminf(near, sqrtf(d2) - rg);
+                if (!bounded) continue;
                 const float D =
                     sqrtf(d2 * (1.0f - (float)(d + 4) * 0x1p-22f)) * (1.0f - 0x1p-20f);
                 // kslack (float data): twice the largest error of a tile key's squared
@@ -2293,24 +2342,42 @@ k_tile_mask(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ 
                 if (!(lbg > 0.0f && lbg * lbg > need)) lb = -1.0f;  // this group may hold one
                 else lb = fminf(lb, lbg);
             }
-            keep = !any || !(lb > 0.0f);
         }
+        const bool keep = !bounded || !any || !(lb > 0.0f);
         if (keep && lane == 0) {
-            atomicOr(&mw[t >> 5], 1u << (t & 31));
-            ++kept;
+            const int idx = atomicAdd(&s_n, 1);
+            sk[idx] = ((uint64_t)f2ord(near) << 32) | (uint32_t)t;
             pairs += (unsigned long long)rows_here * min(bn, pr.n_cols - t * bn);
         }
     }
-    if (lane == 0) {
-        atomicAdd(&s_kept, kept);
-        atomicAdd(&s_pairs, pairs);
-    }
+    if (lane == 0) atomicAdd(&s_pairs, pairs);
     __syncthreads();
-    uint32_t* m = tmask + bid * kt::TM_WORDS;
-    for (int w = threadIdx.x; w < (ntiles + 31) / 32; w += blockDim.x) m[w] = mw[w];
+    const int n = s_n;
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int i = n + threadIdx.x; i < p2; i += blockDim.x) sk[i] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t a = sk[i], b = sk[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        sk[i] = b;
+                        sk[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    uint16_t* tl = tlist + bid * kt::TL_MAX;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tl[i] = (uint16_t)(sk[i] & 0xFFFFu);
     if (threadIdx.x == 0) {
+        tcount[bid] = n;
         atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
-        atomicAdd(&g_prune_stats[1], s_kept);
+        atomicAdd(&g_prune_stats[1], (unsigned long long)n);
         atomicAdd(&g_prune_stats[2], s_pairs);
     }
 }
@@ -2366,7 +2433,8 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
         w.grad = cv.take<float>((size_t)ng);
         w.gmaxn = cv.take<float>((size_t)ng);
         w.bub = cv.take<float>((size_t)w.nblocks);
-        w.tmask = cv.take<uint32_t>((size_t)w.nblocks * kt::TM_WORDS);
+        w.tlist = cv.take<uint16_t>((size_t)w.nblocks * kt::TL_MAX);
+        w.tcount = cv.take<int>((size_t)w.nblocks);
         w.rowub = cv.take<float>((size_t)w.rows_cap);
     } else {
         w.rowub = nullptr;
@@ -2374,7 +2442,8 @@ size_t knn_ws(int C, int64_t rows, const KnnPlan& pl, KnnWs* out, void* base, si
         w.grad = nullptr;
         w.gmaxn = nullptr;
         w.bub = nullptr;
-        w.tmask = nullptr;
+        w.tlist = nullptr;
+        w.tcount = nullptr;
     }
     if (out) *out = w;
     return cv.used + 256;
@@ -2418,6 +2487,11 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
     }
     // merge the two column halves' pools of every row into its sorted list
     const unsigned g = (unsigned)grid;
+    if (P.kprime == 1) {
+        k_pool_finalize1<<<g, kt::BM, 0, st>>>(P);
+        ANN_CHECK_LAUNCH();
+        return ANN_OK;
+    }
     const int ke = P.kprime <= 32 ? 1 : P.kprime <= 64 ? 2 : P.kprime <= 128 ? 4 : 8;
     const int eh = P.ph >> 5;
 #define ANN_FINALIZE(KE, EH)                                  \
@@ -2517,7 +2591,8 @@ static KnnParams base_params(const KnnPlan& pl, int k, const int64_t* blk_off,
     P.out_id = out_id;
     P.out_d = out_d;
     P.status = device_status_ptr();
-    P.tmask = nullptr;
+    P.tlist = nullptr;
+    P.tcount = nullptr;
     P.pool = nullptr;
     P.pool_cnt = nullptr;
     P.ph = pool_half(pl.kprime);
@@ -2699,10 +2774,10 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     const bool skip_u8 = dtype == ANN_U8 && pl.mode == 0 && !pl.rerank && d <= 256 &&
                          d % 4 == 0 && ((uintptr_t)X & 3) == 0;
     const bool skip_f32 = dtype == ANN_F32 && pl.mode == 1 && pl.rerank && d <= 200;
-    if (w.tmask && tile_prune_on() && (skip_u8 || skip_f32)) {
+    if (w.tlist && tile_prune_on() && (skip_u8 || skip_f32)) {
         // 3a. bounds: each row's k'-th distance within its 256-row window (k' = the
-        // heap width), the centre and radius of every 128-row group, and each block's
-        // mask of tiles that may hold a neighbour
+        // list width), the centre and radius of every 128-row group, and each block's
+        // list of the tiles that may hold a neighbour, nearest first
         const int64_t ng = w.rows_cap / kt::BM;
         k_group_geom<<<(unsigned)ng, 128, (size_t)d * sizeof(float), st>>>(
             X, dtype, d, w.src, ng, pl.Kp, w.gcent, w.grad, w.gmaxn);
@@ -2733,11 +2808,12 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                 (const float*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub, w.rowub);
         }
         ANN_CHECK_LAUNCH();
-        k_tile_mask<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
+        k_tile_list<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
             w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.gmaxn, kslack, w.bub, grid,
-            w.tmask);
+            w.tlist, w.tcount);
         ANN_CHECK_LAUNCH();
-        P.tmask = w.tmask;
+        P.tlist = w.tlist;
+        P.tcount = w.tcount;
         // each row's window bound starts its threshold
         P.rowub = w.rowub;
         P.ub_margin = kslack;

@@ -129,7 +129,8 @@ struct KnnWs {
     float* grad;        // [rows_cap / 128] radius bound of the group (-1: empty)
     float* gmaxn;       // [rows_cap / 128] largest |y|^2 of the group
     float* bub;         // [blocks] bound on the k-th squared distance of a row block
-    uint32_t* tmask;    // [blocks x 64] tiles each row block sweeps
+    uint16_t* tlist;    // [blocks x 2048] tiles each row block sweeps, nearest first
+    int* tcount;        // [blocks] their number (-1: every tile)
     float* rowub;       // [rows_cap] bound on each row's k'-th squared distance
     int64_t nblocks;
 };
