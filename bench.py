@@ -55,10 +55,11 @@ def _kernel_source_sha256():
     return h.hexdigest()
 
 
-def _kernel_traffic():
-    """DRAM bytes per distance-tile launch from the committed ncu capture, or None
-    when the kernel source has changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "k_knn_tiles_sift1m_u8.json")
+def _kernel_traffic(workload: str):
+    """DRAM bytes per distance-tile launch from the committed ncu capture of this
+    workload, or None when there is none or the kernel source has changed since
+    the counters were taken."""
+    p = os.path.join(ROOT, "profiles", f"k_knn_tiles_{workload}.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -452,17 +453,6 @@ def main():
     ms = float(np.mean(step_ms))
     tile_source = "timed steps"
     tile_steps = args.steps
-    if tile_n == 0:  # graph replays record no host-side kernel events: one eager step
-        flush.zero_()
-        ann.timing_enable(True)
-        captured_save, captured = captured, None
-        step(Xd)
-        captured = captured_save
-        torch.cuda.synchronize()
-        ann.timing_enable(False)
-        tile_ms, tile_n = ann.timing_read()
-        tile_source = "one eager step after the timed graph replays"
-        tile_steps = 1
 
     # e2e: vectors from pinned host memory in, merged graph out, every step
     e2e_ms = []
@@ -483,6 +473,23 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     clocks.stop()
+    # the graph (and its workspace) is not replayed again: release it, so that the
+    # eager steps below have the memory of one workspace, not two
+    if captured is not None:
+        out = {key: (v.clone() if isinstance(v, torch.Tensor) else v) for key, v in out.items()}
+        captured = o = None
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
+    if tile_n == 0:  # graph replays record no host-side kernel events: one eager step
+        flush.zero_()
+        ann.timing_enable(True)
+        step(Xd)
+        torch.cuda.synchronize()
+        ann.timing_enable(False)
+        tile_ms, tile_n = ann.timing_read()
+        tile_source = "one eager step after the timed graph replays"
+        tile_steps = 1
 
     # quality: the exact form gives the exact graph by construction; a screening form
     # is scored against the exact form's lists on the same partition
@@ -581,9 +588,7 @@ def main():
     if args.tile_counters:
         ann.tile_counters_read()
         ann.tile_counters_enable(True)
-        captured_save, captured = captured, None  # eager: replays keep the captured kernel
-        step(Xd)
-        captured = captured_save
+        step(Xd)  # eager (the graph is released above)
         counters = ann.tile_counters_read()
         ann.tile_counters_enable(False)
 
@@ -694,8 +699,7 @@ def main():
         "roofline": {
             "kernel": "k_knn_tiles", "bound": "tensor", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": (_kernel_traffic() if w.name == "sift1m_d128_u8" and prec == ann.EXACT
-                        else None),
+            "traffic": _kernel_traffic(w.name) if prec == ann.EXACT else None,
             "peak_source": peak_note,
             "algorithmic_flops_per_step": flops,
             "algorithmic_flops_per_launch": flops / max(tile_launches_per_step, 1.0),
