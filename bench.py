@@ -28,6 +28,12 @@ import time
 
 import numpy as np
 
+# Workspaces of the large builds are tens of GB; a cached block that large must not
+# be split to serve the smaller buffers of the next step, or the next step's
+# workspace no longer fits.  Set before the first CUDA allocation.
+if "PYTORCH_CUDA_ALLOC_CONF" not in os.environ:
+    os.environ.setdefault("PYTORCH_ALLOC_CONF", "max_split_size_mb:4096")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

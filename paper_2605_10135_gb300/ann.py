@@ -166,7 +166,7 @@ def timing_read() -> tuple[float, int]:
 TILE_COUNTERS = ("epi_cycles", "epi_wait", "epi_flush", "chunks", "slow_chunks", "flushes",
                  "flush_iters", "inserts", "appends", "mma_wait_full", "mma_wait_acc",
                  "prod_wait", "cta_cycles", "ctas", "ld_wait", "filter", "append",
-                 "mma_issue", "mma_commit", "mma_loop")
+                 "mma_issue", "mma_commit", "mma_loop", "stash", "direct", "flush_loop")
 
 
 def tile_counters_enable(on: bool = True):

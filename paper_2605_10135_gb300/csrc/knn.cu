@@ -103,6 +103,9 @@ enum TileCounter {
     TC_MMA_ISSUE,        // MMA thread: cycles issuing tcgen05.mma
     TC_MMA_COMMIT,       // MMA thread: cycles in tcgen05.commit
     TC_MMA_LOOP,         // MMA thread: cycles from the A wait to the end of the tile loop
+    TC_STASH,            // epilogue threads: cycles writing survivors to the stash
+    TC_DIRECT,           // epilogue threads: cycles appending a chunk straight to the pools
+    TC_FLUSH_LOOP,       // epilogue threads: cycles moving stashed survivors to the pools
     TC_N
 };
 __device__ unsigned long long g_tile_counters[TC_N];
@@ -417,7 +420,7 @@ struct EpiState {
     uint64_t best;        // kp == 1
     // counters (used only by the profiling instantiation)
     unsigned long long c_flush_cyc, c_chunks, c_slow, c_flushes, c_iters, c_app;
-    unsigned long long c_ldw, c_filter, c_append;
+    unsigned long long c_ldw, c_filter, c_append, c_stash, c_direct, c_floop;
 };
 
 // Compact the pools of the rows in `mask` (lanes of this warp) to their kp
@@ -505,6 +508,8 @@ __device__ __forceinline__ void epi_flush_stash(EpiState& s) {
     long long f0 = 0;
     if (PROF) f0 = clock64();
     epi_make_room<PROF, EMX>(s, s.sn);
+    long long fl0 = 0;
+    if (PROF) fl0 = clock64();
     const int lane = threadIdx.x & 31;
     const int mx = __reduce_max_sync(0xffffffffu, (uint32_t)s.sn);
     for (int e0 = 0; e0 < mx; e0 += 4) {
@@ -528,7 +533,11 @@ __device__ __forceinline__ void epi_flush_stash(EpiState& s) {
     }
     s.sn = 0;
     __syncwarp();
-    if (PROF) s.c_append += clock64() - f0;
+    if (PROF) {
+        const long long f1 = clock64();
+        s.c_floop += f1 - fl0;
+        s.c_append += f1 - f0;
+    }
 }
 
 // One 32-column chunk: keys come straight from TMEM; masked columns become NaN
@@ -596,6 +605,8 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
             uint32_t g_l = (uint32_t)(j0 + lane);
             if (s.gidrow && j0 + lane < n_cols) g_l = __ldg(s.gidrow + j0 + lane);
             epi_make_room<PROF, EMX>(s, __popc(surv));
+            long long d0 = 0;
+            if (PROF) d0 = clock64();
             const uint32_t any_col = __reduce_or_sync(0xffffffffu, surv);
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
@@ -608,10 +619,16 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
                     }
                 }
             }
-            if (PROF) s.c_append += clock64() - f0;
+            if (PROF) {
+                const long long f1 = clock64();
+                s.c_direct += f1 - d0;
+                s.c_append += f1 - f0;
+            }
             return;
         }
     }
+    long long w0 = 0;
+    if (PROF) w0 = clock64();
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         if ((surv >> u) & 1u) {
@@ -619,7 +636,11 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
             ++s.sn;
         }
     }
-    if (PROF) s.c_append += clock64() - f0;
+    if (PROF) {
+        const long long f1 = clock64();
+        s.c_stash += f1 - w0;
+        s.c_append += f1 - f0;
+    }
 }
 
 __device__ __forceinline__ void prof_add(int which, unsigned long long v) {
@@ -973,7 +994,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.tau = s.tau_own[s.row];
         s.teff = fminf(s.tau, s.tau_other[s.row]);
         s.c_flush_cyc = s.c_chunks = s.c_slow = s.c_flushes = s.c_iters = s.c_app = 0;
-        s.c_ldw = s.c_filter = s.c_append = 0;
+        s.c_ldw = s.c_filter = s.c_append = s.c_stash = s.c_direct = s.c_floop = 0;
         unsigned long long e_wait = 0;
         long long e_t0 = 0;
         if (PROF) e_t0 = clock64();
@@ -1040,6 +1061,9 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
             prof_add_warp(TC_LD_WAIT, s.c_ldw);
             prof_add_warp(TC_FILTER, s.c_filter);
             prof_add_warp(TC_APPEND, s.c_append);
+            prof_add_warp(TC_STASH, s.c_stash);
+            prof_add_warp(TC_DIRECT, s.c_direct);
+            prof_add_warp(TC_FLUSH_LOOP, s.c_floop);
             if (lane == 0) {
                 prof_add(TC_CHUNKS, s.c_chunks);
                 prof_add(TC_SLOW_CHUNKS, s.c_slow);
@@ -1988,7 +2012,7 @@ bool tile_prune_on() { return g_tile_prune; }
 __device__ unsigned long long g_prune_stats[3];  // tiles, tiles swept, pairs swept
 
 static bool prunable(const KnnPlan& pl) {
-    return !pl.scaled && !pl.elem8 && !pl.a_stream;
+    return !pl.elem8 && !pl.a_stream;
 }
 
 // Centre (mean of the valid rows) and radius bound of every 128-row group of the
@@ -2773,7 +2797,14 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
     const int64_t grid = rows / kt::BM + C + 1;
     const bool skip_u8 = dtype == ANN_U8 && pl.mode == 0 && !pl.rerank && d <= 256 &&
                          d % 4 == 0 && ((uintptr_t)X & 3) == 0;
-    const bool skip_f32 = dtype == ANN_F32 && pl.mode == 1 && pl.rerank && d <= 200;
+    // FP32 data: the split keys of the exact form, or the BF16 screening form (plain
+    // BF16 operands, no scale), or the scaled FP16 form; each with the margin of its
+    // key error below
+    const bool split_keys = pl.mode == 1;
+    const bool bf16_keys = pl.mode == 0 && pl.ab_fmt == 1 && !pl.scaled && !pl.elem8;
+    const bool f16_keys = pl.mode == 0 && pl.ab_fmt == 0 && pl.scaled && !pl.elem8;
+    const bool skip_f32 =
+        dtype == ANN_F32 && pl.rerank && d <= 200 && (split_keys || bf16_keys || f16_keys);
     if (w.tlist && tile_prune_on() && (skip_u8 || skip_f32)) {
         // 3a. bounds: each row's k'-th distance within its 256-row window (k' = the
         // list width), the centre and radius of every 128-row group, and each block's
@@ -2799,8 +2830,14 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         } else {
             // Split BF16 keys (three products, FP32 accumulation): the error of a
             // squared distance stays below (2^-16 + (d + 4) 2^-24)(|x|^2 + |y|^2);
-            // a skipped column must clear the bound by twice that, taken 4x larger.
-            kslack = 8.0f * (0x1p-16f + (float)(d + 4) * 0x1p-24f);
+            // BF16 operands (each rounded once, relative 2^-9; the norms in FP32):
+            // below (2^-8 + (d + 8) 2^-24)(|x|^2 + |y|^2); FP16 operands after an
+            // exact power-of-two scale (relative 2^-11 each): below (2^-10 + (d + 8)
+            // 2^-24)(|x|^2 + |y|^2) in the data's units.  A skipped column must
+            // clear the bound by twice that, taken 4x larger.
+            kslack = split_keys  ? 8.0f * (0x1p-16f + (float)(d + 4) * 0x1p-24f)
+                     : bf16_keys ? 8.0f * (0x1p-8f + (float)(d + 8) * 0x1p-24f)
+                                 : 8.0f * (0x1p-10f + (float)(d + 8) * 0x1p-24f);
             const size_t ubs = (size_t)256 * (d + 1) * sizeof(float);
             ANN_CHECK_CUDA(cudaFuncSetAttribute(
                 k_ub_own_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ubs));
@@ -2814,8 +2851,9 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
         ANN_CHECK_LAUNCH();
         P.tlist = w.tlist;
         P.tcount = w.tcount;
-        // each row's window bound starts its threshold
-        P.rowub = w.rowub;
+        // each row's window bound starts its threshold (keys in the data's units:
+        // not for scaled operands, whose keys carry the square of the scale)
+        P.rowub = pl.scaled ? nullptr : w.rowub;
         P.ub_margin = kslack;
     }
     rc = launch_tiles(pl, w.G, w.rows_cap, w.ones, w.G, w.aug, w.rows_cap, P, grid, st, true);

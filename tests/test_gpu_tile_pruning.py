@@ -97,3 +97,29 @@ def test_float_pruned_sweep_equals_full_sweep(kind):
     (ia, da), (ib, db), st = _both(X, mem, off, 32)
     assert torch.equal(ia, ib) and torch.equal(da, db)
     assert 0 < st["swept"] <= st["tiles"]
+
+
+@pytest.mark.parametrize("prec", [ann.BF16_RERANK, ann.F16_RERANK])
+@pytest.mark.parametrize("kind", ["deep", "gauss"])
+def test_screening_forms_pruned_sweep_equals_full_sweep(kind, prec):
+    """The BF16 and scaled FP16 screening forms skip tiles too, with the margin of
+    their own key error (one rounding of each operand): the screened lists, and so
+    the re-ranked ones, equal the full sweep's bit for bit."""
+    if kind == "deep":
+        X = datagen.anisotropic_mixture(30000, 96, 16, 0.25, True, np.float32, seed=441)
+    else:
+        X = datagen.gaussian_mixture_f32(30000, 64, 12, 6.0, seed=442)
+    mem, off = _shards(X, 2, 443)
+    Xd = torch.from_numpy(X).to(DEV)
+    ann.tile_prune(False)
+    sa = ann.shard_knn_screen(Xd, mem, off, 32, prec, 96)
+    a = ann.shard_knn(Xd, mem, off, 32, precision=prec, rerank_k=96)
+    torch.cuda.synchronize()
+    ann.tile_prune_stats()
+    ann.tile_prune(True)
+    sb = ann.shard_knn_screen(Xd, mem, off, 32, prec, 96)
+    b = ann.shard_knn(Xd, mem, off, 32, precision=prec, rerank_k=96)
+    st = ann.tile_prune_stats()
+    assert torch.equal(sa[0], sb[0]) and torch.equal(sa[1], sb[1])
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert 0 < st["swept"] < st["tiles"]
