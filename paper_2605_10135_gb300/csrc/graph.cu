@@ -90,7 +90,9 @@ __device__ __forceinline__ int64_t row_in_range(const int64_t* __restrict__ star
 // Position of id x in the row's list: a direct-mapped table of TS slots.  The
 // multiplicative hash y = x * A (A odd) is a bijection of 32-bit words, so the
 // slot (the top 10 bits of y) and the low 22 bits of y identify x; one 32-bit
-// word per slot holds those 22 bits (bits 8..29) and the position (bits 0..7).
+// word per slot holds those 22 bits (bits 10..31) and the position (bits 0..9),
+// so a probe's word XOR (y << 10) is the position when the slot holds x and at
+// least 1023 otherwise (an empty slot holds all ones).
 // For each row the warp tries multipliers until none of the row's ids share a
 // slot (about one try in seven succeeds for 64 ids in 1,024 slots); then every
 // lookup is one probe.  A row for which no multiplier is found within PTRY tries
@@ -101,7 +103,7 @@ constexpr uint32_t HM = 2654435761u, TEMPTY = 0xFFFFFFFFu;
 constexpr int PTRY = 32;
 
 __device__ __forceinline__ uint32_t tmult(int a) { return HM + 0x3C6EF372u * (uint32_t)a; }  // odd
-__device__ __forceinline__ uint32_t tkey(uint32_t y) { return (y << 10) >> 2; }  // low 22 bits << 8
+__device__ __forceinline__ uint32_t tkey(uint32_t y) { return y << 10; }  // low 22 bits << 10
 
 // Shared memory of one prune warp: table words [TS], overflow ids and positions
 // [KM each], the neighbours' rows [KM], the overflow count (+pad).
@@ -138,7 +140,9 @@ __device__ __forceinline__ void prune_counts(const uint32_t* __restrict__ knn_id
         for (int g = 0; g < G; ++g) {
             const int i = i0 + g;
             if (i >= m) break;  // warp-uniform
+            // (ANN_PAD entries never match: the table holds only the row's ids)
             uint32_t bits[E];
+            uint64_t bits64 = 0;  // E <= 2: positions 0..63 in one word
 #pragma unroll
             for (int e = 0; e < E; ++e) bits[e] = 0;
 #pragma unroll
@@ -152,11 +156,19 @@ __device__ __forceinline__ void prune_counts(const uint32_t* __restrict__ knn_id
                     for (int o = 0; o < novf; ++o)
                         if (ovf[o] == x[g][e]) dj = ovf_pos[o];
                 }
-                if (x[g][e] != ANN_PAD && dj - thr - 1u < 255u - thr) {
+                if (dj - thr - 1u < 255u - thr) {
+                    if constexpr (E <= 2) {
+                        bits64 |= 1ull << dj;
+                    } else {
 #pragma unroll
-                    for (int e2 = 0; e2 < E; ++e2)
-                        if ((int)(dj >> 5) == e2) bits[e2] |= 1u << (dj & 31u);
+                        for (int e2 = 0; e2 < E; ++e2)
+                            if ((int)(dj >> 5) == e2) bits[e2] |= 1u << (dj & 31u);
+                    }
                 }
+            }
+            if constexpr (E <= 2) {
+                bits[0] = (uint32_t)bits64;
+                if (E == 2) bits[E - 1] = (uint32_t)(bits64 >> 32);
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {

@@ -33,7 +33,7 @@
 //              their global ids to the row's candidate pool for that half (in
 //              global memory, no lock: each half has one writer).  A pool that
 //              would overflow is compacted by its warp: a cooperative selection
-//              finds a bound keeping between k' and k' plus a quarter of the
+//              finds a bound keeping between k' and k' plus an eighth of the
 //              slack entries, the rest are dropped and the threshold lowered.
 //              After the sweep k_pool_finalize selects each row's k' smallest
 //              (key, global id) from its two pools, so ties go to the smaller
@@ -155,11 +155,12 @@ struct KnnParams {
     float ub_margin;
 };
 
-// Entries of a row half's candidate pool, whole warps: twice the list width up to
-// k' = 128, the list width plus 64 above; always at least 32 more than k' (a
-// chunk's survivors fit after a compaction).
+// Entries of a row half's candidate pool, whole warps: 256 (what a compaction holds
+// in registers) for list widths 32 to 128, the list width plus 64 above; always at
+// least 32 more than k' (a chunk's survivors fit after a compaction).  A larger pool
+// compacts less often at the same cost per compaction.
 __host__ __device__ inline int pool_half(int kprime) {
-    int ph = kprime <= 128 ? 2 * kprime : kprime + 64;
+    int ph = kprime < 32 ? 2 * kprime : kprime <= 128 ? 256 : kprime + 64;
     if (ph < kprime + 32) ph = kprime + 32;
     ph = (ph + 31) / 32 * 32;
     return ph > kt::PH_MAX ? kt::PH_MAX : ph;
@@ -448,9 +449,9 @@ __device__ __noinline__ PoolState epi_compact(uint64_t* pool0, int ph, int kp, i
             const int idx = lane + 32 * e;
             v[e] = (e < E && idx < cr) ? pr[idx] : ~0ull;
         }
-        // keep between kp and maxkeep entries: a quarter of the slack may stay
+        // keep between kp and maxkeep entries: an eighth of the slack may stay
         // above the kp-th, which lets the bound stop early
-        int maxkeep = kp + ((ph - kp) >> 2);
+        int maxkeep = kp + ((ph - kp) >> 3);
         if (maxkeep > ph - 32) maxkeep = ph - 32;
         if (maxkeep < kp) maxkeep = kp;
         const uint64_t T = cr > maxkeep ? warp_select_bound(v, cr, kp, maxkeep) : ~0ull - 1;
@@ -2525,9 +2526,12 @@ static int launch_tiles(const KnnPlan& pl, const void* GA, int64_t rowsA, const 
         return ANN_OK;                                        \
     }
     ANN_FINALIZE(1, 2)
+    ANN_FINALIZE(1, 8)
 
     ANN_FINALIZE(2, 3)
     ANN_FINALIZE(2, 4)
+    ANN_FINALIZE(2, 6)
+    ANN_FINALIZE(2, 8)
 
     ANN_FINALIZE(4, 5)
     ANN_FINALIZE(4, 6)
