@@ -72,7 +72,8 @@ constexpr int NAUG = 1;                 // norm-block slots (loaded first in eac
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
 constexpr int PH_MAX = 320;             // candidate pool entries per row half, at most
-constexpr int SC = 16;                  // survivors a thread stashes before a tile's release
+constexpr int SC = 8;                   // survivors a thread stashes before a tile's release
+constexpr int KS = 33;                  // floats per row of a warp's key scratch (32 + 1 pad)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
 constexpr int MAX_NST = 6;
@@ -167,7 +168,7 @@ __host__ __device__ inline int pool_half(int kprime) {
 }
 
 struct KnnSmemLayout {
-    uint32_t a, aaug, b, baug, tau, stash, bars, tmem_slot, abort_flag, total;
+    uint32_t a, aaug, b, baug, tau, stash, kscr, bars, tmem_slot, abort_flag, total;
 };
 
 // a_stream = 0: the CTA's A rows stay resident (nkb_a K blocks) and a ring stage
@@ -193,6 +194,8 @@ __host__ __device__ inline KnnSmemLayout knn_smem_layout(int bn, int nkb_a, int 
     o += 2 * kt::BM * 4;
     L.stash = o;  // [EPI_WARPS][SC][32] survivors (key bits << 32 | column), lane-minor
     o += kt::EPI_WARPS * kt::SC * 32 * 8;
+    L.kscr = o;   // [EPI_WARPS][32][KS] a chunk's keys, one row per thread
+    o += kt::EPI_WARPS * 32 * kt::KS * 4;
     L.bars = o;
     o += (2 * kt::MAX_NST + 2 * kt::NAUG + 2 * kt::NACC + 2) * 8;
     L.tmem_slot = o;
@@ -416,6 +419,7 @@ struct EpiState {
     const volatile float* tau_other;
     uint64_t* stash;      // shared: this warp's stash, entry e of lane l at [e * 32 + l]
     const uint32_t* gidrow;  // global id of each column of the shard (NULL: the column)
+    uint32_t kscr;        // shared address of this thread's row of the key scratch
     int row, kp, ph, c, sn;
     float tau, teff;
     uint64_t best;        // kp == 1
@@ -630,10 +634,16 @@ __device__ __forceinline__ void epi_chunk(EpiState& s, const uint32_t (&v)[32], 
     }
     long long w0 = 0;
     if (PROF) w0 = clock64();
+    // the chunk's keys to this thread's scratch row (a fixed number of stores, rows
+    // padded so the warp's stores hit distinct banks), then only the survivors
+    // into the stash (a loop as long as the thread's survivor count)
+    if (surv) {
 #pragma unroll
-    for (int u = 0; u < 32; ++u) {
-        if ((surv >> u) & 1u) {
-            s.stash[s.sn * 32 + lane] = ((uint64_t)f2ord(key[u]) << 32) | (uint32_t)(j0 + u);
+        for (int u = 0; u < 32; ++u) sts_u32(s.kscr + 4 * u, v[u]);
+        for (uint32_t m = surv; m; m &= m - 1) {
+            const int u = __ffs(m) - 1;
+            const float kv = __uint_as_float(lds_u32(s.kscr + 4 * u));
+            s.stash[s.sn * 32 + lane] = ((uint64_t)f2ord(kv) << 32) | (uint32_t)(j0 + u);
             ++s.sn;
         }
     }
@@ -990,6 +1000,7 @@ __global__ void __launch_bounds__(kt::THREADS, 1)
         s.c = 0;
         s.sn = 0;
         s.stash = (uint64_t*)(base + L.stash) + (warp - 2) * kt::SC * 32;
+        s.kscr = smem_u32(base + L.kscr) + ((warp - 2) * 32 + lane) * kt::KS * 4;
         s.gidrow = P.gid ? P.gid + pr.b_row0 : nullptr;
         s.best = ~0ull;
         s.tau = s.tau_own[s.row];
@@ -2376,113 +2387,198 @@ k_ub_own_f32(const float* __restrict__ X, int d, const int64_t* __restrict__ src
 // a group ball of the tile, (|c_A - c_G| - r_G), so the thresholds tighten on the
 // first tiles of the sweep and fewer candidates pass them later.  tcount[bid]:
 // the number kept (-1 where the shard has more than TL_MAX tiles: the block then
-// sweeps every tile).  One block of 256 threads per row block; a warp per tile
-// with lanes over the dimensions, then a bitonic sort in shared memory.
+// sweeps every tile).
+//
+// One CTA of 256 threads per TLB consecutive row blocks: those of one problem share
+// the column groups, which are staged in shared memory 64 at a time (row stride
+// d | 1, so a warp's 32 groups fall in distinct banks) and each thread takes two
+// (row block, group) pairs, summing (c_A - c_G)^2 over the dimensions in order;
+// then each row block's kept tiles are sorted in shared memory.
+constexpr int TLB = 8, TLG = 64;
+
+struct TileListSmem {
+    size_t ca, cg, gnear, gflag, tkey, tkeep, sk, total;
+};
+__host__ __device__ inline TileListSmem tile_list_smem(int d) {
+    const int sd = d | 1;
+    TileListSmem L;
+    size_t o = 0;
+    L.sk = o;      o += (size_t)kt::TL_MAX * 8;          // sort buffer
+    L.tkey = o;    o += (size_t)TLB * kt::TL_MAX * 4;    // order bits of each tile's key
+    L.tkeep = o;   o += (size_t)TLB * (kt::TL_MAX / 32) * 4;
+    L.ca = o;      o += (size_t)TLB * sd * 4;
+    L.cg = o;      o += (size_t)TLG * sd * 4;
+    L.gnear = o;   o += (size_t)TLB * TLG * 4;
+    L.gflag = o;   o += (size_t)TLB * TLG;
+    L.total = (o + 15) / 16 * 16;
+    return L;
+}
+
 __global__ void __launch_bounds__(256)
 k_tile_list(const int64_t* __restrict__ blk_off, const KnnProblem* __restrict__ probs, int nprob,
             int bn, int d, int ldc, const float* __restrict__ gcent, const float* __restrict__ grad,
             const float* __restrict__ gmaxn, float kslack, const float* __restrict__ bub,
             int64_t nblocks, uint16_t* __restrict__ tlist, int* __restrict__ tcount) {
-    extern __shared__ float ca[];  // [d]
-    __shared__ uint64_t sk[kt::TL_MAX];  // (order bits of the distance << 32 | tile)
+    extern __shared__ __align__(16) uint8_t tsm[];
+    const TileListSmem L = tile_list_smem(d);
+    uint64_t* sk = (uint64_t*)(tsm + L.sk);
+    uint32_t* tkey = (uint32_t*)(tsm + L.tkey);
+    uint32_t* tkeep = (uint32_t*)(tsm + L.tkeep);
+    float* ca = (float*)(tsm + L.ca);
+    float* cg = (float*)(tsm + L.cg);
+    float* gnear = (float*)(tsm + L.gnear);
+    uint8_t* gflag = tsm + L.gflag;  // bit 0: a valid group; bit 1: it may hold a neighbour
     __shared__ int s_n;
     __shared__ unsigned long long s_pairs;
-    const int64_t bid = blockIdx.x;
-    if (bid >= nblocks || bid >= blk_off[nprob]) return;
-    const int p = block_problem(blk_off, nprob, bid);
-    const KnnProblem pr = probs[p];
-    const int rb = (int)(bid - blk_off[p]);
-    const int ntiles = (pr.n_cols + bn - 1) / bn;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int rows_here = min(kt::BM, pr.n_rows - rb * kt::BM);
-    if (ntiles > kt::TL_MAX) {  // no list: the block sweeps every tile
-        if (threadIdx.x == 0) {
-            tcount[bid] = -1;
-            atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
-            atomicAdd(&g_prune_stats[1], (unsigned long long)ntiles);
-            atomicAdd(&g_prune_stats[2], (unsigned long long)rows_here * pr.n_cols);
-        }
-        return;
-    }
-    const int64_t gA = pr.a_row0 / kt::BM + rb;
-    for (int t = threadIdx.x; t < d; t += blockDim.x) ca[t] = gcent[gA * ldc + t];
-    if (threadIdx.x == 0) {
-        s_n = 0;
-        s_pairs = 0;
-    }
-    __syncthreads();
-    const float rA = grad[gA];
-    const float ub = bub[bid];
-    const float nA = gmaxn[gA];
-    const bool bounded = rA >= 0.0f && ub < INFINITY;
+    const int sd = d | 1;
+    const int64_t nb = nblocks < blk_off[nprob] ? nblocks : blk_off[nprob];
     const int gpt = bn / kt::BM;  // groups per tile
-    unsigned long long pairs = 0;
-    for (int t = warp; t < ntiles; t += nw) {
-        float lb = INFINITY;  // smallest bound over the tile's groups (-1: may hold one)
-        float near = INFINITY;  // ordering key
-        bool any = false;
-        if (rA >= 0.0f) {
-            for (int q = 0; q < gpt; ++q) {
-                if ((int64_t)(t * gpt + q) * kt::BM >= pr.n_cols) break;
-                const int64_t g = pr.b_row0 / kt::BM + (int64_t)t * gpt + q;
-                const float rg = grad[g];
-                if (rg < 0.0f) continue;
-                any = true;
-                const float* cg = gcent + g * ldc;
-                float d2 = 0.0f;
-                for (int u = lane; u < d; u += 32) {
-                    const float df = ca[u] - __ldg(cg + u);
-                    d2 = fmaf(df, df, d2);
-                }
-                for (int o = 16; o; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-                near = fminf(near, sqrtf(d2) - rg);
-                if (!bounded) continue;
-                const float D =
-                    sqrtf(d2 * (1.0f - (float)(d + 4) * 0x1p-22f)) * (1.0f - 0x1p-20f);
-                // kslack (float data): twice the largest error of a tile key's squared
-                // distance, which scales with |x|^2 + |y|^2
-                const float lbg = (D - rA - rg) * (1.0f - 0x1p-20f);
-                const float need = ub * (1.0f + 0x1p-18f) + kslack * (nA + gmaxn[g]);
-                if (!(lbg > 0.0f && lbg * lbg > need)) lb = -1.0f;  // this group may hold one
-                else lb = fminf(lb, lbg);
+    for (int64_t r0 = (int64_t)blockIdx.x * TLB; r0 < (int64_t)(blockIdx.x + 1) * TLB && r0 < nb;) {
+        // a run of row blocks of one problem
+        const int p = block_problem(blk_off, nprob, r0);
+        int64_t r1 = (int64_t)(blockIdx.x + 1) * TLB;
+        if (r1 > nb) r1 = nb;
+        if (r1 > blk_off[p + 1]) r1 = blk_off[p + 1];
+        const int na = (int)(r1 - r0);
+        const KnnProblem pr = probs[p];
+        const int ntiles = (pr.n_cols + bn - 1) / bn;
+        if (ntiles > kt::TL_MAX) {  // no list: these blocks sweep every tile
+            if (threadIdx.x < na) {
+                const int rb = (int)(r0 + threadIdx.x - blk_off[p]);
+                const int rows_here = min(kt::BM, pr.n_rows - rb * kt::BM);
+                tcount[r0 + threadIdx.x] = -1;
+                atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
+                atomicAdd(&g_prune_stats[1], (unsigned long long)ntiles);
+                atomicAdd(&g_prune_stats[2], (unsigned long long)rows_here * pr.n_cols);
             }
+            r0 = r1;
+            continue;
         }
-        const bool keep = !bounded || !any || !(lb > 0.0f);
-        if (keep && lane == 0) {
-            const int idx = atomicAdd(&s_n, 1);
-            sk[idx] = ((uint64_t)f2ord(near) << 32) | (uint32_t)t;
-            pairs += (unsigned long long)rows_here * min(bn, pr.n_cols - t * bn);
+        // the run's centres and bounds
+        for (int x = threadIdx.x; x < na * d; x += blockDim.x) {
+            const int a = x / d, u = x - a * d;
+            const int64_t gA = pr.a_row0 / kt::BM + (r0 + a - blk_off[p]);
+            ca[a * sd + u] = gcent[gA * ldc + u];
         }
-    }
-    if (lane == 0) atomicAdd(&s_pairs, pairs);
-    __syncthreads();
-    const int n = s_n;
-    int p2 = 1;
-    while (p2 < n) p2 <<= 1;
-    for (int i = n + threadIdx.x; i < p2; i += blockDim.x) sk[i] = ~0ull;
-    __syncthreads();
-    for (int k = 2; k <= p2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const uint64_t a = sk[i], b = sk[l];
-                    if ((a > b) == ((i & k) == 0)) {
-                        sk[i] = b;
-                        sk[l] = a;
+        for (int x = threadIdx.x; x < TLB * (kt::TL_MAX / 32); x += blockDim.x) tkeep[x] = 0;
+        // (c_A - c_G)^2 sums of the run against the shard's groups, TLG groups at a time
+        const int ngroups = (pr.n_cols + kt::BM - 1) / kt::BM;
+        const int64_t g0s = pr.b_row0 / kt::BM;
+        for (int c0 = 0; c0 < ngroups; c0 += TLG) {
+            const int nc = min(TLG, ngroups - c0);
+            __syncthreads();  // the previous chunk's reads are done
+            for (int x = threadIdx.x; x < nc * d; x += blockDim.x) {
+                const int g = x / d, u = x - g * d;
+                cg[g * sd + u] = __ldg(gcent + (g0s + c0 + g) * ldc + u);
+            }
+            __syncthreads();
+            for (int pi = threadIdx.x; pi < TLB * TLG; pi += blockDim.x) {
+                const int a = pi / TLG, g = pi - a * TLG;
+                if (a >= na || g >= nc) continue;
+                const int64_t gA = pr.a_row0 / kt::BM + (r0 + a - blk_off[p]);
+                const float rA = grad[gA];
+                const float rg = grad[g0s + c0 + g];
+                uint8_t fl = 0;
+                float near = INFINITY;
+                if (rA >= 0.0f && rg >= 0.0f) {
+                    fl = 1;
+                    const float* xa = ca + a * sd;
+                    const float* xg = cg + g * sd;
+                    float d2 = 0.0f;
+                    for (int u = 0; u < d; ++u) {
+                        const float df = xa[u] - xg[u];
+                        d2 = fmaf(df, df, d2);
+                    }
+                    near = sqrtf(d2) - rg;
+                    const float ub = bub[r0 + a];
+                    if (ub < INFINITY) {
+                        const float D =
+                            sqrtf(d2 * (1.0f - (float)(d + 4) * 0x1p-22f)) * (1.0f - 0x1p-20f);
+                        // kslack (float data): twice the largest error of a tile key's
+                        // squared distance, which scales with |x|^2 + |y|^2
+                        const float lbg = (D - rA - rg) * (1.0f - 0x1p-20f);
+                        const float need =
+                            ub * (1.0f + 0x1p-18f) + kslack * (gmaxn[gA] + gmaxn[g0s + c0 + g]);
+                        if (!(lbg > 0.0f && lbg * lbg > need)) fl |= 2;  // may hold one
+                    } else {
+                        fl |= 2;
                     }
                 }
+                gnear[a * TLG + g] = near;
+                gflag[a * TLG + g] = fl;
+            }
+            __syncthreads();
+            // per (row block, tile) of the chunk: keep, and the ordering key
+            const int t0 = c0 / gpt, nt = (c0 + nc + gpt - 1) / gpt - t0;
+            for (int x = threadIdx.x; x < na * nt; x += blockDim.x) {
+                const int a = x / nt, t = t0 + (x - a * nt);
+                float near = INFINITY;
+                bool any = false, may = false;
+                for (int q = 0; q < gpt; ++q) {
+                    const int g = t * gpt + q - c0;
+                    if (t * gpt + q >= ngroups) break;
+                    const uint8_t fl = gflag[a * TLG + g];
+                    any = any || (fl & 1);
+                    may = may || (fl & 2);
+                    near = fminf(near, gnear[a * TLG + g]);
+                }
+                const bool keep = !any || may;
+                tkey[a * kt::TL_MAX + t] = f2ord(near);
+                if (keep) atomicOr(&tkeep[a * (kt::TL_MAX / 32) + (t >> 5)], 1u << (t & 31));
+            }
+        }
+        __syncthreads();
+        // each row block: its kept tiles, sorted by key
+        for (int a = 0; a < na; ++a) {
+            const int64_t bid = r0 + a;
+            const int rb = (int)(bid - blk_off[p]);
+            const int rows_here = min(kt::BM, pr.n_rows - rb * kt::BM);
+            if (threadIdx.x == 0) {
+                s_n = 0;
+                s_pairs = 0;
+            }
+            __syncthreads();
+            unsigned long long pairs = 0;
+            for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+                if ((tkeep[a * (kt::TL_MAX / 32) + (t >> 5)] >> (t & 31)) & 1u) {
+                    const int idx = atomicAdd(&s_n, 1);
+                    sk[idx] = ((uint64_t)tkey[a * kt::TL_MAX + t] << 32) | (uint32_t)t;
+                    pairs += (unsigned long long)rows_here * min(bn, pr.n_cols - t * bn);
+                }
+            }
+            if (pairs) atomicAdd(&s_pairs, pairs);
+            __syncthreads();
+            const int n = s_n;
+            int p2 = 1;
+            while (p2 < n) p2 <<= 1;
+            for (int x = n + threadIdx.x; x < p2; x += blockDim.x) sk[x] = ~0ull;
+            __syncthreads();
+            for (int k = 2; k <= p2; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int x = threadIdx.x; x < p2; x += blockDim.x) {
+                        const int l = x ^ j;
+                        if (l > x) {
+                            const uint64_t va = sk[x], vb = sk[l];
+                            if ((va > vb) == ((x & k) == 0)) {
+                                sk[x] = vb;
+                                sk[l] = va;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            uint16_t* tl = tlist + bid * kt::TL_MAX;
+            for (int x = threadIdx.x; x < n; x += blockDim.x) tl[x] = (uint16_t)(sk[x] & 0xFFFFu);
+            if (threadIdx.x == 0) {
+                tcount[bid] = n;
+                atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
+                atomicAdd(&g_prune_stats[1], (unsigned long long)n);
+                atomicAdd(&g_prune_stats[2], s_pairs);
             }
             __syncthreads();
         }
-    }
-    uint16_t* tl = tlist + bid * kt::TL_MAX;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tl[i] = (uint16_t)(sk[i] & 0xFFFFu);
-    if (threadIdx.x == 0) {
-        tcount[bid] = n;
-        atomicAdd(&g_prune_stats[0], (unsigned long long)ntiles);
-        atomicAdd(&g_prune_stats[1], (unsigned long long)n);
-        atomicAdd(&g_prune_stats[2], s_pairs);
+        r0 = r1;
     }
 }
 
@@ -2933,7 +3029,10 @@ int run_shard_knn(const void* X, int64_t N, int d, int dtype, const uint32_t* me
                 (const float*)X, d, w.src, w.blk_off, w.probs, C, pl.kprime, grid, w.bub, w.rowub);
         }
         ANN_CHECK_LAUNCH();
-        k_tile_list<<<(unsigned)grid, 256, (size_t)d * sizeof(float), st>>>(
+        const size_t tls = tile_list_smem(d).total;
+        ANN_CHECK_CUDA(cudaFuncSetAttribute(k_tile_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)tls));
+        k_tile_list<<<(unsigned)((grid + TLB - 1) / TLB), 256, tls, st>>>(
             w.blk_off, w.probs, C, pl.bn, d, pl.Kp, w.gcent, w.grad, w.gmaxn, kslack, w.bub, grid,
             w.tlist, w.tcount);
         ANN_CHECK_LAUNCH();
