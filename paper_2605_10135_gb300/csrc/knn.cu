@@ -72,7 +72,7 @@ constexpr int NAUG = 1;                 // norm-block slots (loaded first in eac
 constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;            // two warps per TMEM lane quarter
 constexpr int PH_MAX = 320;             // candidate pool entries per row half, at most
-constexpr int SC = 8;                   // survivors a thread stashes before a tile's release
+constexpr int SC = 24;                  // survivors a thread stashes before a tile's release
 constexpr int KS = 33;                  // floats per row of a warp's key scratch (32 + 1 pad)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = NACC * BNMAX;
