@@ -120,11 +120,13 @@ int ann_timing_read(double* tile_ms, int* launches);
  * launches to a variant that accumulates per-role clock64() cycle counts and
  * event counts into a device array; ann_tile_counters_read() synchronises the
  * device, copies up to n counters to host out[] and clears them.  Order:
- * epilogue cycles, epilogue wait cycles, epilogue flush cycles, chunks, slow
- * chunks, flushes, flush iterations, heap inserts, appended survivors, MMA
- * wait-for-data cycles, MMA wait-for-accumulator cycles, producer wait cycles,
- * CTA cycles, CTAs, TMEM-load wait cycles, filter cycles, append cycles, MMA
- * issue cycles, MMA commit cycles, MMA loop cycles. */
+ * epilogue cycles, epilogue wait cycles, pool compaction cycles, chunks, chunks
+ * with survivors, compactions, rows compacted, (unused, 0), appended survivors,
+ * MMA wait-for-data cycles, MMA wait-for-accumulator cycles, producer wait
+ * cycles, CTA cycles, CTAs, TMEM-load wait cycles, filter cycles, append cycles
+ * (everything after the filter, compactions included), MMA issue cycles, MMA
+ * commit cycles, MMA loop cycles, stash-write cycles, cycles appending chunks
+ * straight to the pools, cycles moving the stash to the pools. */
 int ann_tile_counters_enable(int on);
 int ann_tile_counters_read(unsigned long long* out, int n);
 

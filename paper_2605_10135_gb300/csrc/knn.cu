@@ -124,7 +124,7 @@ struct KnnParams {
     int nkb_a;     // A k-blocks (resident unless a_stream)
     int a_stream;  // A blocks per ring stage (0: A resident; large d: 1, or 2 for split)
     int nkb_b;     // B k-blocks per tile
-    int kprime;    // heap entries per row
+    int kprime;    // list width k': candidates kept per row
     int k_out;     // entries written per row
     int nst;       // main pipeline stages
     int kbe;       // elements per 128-byte K block (64 for 16-bit, 128 for 8-bit operands)
