@@ -53,7 +53,7 @@ extern "C" {
 enum ann_status {
     ANN_OK = 0,
     ANN_ERR_INVALID_ARG = 1,  /* a size, pointer or enum outside its documented range */
-    ANN_ERR_UNSUPPORTED = 2,  /* a valid combination this build does not implement */
+    ANN_ERR_UNSUPPORTED = 2,  /* a valid combination the library does not implement */
     ANN_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed */
     ANN_ERR_TIMEOUT = 4,      /* a device-side bounded wait gave up (see ann_device_status) */
     ANN_ERR_WORKSPACE = 5     /* workspace missing or smaller than reported */

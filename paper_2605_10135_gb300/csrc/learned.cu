@@ -2,7 +2,7 @@
 // row's candidate neighbours in embedding space; the candidates are re-ranked
 // with exact FP32 distances in the original space.  The paper builds shard graphs
 // from exact distances only (Sec. II-B, Sec. IV Workflow (2)); this form is an
-// addition beside it, judged by its recall against the exact graph.
+// addition beside it, measured by its recall against the exact graph.
 //
 // Model    f(x) = W2 relu(W1 (x / s) + b1) + b2, s = max |x| over all vectors;
 //          parameters are one FP32 array [W1 (256 x d) | b1 | W2 (32 x 256) | b2].
